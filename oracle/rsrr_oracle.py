@@ -1,0 +1,342 @@
+"""Plain FP64 restatement of RSRR (Algorithm 2) and the modified block SS solver
+(Algorithm 1) of Xiao, Meng, Zhang, Zheng (arXiv:1510.07522).
+
+TEST INFRASTRUCTURE: only tests/, the graft smoke check and bench.py's CPU
+baseline use this module.  Steps follow the paper's order and notation; the
+library primitives used as steps are numpy's SVD/eig/solve and scipy's sparse
+products.  Parity pins live in tests/test_oracle_*.py.
+
+Readings of the paper where it is silent or garbled (each also listed in the
+design notes):
+  * theta_j = 2 pi (j + 1/2) / N_S for j = 0..N_S-1 (Eq. eq-Ap-num prints j = 0..N_S).
+  * V_0 / W_0 are the first nbar columns of V / W (Section 4.3 prints rows).
+  * the singular-value gap rule runs over the whole SVD of H (length K k_S).
+  * i sqrt(z - s) with branch flag 1 is the continued branch -sqrt(s - z).
+  * the sample solves are accepted at normwise backward error
+    eta = ||u - T x||_2 / (||T||_1 ||x||_2 + ||u||_2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import build as _build
+
+_lib = None
+
+
+def _clib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        _lib.orc_zgbtrf.argtypes = [i64, i64, i64, p, i64, p]
+        _lib.orc_zgbtrf.restype = i64
+        _lib.orc_zgbtrs.argtypes = [i64, i64, i64, i64, p, i64, p, p, i64]
+        _lib.orc_zgbtrs.restype = None
+        _lib.orc_zgetrf.argtypes = [i64, p, i64, p]
+        _lib.orc_zgetrf.restype = i64
+        _lib.orc_zgetrs.argtypes = [i64, i64, p, i64, p, p, i64]
+        _lib.orc_zgetrs.restype = None
+    return _lib
+
+
+# ----------------------------------------------------------------------------------------
+# Scalar functions of T(z) = sum_i f_i(z) A_i (Eq. eq-Z-expr) and their derivatives
+# (needed by the winding-number count, Eq. eq-ncs).
+# ----------------------------------------------------------------------------------------
+def coefficients(fns, z):
+    """Return (F, dF): arrays [len(z), J] of f_i(z) and f_i'(z)."""
+    z = np.asarray(z, dtype=np.complex128)
+    F = np.empty(z.shape + (len(fns),), dtype=np.complex128)
+    dF = np.empty_like(F)
+    for i, fn in enumerate(fns):
+        k, p = fn.kind, fn.params()
+        if k == 0:
+            F[..., i], dF[..., i] = 1.0, 0.0
+        elif k == 1:
+            F[..., i], dF[..., i] = z, 1.0
+        elif k == 2:
+            F[..., i], dF[..., i] = z * z, 2.0 * z
+        elif k == 3:
+            s, branch = p[0], p[1]
+            if branch == 0.0:          # i sqrt(z - s), principal root
+                r = np.sqrt(z - s)
+                F[..., i], dF[..., i] = 1j * r, 0.5j / r
+            else:                      # continued branch: i sqrt(z - s) := -sqrt(s - z)
+                r = np.sqrt(s - z)
+                F[..., i], dF[..., i] = -r, 0.5 / r
+        elif k == 4:
+            e = np.exp(-p[0] * z)
+            F[..., i], dF[..., i] = e, -p[0] * e
+        elif k == 5:
+            F[..., i] = p[0] * z / (z + p[1])
+            dF[..., i] = p[0] * p[1] / (z + p[1]) ** 2
+        else:
+            raise ValueError(f"unknown function kind {k}")
+    return F, dF
+
+
+def contour_points(gamma, a, b, N):
+    """Ellipse phi(t) = gamma + a cos t + i b sin t (Eq. eq-contour) at the trapezoid
+    nodes theta_j = 2 pi (j + 1/2)/N (Eq. eq-Ap-num); returns (z, dphi, theta)."""
+    theta = 2.0 * np.pi * (np.arange(N) + 0.5) / N
+    z = gamma + a * np.cos(theta) + 1j * b * np.sin(theta)
+    dphi = -a * np.sin(theta) + 1j * b * np.cos(theta)
+    return z, dphi, theta
+
+
+def inside_contour(lam, gamma, a, b):
+    w = np.asarray(lam) - gamma
+    return (w.real / a) ** 2 + (w.imag / b) ** 2 < 1.0
+
+
+# ----------------------------------------------------------------------------------------
+# Assembly of T(z) (Eq. eq-Z-expr) and the band solves of Algorithm 2, Step 2.
+# ----------------------------------------------------------------------------------------
+def _rows(prob):
+    return np.repeat(np.arange(prob.n, dtype=np.int64), np.diff(prob.rowptr))
+
+
+def assemble_values(prob, Frow):
+    """Values of T(z) on the union pattern: sum_i f_i(z) A_i."""
+    return Frow @ prob.vals
+
+
+def assemble_dense(prob, Frow):
+    T = np.zeros((prob.n, prob.n), dtype=np.complex128)
+    np.add.at(T, (_rows(prob), prob.colind), assemble_values(prob, Frow))
+    return T
+
+
+def bandwidths(prob):
+    d = prob.colind.astype(np.int64) - _rows(prob)
+    return int(max(0, -d.min())), int(max(0, d.max()))
+
+
+def assemble_band(prob, Frow, kl, ku):
+    """T(z) in general-band layout (ldab = 2 kl + ku + 1, fill rows zero)."""
+    ldab = 2 * kl + ku + 1
+    ab = np.zeros((ldab, prob.n), dtype=np.complex128, order="F")
+    r, c = _rows(prob), prob.colind.astype(np.int64)
+    np.add.at(ab, (kl + ku + r - c, c), assemble_values(prob, Frow))
+    return ab
+
+
+def band_lu(ab, kl, ku):
+    ab = np.asfortranarray(ab, dtype=np.complex128).copy(order="F")
+    n = ab.shape[1]
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = _clib().orc_zgbtrf(n, kl, ku, ab.ctypes.data, ab.shape[0], ipiv.ctypes.data)
+    return ab, ipiv, int(info)
+
+
+def band_solve(ab, ipiv, kl, ku, B):
+    X = np.asfortranarray(B, dtype=np.complex128).copy(order="F")
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    n = ab.shape[1]
+    _clib().orc_zgbtrs(n, kl, ku, X.shape[1], ab.ctypes.data, ab.shape[0], ipiv.ctypes.data,
+                       X.ctypes.data, X.shape[0])
+    return X
+
+
+def dense_lu(A):
+    a = np.asfortranarray(A, dtype=np.complex128).copy(order="F")
+    ipiv = np.zeros(a.shape[0], dtype=np.int32)
+    info = _clib().orc_zgetrf(a.shape[0], a.ctypes.data, a.shape[0], ipiv.ctypes.data)
+    return a, ipiv, int(info)
+
+
+def dense_solve(a, ipiv, B):
+    X = np.asfortranarray(B, dtype=np.complex128).copy(order="F")
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    _clib().orc_zgetrs(a.shape[0], X.shape[1], a.ctypes.data, a.shape[0], ipiv.ctypes.data,
+                       X.ctypes.data, X.shape[0])
+    return X
+
+
+def one_norm(prob, Frow):
+    """||T(z)||_1 = max column sum of |T_ij|."""
+    col = np.zeros(prob.n)
+    np.add.at(col, prob.colind, np.abs(assemble_values(prob, Frow)))
+    return float(col.max())
+
+
+def backward_error(prob, Frow, X, U):
+    """Columnwise eta = ||u - T x|| / (||T||_1 ||x|| + ||u||) (normwise, Rigal-Gaches)."""
+    T = sp.csr_matrix((assemble_values(prob, Frow), prob.colind, prob.rowptr), shape=(prob.n, prob.n))
+    R = U - T @ X
+    return np.linalg.norm(R, axis=0) / (one_norm(prob, Frow) * np.linalg.norm(X, axis=0)
+                                        + np.linalg.norm(U, axis=0))
+
+
+def _solve_point(prob, Frow, kl, ku, dense):
+    if dense:
+        a, ipiv, info = dense_lu(assemble_dense(prob, Frow))
+        X = dense_solve(a, ipiv, prob.U)
+    else:
+        ab, ipiv, info = band_lu(assemble_band(prob, Frow, kl, ku), kl, ku)
+        X = band_solve(ab, ipiv, kl, ku, prob.U)
+    return X, info
+
+
+def sample(prob, points=None, threads=None, dense=False, z=None):
+    """Algorithm 2, Step 2 and Eq. eq-hatS: S_hat = [T(z_0)^{-1} U, ..., T(z_{N-1})^{-1} U].
+
+    `points` restricts the work to a subset of the sampling indices (returns only those
+    column blocks).  Returns (S_hat [n, len(points) L], info per point, eta per column).
+    """
+    if z is None:
+        z, _, _ = contour_points(prob.gamma, prob.a, prob.b, prob.N)
+    pts = list(range(len(z))) if points is None else list(points)
+    F, _ = coefficients(prob.fns, z)
+    kl, ku = bandwidths(prob)
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(lambda j: _solve_point(prob, F[j], kl, ku, dense), pts))
+    Shat = np.empty((prob.n, len(pts) * prob.L), dtype=np.complex128, order="F")
+    infos, etas = [], []
+    for k, (j, (X, info)) in enumerate(zip(pts, res)):
+        Shat[:, k * prob.L:(k + 1) * prob.L] = X
+        infos.append(info)
+        etas.append(backward_error(prob, F[j], X, prob.U))
+    return Shat, np.array(infos), np.concatenate(etas) if etas else np.zeros(0)
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 2, Step 3: truncated SVD of S_hat (keep sigma_k > delta sigma_1).
+# ----------------------------------------------------------------------------------------
+def numerical_rank(sigma, delta):
+    sigma = np.asarray(sigma)
+    if sigma.size == 0 or sigma[0] == 0.0:
+        return 0
+    return int(np.count_nonzero(sigma > delta * sigma[0]))
+
+
+def truncated_basis(Shat, delta=1e-14):
+    Ub, sigma, _ = np.linalg.svd(Shat, full_matrices=False)
+    k = numerical_rank(sigma, delta)
+    return np.asfortranarray(Ub[:, :k]), sigma, k
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 2, Step 4 (first half), Eq. eq-Zs-expr: P_i = S^H A_i S.
+# ----------------------------------------------------------------------------------------
+def project(prob, S):
+    return np.stack([S.conj().T @ (prob.term(i) @ S) for i in range(prob.J)])
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 1: modified block SS for T_S(z) = sum_i f_i(z) P_i.
+# ----------------------------------------------------------------------------------------
+def _reduced_T(P, Frow):
+    return np.tensordot(Frow, P, axes=(0, 0))
+
+
+def reduced_ss(P, fns, gamma, a, b, N_S=500, K=2, tol_gap=1e3, return_diag=False):
+    """Returns (lam [nbar], g [k_S, nbar]) plus diagnostics if requested.
+
+    Step 2: moments A_alpha (Eq. eq-Ap-num, rho = max(a, b)) and H, H^< (Eq. eq-HH).
+    Step 3: SVD of H (Eq. eq-svdH) and nbar from the winding number (Eq. eq-ncs) and the
+            singular-value gap (Eq. eq-gap), combined as Section 4.3 suggests.
+    Step 4: A = V_0^H H^< W_0 Sigma_0^{-1} (Eq. eq-A), eig, then Eq. eq-eigens.
+    """
+    k = P.shape[1]
+    rho = max(a, b)
+    z, dphi, _ = contour_points(gamma, a, b, N_S)
+    F, dF = coefficients(fns, z)
+    moments = np.zeros((2 * K, k, k), dtype=np.complex128)
+    wind = 0.0 + 0.0j
+    for j in range(N_S):
+        Ts = _reduced_T(P, F[j])
+        Tinv = np.linalg.solve(Ts, np.eye(k))
+        dTs = _reduced_T(P, dF[j])
+        wind += np.trace(Tinv @ dTs) * dphi[j]
+        w = (z[j] - gamma) / rho
+        for al in range(2 * K):
+            moments[al] += (w ** al) * dphi[j] * Tinv
+    moments /= 1j * N_S
+    wind /= 1j * N_S
+    H = np.block([[moments[r + c] for c in range(K)] for r in range(K)])
+    Hl = np.block([[moments[r + c + 1] for c in range(K)] for r in range(K)])
+    V, sig, Wh = np.linalg.svd(H)
+    W = Wh.conj().T
+    n_w = int(np.rint(wind.real))
+    gaps = sig[:-1] / np.maximum(sig[1:], 1e-300)
+    n_g = int(np.argmax(gaps)) + 1 if gaps.size and gaps.max() >= tol_gap else None
+
+    def extract(nb):
+        if nb <= 0:
+            return np.zeros(0, np.complex128), np.zeros((k, 0), np.complex128)
+        V0, S0, W0 = V[:, :nb], sig[:nb], W[:, :nb]
+        A = V0.conj().T @ Hl @ W0 / S0[None, :]
+        lp, gp = np.linalg.eig(A)
+        Hr = np.hstack([moments[al] for al in range(K)])
+        g = Hr @ (W0 / S0[None, :]) @ gp
+        return rho * lp + gamma, g
+
+    def max_red_res(lam, g):
+        if lam.size == 0:
+            return 0.0
+        Fl, _ = coefficients(fns, lam)
+        r = [np.linalg.norm(_reduced_T(P, Fl[t]) @ g[:, t]) / np.linalg.norm(g[:, t])
+             for t in range(lam.size)]
+        return float(max(r))
+
+    if n_w <= 0:
+        nbar = 0
+    elif n_g is None or n_g == n_w:
+        nbar = n_w
+    else:
+        cand = [(max_red_res(*extract(nn)), nn) for nn in (n_w, n_g)]
+        nbar = min(cand)[1]
+    nbar = min(nbar, K * k)
+    lam, g = extract(nbar)
+    if return_diag:
+        return lam, g, dict(winding=wind, n_winding=n_w, n_gap=n_g, sigma_H=sig, nbar=nbar,
+                            moments=moments)
+    return lam, g
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 2, Step 5 and the residual of Section 7.1.
+# ----------------------------------------------------------------------------------------
+def backmap(S, g):
+    V = S @ g
+    return V / np.linalg.norm(V, axis=0, keepdims=True)
+
+
+def eigen_residuals(prob, lam, V):
+    """(raw ||T(lam) v|| / ||v||, scaled raw / sum_i |f_i(lam)| ||A_i||_F) per pair."""
+    F, _ = coefficients(prob.fns, lam)
+    normA = np.array([np.linalg.norm(prob.vals[i]) for i in range(prob.J)])
+    raw, scaled = [], []
+    for t in range(len(lam)):
+        T = sp.csr_matrix((F[t] @ prob.vals, prob.colind, prob.rowptr), shape=(prob.n, prob.n))
+        r = np.linalg.norm(T @ V[:, t]) / np.linalg.norm(V[:, t])
+        raw.append(r)
+        scaled.append(r / float(np.abs(F[t]) @ normA))
+    return np.array(raw), np.array(scaled)
+
+
+def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False):
+    """Algorithm 2 end to end; eigenvalues strictly inside the ellipse, sorted by |lam|."""
+    Shat, infos, eta = sample(prob, threads=threads, dense=dense)
+    S, sigma, k_S = truncated_basis(Shat, delta)
+    P = project(prob, S)
+    lam, g, diag = reduced_ss(P, prob.fns, prob.gamma, prob.a, prob.b, N_S, K, tol_gap,
+                              return_diag=True)
+    keep = inside_contour(lam, prob.gamma, prob.a, prob.b)
+    lam, g = lam[keep], g[:, keep]
+    order = np.argsort(np.abs(lam), kind="stable")
+    lam, g = lam[order], g[:, order]
+    V = backmap(S, g)
+    raw, scaled = eigen_residuals(prob, lam, V)
+    return dict(lam=lam, V=V, resid=raw, resid_scaled=scaled, k_S=k_S, sigma=sigma, P=P,
+                S=S, Shat=Shat, eta=eta, infos=infos, **diag)

@@ -1,0 +1,222 @@
+"""Pins of the oracle's RSRR (Algorithms 1 and 2) against closed forms, brute force and
+values the paper prints.  None of these re-run the oracle's own formulas."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as w
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
+
+
+def match(a, b):
+    """Pair two eigenvalue lists by minimum-cost bipartite matching; return max rel error."""
+    from scipy.optimize import linear_sum_assignment
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.size == b.size
+    if a.size == 0:
+        return 0.0
+    C = np.abs(a[:, None] - b[None, :])
+    r, c = linear_sum_assignment(C)
+    return float(np.max(np.abs(a[r] - b[c]) / np.abs(b[c])))
+
+
+def test_contour_nodes_and_derivative():
+    z, dphi, th = o.contour_points(1 + 2j, 3.0, 0.5, 8)
+    assert np.allclose(th, 2 * np.pi * (np.arange(8) + 0.5) / 8)
+    # trapezoid rule integrates 1/(z - c) exactly enough for interior / exterior c
+    for c, expect in [(1 + 2j, 1.0), (1.5 + 2.1j, 1.0), (10 + 0j, 0.0)]:
+        z, dphi, _ = o.contour_points(1 + 2j, 3.0, 0.5, 400)
+        val = np.sum(dphi / (z - c)) / (1j * 400)
+        assert abs(val - expect) < 1e-8
+
+
+def test_coefficient_branches():
+    fns = [w.Fn(w.FN_ISQRT_SHIFT, (0.0, 0.0)), w.Fn(w.FN_ISQRT_SHIFT, (100.0, 1.0)),
+           w.Fn(w.FN_EXP_DELAY, (0.7,)), w.Fn(w.FN_RATIONAL, (2.0, -1.0))]
+    z = np.array([50 + 10j, 50 - 10j, 150 + 1e-3j])
+    F, dF = o.coefficients(fns, z)
+    # continued branch agrees with the principal i sqrt(z - s) in the upper half plane
+    assert np.allclose(F[0, 1], 1j * np.sqrt(z[0] - 100.0))
+    # and is continuous across the real axis left of s (where the principal cut lies)
+    F2, _ = o.coefficients(fns, np.array([50 + 1e-9j, 50 - 1e-9j]))
+    assert abs(F2[0, 1] - F2[1, 1]) < 1e-6
+    # derivatives by central differences
+    h = 1e-5
+    Fp, _ = o.coefficients(fns, z + h)
+    Fm, _ = o.coefficients(fns, z - h)
+    assert np.allclose((Fp - Fm) / (2 * h), dF, rtol=1e-6)
+
+
+def test_vandermonde_rank_pin():
+    g = GOLD["vandermonde"]
+    lam = np.linspace(g["lo"], g["hi"], g["nodes"])
+    ranks_mono, ranks_cheb = [], []
+    for Kp in range(10, 101, 5):
+        Bm = np.vander(lam, Kp, increasing=True)
+        Bc = np.polynomial.chebyshev.chebvander(lam, Kp - 1)
+        ranks_mono.append(o.numerical_rank(np.linalg.svd(Bm, compute_uv=False), g["tol"]))
+        ranks_cheb.append((Kp, o.numerical_rank(np.linalg.svd(Bc, compute_uv=False), g["tol"])))
+    assert max(ranks_mono) <= g["monomial_max_rank"]
+    full = [Kp for Kp, r in ranks_cheb if r == g["nodes"]]
+    assert g["chebyshev_full_rank_stated"] <= min(full) <= g["chebyshev_full_rank_by"]
+
+
+def test_linear_laplacian_closed_form():
+    """T(z) = K - z I on the 30x30 grid: eigenvalues 4/h^2 (sin^2(i pi h/2) + sin^2(j pi h/2))."""
+    p = w.config0_linear()
+    h = 1.0 / 31
+    k = np.arange(1, 31)
+    s = 4 / h ** 2 * np.sin(k * np.pi * h / 2) ** 2
+    exact = (s[:, None] + s[None, :]).ravel()
+    exact = exact[o.inside_contour(exact, p.gamma, p.a, p.b)]
+    assert exact.size == 22
+    r = o.rsrr(p)
+    assert r["lam"].size == 22
+    assert match(r["lam"], exact) < 1e-9
+    assert r["resid_scaled"].max() < 1e-10
+
+
+def test_tiny_qep_companion_brute_force():
+    p = w.tiny_qep()
+    K, C, M = (p.term(i).toarray() for i in range(3))
+    n = p.n
+    A = np.block([[np.zeros((n, n)), np.eye(n)], [-K, -C]])
+    B = np.block([[np.eye(n), np.zeros((n, n))], [np.zeros((n, n)), M]])
+    ev = np.linalg.eigvals(np.linalg.solve(B, A))
+    inside = ev[o.inside_contour(ev, p.gamma, p.a, p.b)]
+    r = o.rsrr(p, N_S=500, K=4)
+    assert r["lam"].size == inside.size > 0
+    assert match(r["lam"], inside) < 1e-9
+    assert r["resid"].max() < 1e-10
+
+
+def test_planted_sqrt_closed_form():
+    """d0 - z + i d1 sqrt(z) = 0  <=>  w^2 - i d1 w - d0 = 0, w = sqrt(z), Re w > 0."""
+    p = w.planted_sqrt()
+    d0, d1 = p.meta["d0"], p.meta["d1"]
+    wr = (1j * d1 + np.sqrt(4 * d0 - d1 ** 2 + 0j)) / 2
+    exact = wr ** 2
+    exact = exact[o.inside_contour(exact, p.gamma, p.a, p.b)]
+    r = o.rsrr(p)
+    assert r["lam"].size == exact.size > 5
+    assert match(r["lam"], exact) < 1e-9
+    assert r["resid"].max() < 1e-10
+
+
+def test_planted_sqrt_continued_branch():
+    """Adds -sqrt(sigma^2 - z) d2: scalar roots by Newton, counted by the argument principle."""
+    sigma = 18.0
+    p = w.planted_sqrt(sigma=sigma)
+    d0, d1, d2 = p.meta["d0"], p.meta["d1"], p.meta["d2"]
+    s2 = sigma ** 2
+
+    def f(z, k):
+        return d0[k] - z + 1j * d1[k] * np.sqrt(z) - d2[k] * np.sqrt(s2 - z)
+
+    def df(z, k):
+        return -1 + 0.5j * d1[k] / np.sqrt(z) + 0.5 * d2[k] / np.sqrt(s2 - z)
+
+    zc, dphi, _ = o.contour_points(p.gamma, p.a, p.b, 4000)
+    roots = []
+    for k in range(p.n):
+        cnt = np.sum(df(zc, k) / f(zc, k) * dphi) / (1j * 4000)
+        assert abs(cnt - round(cnt.real)) < 1e-6 and round(cnt.real) in (0, 1)
+        if round(cnt.real) == 1:
+            z = complex(d0[k])
+            for _ in range(60):
+                z = z - f(z, k) / df(z, k)
+            assert abs(f(z, k)) < 1e-10 * abs(z)
+            roots.append(z)
+    r = o.rsrr(p)
+    assert r["lam"].size == len(roots) > 5
+    assert match(r["lam"], roots) < 1e-9
+
+
+def test_planted_delay_lambert_w():
+    """a - z + b exp(-tau z) = 0  <=>  z = a + W(b tau exp(-a tau)) / tau."""
+    from scipy.special import lambertw
+    p = w.planted_delay()
+    a, b, tau = p.meta["a"], p.meta["b"], p.meta["tau"]
+    roots = []
+    for br in range(-3, 4):
+        roots.append(a + lambertw(b * tau * np.exp(-a * tau), br) / tau)
+    roots = np.concatenate(roots)
+    exact = roots[o.inside_contour(roots, p.gamma, p.a, p.b)]
+    r = o.rsrr(p)
+    assert r["lam"].size == exact.size > 5
+    assert match(r["lam"], exact) < 1e-9
+
+
+def test_loaded_string_count_printed():
+    g = GOLD["loaded_string"]
+    p = w.loaded_string(n=g["n"], N=g["N"], L=g["L"])
+    assert (p.gamma, p.a, p.b) == (g["gamma"], g["a"], g["b"])
+    r = o.rsrr(p, N_S=g["N_S"], K=g["K"])
+    assert r["lam"].size == g["count"]
+    assert np.all((r["lam"].real > g["interval"][0]) & (r["lam"].real < g["interval"][1]))
+    assert r["resid_scaled"].max() < 1e-10
+
+
+def test_acoustic_1d_count_printed():
+    g = GOLD["acoustic_1d"]
+    p = w.acoustic_1d(n=g["n"], N=g["N"], L=g["L"])
+    r = o.rsrr(p, N_S=g["N_S"], K=g["K"])
+    assert r["lam"].size == g["count"]
+    assert r["resid_scaled"].max() < 1e-10
+
+
+def test_moment_span_inclusion():
+    """M_hat = S_hat D Z (Eq. eq-hatMS): quadrature moments lie in span(S) (Eq. eq-setsMS)."""
+    p = w.config0_linear(N=16, L=4, nx=12, ny=10)
+    Shat, _, _ = o.sample(p)
+    S, sigma, k = o.truncated_basis(Shat, 1e-14)
+    z, dphi, _ = o.contour_points(p.gamma, p.a, p.b, p.N)
+    omega = dphi / (1j * p.N)
+    for al in range(6):
+        Mh = sum(omega[i] * z[i] ** al * Shat[:, i * p.L:(i + 1) * p.L] for i in range(p.N))
+        res = Mh - S @ (S.conj().T @ Mh)
+        assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(Mh)
+
+
+def test_sample_backward_error_and_dense_path_agree():
+    p = w.config0(N=8, L=3, nx=9, ny=7)
+    Sb, infos, eta = o.sample(p)
+    Sd, _, eta_d = o.sample(p, dense=True)
+    assert np.all(infos == 0)
+    assert eta.max() < 1e-14 and eta_d.max() < 1e-14
+    assert np.allclose(Sb, Sd, rtol=1e-10, atol=1e-13 * np.abs(Sd).max())
+
+
+def test_config0_counts_and_residuals():
+    """Config 0: 22 eigenvalues inside (argument principle on det T, oracle-independent
+    of the subspace), residual scaled <= 1e-10."""
+    p = w.config0()
+    r = o.rsrr(p)
+    assert r["lam"].size == 22
+    assert r["resid_scaled"].max() < 1e-10
+
+
+def test_config1_small_has_no_eigenvalues_inside():
+    """Damped QEP with the config-1 contour: every eigenvalue with Re >= -2.5 has Im < 10
+    (closed form via the pencil K v = mu M v), so the count is 0."""
+    p = w.config1(s=12, N=16, L=4)
+    z = w.problems.damped_eigs(12, 144)
+    assert not np.any(o.inside_contour(z, p.gamma, p.a, p.b))
+    assert not np.any(o.inside_contour(np.conj(z), p.gamma, p.a, p.b))
+    r = o.rsrr(p, N_S=200)
+    assert r["lam"].size == 0
+
+
+def test_config1b_small_closed_form():
+    p = w.config1b(s=20, N=32, L=8)
+    exact = w.problems.damped_eigs(20, 400)
+    exact = np.concatenate([exact, exact.conj()])
+    exact = exact[o.inside_contour(exact, p.gamma, p.a, p.b)]
+    assert exact.size >= 8
+    r = o.rsrr(p, N_S=500)
+    assert r["lam"].size == exact.size
+    assert match(r["lam"], exact) < 1e-9
