@@ -1,0 +1,187 @@
+/*
+ * rsrr.h -- C ABI of the GB300 resolvent-sampling Rayleigh-Ritz (RSRR) library.
+ *
+ * The library computes the hot path of RSRR (Xiao, Meng, Zhang, Zheng,
+ * arXiv:1510.07522) on one CUDA device:
+ *
+ *   rsrr_create_nep  T(z) = sum_i f_i(z) A_i over one sparsity pattern (Eq. eq-Z-expr)
+ *   rsrr_sample      S_hat = [T(z_0)^{-1} U, ..., T(z_{N-1})^{-1} U]     (Eq. eq-hatS,
+ *                    Algorithm 2 Steps 1-2) by band LU + L-column solves
+ *   rsrr_project     truncated SVD of S_hat (Algorithm 2 Step 3), then
+ *                    P_i = S^H A_i S                                      (Eq. eq-Zs-expr)
+ *   rsrr_solve       modified block Sakurai-Sugiura on T_S(z) = sum_i f_i(z) P_i
+ *                    (Algorithm 1) and the back-map v = S g (Algorithm 2 Step 5)
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are interleaved (re, im) pairs of doubles.
+ *   - Matrices are column-major.  Vectors and matrices that the caller passes or
+ *     receives are in the caller's row ordering; the band ordering the library
+ *     chooses internally is invisible.
+ *   - Host pointers unless a flag says otherwise.  Every input is copied before
+ *     the call returns; the caller keeps ownership of all its buffers.
+ *   - Every call is synchronous with respect to the host: when it returns, its
+ *     device work on the handle's stream has completed.
+ *   - Return value 0 on success, a negative RSRR_E* code on failure; the text of
+ *     the last failure on the calling thread is available from rsrr_last_error().
+ *   - One handle must not be used by two host threads at the same time.
+ */
+#ifndef RSRR_H
+#define RSRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define RSRR_OK              0
+#define RSRR_EINVAL         -1  /* bad argument (size, pointer, kind, flag)               */
+#define RSRR_ENOMEM         -2  /* device allocation failed or exceeds the memory budget  */
+#define RSRR_ESINGULAR      -3  /* exactly zero pivot in some T(z_j): z_j is an eigenvalue */
+#define RSRR_ENOTCONVERGED  -4  /* iterative refinement did not reach the tolerance       */
+#define RSRR_ENONFINITE     -5  /* NaN or Inf in the inputs or in a result                */
+#define RSRR_ETIMEOUT       -6  /* a bounded device-side wait gave up                     */
+#define RSRR_ECUDA          -7  /* a CUDA runtime call failed                             */
+#define RSRR_EORDER         -8  /* calls out of order (sample -> project -> solve)        */
+#define RSRR_EUNSUPPORTED   -9  /* the problem's band is wider than the band kernels take */
+
+/* ---- scalar functions f_i of T(z) = sum_i f_i(z) A_i (Eq. eq-Z-expr) ----------------- */
+typedef enum {
+    RSRR_F_CONST = 0,       /* f = 1                                                     */
+    RSRR_F_Z = 1,           /* f = z                                                     */
+    RSRR_F_Z2 = 2,          /* f = z^2                                                   */
+    RSRR_F_ISQRT_SHIFT = 3, /* f = i sqrt(z - p0); p1 = 0: principal root,
+                               p1 = 1: continued branch -sqrt(p0 - z), holomorphic off
+                               [p0, +inf) (gun-type problems, Section 7.2)               */
+    RSRR_F_EXP_DELAY = 4,   /* f = exp(-p0 z)                                            */
+    RSRR_F_RATIONAL = 5     /* f = p0 z / (z + p1)  (Biot / loaded-string terms)         */
+} rsrr_fkind;
+
+typedef struct {
+    int32_t kind;           /* an rsrr_fkind                                             */
+    int32_t reserved;       /* must be 0                                                 */
+    double p[4];            /* parameters, meaning per kind above                        */
+} rsrr_fn;
+
+/* Elliptic contour phi(t) = gamma + a cos t + i b sin t (Eq. eq-contour).  The N
+ * sampling points are the trapezoid nodes t_j = 2 pi (j + 1/2) / N (Eq. eq-Ap-num). */
+typedef struct {
+    double gamma_re, gamma_im;  /* centre                                                */
+    double a, b;                /* semi-axes along re and im, both > 0                   */
+} rsrr_contour;
+
+/* precision of the sample solves (rsrr_sample) */
+#define RSRR_FP64     0  /* complex128 band LU and solves                                */
+#define RSRR_C64_IR   1  /* complex64 band LU and solves, FP64 residual and refinement   */
+
+/* flags of rsrr_create_nep */
+#define RSRR_NATURAL_ORDER 0x1u  /* keep the caller's ordering (skip the band reordering) */
+
+typedef struct rsrr_nep_s* rsrr_nep;
+
+/* ---- rsrr_create_nep ------------------------------------------------------------------
+ * Build a handle for T(z) = sum_{i<J} f_i(z) A_i (Eq. eq-Z-expr, Section 6).
+ *   n         order of T (n >= 1)
+ *   J         number of terms (1 <= J <= 16)
+ *   rowptr    [n+1] CSR row pointers of the union pattern of all A_i (rowptr[0] = 0)
+ *   colind    [nnz] column indices, each row's entries strictly increasing
+ *   vals_reim [J][nnz][2] values of A_i on the union pattern (zeros where A_i has none)
+ *   f         [J] the functions f_i
+ *   flags     RSRR_NATURAL_ORDER or 0
+ *   stream    cudaStream_t on which all device work of this handle runs (NULL = default)
+ *   out       receives the handle
+ * The library picks a row/column ordering (reverse Cuthill-McKee, or the natural one if
+ * its band is no wider) and uploads the pattern and values to the device.
+ * Errors: EINVAL (bad sizes/pattern/kind), ENONFINITE (NaN/Inf value), ENOMEM, ECUDA. */
+int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
+                    const double* vals_reim, const rsrr_fn* f, uint32_t flags,
+                    void* stream, rsrr_nep* out);
+
+/* ---- rsrr_sample ----------------------------------------------------------------------
+ * Algorithm 2, Steps 1-2: for j = 0..N-1, z_j = phi(2 pi (j + 1/2) / N), factor T(z_j)
+ * by band LU with partial pivoting and solve T(z_j) X_j = U; S_hat = [X_0 ... X_{N-1}]
+ * (Eq. eq-hatS, n x N*L) stays on the device.
+ *   C          contour
+ *   N, L       sampling points (1..4096) and probing columns (1..256)
+ *   U_reim     [L][n][2] the probing matrix U (n x L, column-major, caller ordering);
+ *              NULL reuses the U of the previous rsrr_sample on this handle (same n, L)
+ *   precision  RSRR_FP64 or RSRR_C64_IR
+ *   tol        backward-error target per column,
+ *              eta = ||u - T x||_2 / (||T||_1 ||x||_2 + ||u||_2) <= tol  (e.g. 1e-10)
+ *   max_refine refinement sweeps allowed in RSRR_C64_IR (ignored for RSRR_FP64)
+ * Errors: EINVAL, ESINGULAR (a zero pivot: some z_j is an eigenvalue),
+ *         ENOTCONVERGED (eta > tol after max_refine sweeps, or > tol in FP64),
+ *         ENONFINITE, ENOMEM, ECUDA, EUNSUPPORTED (band wider than 480). */
+int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
+                const double* U_reim, int32_t precision, double tol, int32_t max_refine);
+
+/* ---- rsrr_project ---------------------------------------------------------------------
+ * Algorithm 2 Step 3 and Eq. eq-Zs-expr: S_hat = Q R (Householder, FP64), R = W Sigma
+ * Y^H (one-sided Jacobi, FP64); keep the k_S singular values sigma_k > delta sigma_1;
+ * S = Q W[:, :k_S]; P_i = S^H A_i S for every term.  Requires a successful rsrr_sample.
+ *   delta   truncation threshold (the paper uses 1e-14)
+ *   k_S_out receives k_S
+ * Errors: EORDER, EINVAL, ENOMEM, ECUDA, ENONFINITE. */
+int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out);
+
+/* ---- rsrr_solve -----------------------------------------------------------------------
+ * Algorithm 1 on T_S(z) = sum_i f_i(z) P_i with the same contour as rsrr_sample:
+ * moments A_alpha (Eq. eq-Ap-num, rho = max(a, b)), block Hankel H, H^< (Eq. eq-HH),
+ * SVD of H, nbar from the winding number (Eq. eq-ncs) and the singular-value gap
+ * (Eq. eq-gap, gaps over the whole SVD), A = V_0^H H^< W_0 Sigma_0^{-1} (Eq. eq-A), its
+ * eigenpairs, lambda = rho lambda' + gamma, g (Eq. eq-eigens); then v = S g / ||S g||
+ * (Algorithm 2 Step 5) and the residual ||T(lambda) v||_2 (||v|| = 1, Section 7.1).
+ * Only eigenvalues strictly inside the ellipse are returned, sorted by |lambda|.
+ *   N_S, K      quadrature points and Hankel block count (the paper: 500..1000, 2..8)
+ *   tol_gap     gap acceptance threshold (the paper: 1e3)
+ *   cap         capacity of the output arrays
+ *   lambda_reim [cap][2] eigenvalues
+ *   V_reim      [cap][n][2] unit eigenvectors (caller ordering), or NULL
+ *   resid       [cap] residuals ||T(lambda) v||_2, or NULL
+ *   nC_out      receives the number of eigenvalues returned (<= cap)
+ * Errors: EORDER, EINVAL (cap too small: nC_out still holds the count), ESINGULAR
+ *         (T_S(z) singular at a quadrature point), ENOMEM, ECUDA, ENONFINITE. */
+int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap,
+               double* lambda_reim, double* V_reim, double* resid, int32_t* nC_out);
+
+/* ---- introspection (tests, diagnostics) ------------------------------------------------ */
+typedef struct {
+    int64_t n, nnz;
+    int32_t J, N, L;
+    int32_t kl, ku;             /* band of the chosen ordering                             */
+    int32_t natural_order;      /* 1 if the caller's ordering was kept                     */
+    int32_t precision;
+    int32_t refine_sweeps;      /* refinement sweeps run by the last rsrr_sample           */
+    int32_t k_S;                /* after rsrr_project, else -1                             */
+    int32_t nbar;               /* after rsrr_solve (before the inside filter), else -1    */
+    int32_t n_winding, n_gap;   /* after rsrr_solve: the two counts (n_gap -1: no gap)     */
+    double winding_re, winding_im;
+    double max_eta;             /* max backward error over all N*L columns                 */
+    double ms_sample, ms_project, ms_solve;  /* device time of the last calls              */
+    int64_t device_bytes;       /* device memory held by the handle                        */
+} rsrr_info;
+
+int rsrr_get_info(rsrr_nep h, rsrr_info* out);
+/* Column blocks j0..j1-1 of S_hat, n x (j1-j0)*L, caller ordering, into host memory. */
+int rsrr_get_samples(rsrr_nep h, int32_t j0, int32_t j1, double* out_reim);
+/* Backward errors eta of all N*L columns (column jL + l is point j, probe l). */
+int rsrr_get_eta(rsrr_nep h, double* out);
+/* The min(n, N*L) singular values of S_hat, descending (after rsrr_project). */
+int rsrr_get_sigma(rsrr_nep h, double* out);
+/* The orthonormal basis S, n x k_S, caller ordering (after rsrr_project). */
+int rsrr_get_basis(rsrr_nep h, double* out_reim);
+/* The projected matrices P_i, [J][k_S][k_S] column-major (after rsrr_project). */
+int rsrr_get_projected(rsrr_nep h, double* out_reim);
+/* The singular values of H, K*k_S of them, descending (after rsrr_solve). */
+int rsrr_get_hankel_sigma(rsrr_nep h, double* out);
+
+void rsrr_destroy(rsrr_nep h);
+const char* rsrr_last_error(void);
+/* Library version string. */
+const char* rsrr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSRR_H */

@@ -1,0 +1,253 @@
+"""Python binding of librsrr.so, the GB300 (sm_103a) resolvent-sampling Rayleigh-Ritz library.
+
+Argument marshalling only: every step of RSRR runs in the library's CUDA kernels.  The
+functions keep the C names (rsrr_create_nep, rsrr_sample, rsrr_project, rsrr_solve, ...);
+`Nep` is a small convenience wrapper over them.  Importing works without a GPU (the
+library only needs the CUDA runtime to load); calls that touch the device fail with
+RsrrError when no device is present.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librsrr.so")
+
+RSRR_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOTCONVERGED", -5: "ENONFINITE",
+          -6: "ETIMEOUT", -7: "ECUDA", -8: "EORDER", -9: "EUNSUPPORTED"}
+RSRR_FP64 = 0
+RSRR_C64_IR = 1
+RSRR_NATURAL_ORDER = 0x1
+
+F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL = range(6)
+
+
+class RsrrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class rsrr_fn(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p", ctypes.c_double * 4)]
+
+
+class rsrr_contour(ctypes.Structure):
+    _fields_ = [("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
+                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class rsrr_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("J", ctypes.c_int32), ("N", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("kl", ctypes.c_int32), ("ku", ctypes.c_int32), ("natural_order", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32),
+                ("k_S", ctypes.c_int32), ("nbar", ctypes.c_int32),
+                ("n_winding", ctypes.c_int32), ("n_gap", ctypes.c_int32),
+                ("winding_re", ctypes.c_double), ("winding_im", ctypes.c_double),
+                ("max_eta", ctypes.c_double),
+                ("ms_sample", ctypes.c_double), ("ms_project", ctypes.c_double),
+                ("ms_solve", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr_get_info",
+           "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
+           "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
+           "rsrr_version"]
+
+
+def lib():
+    """Load librsrr.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(or python -m paper_1510_07522_gb300._build)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
+    sig = {
+        "rsrr_create_nep": ([I64, I32, P, P, P, P, U32, P, P], ctypes.c_int),
+        "rsrr_sample": ([P, P, I32, I32, P, I32, D, I32], ctypes.c_int),
+        "rsrr_project": ([P, D, P], ctypes.c_int),
+        "rsrr_solve": ([P, I32, I32, D, I32, P, P, P, P], ctypes.c_int),
+        "rsrr_get_info": ([P, P], ctypes.c_int),
+        "rsrr_get_samples": ([P, I32, I32, P], ctypes.c_int),
+        "rsrr_get_eta": ([P, P], ctypes.c_int),
+        "rsrr_get_sigma": ([P, P], ctypes.c_int),
+        "rsrr_get_basis": ([P, P], ctypes.c_int),
+        "rsrr_get_projected": ([P, P], ctypes.c_int),
+        "rsrr_get_hankel_sigma": ([P, P], ctypes.c_int),
+        "rsrr_destroy": ([P], None),
+        "rsrr_last_error": ([], ctypes.c_char_p),
+        "rsrr_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != RSRR_OK:
+        raise RsrrError(rc, lib().rsrr_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c128(a, shape=None, order="F"):
+    a = np.asarray(a, dtype=np.complex128)
+    if shape is not None:
+        a = a.reshape(shape, order=order)
+    return np.require(a, requirements=["F_CONTIGUOUS", "ALIGNED"] if order == "F" else ["C_CONTIGUOUS"])
+
+
+def current_stream():
+    """The caller's CUDA stream from PyTorch (None = the default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001 - torch is optional plumbing
+        pass
+    return None
+
+
+# ---- the C entry points with their own names (marshalling only) ---------------------------
+def rsrr_create_nep(n, rowptr, colind, vals, fns, flags=0, stream=None):
+    """vals: complex [J, nnz] on the union CSR pattern; fns: list of (kind, params)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    vals = np.ascontiguousarray(vals, dtype=np.complex128)
+    J = vals.shape[0]
+    farr = (rsrr_fn * J)()
+    for i, (kind, params) in enumerate(fns):
+        farr[i].kind = int(kind)
+        farr[i].reserved = 0
+        p = list(params) + [0.0] * 4
+        for t in range(4):
+            farr[i].p[t] = float(p[t])
+    h = ctypes.c_void_p()
+    _check(lib().rsrr_create_nep(int(n), int(J), _ptr(rowptr), _ptr(colind), _ptr(vals), farr,
+                                 int(flags), stream if stream is not None else current_stream(),
+                                 ctypes.byref(h)))
+    return h
+
+
+def rsrr_sample(h, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+    C = rsrr_contour(complex(gamma).real, complex(gamma).imag, float(a), float(b))
+    Uc = None if U is None else _c128(U)
+    _check(lib().rsrr_sample(h, ctypes.byref(C), int(N), int(L), _ptr(Uc), int(precision), float(tol),
+                             int(max_refine)))
+
+
+def rsrr_project(h, delta=1e-14):
+    k = ctypes.c_int32()
+    _check(lib().rsrr_project(h, float(delta), ctypes.byref(k)))
+    return k.value
+
+
+def rsrr_solve(h, N_S=500, K=2, tol_gap=1e3, cap=None, n=None, vectors=True):
+    if cap is None:
+        cap = 4096
+    lam = np.zeros(cap, dtype=np.complex128)
+    V = np.zeros((n, cap), dtype=np.complex128, order="F") if (vectors and n) else None
+    res = np.zeros(cap)
+    nC = ctypes.c_int32()
+    _check(lib().rsrr_solve(h, int(N_S), int(K), float(tol_gap), int(cap), _ptr(lam), _ptr(V), _ptr(res),
+                            ctypes.byref(nC)))
+    k = nC.value
+    return lam[:k].copy(), (None if V is None else V[:, :k].copy()), res[:k].copy()
+
+
+def rsrr_get_info(h):
+    info = rsrr_info()
+    _check(lib().rsrr_get_info(h, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in rsrr_info._fields_}
+
+
+def rsrr_destroy(h):
+    if h:
+        lib().rsrr_destroy(h)
+
+
+class Nep:
+    """Handle for T(z) = sum_i f_i(z) A_i on the device (rsrr_create_nep ... rsrr_destroy)."""
+
+    def __init__(self, n, rowptr, colind, vals, fns, flags=0, stream=None):
+        self.n = int(n)
+        self.J = int(np.asarray(vals).shape[0])
+        self.h = rsrr_create_nep(n, rowptr, colind, vals, fns, flags, stream)
+
+    def sample(self, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+        self.N, self.L = int(N), int(L)
+        rsrr_sample(self.h, gamma, a, b, N, L, U, precision, tol, max_refine)
+
+    def project(self, delta=1e-14):
+        self.kS = rsrr_project(self.h, delta)
+        return self.kS
+
+    def solve(self, N_S=500, K=2, tol_gap=1e3, cap=4096, vectors=True):
+        return rsrr_solve(self.h, N_S, K, tol_gap, cap, self.n, vectors)
+
+    def info(self):
+        return rsrr_get_info(self.h)
+
+    def samples(self, j0=0, j1=None):
+        j1 = self.N if j1 is None else j1
+        out = np.zeros((self.n, (j1 - j0) * self.L), dtype=np.complex128, order="F")
+        _check(lib().rsrr_get_samples(self.h, int(j0), int(j1), _ptr(out)))
+        return out
+
+    def eta(self):
+        out = np.zeros(self.N * self.L)
+        _check(lib().rsrr_get_eta(self.h, _ptr(out)))
+        return out
+
+    def sigma(self):
+        out = np.zeros(min(self.n, self.N * self.L))
+        _check(lib().rsrr_get_sigma(self.h, _ptr(out)))
+        return out
+
+    def basis(self):
+        out = np.zeros((self.n, self.kS), dtype=np.complex128, order="F")
+        _check(lib().rsrr_get_basis(self.h, _ptr(out)))
+        return out
+
+    def projected(self):
+        out = np.zeros((self.J, self.kS, self.kS), dtype=np.complex128)
+        _check(lib().rsrr_get_projected(self.h, _ptr(out)))
+        # stored column-major per term
+        return np.ascontiguousarray(np.transpose(out, (0, 2, 1)))
+
+    def hankel_sigma(self, K):
+        out = np.zeros(K * self.kS)
+        _check(lib().rsrr_get_hankel_sigma(self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            rsrr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

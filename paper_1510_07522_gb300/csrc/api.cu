@@ -1,0 +1,317 @@
+// C ABI entry points (rsrr.h): handle life cycle, rsrr_sample, introspection.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace rsrr {
+int sample_run(rsrr_nep h, const double* U_reim, int max_refine);
+int project_run(rsrr_nep h, double delta);
+int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambda_reim, double* V_reim,
+              double* resid, int32_t* nC_out);
+
+namespace {
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Timer {
+    rsrr_nep h;
+    explicit Timer(rsrr_nep hh) : h(hh) { cudaEventRecord(h->ev0, h->stream); }
+    double stop() {
+        cudaEventRecord(h->ev1, h->stream);
+        cudaEventSynchronize(h->ev1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        return ms;
+    }
+};
+}  // namespace
+}  // namespace rsrr
+
+using namespace rsrr;
+
+extern "C" {
+
+const char* rsrr_last_error(void) { return rsrr::last_error(); }
+const char* rsrr_version(void) { return "rsrr-gb300 0.1 (sm_103a)"; }
+
+int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
+                    const double* vals_reim, const rsrr_fn* f, uint32_t flags, void* stream,
+                    rsrr_nep* out) {
+    if (!out) return set_error(RSRR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)INT32_MAX - 1) return set_error(RSRR_EINVAL, "n out of range");
+    if (J < 1 || J > 16) return set_error(RSRR_EINVAL, "J must be in 1..16");
+    if (!rowptr || !colind || !vals_reim || !f) return set_error(RSRR_EINVAL, "NULL input array");
+    if (flags & ~RSRR_NATURAL_ORDER) return set_error(RSRR_EINVAL, "unknown flag bits");
+    if (rowptr[0] != 0) return set_error(RSRR_EINVAL, "rowptr[0] must be 0");
+    for (int64_t r = 0; r < n; ++r) {
+        if (rowptr[r + 1] < rowptr[r]) return set_error(RSRR_EINVAL, "rowptr not monotone");
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            if (colind[k] < 0 || colind[k] >= n) return set_error(RSRR_EINVAL, "column index out of range");
+            if (k > rowptr[r] && colind[k] <= colind[k - 1])
+                return set_error(RSRR_EINVAL, "column indices of a row must be strictly increasing");
+        }
+    }
+    const int64_t nnz = rowptr[n];
+    if (nnz < 1 || nnz > (int64_t)INT32_MAX) return set_error(RSRR_EINVAL, "nnz out of range");
+    for (int i = 0; i < J; ++i) RSRR_TRY(check_fn(f[i]));
+    for (int64_t k = 0; k < 2 * nnz * J; ++k)
+        if (!std::isfinite(vals_reim[k])) return set_error(RSRR_ENONFINITE, "non-finite matrix value");
+
+    auto* h = new rsrr_nep_s();
+    cudaGetDevice(&h->device);
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    h->n = n;
+    h->nnz = nnz;
+    h->J = J;
+    h->fns.assign(f, f + J);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        delete h;
+        return set_error(RSRR_ECUDA, "cudaEventCreate failed");
+    }
+    choose_ordering(n, rowptr, colind, (flags & RSRR_NATURAL_ORDER) != 0, &h->ord);
+    // permuted CSR (rows in new order, columns renumbered and sorted) and values
+    std::vector<int64_t> prow(n + 1, 0);
+    std::vector<int32_t> pcol(nnz), prowidx(nnz);
+    std::vector<int64_t> src(nnz);
+    {
+        std::vector<std::pair<int32_t, int64_t>> tmp;
+        int64_t pos = 0;
+        for (int64_t rn = 0; rn < n; ++rn) {
+            const int64_t ro = h->ord.perm[rn];
+            tmp.clear();
+            for (int64_t k = rowptr[ro]; k < rowptr[ro + 1]; ++k) tmp.emplace_back(h->ord.iperm[colind[k]], k);
+            std::sort(tmp.begin(), tmp.end());
+            for (auto& pr : tmp) {
+                pcol[pos] = pr.first;
+                prowidx[pos] = (int32_t)rn;
+                src[pos] = pr.second;
+                ++pos;
+            }
+            prow[rn + 1] = pos;
+        }
+    }
+    std::vector<c128> pv((size_t)J * nnz);
+    h->normA.assign(J, 0.0);
+    for (int i = 0; i < J; ++i) {
+        double s2 = 0.0;
+        for (int64_t k = 0; k < nnz; ++k) {
+            const double* v = vals_reim + 2 * ((int64_t)i * nnz + src[k]);
+            pv[(size_t)i * nnz + k] = mk<double>(v[0], v[1]);
+            s2 += v[0] * v[0] + v[1] * v[1];
+        }
+        h->normA[i] = std::sqrt(s2);
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = h->stream;
+    int rc = RSRR_OK;
+    if ((rc = dalloc_n(&h->d_rowptr, n + 1, st)) || (rc = dalloc_n(&h->d_colind, nnz, st)) ||
+        (rc = dalloc_n(&h->d_rowidx, nnz, st)) || (rc = dalloc_n(&h->d_vals, (size_t)J * nnz, st)) ||
+        (rc = dalloc_n(&h->d_perm, n, st))) {
+        rsrr_destroy(h);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_rowptr, prow.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_colind, pcol.data(), nnz * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_rowidx, prowidx.data(), nnz * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_vals, pv.data(), pv.size() * sizeof(c128), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_perm, h->ord.perm.data(), n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        rsrr_destroy(h);
+        return set_error(RSRR_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    h->device_bytes = (n + 1) * 8 + nnz * 8 + (int64_t)pv.size() * 16 + n * 4;
+    *out = h;
+    return RSRR_OK;
+}
+
+int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const double* U_reim,
+                int32_t precision, double tol, int32_t max_refine) {
+    if (!h || !C) return set_error(RSRR_EINVAL, "NULL handle or contour");
+    if (N < 1 || N > 4096 || L < 1 || L > 256) return set_error(RSRR_EINVAL, "N or L out of range");
+    if (!(C->a > 0) || !(C->b > 0) || !std::isfinite(C->gamma_re) || !std::isfinite(C->gamma_im) ||
+        !std::isfinite(C->a) || !std::isfinite(C->b))
+        return set_error(RSRR_EINVAL, "bad contour");
+    if (precision != RSRR_FP64 && precision != RSRR_C64_IR) return set_error(RSRR_EINVAL, "unknown precision");
+    if (!(tol > 0) || max_refine < 0 || max_refine > 100) return set_error(RSRR_EINVAL, "bad tol or max_refine");
+    if ((int64_t)N * L * h->n > (int64_t)1 << 34) return set_error(RSRR_ENOMEM, "S_hat too large");
+    DeviceGuard g(h->device);
+    h->C = *C;
+    h->N = N;
+    h->L = L;
+    h->precision = precision;
+    h->tol = tol;
+    h->sampled = h->projected = false;
+    h->kS = -1;
+    h->nbar = -1;
+    Timer t(h);
+    int rc = sample_run(h, U_reim, max_refine);
+    h->ms_sample = t.stop();
+    if (rc != RSRR_OK) return rc;
+    std::vector<double> eta((size_t)N * L);
+    RSRR_CUDA(cudaMemcpy(eta.data(), h->d_eta, eta.size() * 8, cudaMemcpyDeviceToHost));
+    h->max_eta = 0;
+    for (double e : eta) h->max_eta = std::max(h->max_eta, e);
+    h->sampled = true;
+    return RSRR_OK;
+}
+
+int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out) {
+    if (!h) return set_error(RSRR_EINVAL, "NULL handle");
+    if (!h->sampled) return set_error(RSRR_EORDER, "rsrr_project needs a successful rsrr_sample");
+    if (!(delta >= 0) || !(delta < 1)) return set_error(RSRR_EINVAL, "delta must be in [0, 1)");
+    DeviceGuard g(h->device);
+    Timer t(h);
+    int rc = project_run(h, delta);
+    h->ms_project = t.stop();
+    if (rc != RSRR_OK) return rc;
+    h->projected = true;
+    if (k_S_out) *k_S_out = h->kS;
+    return RSRR_OK;
+}
+
+int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, double* lambda_reim,
+               double* V_reim, double* resid, int32_t* nC_out) {
+    if (!h) return set_error(RSRR_EINVAL, "NULL handle");
+    if (!h->projected) return set_error(RSRR_EORDER, "rsrr_solve needs a successful rsrr_project");
+    if (N_S < 4 || N_S > 100000 || K < 1 || K > 64 || !(tol_gap > 1) || cap < 0 || !nC_out ||
+        (cap > 0 && !lambda_reim))
+        return set_error(RSRR_EINVAL, "bad rsrr_solve arguments");
+    DeviceGuard g(h->device);
+    Timer t(h);
+    int rc = solve_run(h, N_S, K, tol_gap, cap, lambda_reim, V_reim, resid, nC_out);
+    h->ms_solve = t.stop();
+    return rc;
+}
+
+int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
+    if (!h || !o) return set_error(RSRR_EINVAL, "NULL argument");
+    std::memset(o, 0, sizeof(*o));
+    o->n = h->n;
+    o->nnz = h->nnz;
+    o->J = h->J;
+    o->N = h->N;
+    o->L = h->L;
+    o->kl = (int32_t)h->ord.kl;
+    o->ku = (int32_t)h->ord.ku;
+    o->natural_order = h->ord.natural ? 1 : 0;
+    o->precision = h->precision;
+    o->refine_sweeps = h->refine_sweeps;
+    o->k_S = h->kS;
+    o->nbar = h->nbar;
+    o->n_winding = h->n_winding;
+    o->n_gap = h->n_gap;
+    o->winding_re = h->winding.real();
+    o->winding_im = h->winding.imag();
+    o->max_eta = h->max_eta;
+    o->ms_sample = h->ms_sample;
+    o->ms_project = h->ms_project;
+    o->ms_solve = h->ms_solve;
+    o->device_bytes = h->device_bytes;
+    return RSRR_OK;
+}
+
+int rsrr_get_samples(rsrr_nep h, int32_t j0, int32_t j1, double* out_reim) {
+    if (!h || !out_reim) return set_error(RSRR_EINVAL, "NULL argument");
+    if (!h->sampled) return set_error(RSRR_EORDER, "no samples");
+    if (j0 < 0 || j1 > h->N || j0 >= j1) return set_error(RSRR_EINVAL, "bad point range");
+    DeviceGuard g(h->device);
+    const int64_t n = h->n, cols = (int64_t)(j1 - j0) * h->L;
+    std::vector<c128> tmp((size_t)(n * cols));
+    RSRR_CUDA(cudaMemcpy(tmp.data(), h->d_S + (int64_t)j0 * h->L * n, tmp.size() * sizeof(c128),
+                         cudaMemcpyDeviceToHost));
+    for (int64_t c = 0; c < cols; ++c)
+        for (int64_t r = 0; r < n; ++r) {
+            const c128 v = tmp[(size_t)(r + c * n)];
+            const int64_t ro = h->ord.perm[r];
+            out_reim[2 * (ro + c * n)] = v.re;
+            out_reim[2 * (ro + c * n) + 1] = v.im;
+        }
+    return RSRR_OK;
+}
+
+int rsrr_get_eta(rsrr_nep h, double* out) {
+    if (!h || !out) return set_error(RSRR_EINVAL, "NULL argument");
+    if (!h->sampled) return set_error(RSRR_EORDER, "no samples");
+    DeviceGuard g(h->device);
+    RSRR_CUDA(cudaMemcpy(out, h->d_eta, (size_t)h->N * h->L * 8, cudaMemcpyDeviceToHost));
+    return RSRR_OK;
+}
+
+int rsrr_get_sigma(rsrr_nep h, double* out) {
+    if (!h || !out) return set_error(RSRR_EINVAL, "NULL argument");
+    if (!h->projected) return set_error(RSRR_EORDER, "no projection");
+    std::copy(h->sigma.begin(), h->sigma.end(), out);
+    return RSRR_OK;
+}
+
+int rsrr_get_basis(rsrr_nep h, double* out_reim) {
+    if (!h || !out_reim) return set_error(RSRR_EINVAL, "NULL argument");
+    if (!h->projected) return set_error(RSRR_EORDER, "no projection");
+    DeviceGuard g(h->device);
+    const int64_t n = h->n;
+    std::vector<c128> tmp((size_t)(n * h->kS));
+    if (!tmp.empty())
+        RSRR_CUDA(cudaMemcpy(tmp.data(), h->d_Q, tmp.size() * sizeof(c128), cudaMemcpyDeviceToHost));
+    for (int64_t c = 0; c < h->kS; ++c)
+        for (int64_t r = 0; r < n; ++r) {
+            const c128 v = tmp[(size_t)(r + c * n)];
+            const int64_t ro = h->ord.perm[r];
+            out_reim[2 * (ro + c * n)] = v.re;
+            out_reim[2 * (ro + c * n) + 1] = v.im;
+        }
+    return RSRR_OK;
+}
+
+int rsrr_get_projected(rsrr_nep h, double* out_reim) {
+    if (!h || !out_reim) return set_error(RSRR_EINVAL, "NULL argument");
+    if (!h->projected) return set_error(RSRR_EORDER, "no projection");
+    DeviceGuard g(h->device);
+    const size_t cnt = (size_t)h->J * h->kS * h->kS;
+    if (cnt) RSRR_CUDA(cudaMemcpy(out_reim, h->d_P, cnt * sizeof(c128), cudaMemcpyDeviceToHost));
+    return RSRR_OK;
+}
+
+int rsrr_get_hankel_sigma(rsrr_nep h, double* out) {
+    if (!h || !out) return set_error(RSRR_EINVAL, "NULL argument");
+    if (h->nbar < 0) return set_error(RSRR_EORDER, "no reduced solve");
+    std::copy(h->sigma_H.begin(), h->sigma_H.end(), out);
+    return RSRR_OK;
+}
+
+void rsrr_destroy(rsrr_nep h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaStream_t st = h->stream;
+    dfree(h->d_rowptr, st);
+    dfree(h->d_colind, st);
+    dfree(h->d_rowidx, st);
+    dfree(h->d_vals, st);
+    dfree(h->d_perm, st);
+    dfree(h->d_U, st);
+    dfree(h->d_S, st);
+    dfree(h->d_eta, st);
+    dfree(h->d_Q, st);
+    dfree(h->d_P, st);
+    cudaStreamSynchronize(st);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Dense FP64 complex kernels: tiled ZGEMM, bounded grid barrier, one-sided Jacobi.
+#include <algorithm>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace rsrr {
+
+// ---------------------------------------------------------------------------------------------
+// ZGEMM: 64 x 64 output tile per CTA, K in steps of 8, 256 threads each owning a 4 x 4 grid of
+// outputs spaced 16 apart.  FP64 FMA throughput bounds it on this part; the tiling keeps the
+// operands in shared memory so global traffic is (M + N) K / 64 elements per tile.
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr int BM = 64, BN = 64, BK = 8;
+
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
+    __shared__ c128 As[BK][BM + 1];
+    __shared__ c128 Bs[BK][BN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int bm = blockIdx.x * BM, bn = blockIdx.y * BN;
+    const int bz = blockIdx.z, b = bz / g.ksplit, ks = bz % g.ksplit;
+    const c128* A = g.A + b * g.sA;
+    const c128* B = g.B + b * g.sB;
+    c128* C = g.C + b * g.sC;
+    const int k_begin = ks * kchunk, k_end = min(g.K, k_begin + kchunk);
+    c128 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = czero<double>();
+    for (int k0 = k_begin; k0 < k_end; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + 256 * r;
+            int i, k;
+            if (OPA == OP_N) { i = idx % BM; k = idx / BM; } else { k = idx % BK; i = idx / BK; }
+            const int gi = bm + i, gk = k0 + k;
+            c128 v = czero<double>();
+            if (gi < g.M && gk < k_end) {
+                v = (OPA == OP_N) ? A[gi + (int64_t)gk * g.lda] : A[gk + (int64_t)gi * g.lda];
+                if (OPA == OP_C) v.im = -v.im;
+            }
+            As[k][i] = v;
+            int j;
+            if (OPB == OP_N) { k = idx % BK; j = idx / BK; } else { j = idx % BN; k = idx / BN; }
+            const int gj = bn + j;
+            const int gk2 = k0 + k;
+            c128 w = czero<double>();
+            if (gj < g.N && gk2 < k_end) {
+                w = (OPB == OP_N) ? B[gk2 + (int64_t)gj * g.ldb] : B[gj + (int64_t)gk2 * g.ldb];
+                if (OPB == OP_C) w.im = -w.im;
+            }
+            Bs[k][j] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            c128 a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gi = bm + ty + 16 * i;
+        if (gi >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gj = bn + tx + 16 * j;
+            if (gj >= g.N) continue;
+            c128* c = C + gi + (int64_t)gj * g.ldc;
+            const c128 v = g.alpha * acc[i][j];
+            if (g.ksplit > 1) {
+                atomicAdd(&c->re, v.re);
+                atomicAdd(&c->im, v.im);
+            } else if (g.beta.re == 0.0 && g.beta.im == 0.0) {
+                *c = v;
+            } else {
+                *c = v + g.beta * (*c);
+            }
+        }
+    }
+}
+
+__global__ void scale_kernel(c128* C, int M, int N, int64_t ldc, int64_t sC, c128 beta) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (idx >= (int64_t)M * N) return;
+    const int64_t i = idx % M, j = idx / M;
+    c128* c = C + b * sC + i + j * ldc;
+    *c = (beta.re == 0.0 && beta.im == 0.0) ? czero<double>() : beta * (*c);
+}
+}  // namespace
+
+int zgemm(const Zgemm& g0, cudaStream_t s) {
+    Zgemm g = g0;
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return RSRR_OK;
+    const int tm = (int)ceil_div(g.M, BM), tn = (int)ceil_div(g.N, BN);
+    if (g.K <= 0) {
+        dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
+        scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta);
+        RSRR_CUDA(cudaGetLastError());
+        return RSRR_OK;
+    }
+    if (g.ksplit <= 0) {
+        const int64_t tiles = (int64_t)tm * tn * g.batch;
+        int ks = 1;
+        while (tiles * ks < 2 * 152 && (int64_t)g.K / (ks * 2) >= 256) ks *= 2;
+        g.ksplit = ks;
+    }
+    int kchunk = (int)ceil_div(ceil_div(g.K, g.ksplit), BK) * BK;
+    g.ksplit = (int)ceil_div(g.K, kchunk);
+    if (g.ksplit > 1) {
+        dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
+        scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta);
+    }
+    dim3 grid(tm, tn, g.batch * g.ksplit);
+#define ZG(a, b) zgemm_kernel<a, b><<<grid, 256, 0, s>>>(g, kchunk)
+    if (g.opA == OP_N && g.opB == OP_N) ZG(OP_N, OP_N);
+    else if (g.opA == OP_N && g.opB == OP_T) ZG(OP_N, OP_T);
+    else if (g.opA == OP_N && g.opB == OP_C) ZG(OP_N, OP_C);
+    else if (g.opA == OP_T && g.opB == OP_N) ZG(OP_T, OP_N);
+    else if (g.opA == OP_C && g.opB == OP_N) ZG(OP_C, OP_N);
+    else if (g.opA == OP_C && g.opB == OP_C) ZG(OP_C, OP_C);
+    else if (g.opA == OP_T && g.opB == OP_T) ZG(OP_T, OP_T);
+    else return set_error(RSRR_EINVAL, "zgemm: unsupported op combination");
+#undef ZG
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Grid barrier (cooperative launches only: all CTAs are co-resident).
+// ---------------------------------------------------------------------------------------------
+__device__ bool grid_sync(const GridBar& gb) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = gb.gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(gb.count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1LL << 24)) {  // ~seconds: give up, report, return
+                    atomicExch(gb.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int*)gb.err == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Norms
+// ---------------------------------------------------------------------------------------------
+namespace {
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    }
+    return r;  // valid in thread 0
+}
+
+__global__ void colnorm_kernel(const c128* B, int mb, int64_t ld, double* out) {
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < mb; i += blockDim.x) s += cnorm2(B[i + (int64_t)c * ld]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[c] = sqrt(s);
+}
+
+__global__ void blocknorm_kernel(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, double* out) {
+    const int64_t rows = r1 - r0;
+    const int64_t total = rows * (c1 - c0);
+    double s = 0.0;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = r0 + idx % rows, j = c0 + idx / rows;
+        s += cnorm2(A[i + j * lda]);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+}  // namespace
+
+void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s) {
+    if (k > 0) colnorm_kernel<<<k, 256, 0, s>>>(B, mb, ld, out);
+}
+
+void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, double* out, cudaStream_t s) {
+    if (r1 <= r0 || c1 <= c0) return;
+    const int64_t total = (int64_t)(r1 - r0) * (c1 - c0);
+    const int blocks = (int)std::min<int64_t>(4 * 152, ceil_div(total, 256));
+    blocknorm_kernel<<<blocks, 256, 0, s>>>(A, lda, r0, r1, c0, c1, out);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One-sided Jacobi: one CTA per column pair of a round-robin round.
+// ---------------------------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ int rr_pos(int k, int r, int n) {  // player at seat k in round r
+    return k == 0 ? 0 : ((k - 1 + r) % (n - 1)) + 1;
+}
+
+__global__ void __launch_bounds__(256) jacobi_round_kernel(c128* B, int mb, int kk, int npad, c128* J,
+                                                          int round, double tol,
+                                                          unsigned long long* max_off, int* rotations) {
+    const int i = blockIdx.x;
+    int p = rr_pos(i, round, npad), q = rr_pos(npad - 1 - i, round, npad);
+    if (p > q) { const int t = p; p = q; q = t; }
+    if (q >= kk) return;  // padding seat
+    c128* bp = B + (int64_t)p * mb;
+    c128* bq = B + (int64_t)q * mb;
+    double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
+    for (int r = threadIdx.x; r < mb; r += blockDim.x) {
+        const c128 x = bp[r], y = bq[r];
+        a += cnorm2(x);
+        b += cnorm2(y);
+        gr += x.re * y.re + x.im * y.im;  // conj(x) y
+        gi += x.re * y.im - x.im * y.re;
+    }
+    __shared__ double sh[4];
+    a = block_sum(a);
+    if (threadIdx.x == 0) sh[0] = a;
+    b = block_sum(b);
+    if (threadIdx.x == 0) sh[1] = b;
+    gr = block_sum(gr);
+    if (threadIdx.x == 0) sh[2] = gr;
+    gi = block_sum(gi);
+    if (threadIdx.x == 0) sh[3] = gi;
+    __syncthreads();
+    a = sh[0]; b = sh[1]; gr = sh[2]; gi = sh[3];
+    const double g = sqrt(gr * gr + gi * gi);
+    if (a == 0.0 || b == 0.0 || g == 0.0) return;
+    const double off = g / sqrt(a * b);
+    if (threadIdx.x == 0) atomicMax(max_off, (unsigned long long)__double_as_longlong(off));
+    if (off <= tol) return;
+    // make the pair's inner product real by the phase e^{-i phi} on column q, then rotate
+    const double er = gr / g, ei = -gi / g;  // e^{-i phi}
+    const double zeta = (b - a) / (2.0 * g);
+    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+    const c128 ph = mk<double>(er, ei);
+    for (int r = threadIdx.x; r < mb; r += blockDim.x) {
+        const c128 x = bp[r], y = ph * bq[r];
+        bp[r] = cscale(x, c) - cscale(y, s);
+        bq[r] = cscale(x, s) + cscale(y, c);
+    }
+    if (J) {
+        c128* jp = J + (int64_t)p * kk;
+        c128* jq = J + (int64_t)q * kk;
+        for (int r = threadIdx.x; r < kk; r += blockDim.x) {
+            const c128 x = jp[r], y = ph * jq[r];
+            jp[r] = cscale(x, c) - cscale(y, s);
+            jq[r] = cscale(x, s) + cscale(y, c);
+        }
+    }
+    if (threadIdx.x == 0) atomicAdd(rotations, 1);
+}
+}  // namespace
+
+int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out) {
+    if (sweeps_out) *sweeps_out = 0;
+    if (k < 2) return RSRR_OK;
+    const int npad = k + (k & 1);
+    const double tol = sqrt((double)mb) * 1.1102230246251565e-16;
+    unsigned long long* dmax = nullptr;
+    int* drot = nullptr;
+    RSRR_TRY(dalloc_n(&dmax, 1, s));
+    RSRR_TRY(dalloc_n(&drot, 1, s));
+    int sweep = 0;
+    int rc = RSRR_OK;
+    for (; sweep < max_sweeps; ++sweep) {
+        cudaMemsetAsync(dmax, 0, 8, s);
+        cudaMemsetAsync(drot, 0, 4, s);
+        for (int r = 0; r < npad - 1; ++r)
+            jacobi_round_kernel<<<npad / 2, 256, 0, s>>>(B, mb, k, npad, J, r, tol, dmax, drot);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { rc = set_error(RSRR_ECUDA, cudaGetErrorString(e)); break; }
+        int hrot = 0;
+        cudaMemcpyAsync(&hrot, drot, 4, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
+        if (hrot == 0) { ++sweep; break; }
+    }
+    dfree(dmax, s);
+    dfree(drot, s);
+    if (sweeps_out) *sweeps_out = sweep;
+    return rc;
+}
+
+}  // namespace rsrr

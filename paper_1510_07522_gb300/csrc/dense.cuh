@@ -1,0 +1,49 @@
+// Dense FP64 complex building blocks for the projection and reduced-solve stages.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsrr {
+
+enum { OP_N = 0, OP_T = 1, OP_C = 2 };
+
+// C = alpha op(A) op(B) + beta C for `batch` independent problems (strided).  With ksplit > 1
+// the K range is cut into slices whose products are added to C atomically (beta is applied
+// first by a separate pass).  op(A) is M x K, op(B) is K x N, all column-major.
+struct Zgemm {
+    int opA = OP_N, opB = OP_N;
+    int M = 0, N = 0, K = 0;
+    c128 alpha{1, 0}, beta{0, 0};
+    const c128* A = nullptr;
+    int64_t lda = 0, sA = 0;
+    const c128* B = nullptr;
+    int64_t ldb = 0, sB = 0;
+    c128* C = nullptr;
+    int64_t ldc = 0, sC = 0;
+    int batch = 1;
+    int ksplit = 0;  // 0 = choose
+};
+int zgemm(const Zgemm& g, cudaStream_t s);
+
+// Device-wide barrier for cooperative kernels.  Every wait is bounded: after the spin limit
+// the barrier records a timeout in *err and returns false, and the kernel returns.
+struct GridBar {
+    unsigned* count;
+    unsigned* gen;
+    int* err;
+};
+__device__ bool grid_sync(const GridBar& gb);
+
+// One-sided (Hestenes) Jacobi on the k columns of B (mb x k, ld mb), accumulating the
+// rotations into J (k x k, ld k, initialised to I by the caller when wanted; may be null).
+// On return the columns of B are mutually orthogonal to working accuracy.
+int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out);
+
+// Column 2-norms of B (mb x k) into out[k] (device).
+void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s);
+
+// Frobenius norm squared of the block rows [r0, r1) x cols [c0, c1) of A (ld lda), added
+// atomically to *out (device, caller zeroes it).
+void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, double* out, cudaStream_t s);
+
+}  // namespace rsrr

@@ -1,0 +1,237 @@
+// Host-side parts of the RSRR library: error state, the scalar functions f_i(z) of
+// T(z) = sum_i f_i(z) A_i (Eq. eq-Z-expr), contour nodes, and the band-reducing ordering.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+
+#include "internal.h"
+
+namespace rsrr {
+
+// ---- error state -----------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+const char* last_error() { return g_last_error.c_str(); }
+
+// ---- stream-ordered allocation -----------------------------------------------------------
+int dalloc(void** p, size_t bytes, cudaStream_t s) {
+    static thread_local int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        configured_device = dev;
+    }
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(RSRR_ENOMEM, "device allocation of " + std::to_string(bytes) +
+                                          " bytes failed: " + cudaGetErrorString(e));
+    }
+    return RSRR_OK;
+}
+
+void dfree(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---- scalar functions ----------------------------------------------------------------------
+int check_fn(const rsrr_fn& f) {
+    if (f.kind < RSRR_F_CONST || f.kind > RSRR_F_RATIONAL)
+        return set_error(RSRR_EINVAL, "unknown function kind " + std::to_string(f.kind));
+    for (double v : f.p)
+        if (!std::isfinite(v)) return set_error(RSRR_ENONFINITE, "non-finite function parameter");
+    if (f.kind == RSRR_F_ISQRT_SHIFT && f.p[1] != 0.0 && f.p[1] != 1.0)
+        return set_error(RSRR_EINVAL, "sqrt branch flag must be 0 or 1");
+    return RSRR_OK;
+}
+
+void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv) {
+    const zd I(0.0, 1.0);
+    switch (f.kind) {
+        case RSRR_F_CONST: *val = 1.0; *deriv = 0.0; break;
+        case RSRR_F_Z: *val = z; *deriv = 1.0; break;
+        case RSRR_F_Z2: *val = z * z; *deriv = 2.0 * z; break;
+        case RSRR_F_ISQRT_SHIFT:
+            if (f.p[1] == 0.0) {  // i sqrt(z - s), principal root
+                zd r = std::sqrt(z - f.p[0]);
+                *val = I * r;
+                *deriv = 0.5 * I / r;
+            } else {              // continued branch: i sqrt(z - s) := -sqrt(s - z)
+                zd r = std::sqrt(f.p[0] - z);
+                *val = -r;
+                *deriv = 0.5 / r;
+            }
+            break;
+        case RSRR_F_EXP_DELAY: {
+            zd e = std::exp(-f.p[0] * z);
+            *val = e;
+            *deriv = -f.p[0] * e;
+            break;
+        }
+        case RSRR_F_RATIONAL: {
+            zd d = z + f.p[1];
+            *val = f.p[0] * z / d;
+            *deriv = f.p[0] * f.p[1] / (d * d);
+            break;
+        }
+        default: *val = 0.0; *deriv = 0.0;
+    }
+}
+
+void contour_nodes(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* dphi) {
+    z->resize(N);
+    if (dphi) dphi->resize(N);
+    const double pi = 3.14159265358979323846;
+    for (int j = 0; j < N; ++j) {
+        double t = 2.0 * pi * (j + 0.5) / N;
+        (*z)[j] = zd(C.gamma_re + C.a * std::cos(t), C.gamma_im + C.b * std::sin(t));
+        if (dphi) (*dphi)[j] = zd(-C.a * std::sin(t), C.b * std::cos(t));
+    }
+}
+
+// ---- ordering --------------------------------------------------------------------------------
+void band_of(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* iperm,
+             int64_t* kl, int64_t* ku) {
+    int64_t l = 0, u = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        int64_t rn = iperm ? iperm[r] : r;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            int64_t cn = iperm ? iperm[colind[k]] : colind[k];
+            l = std::max(l, rn - cn);
+            u = std::max(u, cn - rn);
+        }
+    }
+    *kl = l;
+    *ku = u;
+}
+
+// Reverse Cuthill-McKee on the symmetrised pattern; each connected component starts from a
+// pseudo-peripheral node found by repeated breadth-first searches (George-Liu).
+static void rcm(int64_t n, const std::vector<int64_t>& adjp, const std::vector<int32_t>& adj,
+                std::vector<int32_t>* order) {
+    std::vector<int32_t> deg(n);
+    for (int64_t v = 0; v < n; ++v) deg[v] = (int32_t)(adjp[v + 1] - adjp[v]);
+    std::vector<char> done(n, 0);
+    std::vector<int32_t> level(n, -1);
+    order->clear();
+    order->reserve(n);
+    auto bfs_last_level = [&](int32_t s, int32_t* ecc, std::vector<int32_t>* last) {
+        std::vector<int32_t> touched{s};
+        level[s] = 0;
+        size_t head = 0;
+        int32_t maxl = 0;
+        while (head < touched.size()) {
+            int32_t v = touched[head++];
+            for (int64_t k = adjp[v]; k < adjp[v + 1]; ++k) {
+                int32_t w = adj[k];
+                if (level[w] < 0 && !done[w]) {
+                    level[w] = level[v] + 1;
+                    maxl = std::max(maxl, level[w]);
+                    touched.push_back(w);
+                }
+            }
+        }
+        last->clear();
+        for (int32_t v : touched)
+            if (level[v] == maxl) last->push_back(v);
+        for (int32_t v : touched) level[v] = -1;
+        *ecc = maxl;
+    };
+    for (int64_t s0 = 0; s0 < n; ++s0) {
+        if (done[s0]) continue;
+        int32_t s = (int32_t)s0, ecc = 0;
+        std::vector<int32_t> last;
+        bfs_last_level(s, &ecc, &last);
+        for (int it = 0; it < 8; ++it) {
+            int32_t best = last[0];
+            for (int32_t v : last)
+                if (deg[v] < deg[best]) best = v;
+            int32_t ecc2;
+            std::vector<int32_t> last2;
+            bfs_last_level(best, &ecc2, &last2);
+            if (ecc2 <= ecc) break;
+            s = best;
+            ecc = ecc2;
+            last.swap(last2);
+        }
+        // Cuthill-McKee from s
+        size_t head = order->size();
+        order->push_back(s);
+        done[s] = 1;
+        std::vector<int32_t> nb;
+        while (head < order->size()) {
+            int32_t v = (*order)[head++];
+            nb.clear();
+            for (int64_t k = adjp[v]; k < adjp[v + 1]; ++k)
+                if (!done[adj[k]]) { nb.push_back(adj[k]); done[adj[k]] = 1; }
+            std::stable_sort(nb.begin(), nb.end(),
+                             [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+            order->insert(order->end(), nb.begin(), nb.end());
+        }
+    }
+    std::reverse(order->begin(), order->end());
+}
+
+void choose_ordering(int64_t n, const int64_t* rowptr, const int32_t* colind, bool force_natural,
+                     Ordering* out) {
+    int64_t kl0, ku0;
+    band_of(n, rowptr, colind, nullptr, &kl0, &ku0);
+    out->perm.resize(n);
+    out->iperm.resize(n);
+    std::iota(out->perm.begin(), out->perm.end(), 0);
+    std::iota(out->iperm.begin(), out->iperm.end(), 0);
+    out->kl = kl0;
+    out->ku = ku0;
+    out->natural = true;
+    if (force_natural || n <= 2) return;
+    // symmetrised adjacency without the diagonal
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k)
+            if (colind[k] != r) { cnt[r + 1]++; cnt[colind[k] + 1]++; }
+    for (int64_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+    std::vector<int32_t> adj(cnt[n]);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k)
+            if (colind[k] != r) { adj[fill[r]++] = colind[k]; adj[fill[colind[k]]++] = (int32_t)r; }
+    std::vector<int64_t> adjp(n + 1);
+    std::vector<int32_t> adju;
+    adju.reserve(adj.size());
+    adjp[0] = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        std::sort(adj.begin() + cnt[v], adj.begin() + cnt[v + 1]);
+        auto e = std::unique(adj.begin() + cnt[v], adj.begin() + cnt[v + 1]);
+        adju.insert(adju.end(), adj.begin() + cnt[v], e);
+        adjp[v + 1] = (int64_t)adju.size();
+    }
+    std::vector<int32_t> order;
+    rcm(n, adjp, adju, &order);
+    std::vector<int32_t> iperm(n);
+    for (int64_t i = 0; i < n; ++i) iperm[order[i]] = (int32_t)i;
+    int64_t kl1, ku1;
+    band_of(n, rowptr, colind, iperm.data(), &kl1, &ku1);
+    if (kl1 + ku1 < kl0 + ku0) {
+        out->perm = order;
+        out->iperm = iperm;
+        out->kl = kl1;
+        out->ku = ku1;
+        out->natural = false;
+    }
+}
+
+}  // namespace rsrr

@@ -1,0 +1,82 @@
+// Internal declarations of the RSRR library: the handle, host-side ordering and
+// coefficient evaluation, and the launch wrappers of each device stage.
+#pragma once
+
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rsrr {
+
+using zd = std::complex<double>;
+
+// ---- host: scalar functions f_i and their derivatives (Eq. eq-Z-expr, Eq. eq-ncs) -----
+int check_fn(const rsrr_fn& f);
+void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv);
+
+// ---- host: contour nodes (Eq. eq-contour, Eq. eq-Ap-num) --------------------------------
+void contour_nodes(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* dphi);
+
+// ---- host: band-reducing ordering ---------------------------------------------------------
+struct Ordering {
+    std::vector<int32_t> perm;   // perm[new] = old
+    std::vector<int32_t> iperm;  // iperm[old] = new
+    int64_t kl = 0, ku = 0;
+    bool natural = true;
+};
+void band_of(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* iperm,
+             int64_t* kl, int64_t* ku);
+void choose_ordering(int64_t n, const int64_t* rowptr, const int32_t* colind, bool force_natural,
+                     Ordering* out);
+
+// ---- device stage launchers ----------------------------------------------------------------
+struct SampleWork;  // defined in sample.cu
+
+}  // namespace rsrr
+
+struct rsrr_nep_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // problem (permuted ordering on the device)
+    int64_t n = 0, nnz = 0;
+    int32_t J = 0;
+    std::vector<rsrr_fn> fns;
+    rsrr::Ordering ord;
+    int64_t* d_rowptr = nullptr;   // [n+1]
+    int32_t* d_colind = nullptr;   // [nnz]
+    int32_t* d_rowidx = nullptr;   // [nnz] row of each entry
+    rsrr::c128* d_vals = nullptr;  // [J][nnz]
+    int32_t* d_perm = nullptr;     // [n] perm[new] = old
+    std::vector<double> normA;     // ||A_i||_F
+
+    // sampling state
+    int32_t N = 0, L = 0, precision = 0;
+    rsrr_contour C{};
+    double tol = 0;
+    int32_t refine_sweeps = 0;
+    double max_eta = 0;
+    bool sampled = false;
+    rsrr::c128* d_U = nullptr;     // [L][n] permuted probing matrix
+    int32_t U_L = 0;
+    rsrr::c128* d_S = nullptr;     // [N*L][n] S_hat (permuted rows)
+    double* d_eta = nullptr;       // [N*L]
+    size_t S_cols_cap = 0;
+
+    // projection state
+    bool projected = false;
+    int32_t kS = -1;
+    rsrr::c128* d_Q = nullptr;     // [kS][n] orthonormal basis S (permuted rows)
+    rsrr::c128* d_P = nullptr;     // [J][kS][kS]
+    std::vector<double> sigma;     // singular values of S_hat
+
+    // reduced solve state
+    int32_t nbar = -1, n_winding = 0, n_gap = -1;
+    std::complex<double> winding{0, 0};
+    std::vector<double> sigma_H;
+
+    double ms_sample = 0, ms_project = 0, ms_solve = 0;
+    int64_t device_bytes = 0;
+};

@@ -1,0 +1,382 @@
+// rsrr_sample: Algorithm 2 Steps 1-2 (Eq. eq-hatS) on the device.
+//
+// For every sampling point z_j of the contour:
+//   assemble T(z_j) = sum_i f_i(z_j) A_i into band storage        (Eq. eq-Z-expr)
+//   factor T(z_j) = P L U (band LU, partial pivoting)           (band.cu)
+//   X_j = U^{-1} L^{-1} P U_probe                                (band.cu)
+//   FP64 residual R = U_probe - T(z_j) X_j from the CSR values, normwise backward error
+//   eta = ||r|| / (||T||_1 ||x|| + ||u||) per column; in complex64 mode, refinement sweeps
+//   X_j += (LU)^{-1} R until eta <= tol.
+// All points of a chunk run concurrently (one CTA per point); chunks are sized so the
+// factors fit in free device memory.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "band.cuh"
+#include "internal.h"
+
+namespace rsrr {
+
+namespace {
+
+// T values of each point on the CSR pattern (FP64) and the band image (precision R).
+template <typename R>
+__global__ void assemble_kernel(const c128* __restrict__ vals, int J, int64_t nnz,
+                                const int32_t* __restrict__ rowidx, const int32_t* __restrict__ colind,
+                                const c128* __restrict__ F, int j0, int kv, int ldab,
+                                c128* __restrict__ tvals, cplx<R>* __restrict__ ab, int64_t ab_stride) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pt = blockIdx.y;
+    if (k >= nnz) return;
+    const c128* f = F + (int64_t)(j0 + pt) * J;
+    c128 v = czero<double>();
+    for (int i = 0; i < J; ++i) cfma(v, f[i], vals[(int64_t)i * nnz + k]);
+    tvals[(int64_t)pt * nnz + k] = v;
+    if (ab) {
+        const int r = rowidx[k], c = colind[k];
+        ab[pt * ab_stride + (int64_t)(kv + r - c) + (int64_t)c * ldab] = ccast<R>(v);
+    }
+}
+
+// ||T(z_j)||_1: column sums of |T_rc| (atomics), then the maximum.
+__global__ void colsum_kernel(const c128* __restrict__ tvals, int64_t nnz, const int32_t* __restrict__ colind,
+                              int64_t n, double* __restrict__ colsum) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pt = blockIdx.y;
+    if (k >= nnz) return;
+    const c128 v = tvals[(int64_t)pt * nnz + k];
+    atomicAdd(&colsum[(int64_t)pt * n + colind[k]], sqrt(cnorm2(v)));
+}
+
+__global__ void max_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+    const int pt = blockIdx.x;
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, x[(int64_t)pt * n + i]);
+    __shared__ double red[32];
+    for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+        if (threadIdx.x == 0) out[pt] = m;
+    }
+}
+
+// B_j = U (converted to precision R) for every point of the chunk.
+template <typename R>
+__global__ void broadcast_rhs_kernel(const c128* __restrict__ U, int64_t nl, cplx<R>* __restrict__ B) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nl) return;
+    B[(int64_t)blockIdx.y * nl + k] = ccast<R>(U[k]);
+}
+
+// X = B (first solve) or X += B (refinement), X in FP64.
+template <typename R>
+__global__ void accumulate_kernel(c128* __restrict__ X, const cplx<R>* __restrict__ B, int64_t nl,
+                                  int add, const int32_t* __restrict__ active) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pt = blockIdx.y;
+    if (k >= nl || (active && !active[pt])) return;
+    const c128 b = ccast<double>(B[(int64_t)pt * nl + k]);
+    c128& x = X[(int64_t)pt * nl + k];
+    x = add ? x + b : b;
+}
+
+// R = U - T X in FP64 (CSR rows, one thread per row, all L columns); R goes to B in
+// precision R; per-column ||r||^2 and ||x||^2 accumulate in rn2 / xn2.
+template <typename R>
+__global__ void residual_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                const c128* __restrict__ tvals, int64_t nnz, int64_t n, int L,
+                                const c128* __restrict__ U, const c128* __restrict__ X,
+                                cplx<R>* __restrict__ B, double* __restrict__ rn2, double* __restrict__ xn2,
+                                const int32_t* __restrict__ active) {
+    const int pt = blockIdx.y;
+    if (active && !active[pt]) return;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = r < n;
+    const c128* tv = tvals + (int64_t)pt * nnz;
+    const c128* Xp = X + (int64_t)pt * n * L;
+    cplx<R>* Bp = B + (int64_t)pt * n * L;
+    const int64_t k0 = valid ? rowptr[r] : 0, k1 = valid ? rowptr[r + 1] : 0;
+    for (int l = 0; l < L; ++l) {
+        double sr = 0.0, sx = 0.0;
+        if (valid) {
+            c128 acc = U[r + (int64_t)l * n];
+            for (int64_t k = k0; k < k1; ++k) cfms(acc, tv[k], Xp[colind[k] + (int64_t)l * n]);
+            if (B) Bp[r + (int64_t)l * n] = ccast<R>(acc);
+            sr = cnorm2(acc);
+            sx = cnorm2(Xp[r + (int64_t)l * n]);
+        }
+        for (int off = 16; off; off >>= 1) {
+            sr += __shfl_down_sync(0xffffffffu, sr, off);
+            sx += __shfl_down_sync(0xffffffffu, sx, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&rn2[(int64_t)pt * L + l], sr);
+            atomicAdd(&xn2[(int64_t)pt * L + l], sx);
+        }
+    }
+}
+
+// eta per column.  A point stays active (gets another refinement sweep) while some column is
+// above tol and its worst eta fell at least twofold in the last sweep; a point above tol that
+// stopped improving is counted as stagnated.  counters: [0] active, [1] non-finite, [2] stagnated.
+__global__ void eta_kernel(const double* __restrict__ rn2, const double* __restrict__ xn2,
+                           const double* __restrict__ un2, const double* __restrict__ normT, int npts, int L,
+                           double tol, double* __restrict__ eta, int32_t* __restrict__ active,
+                           double* __restrict__ prev_max, int32_t* __restrict__ counters, int first) {
+    const int pt = blockIdx.x;
+    if (!first && !active[pt]) return;  // residual not recomputed for this point
+    double mx = 0.0;
+    int nonfinite = 0;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const double e = sqrt(rn2[pt * L + l]) / (normT[pt] * sqrt(xn2[pt * L + l]) + sqrt(un2[l]));
+        eta[(int64_t)pt * L + l] = e;
+        if (!isfinite(e)) nonfinite = 1;
+        mx = fmax(mx, e);
+    }
+    for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    nonfinite = __any_sync(0xffffffffu, nonfinite);
+    if (threadIdx.x == 0) {
+        if (nonfinite) atomicOr(&counters[1], 1);
+        int act = 0;
+        if (!(mx <= tol)) {
+            if (first || mx < 0.5 * prev_max[pt]) act = 1;
+            else atomicAdd(&counters[2], 1);
+        }
+        prev_max[pt] = mx;
+        active[pt] = act;
+        if (act) atomicAdd(&counters[0], 1);
+    }
+}
+
+__global__ void column_norm2_kernel(const c128* __restrict__ U, int64_t n, double* __restrict__ out) {
+    const int l = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += cnorm2(U[i + (int64_t)l * n]);
+    __shared__ double red[32];
+    for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) out[l] = s;
+    }
+}
+
+__global__ void gather_rows_kernel(const c128* __restrict__ src, const int32_t* __restrict__ perm, int64_t n,
+                                   int cols, c128* __restrict__ dst) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * cols) return;
+    const int64_t r = k % n, c = k / n;
+    dst[k] = src[perm[r] + c * n];
+}
+
+int pick_dims(int64_t n, int64_t kl, int64_t ku, bool c64, BandDims* d) {
+    if (kl > 1024 || ku > 1024) return set_error(RSRR_EUNSUPPORTED, "band too wide for the band kernels");
+    d->n = (int)n;
+    d->kl = (int)kl;
+    d->ku = (int)ku;
+    d->kv = d->kl + d->ku;
+    d->ldab = 2 * d->kl + d->ku + 1;
+    const size_t es = c64 ? sizeof(c64) : sizeof(c128);
+    const size_t limit = 200 * 1024;
+    for (int nb : {32, 16, 8}) {
+        d->nb = nb;
+        d->ldp = (int)ceil_div(nb + d->kl, 32) * 32;
+        size_t s = (size_t)d->ldp * nb * es + (size_t)d->ldp * 4 + 16 * 32 * 4 * es;
+        if (s <= limit) break;
+        if (nb == 8) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory panels");
+    }
+    for (int nbb : {32, 16, 8}) {
+        d->nbb = nbb;
+        d->ldb = (int)ceil_div(nbb + d->kv, 32) * 32;
+        size_t s = (size_t)d->ldb * nbb * es + 8 * 32 * 4 * es;
+        if (s <= limit) break;
+        if (nbb == 8) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
+    }
+    d->npanels = (int)ceil_div(n, d->nb);
+    return RSRR_OK;
+}
+
+template <typename R>
+int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
+    cudaStream_t st = h->stream;
+    const int64_t n = h->n, nnz = h->nnz;
+    const int N = h->N, L = h->L, J = h->J;
+    BandDims d;
+    RSRR_TRY(pick_dims(n, h->ord.kl, h->ord.ku, sizeof(R) == 4, &d));
+    const int64_t nl = n * L;
+    // per-point footprint
+    const size_t es = sizeof(cplx<R>);
+    const size_t ab_b = (size_t)d.ldab * n * es;
+    const size_t lp_b = (size_t)d.npanels * d.ldp * d.nb * es;
+    const size_t perm_b = (size_t)d.npanels * d.ldp * 4;
+    const size_t per_pt = ab_b + lp_b + perm_b + (size_t)n * 4 + (size_t)nl * es + (size_t)nnz * 16 +
+                          (size_t)n * 8 + 256;
+    size_t free_b = 0, total_b = 0;
+    RSRR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = (size_t)(0.8 * (double)free_b);
+    int chunk = (int)std::min<int64_t>(N, std::max<int64_t>(1, budget / per_pt));
+    if ((size_t)chunk * per_pt > budget) return set_error(RSRR_ENOMEM, "one sampling point does not fit in device memory");
+
+    c128* dF = nullptr;
+    RSRR_TRY(dalloc_n(&dF, F.size(), st));
+    RSRR_CUDA(cudaMemcpyAsync(dF, F.data(), F.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
+    cplx<R>*ab = nullptr, *lp = nullptr, *B = nullptr;
+    int32_t *perm = nullptr, *ipiv = nullptr, *info = nullptr, *active = nullptr, *counters = nullptr;
+    c128* tvals = nullptr;
+    double *colsum = nullptr, *normT = nullptr, *rn2 = nullptr, *xn2 = nullptr, *un2 = nullptr,
+           *prev_max = nullptr;
+    int rc = RSRR_OK;
+    auto cleanup = [&]() {
+        dfree(dF, st); dfree(ab, st); dfree(lp, st); dfree(B, st); dfree(perm, st); dfree(ipiv, st);
+        dfree(info, st); dfree(active, st); dfree(counters, st); dfree(tvals, st); dfree(colsum, st);
+        dfree(normT, st); dfree(rn2, st); dfree(xn2, st); dfree(un2, st); dfree(prev_max, st);
+    };
+#define TRYC(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); return rc; } } while (0)
+#define CUDAC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); return set_error(RSRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
+    TRYC(dalloc(reinterpret_cast<void**>(&ab), ab_b * chunk, st));
+    TRYC(dalloc(reinterpret_cast<void**>(&lp), lp_b * chunk, st));
+    TRYC(dalloc_n(&B, (size_t)nl * chunk, st));
+    TRYC(dalloc_n(&perm, (size_t)d.npanels * d.ldp * chunk, st));
+    TRYC(dalloc_n(&ipiv, (size_t)n * chunk, st));
+    TRYC(dalloc_n(&info, (size_t)chunk, st));
+    TRYC(dalloc_n(&active, (size_t)chunk, st));
+    TRYC(dalloc_n(&counters, 4, st));
+    TRYC(dalloc_n(&prev_max, (size_t)chunk, st));
+    TRYC(dalloc_n(&tvals, (size_t)nnz * chunk, st));
+    TRYC(dalloc_n(&colsum, (size_t)n * chunk, st));
+    TRYC(dalloc_n(&normT, (size_t)chunk, st));
+    TRYC(dalloc_n(&rn2, (size_t)L * chunk, st));
+    TRYC(dalloc_n(&xn2, (size_t)L * chunk, st));
+    TRYC(dalloc_n(&un2, (size_t)L, st));
+    column_norm2_kernel<<<L, 256, 0, st>>>(h->d_U, n, un2);
+
+    int max_sweeps = 0;
+    bool singular = false, nonfinite = false, notconv = false;
+    for (int j0 = 0; j0 < N; j0 += chunk) {
+        const int np = std::min(chunk, N - j0);
+        c128* X = h->d_S + (int64_t)j0 * nl;
+        double* eta = h->d_eta + (int64_t)j0 * L;
+        CUDAC(cudaMemsetAsync(ab, 0, ab_b * np, st));
+        {
+            dim3 g((unsigned)ceil_div(nnz, 256), np);
+            assemble_kernel<R><<<g, 256, 0, st>>>(h->d_vals, J, nnz, h->d_rowidx, h->d_colind, dF, j0, d.kv,
+                                                  d.ldab, tvals, ab, (int64_t)(ab_b / es));
+            CUDAC(cudaGetLastError());
+            CUDAC(cudaMemsetAsync(colsum, 0, (size_t)n * np * 8, st));
+            colsum_kernel<<<g, 256, 0, st>>>(tvals, nnz, h->d_colind, n, colsum);
+            max_kernel<<<np, 256, 0, st>>>(colsum, n, normT);
+        }
+        FactorArgs<R> fa{d, ab, (int64_t)(ab_b / es), lp, (int64_t)(lp_b / es), perm,
+                         (int64_t)d.npanels * d.ldp, ipiv, info};
+        TRYC(launch_factor<R>(fa, np, st));
+        std::vector<int32_t> hinfo(np);
+        CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
+        CUDAC(cudaStreamSynchronize(st));
+        for (int k = 0; k < np; ++k)
+            if (hinfo[k]) singular = true;
+        if (singular) break;
+        SolveArgs<R> sa{d, ab, (int64_t)(ab_b / es), lp, (int64_t)(lp_b / es), perm,
+                        (int64_t)d.npanels * d.ldp, B, nl, L, nullptr};
+        {
+            dim3 g((unsigned)ceil_div(nl, 256), np);
+            broadcast_rhs_kernel<R><<<g, 256, 0, st>>>(h->d_U, nl, B);
+        }
+        TRYC(launch_fwd<R>(sa, np, st));
+        TRYC(launch_bwd<R>(sa, np, st));
+        {
+            dim3 g((unsigned)ceil_div(nl, 256), np);
+            accumulate_kernel<R><<<g, 256, 0, st>>>(X, B, nl, 0, nullptr);
+        }
+        int sweeps = 0;
+        for (;;) {
+            CUDAC(cudaMemsetAsync(rn2, 0, (size_t)L * np * 8, st));
+            CUDAC(cudaMemsetAsync(xn2, 0, (size_t)L * np * 8, st));
+            CUDAC(cudaMemsetAsync(counters, 0, 16, st));
+            dim3 g((unsigned)ceil_div(n, 128), np);
+            residual_kernel<R><<<g, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, nnz, n, L, h->d_U, X, B, rn2, xn2,
+                                                  sweeps == 0 ? nullptr : active);
+            eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, eta, active, prev_max,
+                                          counters, sweeps == 0 ? 1 : 0);
+            int32_t hc[4];
+            CUDAC(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, st));
+            CUDAC(cudaStreamSynchronize(st));
+            if (hc[1]) { nonfinite = true; break; }
+            if (hc[2]) { notconv = true; break; }
+            if (hc[0] == 0) break;
+            if (sweeps >= max_refine) { notconv = true; break; }
+            sa.active = active;
+            TRYC(launch_fwd<R>(sa, np, st));
+            TRYC(launch_bwd<R>(sa, np, st));
+            dim3 ga((unsigned)ceil_div(nl, 256), np);
+            accumulate_kernel<R><<<ga, 256, 0, st>>>(X, B, nl, 1, active);
+            sa.active = nullptr;
+            ++sweeps;
+        }
+        max_sweeps = std::max(max_sweeps, sweeps);
+        if (nonfinite || notconv) break;
+    }
+    CUDAC(cudaStreamSynchronize(st));
+    cleanup();
+#undef TRYC
+#undef CUDAC
+    h->refine_sweeps = max_sweeps;
+    if (singular) return set_error(RSRR_ESINGULAR, "zero pivot: a sampling point is an eigenvalue of T");
+    if (nonfinite) return set_error(RSRR_ENONFINITE, "non-finite backward error in a sample solve");
+    if (notconv) return set_error(RSRR_ENOTCONVERGED, "sample solves did not reach the backward-error tolerance");
+    return RSRR_OK;
+}
+
+}  // namespace
+
+int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
+    cudaStream_t st = h->stream;
+    const int64_t n = h->n;
+    const int N = h->N, L = h->L, J = h->J;
+    // coefficient table F[j][i] = f_i(z_j) (host FP64)
+    std::vector<zd> z;
+    contour_nodes(h->C, N, &z, nullptr);
+    std::vector<c128> F((size_t)N * J);
+    for (int j = 0; j < N; ++j)
+        for (int i = 0; i < J; ++i) {
+            zd v, dv;
+            eval_fn(h->fns[i], z[j], &v, &dv);
+            if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+                return set_error(RSRR_ENONFINITE, "f_i(z_j) is not finite (a sampling point at a pole?)");
+            F[(size_t)j * J + i] = fromstd(v);
+        }
+    // probing matrix: upload and permute to the band ordering
+    if (U_reim) {
+        if (h->d_U && h->U_L != L) { dfree(h->d_U, st); h->d_U = nullptr; }
+        if (!h->d_U) RSRR_TRY(dalloc_n(&h->d_U, (size_t)n * L, st));
+        c128* raw = nullptr;
+        RSRR_TRY(dalloc_n(&raw, (size_t)n * L, st));
+        RSRR_CUDA(cudaMemcpyAsync(raw, U_reim, (size_t)n * L * sizeof(c128), cudaMemcpyHostToDevice, st));
+        gather_rows_kernel<<<(unsigned)ceil_div(n * L, 256), 256, 0, st>>>(raw, h->d_perm, n, L, h->d_U);
+        RSRR_CUDA(cudaGetLastError());
+        dfree(raw, st);
+        h->U_L = L;
+    } else if (!h->d_U || h->U_L != L) {
+        return set_error(RSRR_EINVAL, "U_reim is NULL but no probing matrix with this L is resident");
+    }
+    const size_t cols = (size_t)N * L;
+    if (h->S_cols_cap < cols) {
+        dfree(h->d_S, st);
+        dfree(h->d_eta, st);
+        h->d_S = nullptr;
+        h->d_eta = nullptr;
+        h->S_cols_cap = 0;
+        RSRR_TRY(dalloc_n(&h->d_S, cols * n, st));
+        RSRR_TRY(dalloc_n(&h->d_eta, cols, st));
+        h->S_cols_cap = cols;
+    }
+    if (h->precision == RSRR_FP64) return sample_impl<double>(h, F, max_refine);
+    return sample_impl<float>(h, F, max_refine);
+}
+
+}  // namespace rsrr

@@ -93,7 +93,8 @@ def _union(mats: Sequence[sp.spmatrix]):
     n = mats[0].shape[0]
     pat = None
     for m in mats:
-        q = sp.csr_matrix((np.ones(m.nnz), m.nonzero()), shape=(n, n))
+        c = sp.coo_matrix(m)
+        q = sp.csr_matrix((np.ones(c.nnz), (c.row, c.col)), shape=(n, n))
         pat = q if pat is None else (pat + q)
     pat = pat.tocsr()
     pat.sort_indices()
