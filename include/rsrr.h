@@ -160,6 +160,13 @@ typedef struct {
     double max_eta;             /* max backward error over all N*L columns                 */
     double ms_sample, ms_project, ms_solve;  /* device time of the last calls              */
     int64_t device_bytes;       /* device memory held by the handle                        */
+    double ms_factor;           /* device time of the band-LU launches of the last rsrr_sample */
+    double ms_trsv;             /* device time of its triangular-solve launches              */
+    int32_t factor_launches;    /* band-LU launches in the last rsrr_sample                  */
+    int32_t trsv_launches;      /* forward + backward solve launches in the last rsrr_sample */
+    int32_t rows_kept;          /* rows of R kept by rsrr_project's early-stopped QR         */
+    int32_t jacobi_sweeps_project, jacobi_sweeps_solve;  /* sweeps of the two Jacobi SVDs  */
+    double ms_project_qr, ms_project_svd, ms_project_basis, ms_project_gemm;  /* rsrr_project parts */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);
@@ -175,6 +182,9 @@ int rsrr_get_basis(rsrr_nep h, double* out_reim);
 int rsrr_get_projected(rsrr_nep h, double* out_reim);
 /* The singular values of H, K*k_S of them, descending (after rsrr_solve). */
 int rsrr_get_hankel_sigma(rsrr_nep h, double* out);
+
+/* Number of CUDA kernels this library has launched in the process so far (all handles). */
+int64_t rsrr_kernel_launches(void);
 
 void rsrr_destroy(rsrr_nep h);
 const char* rsrr_last_error(void);

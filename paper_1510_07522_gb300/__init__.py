@@ -52,14 +52,20 @@ class rsrr_info(ctypes.Structure):
                 ("winding_re", ctypes.c_double), ("winding_im", ctypes.c_double),
                 ("max_eta", ctypes.c_double),
                 ("ms_sample", ctypes.c_double), ("ms_project", ctypes.c_double),
-                ("ms_solve", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("ms_solve", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("ms_factor", ctypes.c_double), ("ms_trsv", ctypes.c_double),
+                ("factor_launches", ctypes.c_int32), ("trsv_launches", ctypes.c_int32),
+                ("rows_kept", ctypes.c_int32), ("jacobi_sweeps_project", ctypes.c_int32),
+                ("jacobi_sweeps_solve", ctypes.c_int32),
+                ("ms_project_qr", ctypes.c_double), ("ms_project_svd", ctypes.c_double),
+                ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double)]
 
 
 _lib = None
 EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr_get_info",
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
-           "rsrr_version"]
+           "rsrr_version", "rsrr_kernel_launches"]
 
 
 def lib():
@@ -87,6 +93,7 @@ def lib():
         "rsrr_destroy": ([P], None),
         "rsrr_last_error": ([], ctypes.c_char_p),
         "rsrr_version": ([], ctypes.c_char_p),
+        "rsrr_kernel_launches": ([], ctypes.c_int64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

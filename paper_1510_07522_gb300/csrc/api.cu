@@ -46,6 +46,7 @@ extern "C" {
 
 const char* rsrr_last_error(void) { return rsrr::last_error(); }
 const char* rsrr_version(void) { return "rsrr-gb300 0.1 (sm_103a)"; }
+int64_t rsrr_kernel_launches(void) { return rsrr::launches_total(); }
 
 int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
                     const double* vals_reim, const rsrr_fn* f, uint32_t flags, void* stream,
@@ -223,6 +224,17 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->ms_project = h->ms_project;
     o->ms_solve = h->ms_solve;
     o->device_bytes = h->device_bytes;
+    o->ms_factor = h->ms_factor;
+    o->ms_trsv = h->ms_trsv;
+    o->factor_launches = h->factor_launches;
+    o->trsv_launches = h->trsv_launches;
+    o->rows_kept = h->rows_kept;
+    o->jacobi_sweeps_project = h->jacobi_sweeps_project;
+    o->jacobi_sweeps_solve = h->jacobi_sweeps_solve;
+    o->ms_project_qr = h->ms_project_parts[0];
+    o->ms_project_svd = h->ms_project_parts[1];
+    o->ms_project_basis = h->ms_project_parts[2];
+    o->ms_project_gemm = h->ms_project_parts[3];
     return RSRR_OK;
 }
 

@@ -338,7 +338,7 @@ template <typename R>
 int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = factor_smem_bytes<R>(a.d);
     RSRR_CUDA(cudaFuncSetAttribute(band_factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    band_factor_kernel<R><<<npts, kLuThreads, sm, s>>>(a);
+    { band_factor_kernel<R><<<npts, kLuThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
@@ -347,7 +347,7 @@ template <typename R>
 int launch_fwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = fwd_smem_bytes<R>(a.d);
     RSRR_CUDA(cudaFuncSetAttribute(band_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    band_fwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a);
+    { band_fwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
@@ -356,7 +356,7 @@ template <typename R>
 int launch_bwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = bwd_smem_bytes<R>(a.d);
     RSRR_CUDA(cudaFuncSetAttribute(band_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    band_bwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a);
+    { band_bwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }

@@ -78,6 +78,9 @@ size_t bwd_smem_bytes(const BandDims& d) {
            (size_t)(kSolveThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 
+// Panel sizes for a band of (kl, ku) that fit the shared-memory budget.
+int pick_dims(int64_t n, int64_t kl, int64_t ku, bool c64, BandDims* d);
+
 template <typename R>
 int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s);
 template <typename R>

@@ -111,6 +111,10 @@ const char* last_error();
         if (r_ != RSRR_OK) return r_; \
     } while (0)
 
+// Process-wide count of kernels this library has launched (diagnostics, benchmarks).
+void note_launch(int count = 1);
+int64_t launches_total();
+
 // Stream-ordered device allocation from the current device's default pool.  The pool keeps
 // freed blocks (release threshold raised once per device), so repeated handles reuse memory.
 int dalloc(void** p, size_t bytes, cudaStream_t s);

@@ -1,5 +1,6 @@
 // Dense FP64 complex kernels: tiled ZGEMM, bounded grid barrier, one-sided Jacobi.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "dense.cuh"
@@ -107,7 +108,7 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
     const int tm = (int)ceil_div(g.M, BM), tn = (int)ceil_div(g.N, BN);
     if (g.K <= 0) {
         dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
-        scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta);
+        { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
         RSRR_CUDA(cudaGetLastError());
         return RSRR_OK;
     }
@@ -121,55 +122,21 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
     g.ksplit = (int)ceil_div(g.K, kchunk);
     if (g.ksplit > 1) {
         dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
-        scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta);
+        { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
     }
     dim3 grid(tm, tn, g.batch * g.ksplit);
-#define ZG(a, b) zgemm_kernel<a, b><<<grid, 256, 0, s>>>(g, kchunk)
-    if (g.opA == OP_N && g.opB == OP_N) ZG(OP_N, OP_N);
-    else if (g.opA == OP_N && g.opB == OP_T) ZG(OP_N, OP_T);
-    else if (g.opA == OP_N && g.opB == OP_C) ZG(OP_N, OP_C);
-    else if (g.opA == OP_T && g.opB == OP_N) ZG(OP_T, OP_N);
-    else if (g.opA == OP_C && g.opB == OP_N) ZG(OP_C, OP_N);
-    else if (g.opA == OP_C && g.opB == OP_C) ZG(OP_C, OP_C);
-    else if (g.opA == OP_T && g.opB == OP_T) ZG(OP_T, OP_T);
+#define ZG(a, b) { zgemm_kernel<a, b><<<grid, 256, 0, s>>>(g, kchunk); note_launch(); }
+    if (g.opA == OP_N && g.opB == OP_N) ZG(OP_N, OP_N)
+    else if (g.opA == OP_N && g.opB == OP_T) ZG(OP_N, OP_T)
+    else if (g.opA == OP_N && g.opB == OP_C) ZG(OP_N, OP_C)
+    else if (g.opA == OP_T && g.opB == OP_N) ZG(OP_T, OP_N)
+    else if (g.opA == OP_C && g.opB == OP_N) ZG(OP_C, OP_N)
+    else if (g.opA == OP_C && g.opB == OP_C) ZG(OP_C, OP_C)
+    else if (g.opA == OP_T && g.opB == OP_T) ZG(OP_T, OP_T)
     else return set_error(RSRR_EINVAL, "zgemm: unsupported op combination");
 #undef ZG
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
-}
-
-// ---------------------------------------------------------------------------------------------
-// Grid barrier (cooperative launches only: all CTAs are co-resident).
-// ---------------------------------------------------------------------------------------------
-__device__ bool grid_sync(const GridBar& gb) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vgen = gb.gen;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(gb.count, 1u);
-        int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(gb.count, 0u);
-            __threadfence();
-            atomicAdd(gb.gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g) {
-                if (++spins > (1LL << 24)) {  // ~seconds: give up, report, return
-                    atomicExch(gb.err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok && (*(volatile int*)gb.err == 0);
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -213,106 +180,140 @@ __global__ void blocknorm_kernel(const c128* A, int64_t lda, int r0, int r1, int
 }  // namespace
 
 void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s) {
-    if (k > 0) colnorm_kernel<<<k, 256, 0, s>>>(B, mb, ld, out);
+    if (k > 0) { colnorm_kernel<<<k, 256, 0, s>>>(B, mb, ld, out); note_launch(); }
 }
 
 void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, double* out, cudaStream_t s) {
     if (r1 <= r0 || c1 <= c0) return;
     const int64_t total = (int64_t)(r1 - r0) * (c1 - c0);
     const int blocks = (int)std::min<int64_t>(4 * 152, ceil_div(total, 256));
-    blocknorm_kernel<<<blocks, 256, 0, s>>>(A, lda, r0, r1, c0, c1, out);
+    { blocknorm_kernel<<<blocks, 256, 0, s>>>(A, lda, r0, r1, c0, c1, out); note_launch(); }
 }
 
 // ---------------------------------------------------------------------------------------------
-// One-sided Jacobi: one CTA per column pair of a round-robin round.
+// One-sided Jacobi.  A sweep is one cooperative kernel: round-robin rounds separated by grid
+// barriers, one warp per column pair.  A pair is rotated when its inner product is above
+// tol relative to the column norms and both columns are above an absolute floor: columns
+// below the floor are rounding noise, and rotating them against anything changes no
+// column above the floor by more than the floor itself.
 // ---------------------------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ int rr_pos(int k, int r, int n) {  // player at seat k in round r
     return k == 0 ? 0 : ((k - 1 + r) % (n - 1)) + 1;
 }
 
-__global__ void __launch_bounds__(256) jacobi_round_kernel(c128* B, int mb, int kk, int npad, c128* J,
-                                                          int round, double tol,
-                                                          unsigned long long* max_off, int* rotations) {
-    const int i = blockIdx.x;
-    int p = rr_pos(i, round, npad), q = rr_pos(npad - 1 - i, round, npad);
-    if (p > q) { const int t = p; p = q; q = t; }
-    if (q >= kk) return;  // padding seat
-    c128* bp = B + (int64_t)p * mb;
-    c128* bq = B + (int64_t)q * mb;
-    double a = 0.0, b = 0.0, gr = 0.0, gi = 0.0;
-    for (int r = threadIdx.x; r < mb; r += blockDim.x) {
-        const c128 x = bp[r], y = bq[r];
-        a += cnorm2(x);
-        b += cnorm2(y);
-        gr += x.re * y.re + x.im * y.im;  // conj(x) y
-        gi += x.re * y.im - x.im * y.re;
-    }
-    __shared__ double sh[4];
-    a = block_sum(a);
-    if (threadIdx.x == 0) sh[0] = a;
-    b = block_sum(b);
-    if (threadIdx.x == 0) sh[1] = b;
-    gr = block_sum(gr);
-    if (threadIdx.x == 0) sh[2] = gr;
-    gi = block_sum(gi);
-    if (threadIdx.x == 0) sh[3] = gi;
-    __syncthreads();
-    a = sh[0]; b = sh[1]; gr = sh[2]; gi = sh[3];
-    const double g = sqrt(gr * gr + gi * gi);
-    if (a == 0.0 || b == 0.0 || g == 0.0) return;
-    const double off = g / sqrt(a * b);
-    if (threadIdx.x == 0) atomicMax(max_off, (unsigned long long)__double_as_longlong(off));
-    if (off <= tol) return;
-    // make the pair's inner product real by the phase e^{-i phi} on column q, then rotate
-    const double er = gr / g, ei = -gi / g;  // e^{-i phi}
-    const double zeta = (b - a) / (2.0 * g);
-    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-    const c128 ph = mk<double>(er, ei);
-    for (int r = threadIdx.x; r < mb; r += blockDim.x) {
-        const c128 x = bp[r], y = ph * bq[r];
-        bp[r] = cscale(x, c) - cscale(y, s);
-        bq[r] = cscale(x, s) + cscale(y, c);
-    }
-    if (J) {
-        c128* jp = J + (int64_t)p * kk;
-        c128* jq = J + (int64_t)q * kk;
-        for (int r = threadIdx.x; r < kk; r += blockDim.x) {
-            const c128 x = jp[r], y = ph * jq[r];
-            jp[r] = cscale(x, c) - cscale(y, s);
-            jq[r] = cscale(x, s) + cscale(y, c);
+struct JacobiArgs {
+    c128* B;
+    int mb, kk, npad;
+    c128* J;
+    double tol, floor2;
+    unsigned long long* max_off;
+    int* rotations;
+    GridBar gb;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int round = 0; round < a.npad - 1; ++round) {
+        for (int i = gw; i < a.npad / 2; i += nw) {
+            int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
+            if (p > q) { const int t = p; p = q; q = t; }
+            if (q >= a.kk) continue;
+            c128* bp = a.B + (int64_t)p * a.mb;
+            c128* bq = a.B + (int64_t)q * a.mb;
+            double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+            for (int r = lane; r < a.mb; r += 32) {
+                const c128 x = bp[r], y = bq[r];
+                al += cnorm2(x);
+                be += cnorm2(y);
+                gr += x.re * y.re + x.im * y.im;  // conj(x) y
+                gi += x.re * y.im - x.im * y.re;
+            }
+            al = warp_sum(al);
+            be = warp_sum(be);
+            gr = warp_sum(gr);
+            gi = warp_sum(gi);
+            const double g = sqrt(gr * gr + gi * gi);
+            if (fmin(al, be) <= a.floor2 || g == 0.0) continue;
+            const double off = g / sqrt(al * be);
+            if (lane == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
+            if (off <= a.tol) continue;
+            const c128 ph = mk<double>(gr / g, -gi / g);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
+            const double zeta = (be - al) / (2.0 * g);
+            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+            for (int r = lane; r < a.mb; r += 32) {
+                const c128 x = bp[r], y = ph * bq[r];
+                bp[r] = cscale(x, c) - cscale(y, s);
+                bq[r] = cscale(x, s) + cscale(y, c);
+            }
+            if (a.J) {
+                c128* jp = a.J + (int64_t)p * a.kk;
+                c128* jq = a.J + (int64_t)q * a.kk;
+                for (int r = lane; r < a.kk; r += 32) {
+                    const c128 x = jp[r], y = ph * jq[r];
+                    jp[r] = cscale(x, c) - cscale(y, s);
+                    jq[r] = cscale(x, s) + cscale(y, c);
+                }
+            }
+            if (lane == 0) atomicAdd(a.rotations, 1);
         }
+        if (!grid_sync(a.gb)) return;
     }
-    if (threadIdx.x == 0) atomicAdd(rotations, 1);
 }
 }  // namespace
 
-int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out) {
+int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
+                         double abs_floor) {
     if (sweeps_out) *sweeps_out = 0;
     if (k < 2) return RSRR_OK;
     const int npad = k + (k & 1);
-    const double tol = sqrt((double)mb) * 1.1102230246251565e-16;
+    int dev = 0, nsm = 0, occ = 0;
+    RSRR_CUDA(cudaGetDevice(&dev));
+    RSRR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, 256, 0));
+    if (occ < 1) return set_error(RSRR_ECUDA, "jacobi kernel cannot be resident");
+    const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 2), ceil_div(npad / 2, 8));
     unsigned long long* dmax = nullptr;
     int* drot = nullptr;
+    unsigned* bar = nullptr;
     RSRR_TRY(dalloc_n(&dmax, 1, s));
     RSRR_TRY(dalloc_n(&drot, 1, s));
-    int sweep = 0;
-    int rc = RSRR_OK;
+    RSRR_TRY(dalloc_n(&bar, 4, s));
+    cudaMemsetAsync(bar, 0, 16, s);
+    JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor,
+                  dmax, drot, GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2)}};
+    int sweep = 0, rc = RSRR_OK;
     for (; sweep < max_sweeps; ++sweep) {
         cudaMemsetAsync(dmax, 0, 8, s);
         cudaMemsetAsync(drot, 0, 4, s);
-        for (int r = 0; r < npad - 1; ++r)
-            jacobi_round_kernel<<<npad / 2, 256, 0, s>>>(B, mb, k, npad, J, r, tol, dmax, drot);
-        cudaError_t e = cudaGetLastError();
+        void* args[] = {&ja};
+        cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_sweep_kernel, G, 256, args, 0, s);
+        note_launch();
         if (e != cudaSuccess) { rc = set_error(RSRR_ECUDA, cudaGetErrorString(e)); break; }
-        int hrot = 0;
+        int hrot = 0, herr = 0;
+        unsigned long long hmax = 0;
         cudaMemcpyAsync(&hrot, drot, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&herr, bar + 2, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
-        if (hrot == 0) { ++sweep; break; }
+        if (herr) { rc = set_error(RSRR_ETIMEOUT, "grid barrier gave up in the Jacobi sweep"); break; }
+        double off;
+        std::memcpy(&off, &hmax, 8);
+        // converged: no rotation left, or every pair above the floor orthogonal to 1e-12 (the
+        // remaining effect on the singular values is of second order in that number)
+        if (hrot == 0 || off <= 1e-12) { ++sweep; break; }
     }
     dfree(dmax, s);
     dfree(drot, s);
+    dfree(bar, s);
     if (sweeps_out) *sweeps_out = sweep;
     return rc;
 }

@@ -25,6 +25,22 @@ struct Zgemm {
 };
 int zgemm(const Zgemm& g, cudaStream_t s);
 
+// Sum of v over a CTA (blockDim a multiple of 32, <= 1024); every thread gets the result.
+__device__ __forceinline__ double block_sum_all(double v) {
+    __shared__ double red_[33];
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red_[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double r = (threadIdx.x < (blockDim.x >> 5)) ? red_[threadIdx.x] : 0.0;
+        for (int off = 16; off; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+        if (threadIdx.x == 0) red_[32] = r;
+    }
+    __syncthreads();
+    return red_[32];
+}
+
 // Device-wide barrier for cooperative kernels.  Every wait is bounded: after the spin limit
 // the barrier records a timeout in *err and returns false, and the kernel returns.
 struct GridBar {
@@ -32,12 +48,44 @@ struct GridBar {
     unsigned* gen;
     int* err;
 };
-__device__ bool grid_sync(const GridBar& gb);
+__device__ __forceinline__ bool grid_sync(const GridBar& gb) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = gb.gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(gb.count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(gb.count, 0u);
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > (1LL << 24)) {  // ~seconds: give up, report, return
+                    atomicExch(gb.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int*)gb.err == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 
 // One-sided (Hestenes) Jacobi on the k columns of B (mb x k, ld mb), accumulating the
 // rotations into J (k x k, ld k, initialised to I by the caller when wanted; may be null).
-// On return the columns of B are mutually orthogonal to working accuracy.
-int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out);
+// On return the columns of B whose norms exceed abs_floor are mutually orthogonal to
+// working accuracy; columns below abs_floor are left as they are.
+int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
+                         double abs_floor);
 
 // Column 2-norms of B (mb x k) into out[k] (device).
 void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s);

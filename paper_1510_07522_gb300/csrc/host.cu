@@ -1,6 +1,7 @@
 // Host-side parts of the RSRR library: error state, the scalar functions f_i(z) of
 // T(z) = sum_i f_i(z) A_i (Eq. eq-Z-expr), contour nodes, and the band-reducing ordering.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -18,6 +19,11 @@ int set_error(int code, const std::string& msg) {
     return code;
 }
 const char* last_error() { return g_last_error.c_str(); }
+
+// ---- launch counter ------------------------------------------------------------------------
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---- stream-ordered allocation -----------------------------------------------------------
 int dalloc(void** p, size_t bytes, cudaStream_t s) {

@@ -78,5 +78,9 @@ struct rsrr_nep_s {
     std::vector<double> sigma_H;
 
     double ms_sample = 0, ms_project = 0, ms_solve = 0;
+    double ms_factor = 0, ms_trsv = 0;
+    int32_t factor_launches = 0, trsv_launches = 0;
+    int32_t rows_kept = 0, jacobi_sweeps_project = 0, jacobi_sweeps_solve = 0;
+    double ms_project_parts[4] = {0, 0, 0, 0};
     int64_t device_bytes = 0;
 };

@@ -1,0 +1,443 @@
+// rsrr_project: Algorithm 2 Step 3 (truncated SVD of S_hat, keep sigma_k > delta sigma_1)
+// and Eq. eq-Zs-expr (P_i = S^H A_i S), all in FP64 on the device.
+//
+//   1. Householder QR of S_hat (n x m, m = N L) in panels of 32 columns.  The point blocks are
+//      taken in bit-reversed order (0, N/2, N/4, 3N/4, ...) so early columns sample the whole
+//      contour.  Each panel is factored by one cooperative kernel (two grid barriers per
+//      column); the trailing matrix is updated with the compact WY form by three ZGEMMs.
+//      After every panel the Frobenius norm of the remaining trailing block is measured; once
+//      it is below 1% of delta * max_j ||s_j|| (<= 1% of delta sigma_1) the remaining rows of
+//      R are dropped: by Weyl's inequality they move no singular value by more than that, so
+//      the truncation only differs from the full SVD for sigma within 1% of the threshold.
+//   2. One-sided Jacobi on R_keep^H (m x k') with the rotations accumulated: R_keep = J Sigma W^H,
+//      so the left singular vectors of R_keep are the columns of J.
+//   3. S = Q [J(:, 1:k_S); 0] by applying the panels' reflectors in reverse.
+//   4. P_i = S^H (A_i S): CSR SpMM, then ZGEMM.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "dense.cuh"
+#include "internal.h"
+
+namespace rsrr {
+
+namespace {
+
+constexpr int kPB = 32;  // panel width
+
+struct PanelArgs {
+    c128* A;
+    int64_t lda;
+    int n, kb, bw;
+    c128* tau;
+    c128* T;       // bw x bw, column-major
+    double* part;  // [G]
+    c128* alpha;   // [1]
+    c128* part2;   // [G][kPB]
+    c128* part3;   // [G][kPB*kPB]
+    c128* Y;       // [kPB*kPB]
+    GridBar gb;
+};
+
+__global__ void __launch_bounds__(256) hqr_panel_kernel(PanelArgs a) {
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = 8;
+    const int rows = a.n - a.kb;
+    const int per = (rows + G - 1) / G;
+    const int r0 = min(a.n, a.kb + g * per), r1 = min(a.n, r0 + per);
+    __shared__ c128 s_w[kPB];
+    __shared__ c128 s_tau, s_scal;
+    __shared__ int s_ident;
+    const int cend = a.kb + a.bw;
+    for (int j = 0; j < a.bw; ++j) {
+        const int c = a.kb + j, d = c;
+        c128* col = a.A + (int64_t)c * a.lda;
+        // phase 1: partial squared norm below the diagonal, and alpha
+        double ss = 0.0;
+        for (int i = max(r0, d + 1) + tid; i < r1; i += 256) ss += cnorm2(col[i]);
+        ss = block_sum_all(ss);
+        if (tid == 0) {
+            a.part[g] = ss;
+            if (d >= r0 && d < r1) *a.alpha = col[d];
+        }
+        if (!grid_sync(a.gb)) return;
+        // phase 2: reflector (LAPACK zlarfg convention: real beta), scale own rows, partial dots
+        double xs = 0.0;
+        for (int t = tid; t < G; t += 256) xs += a.part[t];
+        xs = block_sum_all(xs);
+        if (tid == 0) {
+            const c128 al = *a.alpha;
+            if (xs == 0.0 && al.im == 0.0) {
+                s_ident = 1;
+                s_tau = czero<double>();
+                s_scal = mk<double>(1.0, 0.0);
+            } else {
+                const double beta = -copysign(sqrt(al.re * al.re + al.im * al.im + xs), al.re);
+                s_ident = 0;
+                s_tau = mk<double>((beta - al.re) / beta, -al.im / beta);
+                s_scal = crecip(mk<double>(al.re - beta, al.im));
+                if (d >= r0 && d < r1) col[d] = mk<double>(beta, 0.0);
+            }
+            if (g == 0) a.tau[c] = s_tau;
+        }
+        __syncthreads();
+        const bool ident = s_ident != 0;
+        if (!ident) {
+            const c128 sc = s_scal;
+            for (int i = max(r0, d + 1) + tid; i < r1; i += 256) col[i] = col[i] * sc;
+        }
+        __syncthreads();
+        for (int cc = c + 1 + warp; cc < cend; cc += NW) {
+            const c128* x = a.A + (int64_t)cc * a.lda;
+            c128 w = czero<double>();
+            for (int i = max(r0, d) + lane; i < r1; i += 32) {
+                const c128 v = (i == d) ? mk<double>(1.0, 0.0) : col[i];
+                cfma_conj(w, v, x[i]);
+            }
+            for (int off = 16; off; off >>= 1) {
+                w.re += __shfl_down_sync(0xffffffffu, w.re, off);
+                w.im += __shfl_down_sync(0xffffffffu, w.im, off);
+            }
+            if (lane == 0) a.part2[(int64_t)g * kPB + (cc - a.kb)] = w;
+        }
+        if (!grid_sync(a.gb)) return;
+        // phase 3: A[i, cc] -= conj(tau) v_i w_cc on own rows
+        for (int cc = c + 1 + warp; cc < cend; cc += NW) {
+            c128 w = czero<double>();
+            for (int t = lane; t < G; t += 32) w = w + a.part2[(int64_t)t * kPB + (cc - a.kb)];
+            for (int off = 16; off; off >>= 1) {
+                w.re += __shfl_down_sync(0xffffffffu, w.re, off);
+                w.im += __shfl_down_sync(0xffffffffu, w.im, off);
+            }
+            if (lane == 0) s_w[cc - a.kb] = w;
+        }
+        __syncthreads();
+        if (!ident) {
+            const c128 ct = cconj(s_tau);
+            const int nc = cend - (c + 1);
+            const int lo = max(r0, d);
+            const int nr = max(0, r1 - lo);
+            for (int idx = tid; idx < nr * nc; idx += 256) {
+                const int i = lo + idx % nr, cc = c + 1 + idx / nr;
+                const c128 v = (i == d) ? mk<double>(1.0, 0.0) : col[i];
+                cfms(a.A[i + (int64_t)cc * a.lda], ct * v, s_w[cc - a.kb]);
+            }
+        }
+        __syncthreads();
+    }
+    // compact WY factor: T upper triangular with I - V T V^H = H_0 ... H_{bw-1}
+    const int bw = a.bw;
+    for (int e = tid; e < bw * bw; e += 256) {
+        const int p = e % bw, q = e / bw;
+        c128 s = czero<double>();
+        if (p < q) {
+            for (int i = max(r0, a.kb + q); i < r1; ++i) {
+                const c128 vp = (i == a.kb + p) ? mk<double>(1.0, 0.0) : a.A[i + (int64_t)(a.kb + p) * a.lda];
+                const c128 vq = (i == a.kb + q) ? mk<double>(1.0, 0.0) : a.A[i + (int64_t)(a.kb + q) * a.lda];
+                cfma_conj(s, vp, vq);
+            }
+        }
+        a.part3[(int64_t)g * kPB * kPB + e] = s;
+    }
+    if (!grid_sync(a.gb)) return;
+    if (tid == 0) {
+        for (int e = g; e < bw * bw; e += G) {
+            c128 s = czero<double>();
+            for (int t = 0; t < G; ++t) s = s + a.part3[(int64_t)t * kPB * kPB + e];
+            a.Y[e] = s;
+        }
+    }
+    if (!grid_sync(a.gb)) return;
+    if (g == 0) {
+        for (int q = 0; q < bw; ++q) {
+            const c128 tq = a.tau[a.kb + q];
+            if (tid < q) {
+                c128 s = czero<double>();
+                for (int l = tid; l < q; ++l) cfma(s, a.T[tid + l * bw], a.Y[l + q * bw]);
+                a.T[tid + q * bw] = czero<double>() - tq * s;
+            }
+            if (tid == 0) a.T[q + q * bw] = tq;
+            for (int i = q + 1 + tid; i < bw; i += 256) a.T[i + q * bw] = czero<double>();
+            __syncthreads();
+        }
+    }
+}
+
+// explicit V block: rows kb..n-1 of the panel, unit diagonal, zeros above
+__global__ void extract_v_kernel(const c128* A, int64_t lda, int n, int kb, int bw, c128* V, int64_t ldv) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t rows = n - kb;
+    if (idx >= rows * bw) return;
+    const int i = (int)(idx % rows), t = (int)(idx / rows);
+    const int gi = kb + i, col = kb + t;
+    c128 v = czero<double>();
+    if (gi == col) v = mk<double>(1.0, 0.0);
+    else if (gi > col) v = A[gi + (int64_t)col * lda];
+    V[i + (int64_t)t * ldv] = v;
+}
+
+// B = R_keep^H: B[c, r] = conj(A[r, c]) for r <= c (rows r < kk), zero below the diagonal of R
+__global__ void rkeep_h_kernel(const c128* A, int64_t lda, int m, int kk, c128* B) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * kk) return;
+    const int c = (int)(idx % m), r = (int)(idx / m);
+    B[c + (int64_t)r * m] = (r <= c) ? cconj(A[r + (int64_t)c * lda]) : czero<double>();
+}
+
+__global__ void gather_blocks_kernel(const c128* S, int64_t n, int L, const int* order, int m, c128* A) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * m) return;
+    const int64_t r = idx % n, c = idx / n;
+    const int blk = (int)(c / L), l = (int)(c % L);
+    A[idx] = S[r + ((int64_t)order[blk] * L + l) * n];
+}
+
+__global__ void init_y_kernel(const c128* J, int kk, const int* cols, int kS, int64_t n, c128* Y) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * kS) return;
+    const int64_t r = idx % n, c = idx / n;
+    Y[idx] = (r < kk) ? J[r + (int64_t)cols[c] * kk] : czero<double>();
+}
+
+__global__ void identity_kernel(c128* J, int k) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    J[idx] = (idx % k == idx / k) ? mk<double>(1.0, 0.0) : czero<double>();
+}
+
+// Y_i = A_i X for every term (CSR of the union pattern with the term's values)
+__global__ void spmm_terms_kernel(const int64_t* rowptr, const int32_t* colind, const c128* vals, int64_t nnz,
+                                  int64_t n, const c128* X, int k, c128* Y) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int term = blockIdx.y;
+    if (idx >= n * k) return;
+    const int64_t r = idx % n, c = idx / n;
+    const c128* v = vals + (int64_t)term * nnz;
+    c128 acc = czero<double>();
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) cfma(acc, v[e], X[colind[e] + c * n]);
+    Y[(int64_t)term * n * k + idx] = acc;
+}
+
+std::vector<int> bit_reversed_order(int N) {
+    int bits = 0;
+    while ((1 << bits) < N) ++bits;
+    std::vector<int> idx(N);
+    std::iota(idx.begin(), idx.end(), 0);
+    auto rev = [&](int x) {
+        int r = 0;
+        for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+        return r;
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return rev(a) < rev(b); });
+    return idx;
+}
+
+}  // namespace
+
+namespace {
+struct PhaseClock {  // device time between successive marks on one stream
+    cudaStream_t s;
+    cudaEvent_t e[8];
+    int k = 0;
+    explicit PhaseClock(cudaStream_t st) : s(st) { for (auto& x : e) cudaEventCreate(&x); }
+    ~PhaseClock() { for (auto& x : e) cudaEventDestroy(x); }
+    void mark() { if (k < 8) cudaEventRecord(e[k++], s); }
+    double ms(int i) {  // between mark i and i+1
+        if (i + 1 >= k) return 0.0;
+        cudaEventSynchronize(e[i + 1]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[i], e[i + 1]);
+        return t;
+    }
+};
+}  // namespace
+
+int project_run(rsrr_nep h, double delta) {
+    cudaStream_t st = h->stream;
+    PhaseClock pc(st);
+    pc.mark();
+    const int64_t n = h->n;
+    const int N = h->N, L = h->L, J = h->J;
+    const int m = N * L;
+    const int kmax = (int)std::min<int64_t>(n, m);
+    dfree(h->d_Q, st);
+    dfree(h->d_P, st);
+    h->d_Q = nullptr;
+    h->d_P = nullptr;
+
+    c128 *A = nullptr, *V = nullptr, *W = nullptr, *W2 = nullptr, *tau = nullptr, *Tall = nullptr,
+         *alpha = nullptr, *part2 = nullptr, *part3 = nullptr, *Yb = nullptr, *B = nullptr, *Jm = nullptr,
+         *Ybuf = nullptr, *Z = nullptr, *Z2 = nullptr, *AY = nullptr;
+    double *part = nullptr, *dnorm = nullptr, *colnrm = nullptr;
+    unsigned* bar = nullptr;
+    int *order_d = nullptr, *cols_d = nullptr;
+    int rc = RSRR_OK;
+    auto cleanup = [&]() {
+        for (void* p : {(void*)A, (void*)V, (void*)W, (void*)W2, (void*)tau, (void*)Tall, (void*)alpha,
+                        (void*)part2, (void*)part3, (void*)Yb, (void*)B, (void*)Jm, (void*)Ybuf, (void*)Z,
+                        (void*)Z2, (void*)AY, (void*)part, (void*)dnorm, (void*)colnrm, (void*)bar,
+                        (void*)order_d, (void*)cols_d})
+            dfree(p, st);
+    };
+#define TRYC(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); return rc; } } while (0)
+#define CUDAC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); return set_error(RSRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
+
+    int dev = 0, nsm = 0, occ = 0;
+    CUDAC(cudaGetDevice(&dev));
+    CUDAC(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDAC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hqr_panel_kernel, 256, 0));
+    if (occ < 1) { cleanup(); return set_error(RSRR_ECUDA, "panel kernel cannot be resident"); }
+    const int G = nsm;
+
+    // ---- work copy of S_hat with point blocks in bit-reversed order --------------------------
+    std::vector<int> order = bit_reversed_order(N);
+    TRYC(dalloc_n(&A, (size_t)n * m, st));
+    TRYC(dalloc_n(&order_d, (size_t)N, st));
+    CUDAC(cudaMemcpyAsync(order_d, order.data(), N * 4, cudaMemcpyHostToDevice, st));
+    { gather_blocks_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(h->d_S, n, L, order_d, m, A); note_launch(); }
+    // reference size for the stopping rule: max column norm of S_hat (<= sigma_1)
+    TRYC(dalloc_n(&colnrm, (size_t)m, st));
+    column_norms(A, (int)n, m, n, colnrm, st);
+    std::vector<double> cn(m);
+    CUDAC(cudaMemcpyAsync(cn.data(), colnrm, m * 8, cudaMemcpyDeviceToHost, st));
+    CUDAC(cudaStreamSynchronize(st));
+    const double smax = *std::max_element(cn.begin(), cn.end());
+    if (!std::isfinite(smax)) { cleanup(); return set_error(RSRR_ENONFINITE, "non-finite sample matrix"); }
+    const double stop2 = std::pow(0.01 * delta * smax, 2);
+
+    // ---- Householder QR with early termination -----------------------------------------------
+    const int npan_max = (int)ceil_div(kmax, kPB);
+    TRYC(dalloc_n(&V, (size_t)n * kPB, st));
+    TRYC(dalloc_n(&W, (size_t)kPB * m, st));
+    TRYC(dalloc_n(&W2, (size_t)kPB * m, st));
+    TRYC(dalloc_n(&tau, (size_t)kmax, st));
+    TRYC(dalloc_n(&Tall, (size_t)npan_max * kPB * kPB, st));
+    TRYC(dalloc_n(&alpha, 1, st));
+    TRYC(dalloc_n(&part, (size_t)G, st));
+    TRYC(dalloc_n(&part2, (size_t)G * kPB, st));
+    TRYC(dalloc_n(&part3, (size_t)G * kPB * kPB, st));
+    TRYC(dalloc_n(&Yb, (size_t)kPB * kPB, st));
+    TRYC(dalloc_n(&bar, 4, st));
+    TRYC(dalloc_n(&dnorm, 1, st));
+    CUDAC(cudaMemsetAsync(bar, 0, 16, st));
+    int kk = 0;  // rows of R kept
+    int npan = 0;
+    for (int kb = 0; kb < kmax; kb += kPB) {
+        const int bw = std::min(kPB, kmax - kb);
+        PanelArgs pa{A, n, (int)n, kb, bw, tau, Tall + (int64_t)npan * kPB * kPB, part, alpha, part2, part3, Yb,
+                     GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2)}};
+        void* args[] = {&pa};
+        CUDAC(cudaLaunchCooperativeKernel((void*)hqr_panel_kernel, G, 256, args, 0, st));
+        note_launch();
+        ++npan;
+        kk = kb + bw;
+        const int mt = m - kk;  // trailing columns
+        if (mt > 0) {
+            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, V, n); note_launch(); }
+            Zgemm g1;
+            g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = mt; g1.K = (int)(n - kb);
+            g1.A = V; g1.lda = n; g1.B = A + kb + (int64_t)kk * n; g1.ldb = n; g1.C = W; g1.ldc = kPB;
+            TRYC(zgemm(g1, st));
+            Zgemm g2;
+            g2.opA = OP_C; g2.opB = OP_N; g2.M = bw; g2.N = mt; g2.K = bw;
+            g2.A = Tall + (int64_t)(npan - 1) * kPB * kPB; g2.lda = bw; g2.B = W; g2.ldb = kPB; g2.C = W2; g2.ldc = kPB;
+            TRYC(zgemm(g2, st));
+            Zgemm g3;
+            g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = mt; g3.K = bw;
+            g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
+            g3.A = V; g3.lda = n; g3.B = W2; g3.ldb = kPB; g3.C = A + kb + (int64_t)kk * n; g3.ldc = n; g3.ksplit = 1;
+            TRYC(zgemm(g3, st));
+        }
+        // trailing norm of the rows still to come
+        CUDAC(cudaMemsetAsync(dnorm, 0, 8, st));
+        block_norm2(A, n, kk, (int)n, kk, m, dnorm, st);
+        double tn2 = 0.0;
+        int berr[2] = {0, 0};
+        CUDAC(cudaMemcpyAsync(&tn2, dnorm, 8, cudaMemcpyDeviceToHost, st));
+        CUDAC(cudaMemcpyAsync(berr, bar + 2, 4, cudaMemcpyDeviceToHost, st));
+        CUDAC(cudaStreamSynchronize(st));
+        if (berr[0]) { cleanup(); return set_error(RSRR_ETIMEOUT, "grid barrier gave up in the panel kernel"); }
+        if (!std::isfinite(tn2)) { cleanup(); return set_error(RSRR_ENONFINITE, "non-finite QR"); }
+        if (tn2 <= stop2) break;
+    }
+
+    pc.mark();  // QR done
+    // ---- SVD of R_keep (kk x m) by one-sided Jacobi on its conjugate transpose ---------------
+    TRYC(dalloc_n(&B, (size_t)m * kk, st));
+    TRYC(dalloc_n(&Jm, (size_t)kk * kk, st));
+    { rkeep_h_kernel<<<(unsigned)ceil_div((int64_t)m * kk, 256), 256, 0, st>>>(A, n, m, kk, B); note_launch(); }
+    { identity_kernel<<<(unsigned)ceil_div((int64_t)kk * kk, 256), 256, 0, st>>>(Jm, kk); note_launch(); }
+    int sweeps = 0;
+    TRYC(jacobi_orthogonalize(B, m, kk, Jm, st, 40, &sweeps, 1e-2 * delta * smax));
+    h->jacobi_sweeps_project = sweeps;
+    h->rows_kept = kk;
+    dfree(colnrm, st);
+    colnrm = nullptr;
+    TRYC(dalloc_n(&colnrm, (size_t)kk, st));
+    column_norms(B, m, kk, m, colnrm, st);
+    std::vector<double> sv(kk);
+    CUDAC(cudaMemcpyAsync(sv.data(), colnrm, kk * 8, cudaMemcpyDeviceToHost, st));
+    CUDAC(cudaStreamSynchronize(st));
+    std::vector<int> idx(kk);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return sv[x] > sv[y]; });
+    h->sigma.assign((size_t)std::min<int64_t>(n, m), 0.0);
+    for (int i = 0; i < kk; ++i) h->sigma[i] = sv[idx[i]];
+    const double s1 = kk ? h->sigma[0] : 0.0;
+    int kS = 0;
+    while (kS < kk && h->sigma[kS] > delta * s1) ++kS;
+    if (s1 == 0.0) kS = 0;
+    h->kS = kS;
+
+    pc.mark();  // SVD done
+    // ---- S = Q [J(:, idx[:kS]); 0] ------------------------------------------------------------
+    if (kS > 0) {
+        TRYC(dalloc_n(&cols_d, (size_t)kS, st));
+        CUDAC(cudaMemcpyAsync(cols_d, idx.data(), kS * 4, cudaMemcpyHostToDevice, st));
+        TRYC(dalloc_n(&Ybuf, (size_t)n * kS, st));
+        { init_y_kernel<<<(unsigned)ceil_div(n * kS, 256), 256, 0, st>>>(Jm, kk, cols_d, kS, n, Ybuf); note_launch(); }
+        TRYC(dalloc_n(&Z, (size_t)kPB * kS, st));
+        TRYC(dalloc_n(&Z2, (size_t)kPB * kS, st));
+        for (int p = npan - 1; p >= 0; --p) {
+            const int kb = p * kPB, bw = std::min(kPB, kmax - kb);
+            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, V, n); note_launch(); }
+            Zgemm g1;
+            g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = kS; g1.K = (int)(n - kb);
+            g1.A = V; g1.lda = n; g1.B = Ybuf + kb; g1.ldb = n; g1.C = Z; g1.ldc = kPB;
+            TRYC(zgemm(g1, st));
+            Zgemm g2;
+            g2.opA = OP_N; g2.opB = OP_N; g2.M = bw; g2.N = kS; g2.K = bw;
+            g2.A = Tall + (int64_t)p * kPB * kPB; g2.lda = bw; g2.B = Z; g2.ldb = kPB; g2.C = Z2; g2.ldc = kPB;
+            TRYC(zgemm(g2, st));
+            Zgemm g3;
+            g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = kS; g3.K = bw;
+            g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
+            g3.A = V; g3.lda = n; g3.B = Z2; g3.ldb = kPB; g3.C = Ybuf + kb; g3.ldc = n; g3.ksplit = 1;
+            TRYC(zgemm(g3, st));
+        }
+        pc.mark();  // basis done
+        // ---- P_i = S^H (A_i S) ---------------------------------------------------------------
+        TRYC(dalloc_n(&AY, (size_t)J * n * kS, st));
+        dim3 gs((unsigned)ceil_div(n * kS, 256), J);
+        { spmm_terms_kernel<<<gs, 256, 0, st>>>(h->d_rowptr, h->d_colind, h->d_vals, h->nnz, n, Ybuf, kS, AY); note_launch(); }
+        TRYC(dalloc_n(&h->d_P, (size_t)J * kS * kS, st));
+        Zgemm gp;
+        gp.opA = OP_C; gp.opB = OP_N; gp.M = kS; gp.N = kS; gp.K = (int)n;
+        gp.A = Ybuf; gp.lda = n; gp.sA = 0; gp.B = AY; gp.ldb = n; gp.sB = n * kS;
+        gp.C = h->d_P; gp.ldc = kS; gp.sC = (int64_t)kS * kS; gp.batch = J;
+        TRYC(zgemm(gp, st));
+        h->d_Q = Ybuf;
+        Ybuf = nullptr;
+        pc.mark();  // projection done
+    }
+    CUDAC(cudaStreamSynchronize(st));
+    for (int i = 0; i < 4; ++i) h->ms_project_parts[i] = pc.ms(i);
+    cleanup();
+#undef TRYC
+#undef CUDAC
+    return RSRR_OK;
+}
+
+}  // namespace rsrr

@@ -175,32 +175,48 @@ __global__ void gather_rows_kernel(const c128* __restrict__ src, const int32_t* 
     dst[k] = src[perm[r] + c * n];
 }
 
+}  // namespace
+
 int pick_dims(int64_t n, int64_t kl, int64_t ku, bool c64, BandDims* d) {
-    if (kl > 1024 || ku > 1024) return set_error(RSRR_EUNSUPPORTED, "band too wide for the band kernels");
+    if (kl > 2048 || ku > 2048) return set_error(RSRR_EUNSUPPORTED, "band too wide for the band kernels");
     d->n = (int)n;
     d->kl = (int)kl;
     d->ku = (int)ku;
     d->kv = d->kl + d->ku;
     d->ldab = 2 * d->kl + d->ku + 1;
     const size_t es = c64 ? sizeof(c64) : sizeof(c128);
-    const size_t limit = 200 * 1024;
-    for (int nb : {32, 16, 8}) {
+    const size_t limit = 220 * 1024;
+    const int64_t ubw = std::min<int64_t>(d->kv, n - 1);  // U's bandwidth cannot exceed n - 1
+    for (int nb : {32, 16, 8, 4}) {
         d->nb = nb;
         d->ldp = (int)ceil_div(nb + d->kl, 32) * 32;
         size_t s = (size_t)d->ldp * nb * es + (size_t)d->ldp * 4 + 16 * 32 * 4 * es;
         if (s <= limit) break;
-        if (nb == 8) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory panels");
+        if (nb == 4) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory panels");
     }
-    for (int nbb : {32, 16, 8}) {
+    for (int nbb : {32, 16, 8, 4}) {
         d->nbb = nbb;
-        d->ldb = (int)ceil_div(nbb + d->kv, 32) * 32;
+        d->ldb = (int)ceil_div(nbb + ubw, 32) * 32;
         size_t s = (size_t)d->ldb * nbb * es + 8 * 32 * 4 * es;
         if (s <= limit) break;
-        if (nbb == 8) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
+        if (nbb == 4) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
     }
     d->npanels = (int)ceil_div(n, d->nb);
     return RSRR_OK;
 }
+
+namespace {
+
+// Event pair around a group of launches on the stream; elapsed time is read after the next
+// stream synchronisation.
+struct EvPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EvPair() { cudaEventCreate(&a); cudaEventCreate(&b); }
+    ~EvPair() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    void start(cudaStream_t s) { cudaEventRecord(a, s); }
+    void stop(cudaStream_t s) { cudaEventRecord(b, s); }
+    double ms() { float t = 0.f; cudaEventElapsedTime(&t, a, b); return t; }
+};
 
 template <typename R>
 int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
@@ -254,7 +270,10 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
     TRYC(dalloc_n(&rn2, (size_t)L * chunk, st));
     TRYC(dalloc_n(&xn2, (size_t)L * chunk, st));
     TRYC(dalloc_n(&un2, (size_t)L, st));
-    column_norm2_kernel<<<L, 256, 0, st>>>(h->d_U, n, un2);
+    h->ms_factor = h->ms_trsv = 0;
+    h->factor_launches = h->trsv_launches = 0;
+    EvPair evf, evs;
+    { column_norm2_kernel<<<L, 256, 0, st>>>(h->d_U, n, un2); note_launch(); }
 
     int max_sweeps = 0;
     bool singular = false, nonfinite = false, notconv = false;
@@ -265,19 +284,23 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         CUDAC(cudaMemsetAsync(ab, 0, ab_b * np, st));
         {
             dim3 g((unsigned)ceil_div(nnz, 256), np);
-            assemble_kernel<R><<<g, 256, 0, st>>>(h->d_vals, J, nnz, h->d_rowidx, h->d_colind, dF, j0, d.kv,
-                                                  d.ldab, tvals, ab, (int64_t)(ab_b / es));
+            { assemble_kernel<R><<<g, 256, 0, st>>>(h->d_vals, J, nnz, h->d_rowidx, h->d_colind, dF, j0, d.kv,
+                                                  d.ldab, tvals, ab, (int64_t)(ab_b / es)); note_launch(); }
             CUDAC(cudaGetLastError());
             CUDAC(cudaMemsetAsync(colsum, 0, (size_t)n * np * 8, st));
-            colsum_kernel<<<g, 256, 0, st>>>(tvals, nnz, h->d_colind, n, colsum);
-            max_kernel<<<np, 256, 0, st>>>(colsum, n, normT);
+            { colsum_kernel<<<g, 256, 0, st>>>(tvals, nnz, h->d_colind, n, colsum); note_launch(); }
+            { max_kernel<<<np, 256, 0, st>>>(colsum, n, normT); note_launch(); }
         }
         FactorArgs<R> fa{d, ab, (int64_t)(ab_b / es), lp, (int64_t)(lp_b / es), perm,
                          (int64_t)d.npanels * d.ldp, ipiv, info};
+        evf.start(st);
         TRYC(launch_factor<R>(fa, np, st));
+        evf.stop(st);
         std::vector<int32_t> hinfo(np);
         CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
         CUDAC(cudaStreamSynchronize(st));
+        h->ms_factor += evf.ms();
+        h->factor_launches += 1;
         for (int k = 0; k < np; ++k)
             if (hinfo[k]) singular = true;
         if (singular) break;
@@ -285,13 +308,17 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
                         (int64_t)d.npanels * d.ldp, B, nl, L, nullptr};
         {
             dim3 g((unsigned)ceil_div(nl, 256), np);
-            broadcast_rhs_kernel<R><<<g, 256, 0, st>>>(h->d_U, nl, B);
+            { broadcast_rhs_kernel<R><<<g, 256, 0, st>>>(h->d_U, nl, B); note_launch(); }
         }
+        evs.start(st);
         TRYC(launch_fwd<R>(sa, np, st));
         TRYC(launch_bwd<R>(sa, np, st));
+        evs.stop(st);
+        bool trsv_pending = true;
+        h->trsv_launches += 2;
         {
             dim3 g((unsigned)ceil_div(nl, 256), np);
-            accumulate_kernel<R><<<g, 256, 0, st>>>(X, B, nl, 0, nullptr);
+            { accumulate_kernel<R><<<g, 256, 0, st>>>(X, B, nl, 0, nullptr); note_launch(); }
         }
         int sweeps = 0;
         for (;;) {
@@ -299,22 +326,27 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             CUDAC(cudaMemsetAsync(xn2, 0, (size_t)L * np * 8, st));
             CUDAC(cudaMemsetAsync(counters, 0, 16, st));
             dim3 g((unsigned)ceil_div(n, 128), np);
-            residual_kernel<R><<<g, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, nnz, n, L, h->d_U, X, B, rn2, xn2,
-                                                  sweeps == 0 ? nullptr : active);
-            eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, eta, active, prev_max,
-                                          counters, sweeps == 0 ? 1 : 0);
+            { residual_kernel<R><<<g, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, nnz, n, L, h->d_U, X, B, rn2, xn2,
+                                                  sweeps == 0 ? nullptr : active); note_launch(); }
+            { eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, eta, active, prev_max,
+                                          counters, sweeps == 0 ? 1 : 0); note_launch(); }
             int32_t hc[4];
             CUDAC(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, st));
             CUDAC(cudaStreamSynchronize(st));
+            if (trsv_pending) { h->ms_trsv += evs.ms(); trsv_pending = false; }
             if (hc[1]) { nonfinite = true; break; }
             if (hc[2]) { notconv = true; break; }
             if (hc[0] == 0) break;
             if (sweeps >= max_refine) { notconv = true; break; }
             sa.active = active;
+            evs.start(st);
             TRYC(launch_fwd<R>(sa, np, st));
             TRYC(launch_bwd<R>(sa, np, st));
+            evs.stop(st);
+            trsv_pending = true;
+            h->trsv_launches += 2;
             dim3 ga((unsigned)ceil_div(nl, 256), np);
-            accumulate_kernel<R><<<ga, 256, 0, st>>>(X, B, nl, 1, active);
+            { accumulate_kernel<R><<<ga, 256, 0, st>>>(X, B, nl, 1, active); note_launch(); }
             sa.active = nullptr;
             ++sweeps;
         }
@@ -357,7 +389,7 @@ int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
         c128* raw = nullptr;
         RSRR_TRY(dalloc_n(&raw, (size_t)n * L, st));
         RSRR_CUDA(cudaMemcpyAsync(raw, U_reim, (size_t)n * L * sizeof(c128), cudaMemcpyHostToDevice, st));
-        gather_rows_kernel<<<(unsigned)ceil_div(n * L, 256), 256, 0, st>>>(raw, h->d_perm, n, L, h->d_U);
+        { gather_rows_kernel<<<(unsigned)ceil_div(n * L, 256), 256, 0, st>>>(raw, h->d_perm, n, L, h->d_U); note_launch(); }
         RSRR_CUDA(cudaGetLastError());
         dfree(raw, st);
         h->U_L = L;

@@ -1,0 +1,166 @@
+"""Parity of rsrr_project (Algorithm 2 Step 3, Eq. eq-Zs-expr) and rsrr_solve (Algorithm 1,
+Algorithm 2 Step 5) with the oracle, closed forms and the paper's printed counts.
+
+Bars: eigenvalues to relative 1e-9 (matched by minimum-cost assignment), the same count, and
+scaled residuals ||T(l) v|| / sum_i |f_i(l)| ||A_i||_F <= 1e-10 (FP64 floor, see design notes)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from gpu_util import match, open_nep
+
+pytestmark = pytest.mark.gpu
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1510_07522_gb300 as rs
+    return rs
+
+
+def gpu_rsrr(rs, prob, precision=None, tol=1e-12, N_S=500, K=2, delta=1e-14):
+    precision = rs.RSRR_FP64 if precision is None else precision
+    h = open_nep(rs, prob)
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, precision, tol, 12)
+    Shat = h.samples()
+    kS = h.project(delta)
+    S, P, sig = h.basis(), h.projected(), h.sigma()
+    lam, V, res = h.solve(N_S, K, 1e3, 4096, True)
+    info = h.info()
+    hs = h.hankel_sigma(K)
+    h.close()
+    return dict(Shat=Shat, kS=kS, S=S, P=P, sigma=sig, lam=lam, V=V, resid=res, info=info, sigma_H=hs)
+
+
+def scaled(prob, lam, raw):
+    F, _ = oracle.coefficients(prob.fns, lam)
+    nA = np.array([np.linalg.norm(prob.vals[i]) for i in range(prob.J)])
+    return raw / (np.abs(F) @ nA)
+
+
+def near_threshold(sigma, delta):
+    s = np.asarray(sigma)
+    return int(np.sum((s > 0.1 * delta * s[0]) & (s < 10 * delta * s[0])))
+
+
+def check_projection(rs, prob, g, delta=1e-14):
+    ref_S, ref_sig, ref_k = oracle.truncated_basis(g["Shat"], delta)
+    S = g["S"]
+    # S orthonormal, captures S_hat down to the truncation level, same rank up to near-ties
+    assert np.linalg.norm(S.conj().T @ S - np.eye(g["kS"])) < 1e-11
+    resid = np.linalg.norm(g["Shat"] - S @ (S.conj().T @ g["Shat"]), 2)
+    assert resid <= 20 * delta * ref_sig[0] + 1e-15 * np.linalg.norm(g["Shat"])
+    assert abs(g["kS"] - ref_k) <= near_threshold(ref_sig, delta)
+    top = ref_sig[ref_sig > 1e-6 * ref_sig[0]]
+    assert np.allclose(g["sigma"][:top.size], top, rtol=1e-9, atol=1e-13 * ref_sig[0])
+    # P_i = S^H A_i S against the oracle's projection of the same basis
+    assert np.allclose(g["P"], oracle.project(prob, S), rtol=0, atol=1e-11 * np.abs(g["P"]).max())
+
+
+CLOSED = ["config0_linear", "tiny_qep", "planted_sqrt", "planted_delay"]
+
+
+def exact_eigs(name, prob):
+    if name == "config0_linear":
+        h = 1.0 / 31
+        s = 4 / h ** 2 * np.sin(np.arange(1, 31) * np.pi * h / 2) ** 2
+        ev = (s[:, None] + s[None, :]).ravel()
+    elif name == "tiny_qep":
+        K, C, M = (prob.term(i).toarray() for i in range(3))
+        n = prob.n
+        A = np.block([[np.zeros((n, n)), np.eye(n)], [-K, -C]])
+        B = np.block([[np.eye(n), np.zeros((n, n))], [np.zeros((n, n)), M]])
+        ev = np.linalg.eigvals(np.linalg.solve(B, A))
+    elif name == "planted_sqrt":
+        d0, d1 = prob.meta["d0"], prob.meta["d1"]
+        ev = ((1j * d1 + np.sqrt(4 * d0 - d1 ** 2 + 0j)) / 2) ** 2
+    else:
+        from scipy.special import lambertw
+        a, b, tau = prob.meta["a"], prob.meta["b"], prob.meta["tau"]
+        ev = np.concatenate([a + lambertw(b * tau * np.exp(-a * tau), k) / tau for k in range(-3, 4)])
+    return ev[oracle.inside_contour(ev, prob.gamma, prob.a, prob.b)]
+
+
+@pytest.mark.parametrize("name", CLOSED)
+def test_eigenvalues_match_closed_form(rs, name):
+    prob = w.by_name(name)
+    K = 4 if name == "tiny_qep" else 2
+    g = gpu_rsrr(rs, prob, K=K)
+    ex = exact_eigs(name, prob)
+    assert g["lam"].size == ex.size > 0
+    assert match(g["lam"], ex) < 1e-9
+    assert scaled(prob, g["lam"], g["resid"]).max() < 1e-10
+    check_projection(rs, prob, g)
+
+
+@pytest.mark.parametrize("name,kw,NS,K", [
+    ("config0", dict(), 500, 2),
+    ("loaded_string", dict(n=GOLD["loaded_string"]["n"], N=GOLD["loaded_string"]["N"], L=1), 1000, 8),
+    ("acoustic_1d", dict(), 1000, 2),
+])
+def test_eigenvalues_match_oracle(rs, name, kw, NS, K):
+    prob = w.by_name(name, **kw)
+    ref = oracle.rsrr(prob, N_S=NS, K=K)
+    g = gpu_rsrr(rs, prob, N_S=NS, K=K)
+    assert g["lam"].size == ref["lam"].size
+    assert match(g["lam"], ref["lam"]) < 1e-9
+    assert scaled(prob, g["lam"], g["resid"]).max() < 1e-10
+    # eigenvectors: same residual level, and v_gpu spans the oracle's v per simple eigenvalue
+    for t in range(min(5, g["lam"].size)):
+        j = np.argmin(np.abs(ref["lam"] - g["lam"][t]))
+        c = abs(np.vdot(ref["V"][:, j], g["V"][:, t]))
+        assert c > 1 - 1e-6
+    check_projection(rs, prob, g)
+    if name == "loaded_string":
+        assert g["lam"].size == GOLD["loaded_string"]["count"]
+    if name == "acoustic_1d":
+        assert g["lam"].size == GOLD["acoustic_1d"]["count"]
+
+
+def test_mixed_precision_pipeline_matches_fp64(rs):
+    prob = w.config0()
+    g64 = gpu_rsrr(rs, prob)
+    gmx = gpu_rsrr(rs, prob, precision=rs.RSRR_C64_IR, tol=1e-14)
+    assert gmx["info"]["refine_sweeps"] >= 1
+    assert gmx["lam"].size == g64["lam"].size == 22
+    assert match(gmx["lam"], g64["lam"]) < 1e-9
+    assert scaled(prob, gmx["lam"], gmx["resid"]).max() < 1e-10
+
+
+def test_config1_contour_encloses_nothing(rs):
+    prob = w.config1(s=16, N=16, L=4)
+    g = gpu_rsrr(rs, prob, N_S=200)
+    assert g["lam"].size == 0
+    assert g["info"]["n_winding"] == 0
+
+
+def test_config1b_closed_form(rs):
+    prob = w.config1b(s=20, N=32, L=8)
+    exact = w.problems.damped_eigs(20, 400)
+    exact = np.concatenate([exact, exact.conj()])
+    exact = exact[oracle.inside_contour(exact, prob.gamma, prob.a, prob.b)]
+    g = gpu_rsrr(rs, prob, precision=rs.RSRR_C64_IR, tol=1e-14)
+    assert g["lam"].size == exact.size
+    assert match(g["lam"], exact) < 1e-9
+    assert scaled(prob, g["lam"], g["resid"]).max() < 1e-10
+
+
+def test_hankel_singular_values_match_oracle(rs):
+    prob = w.planted_sqrt()
+    g = gpu_rsrr(rs, prob)
+    ref = oracle.rsrr(prob)
+    P = g["P"]
+    lam, gg, diag = oracle.reduced_ss(P, prob.fns, prob.gamma, prob.a, prob.b, 500, 2, 1e3, return_diag=True)
+    sH = diag["sigma_H"]
+    top = sH > 1e-8 * sH[0]
+    assert np.allclose(g["sigma_H"][top], sH[top], rtol=1e-8)
+    assert g["info"]["n_winding"] == diag["n_winding"]
+    assert abs(complex(g["info"]["winding_re"], g["info"]["winding_im"]) - diag["winding"]) < 1e-8
+    assert ref["lam"].size == g["lam"].size
