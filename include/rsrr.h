@@ -74,6 +74,9 @@ typedef struct {
 /* precision of the sample solves (rsrr_sample) */
 #define RSRR_FP64     0  /* complex128 band LU and solves                                */
 #define RSRR_C64_IR   1  /* complex64 band LU and solves, FP64 residual and refinement   */
+/* flag OR-ed into precision: keep refining every point while its worst eta still halves per
+ * sweep (working accuracy), not only until eta <= tol; acceptance is still eta <= tol */
+#define RSRR_REFINE_FULL 0x100
 
 /* flags of rsrr_create_nep */
 #define RSRR_NATURAL_ORDER 0x1u  /* keep the caller's ordering (skip the band reordering) */
@@ -106,7 +109,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
  *   N, L       sampling points (1..4096) and probing columns (1..256)
  *   U_reim     [L][n][2] the probing matrix U (n x L, column-major, caller ordering);
  *              NULL reuses the U of the previous rsrr_sample on this handle (same n, L)
- *   precision  RSRR_FP64 or RSRR_C64_IR
+ *   precision  RSRR_FP64 or RSRR_C64_IR, optionally | RSRR_REFINE_FULL
  *   tol        backward-error target per column,
  *              eta = ||u - T x||_2 / (||T||_1 ||x||_2 + ||u||_2) <= tol  (e.g. 1e-10)
  *   max_refine refinement sweeps allowed in RSRR_C64_IR (ignored for RSRR_FP64)
@@ -167,6 +170,8 @@ typedef struct {
     int32_t rows_kept;          /* rows of R kept by rsrr_project's early-stopped QR         */
     int32_t jacobi_sweeps_project, jacobi_sweeps_solve;  /* sweeps of the two Jacobi SVDs  */
     double ms_project_qr, ms_project_svd, ms_project_basis, ms_project_gemm;  /* rsrr_project parts */
+    double ms_solve_inverse, ms_solve_svd, ms_solve_extract;  /* rsrr_solve parts: reduced inverses
+                                   with moments and traces; Hankel SVD; count, eig, back-map */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

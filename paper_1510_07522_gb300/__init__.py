@@ -21,6 +21,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESINGULAR", -4: "ENOTCONVERGED", -5: 
           -6: "ETIMEOUT", -7: "ECUDA", -8: "EORDER", -9: "EUNSUPPORTED"}
 RSRR_FP64 = 0
 RSRR_C64_IR = 1
+RSRR_REFINE_FULL = 0x100
 RSRR_NATURAL_ORDER = 0x1
 
 F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL = range(6)
@@ -58,7 +59,9 @@ class rsrr_info(ctypes.Structure):
                 ("rows_kept", ctypes.c_int32), ("jacobi_sweeps_project", ctypes.c_int32),
                 ("jacobi_sweeps_solve", ctypes.c_int32),
                 ("ms_project_qr", ctypes.c_double), ("ms_project_svd", ctypes.c_double),
-                ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double)]
+                ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double),
+                ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
+                ("ms_solve_extract", ctypes.c_double)]
 
 
 _lib = None

@@ -148,14 +148,17 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const d
     if (!(C->a > 0) || !(C->b > 0) || !std::isfinite(C->gamma_re) || !std::isfinite(C->gamma_im) ||
         !std::isfinite(C->a) || !std::isfinite(C->b))
         return set_error(RSRR_EINVAL, "bad contour");
-    if (precision != RSRR_FP64 && precision != RSRR_C64_IR) return set_error(RSRR_EINVAL, "unknown precision");
+    const int mode = precision & 0xff;
+    if ((mode != RSRR_FP64 && mode != RSRR_C64_IR) || (precision & ~(0xff | RSRR_REFINE_FULL)))
+        return set_error(RSRR_EINVAL, "unknown precision or flag");
     if (!(tol > 0) || max_refine < 0 || max_refine > 100) return set_error(RSRR_EINVAL, "bad tol or max_refine");
     if ((int64_t)N * L * h->n > (int64_t)1 << 34) return set_error(RSRR_ENOMEM, "S_hat too large");
     DeviceGuard g(h->device);
     h->C = *C;
     h->N = N;
     h->L = L;
-    h->precision = precision;
+    h->precision = mode;
+    h->refine_full = (precision & RSRR_REFINE_FULL) != 0;
     h->tol = tol;
     h->sampled = h->projected = false;
     h->kS = -1;
@@ -235,6 +238,9 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->ms_project_svd = h->ms_project_parts[1];
     o->ms_project_basis = h->ms_project_parts[2];
     o->ms_project_gemm = h->ms_project_parts[3];
+    o->ms_solve_inverse = h->ms_solve_parts[0];
+    o->ms_solve_svd = h->ms_solve_parts[1];
+    o->ms_solve_extract = h->ms_solve_parts[2];
     return RSRR_OK;
 }
 

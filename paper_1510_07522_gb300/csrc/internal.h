@@ -54,6 +54,7 @@ struct rsrr_nep_s {
 
     // sampling state
     int32_t N = 0, L = 0, precision = 0;
+    bool refine_full = false;
     rsrr_contour C{};
     double tol = 0;
     int32_t refine_sweeps = 0;
@@ -82,5 +83,6 @@ struct rsrr_nep_s {
     int32_t factor_launches = 0, trsv_launches = 0;
     int32_t rows_kept = 0, jacobi_sweeps_project = 0, jacobi_sweeps_solve = 0;
     double ms_project_parts[4] = {0, 0, 0, 0};
+    double ms_solve_parts[3] = {0, 0, 0};
     int64_t device_bytes = 0;
 };

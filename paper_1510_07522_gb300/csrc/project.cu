@@ -5,12 +5,14 @@
 //      taken in bit-reversed order (0, N/2, N/4, 3N/4, ...) so early columns sample the whole
 //      contour.  Each panel is factored by one cooperative kernel (two grid barriers per
 //      column); the trailing matrix is updated with the compact WY form by three ZGEMMs.
-//      After every panel the Frobenius norm of the remaining trailing block is measured; once
-//      it is below 1% of delta * max_j ||s_j|| (<= 1% of delta sigma_1) the remaining rows of
-//      R are dropped: by Weyl's inequality they move no singular value by more than that, so
-//      the truncation only differs from the full SVD for sigma within 1% of the threshold.
-//   2. One-sided Jacobi on R_keep^H (m x k') with the rotations accumulated: R_keep = J Sigma W^H,
-//      so the left singular vectors of R_keep are the columns of J.
+//      After every panel the remaining trailing block is measured (Frobenius norm, then a
+//      power-iteration estimate of its 2-norm with a safety factor of 3); once its 2-norm is
+//      below 10% of delta * max_j ||s_j|| (<= 10% of delta sigma_1) the remaining rows of R are
+//      dropped: by Weyl's inequality they move no singular value by more than that, so the
+//      truncation only differs from the full SVD for sigma within 10% of the threshold.
+//   2. A second QR, of R_keep^H (m x k'), keeps only its k' x k' triangle R2; one-sided Jacobi
+//      on R2 with the rotations accumulated gives R2^H = J Sigma W^H, and the left singular
+//      vectors of R_keep = R2^H Q2^H are the columns of J.
 //   3. S = Q [J(:, 1:k_S); 0] by applying the panels' reflectors in reverse.
 //   4. P_i = S^H (A_i S): CSR SpMM, then ZGEMM.
 #include <algorithm>
@@ -234,6 +236,188 @@ std::vector<int> bit_reversed_order(int N) {
     return idx;
 }
 
+// Householder QR of A (rows x cols, ld lda) in place: R in the upper triangle, the
+// reflectors below it, T factors of each panel in Tall.  When stop2 >= 0 the factorisation
+// stops after the first panel whose remaining trailing block has squared Frobenius norm
+// <= stop2.  Returns the number of rows of R produced in *kk and panels in *npan.
+struct HqrWork {
+    c128 *V = nullptr, *W = nullptr, *W2 = nullptr, *tau = nullptr, *Tall = nullptr, *alpha = nullptr,
+         *part2 = nullptr, *part3 = nullptr, *Yb = nullptr;
+    double *part = nullptr, *dnorm = nullptr;
+    c128 *px = nullptr, *py = nullptr;
+    unsigned* bar = nullptr;
+    int G = 0;
+    cudaStream_t st = nullptr;
+    int alloc(int64_t rows, int cols, int kmax, cudaStream_t s) {
+        st = s;
+        int dev = 0, nsm = 0, occ = 0;
+        RSRR_CUDA(cudaGetDevice(&dev));
+        RSRR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hqr_panel_kernel, 256, 0));
+        if (occ < 1) return set_error(RSRR_ECUDA, "panel kernel cannot be resident");
+        G = nsm;
+        const int np = (int)ceil_div(kmax, kPB);
+        RSRR_TRY(dalloc_n(&V, (size_t)rows * kPB, s));
+        RSRR_TRY(dalloc_n(&W, (size_t)kPB * cols, s));
+        RSRR_TRY(dalloc_n(&W2, (size_t)kPB * cols, s));
+        RSRR_TRY(dalloc_n(&tau, (size_t)kmax, s));
+        RSRR_TRY(dalloc_n(&Tall, (size_t)np * kPB * kPB, s));
+        RSRR_TRY(dalloc_n(&alpha, 1, s));
+        RSRR_TRY(dalloc_n(&part, (size_t)G, s));
+        RSRR_TRY(dalloc_n(&part2, (size_t)G * kPB, s));
+        RSRR_TRY(dalloc_n(&part3, (size_t)G * kPB * kPB, s));
+        RSRR_TRY(dalloc_n(&Yb, (size_t)kPB * kPB, s));
+        RSRR_TRY(dalloc_n(&bar, 4, s));
+        RSRR_TRY(dalloc_n(&dnorm, 1, s));
+        RSRR_TRY(dalloc_n(&px, (size_t)cols, s));
+        RSRR_TRY(dalloc_n(&py, (size_t)rows, s));
+        RSRR_CUDA(cudaMemsetAsync(bar, 0, 16, s));
+        return RSRR_OK;
+    }
+    ~HqrWork() {
+        for (void* p : {(void*)V, (void*)W, (void*)W2, (void*)tau, (void*)Tall, (void*)alpha, (void*)part2,
+                        (void*)part3, (void*)Yb, (void*)part, (void*)dnorm, (void*)bar, (void*)px, (void*)py})
+            dfree(p, st);
+    }
+};
+
+int block_norm2_est(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, int iters, c128* x, c128* y,
+                    double* dn, cudaStream_t st, double* est);
+
+// stop_norm >= 0: stop after the first panel whose remaining trailing block has 2-norm at most
+// stop_norm, tested by the Frobenius norm (an upper bound) or, once that is within
+// sqrt(min(rows, cols)) of the target, by three times a power-iteration estimate.
+int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, double stop_norm, int* kk_out,
+                   int* npan_out) {
+    cudaStream_t st = w.st;
+    const int kmax = (int)std::min<int64_t>(rows, cols);
+    int kk = 0, npan = 0;
+    for (int kb = 0; kb < kmax; kb += kPB) {
+        const int bw = std::min(kPB, kmax - kb);
+        PanelArgs pa{A, lda, (int)rows, kb, bw, w.tau, w.Tall + (int64_t)npan * kPB * kPB, w.part, w.alpha,
+                     w.part2, w.part3, w.Yb, GridBar{w.bar, w.bar + 1, reinterpret_cast<int*>(w.bar + 2)}};
+        void* args[] = {&pa};
+        RSRR_CUDA(cudaLaunchCooperativeKernel((void*)hqr_panel_kernel, w.G, 256, args, 0, st));
+        note_launch();
+        ++npan;
+        kk = kb + bw;
+        const int mt = cols - kk;
+        if (mt > 0) {
+            { extract_v_kernel<<<(unsigned)ceil_div((rows - kb) * bw, 256), 256, 0, st>>>(A, lda, (int)rows, kb, bw, w.V, rows); note_launch(); }
+            Zgemm g1;
+            g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = mt; g1.K = (int)(rows - kb);
+            g1.A = w.V; g1.lda = rows; g1.B = A + kb + (int64_t)kk * lda; g1.ldb = lda; g1.C = w.W; g1.ldc = kPB;
+            RSRR_TRY(zgemm(g1, st));
+            Zgemm g2;
+            g2.opA = OP_C; g2.opB = OP_N; g2.M = bw; g2.N = mt; g2.K = bw;
+            g2.A = w.Tall + (int64_t)(npan - 1) * kPB * kPB; g2.lda = bw; g2.B = w.W; g2.ldb = kPB; g2.C = w.W2;
+            g2.ldc = kPB;
+            RSRR_TRY(zgemm(g2, st));
+            Zgemm g3;
+            g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(rows - kb); g3.N = mt; g3.K = bw;
+            g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
+            g3.A = w.V; g3.lda = rows; g3.B = w.W2; g3.ldb = kPB; g3.C = A + kb + (int64_t)kk * lda; g3.ldc = lda;
+            g3.ksplit = 1;
+            RSRR_TRY(zgemm(g3, st));
+        }
+        int berr = 0;
+        double tn2 = 0.0;
+        if (stop_norm >= 0.0) {
+            RSRR_CUDA(cudaMemsetAsync(w.dnorm, 0, 8, st));
+            block_norm2(A, lda, kk, (int)rows, kk, cols, w.dnorm, st);
+            RSRR_CUDA(cudaMemcpyAsync(&tn2, w.dnorm, 8, cudaMemcpyDeviceToHost, st));
+        }
+        RSRR_CUDA(cudaMemcpyAsync(&berr, w.bar + 2, 4, cudaMemcpyDeviceToHost, st));
+        RSRR_CUDA(cudaStreamSynchronize(st));
+        if (berr) return set_error(RSRR_ETIMEOUT, "grid barrier gave up in the panel kernel");
+        if (!std::isfinite(tn2)) return set_error(RSRR_ENONFINITE, "non-finite QR");
+        if (stop_norm >= 0.0 && kk < kmax) {
+            const double fro = sqrt(tn2);
+            if (fro <= stop_norm) break;
+            const double dimf = sqrt((double)std::min<int64_t>(rows - kk, cols - kk));
+            if (fro <= stop_norm * dimf) {
+                double est = 0.0;
+                RSRR_TRY(block_norm2_est(A, lda, kk, (int)rows, kk, cols, 12, w.px, w.py, w.dnorm, st, &est));
+                if (3.0 * est <= stop_norm) break;
+            }
+        }
+    }
+    *kk_out = kk;
+    *npan_out = npan;
+    return RSRR_OK;
+}
+
+// y = A x for the block rows [r0, r1) x cols [c0, c1) (one thread per row)
+__global__ void gemv_n_kernel(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, const c128* x, c128* y) {
+    const int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r1) return;
+    c128 acc = czero<double>();
+    for (int c = c0; c < c1; ++c) cfma(acc, A[i + (int64_t)c * lda], x[c - c0]);
+    y[i - r0] = acc;
+}
+// x = A^H y for the same block (one warp per column); also accumulates ||x||^2 into *nrm
+__global__ void gemv_c_kernel(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, const c128* y, c128* x,
+                              double* nrm) {
+    const int c = c0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= c1) return;
+    c128 acc = czero<double>();
+    for (int i = r0 + lane; i < r1; i += 32) cfma_conj(acc, A[i + (int64_t)c * lda], y[i - r0]);
+    for (int off = 16; off; off >>= 1) {
+        acc.re += __shfl_down_sync(0xffffffffu, acc.re, off);
+        acc.im += __shfl_down_sync(0xffffffffu, acc.im, off);
+    }
+    if (lane == 0) {
+        x[c - c0] = acc;
+        atomicAdd(nrm, cnorm2(acc));
+    }
+}
+__global__ void scale_vec_kernel(c128* x, int n, const double* nrm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = cscale(x[i], 1.0 / sqrt(fmax(*nrm, 1e-300)));
+}
+__global__ void seed_vec_kernel(c128* x, int n) {  // fixed pseudo-random start vector
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned h = 2166136261u ^ (unsigned)i;
+    h *= 16777619u; h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+    x[i] = mk<double>(((h & 0xffff) / 65536.0) - 0.5, ((h >> 16) / 65536.0) - 0.5);
+}
+
+// Power-iteration estimate of the 2-norm of the block (a lower bound that converges from
+// below; the caller applies a safety factor).
+int block_norm2_est(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, int iters, c128* x, c128* y,
+                    double* dn, cudaStream_t st, double* est) {
+    const int nr = r1 - r0, nc = c1 - c0;
+    *est = 0.0;
+    if (nr <= 0 || nc <= 0) return RSRR_OK;
+    { seed_vec_kernel<<<(unsigned)ceil_div(nc, 256), 256, 0, st>>>(x, nc); note_launch(); }
+    double prev = 0.0, cur = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        { gemv_n_kernel<<<(unsigned)ceil_div(nr, 128), 128, 0, st>>>(A, lda, r0, r1, c0, c1, x, y); note_launch(); }
+        RSRR_CUDA(cudaMemsetAsync(dn, 0, 8, st));
+        { gemv_c_kernel<<<(unsigned)ceil_div(nc, 8), 256, 0, st>>>(A, lda, r0, r1, c0, c1, y, x, dn); note_launch(); }
+        double h2 = 0.0;
+        RSRR_CUDA(cudaMemcpyAsync(&h2, dn, 8, cudaMemcpyDeviceToHost, st));
+        { scale_vec_kernel<<<(unsigned)ceil_div(nc, 256), 256, 0, st>>>(x, nc, dn); note_launch(); }
+        RSRR_CUDA(cudaStreamSynchronize(st));
+        // x had unit norm (after the first step): ||A^H A x|| -> sigma_max^2
+        cur = (it == 0) ? 0.0 : sqrt(sqrt(h2));
+        if (it >= 2 && cur <= 1.02 * prev) { prev = cur; break; }
+        prev = cur;
+    }
+    *est = prev;
+    return RSRR_OK;
+}
+
+// upper triangle (rows < k, cols < k) of a factored matrix into a dense k x k matrix
+__global__ void upper_kernel(const c128* A, int64_t lda, int k, c128* R) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    const int r = (int)(idx % k), c = (int)(idx / k);
+    R[idx] = (r <= c) ? A[r + (int64_t)c * lda] : czero<double>();
+}
+
 }  // namespace
 
 namespace {
@@ -305,78 +489,44 @@ int project_run(rsrr_nep h, double delta) {
     CUDAC(cudaStreamSynchronize(st));
     const double smax = *std::max_element(cn.begin(), cn.end());
     if (!std::isfinite(smax)) { cleanup(); return set_error(RSRR_ENONFINITE, "non-finite sample matrix"); }
-    const double stop2 = std::pow(0.01 * delta * smax, 2);
 
     // ---- Householder QR with early termination -----------------------------------------------
-    const int npan_max = (int)ceil_div(kmax, kPB);
-    TRYC(dalloc_n(&V, (size_t)n * kPB, st));
-    TRYC(dalloc_n(&W, (size_t)kPB * m, st));
-    TRYC(dalloc_n(&W2, (size_t)kPB * m, st));
-    TRYC(dalloc_n(&tau, (size_t)kmax, st));
-    TRYC(dalloc_n(&Tall, (size_t)npan_max * kPB * kPB, st));
-    TRYC(dalloc_n(&alpha, 1, st));
-    TRYC(dalloc_n(&part, (size_t)G, st));
-    TRYC(dalloc_n(&part2, (size_t)G * kPB, st));
-    TRYC(dalloc_n(&part3, (size_t)G * kPB * kPB, st));
-    TRYC(dalloc_n(&Yb, (size_t)kPB * kPB, st));
-    TRYC(dalloc_n(&bar, 4, st));
-    TRYC(dalloc_n(&dnorm, 1, st));
-    CUDAC(cudaMemsetAsync(bar, 0, 16, st));
-    int kk = 0;  // rows of R kept
-    int npan = 0;
-    for (int kb = 0; kb < kmax; kb += kPB) {
-        const int bw = std::min(kPB, kmax - kb);
-        PanelArgs pa{A, n, (int)n, kb, bw, tau, Tall + (int64_t)npan * kPB * kPB, part, alpha, part2, part3, Yb,
-                     GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2)}};
-        void* args[] = {&pa};
-        CUDAC(cudaLaunchCooperativeKernel((void*)hqr_panel_kernel, G, 256, args, 0, st));
-        note_launch();
-        ++npan;
-        kk = kb + bw;
-        const int mt = m - kk;  // trailing columns
-        if (mt > 0) {
-            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, V, n); note_launch(); }
-            Zgemm g1;
-            g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = mt; g1.K = (int)(n - kb);
-            g1.A = V; g1.lda = n; g1.B = A + kb + (int64_t)kk * n; g1.ldb = n; g1.C = W; g1.ldc = kPB;
-            TRYC(zgemm(g1, st));
-            Zgemm g2;
-            g2.opA = OP_C; g2.opB = OP_N; g2.M = bw; g2.N = mt; g2.K = bw;
-            g2.A = Tall + (int64_t)(npan - 1) * kPB * kPB; g2.lda = bw; g2.B = W; g2.ldb = kPB; g2.C = W2; g2.ldc = kPB;
-            TRYC(zgemm(g2, st));
-            Zgemm g3;
-            g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = mt; g3.K = bw;
-            g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
-            g3.A = V; g3.lda = n; g3.B = W2; g3.ldb = kPB; g3.C = A + kb + (int64_t)kk * n; g3.ldc = n; g3.ksplit = 1;
-            TRYC(zgemm(g3, st));
-        }
-        // trailing norm of the rows still to come
-        CUDAC(cudaMemsetAsync(dnorm, 0, 8, st));
-        block_norm2(A, n, kk, (int)n, kk, m, dnorm, st);
-        double tn2 = 0.0;
-        int berr[2] = {0, 0};
-        CUDAC(cudaMemcpyAsync(&tn2, dnorm, 8, cudaMemcpyDeviceToHost, st));
-        CUDAC(cudaMemcpyAsync(berr, bar + 2, 4, cudaMemcpyDeviceToHost, st));
-        CUDAC(cudaStreamSynchronize(st));
-        if (berr[0]) { cleanup(); return set_error(RSRR_ETIMEOUT, "grid barrier gave up in the panel kernel"); }
-        if (!std::isfinite(tn2)) { cleanup(); return set_error(RSRR_ENONFINITE, "non-finite QR"); }
-        if (tn2 <= stop2) break;
-    }
-
+    // stop once the trailing block's 2-norm is below 0.1 delta sigma_1: dropping it moves no
+    // singular value by more than a tenth of the truncation level (Weyl)
+    HqrWork hw;
+    TRYC(hw.alloc(n, m, kmax, st));
+    int kk = 0, npan = 0;
+    TRYC(householder_qr(A, n, m, n, hw, 0.1 * delta * smax, &kk, &npan));
     pc.mark();  // QR done
-    // ---- SVD of R_keep (kk x m) by one-sided Jacobi on its conjugate transpose ---------------
+    // ---- SVD of R_keep (kk x m) ---------------------------------------------------------------
+    // R_keep^H = Q2 R2 (a second QR, only R2 kept), so R_keep = R2^H Q2^H and the left singular
+    // vectors of R_keep are those of R2^H.  One-sided Jacobi on the columns of R2 with the
+    // rotations accumulated: R2 J = W orthogonal => R2^H = J Sigma (W Sigma^{-1})^H.
     TRYC(dalloc_n(&B, (size_t)m * kk, st));
-    TRYC(dalloc_n(&Jm, (size_t)kk * kk, st));
     { rkeep_h_kernel<<<(unsigned)ceil_div((int64_t)m * kk, 256), 256, 0, st>>>(A, n, m, kk, B); note_launch(); }
+    c128* R2 = nullptr;
+    {
+        HqrWork hw2;
+        TRYC(hw2.alloc(m, kk, std::min(m, kk), st));
+        int kk2 = 0, np2 = 0;
+        TRYC(householder_qr(B, m, kk, m, hw2, -1.0, &kk2, &np2));
+        TRYC(dalloc_n(&R2, (size_t)kk * kk, st));
+        const int kr = std::min(m, kk);
+        CUDAC(cudaMemsetAsync(R2, 0, (size_t)kk * kk * sizeof(c128), st));
+        { upper_kernel<<<(unsigned)ceil_div((int64_t)kk * kk, 256), 256, 0, st>>>(B, m, kk, R2); note_launch(); }
+        (void)kr;
+    }
+    TRYC(dalloc_n(&Jm, (size_t)kk * kk, st));
     { identity_kernel<<<(unsigned)ceil_div((int64_t)kk * kk, 256), 256, 0, st>>>(Jm, kk); note_launch(); }
     int sweeps = 0;
-    TRYC(jacobi_orthogonalize(B, m, kk, Jm, st, 40, &sweeps, 1e-2 * delta * smax));
+    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 1e-2 * delta * smax));
     h->jacobi_sweeps_project = sweeps;
     h->rows_kept = kk;
     dfree(colnrm, st);
     colnrm = nullptr;
     TRYC(dalloc_n(&colnrm, (size_t)kk, st));
-    column_norms(B, m, kk, m, colnrm, st);
+    column_norms(R2, kk, kk, kk, colnrm, st);
+    dfree(R2, st);
     std::vector<double> sv(kk);
     CUDAC(cudaMemcpyAsync(sv.data(), colnrm, kk * 8, cudaMemcpyDeviceToHost, st));
     CUDAC(cudaStreamSynchronize(st));
@@ -402,19 +552,19 @@ int project_run(rsrr_nep h, double delta) {
         TRYC(dalloc_n(&Z2, (size_t)kPB * kS, st));
         for (int p = npan - 1; p >= 0; --p) {
             const int kb = p * kPB, bw = std::min(kPB, kmax - kb);
-            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, V, n); note_launch(); }
+            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, hw.V, n); note_launch(); }
             Zgemm g1;
             g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = kS; g1.K = (int)(n - kb);
-            g1.A = V; g1.lda = n; g1.B = Ybuf + kb; g1.ldb = n; g1.C = Z; g1.ldc = kPB;
+            g1.A = hw.V; g1.lda = n; g1.B = Ybuf + kb; g1.ldb = n; g1.C = Z; g1.ldc = kPB;
             TRYC(zgemm(g1, st));
             Zgemm g2;
             g2.opA = OP_N; g2.opB = OP_N; g2.M = bw; g2.N = kS; g2.K = bw;
-            g2.A = Tall + (int64_t)p * kPB * kPB; g2.lda = bw; g2.B = Z; g2.ldb = kPB; g2.C = Z2; g2.ldc = kPB;
+            g2.A = hw.Tall + (int64_t)p * kPB * kPB; g2.lda = bw; g2.B = Z; g2.ldb = kPB; g2.C = Z2; g2.ldc = kPB;
             TRYC(zgemm(g2, st));
             Zgemm g3;
             g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = kS; g3.K = bw;
             g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
-            g3.A = V; g3.lda = n; g3.B = Z2; g3.ldb = kPB; g3.C = Ybuf + kb; g3.ldc = n; g3.ksplit = 1;
+            g3.A = hw.V; g3.lda = n; g3.B = Z2; g3.ldb = kPB; g3.C = Ybuf + kb; g3.ldc = n; g3.ksplit = 1;
             TRYC(zgemm(g3, st));
         }
         pc.mark();  // basis done

@@ -319,6 +319,11 @@ int alloc_zero(c128** p, size_t n, cudaStream_t s) {
 int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambda_reim, double* V_reim,
               double* resid, int32_t* nC_out) {
     cudaStream_t st = h->stream;
+    cudaEvent_t ev[4];
+    for (auto& e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    cudaEventRecord(ev[0], st);
+    for (double& x : h->ms_solve_parts) x = 0.0;
     const int k = h->kS, J = h->J;
     const int64_t n = h->n;
     *nC_out = 0;
@@ -423,6 +428,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         gt.A = X; gt.lda = kk; gt.B = Pt; gt.ldb = kk; gt.C = trc + j0; gt.ldc = N_S;
         TRYC(zgemm(gt, st));
     }
+    cudaEventRecord(ev[1], st);  // inverses, moments, traces done
     std::vector<c128> htr((size_t)N_S * J);
     CUDAC(cudaMemcpyAsync(htr.data(), trc, htr.size() * sizeof(c128), cudaMemcpyDeviceToHost, st));
     CUDAC(cudaStreamSynchronize(st));
@@ -457,6 +463,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     }
     TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax));
     h->jacobi_sweeps_solve = sweeps;
+    cudaEventRecord(ev[2], st);  // Hankel SVD done
     TRYC(dalloc_n(&sig, (size_t)D, st));
     column_norms(H, D, D, D, sig, st);
     std::vector<double> sv(D);
@@ -647,7 +654,13 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
                 }
         }
     }
+    cudaEventRecord(ev[3], st);
     CUDAC(cudaStreamSynchronize(st));
+    for (int i = 0; i < 3; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        h->ms_solve_parts[i] = t;
+    }
     cleanup();
 #undef TRYC
 #undef CUDAC

@@ -120,12 +120,13 @@ __global__ void residual_kernel(const int64_t* __restrict__ rowptr, const int32_
     }
 }
 
-// eta per column.  A point stays active (gets another refinement sweep) while some column is
-// above tol and its worst eta fell at least twofold in the last sweep; a point above tol that
-// stopped improving is counted as stagnated.  counters: [0] active, [1] non-finite, [2] stagnated.
+// eta per column.  A point stays active (gets another refinement sweep) while its worst eta is
+// above the target (tol, or 0 when refining to working accuracy) and fell at least twofold in
+// the last sweep; a point still above tol that stopped improving is counted as stagnated.
+// counters: [0] active, [1] non-finite, [2] stagnated.
 __global__ void eta_kernel(const double* __restrict__ rn2, const double* __restrict__ xn2,
                            const double* __restrict__ un2, const double* __restrict__ normT, int npts, int L,
-                           double tol, double* __restrict__ eta, int32_t* __restrict__ active,
+                           double tol, double target, double* __restrict__ eta, int32_t* __restrict__ active,
                            double* __restrict__ prev_max, int32_t* __restrict__ counters, int first) {
     const int pt = blockIdx.x;
     if (!first && !active[pt]) return;  // residual not recomputed for this point
@@ -142,10 +143,9 @@ __global__ void eta_kernel(const double* __restrict__ rn2, const double* __restr
     if (threadIdx.x == 0) {
         if (nonfinite) atomicOr(&counters[1], 1);
         int act = 0;
-        if (!(mx <= tol)) {
-            if (first || mx < 0.5 * prev_max[pt]) act = 1;
-            else atomicAdd(&counters[2], 1);
-        }
+        const bool improving = first || mx < 0.5 * prev_max[pt];
+        if (!(mx <= target) && improving) act = 1;
+        else if (!(mx <= tol)) atomicAdd(&counters[2], 1);
         prev_max[pt] = mx;
         active[pt] = act;
         if (act) atomicAdd(&counters[0], 1);
@@ -328,8 +328,8 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             dim3 g((unsigned)ceil_div(n, 128), np);
             { residual_kernel<R><<<g, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, nnz, n, L, h->d_U, X, B, rn2, xn2,
                                                   sweeps == 0 ? nullptr : active); note_launch(); }
-            { eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, eta, active, prev_max,
-                                          counters, sweeps == 0 ? 1 : 0); note_launch(); }
+            { eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, h->refine_full ? 0.0 : h->tol,
+                                          eta, active, prev_max, counters, sweeps == 0 ? 1 : 0); note_launch(); }
             int32_t hc[4];
             CUDAC(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, st));
             CUDAC(cudaStreamSynchronize(st));
@@ -337,7 +337,14 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             if (hc[1]) { nonfinite = true; break; }
             if (hc[2]) { notconv = true; break; }
             if (hc[0] == 0) break;
-            if (sweeps >= max_refine) { notconv = true; break; }
+            if (sweeps >= max_refine) {
+                // out of sweeps: fine if every column already meets tol (possible in full mode)
+                std::vector<double> he((size_t)np * L);
+                CUDAC(cudaMemcpyAsync(he.data(), eta, he.size() * 8, cudaMemcpyDeviceToHost, st));
+                CUDAC(cudaStreamSynchronize(st));
+                for (double e : he) if (!(e <= h->tol)) notconv = true;
+                break;
+            }
             sa.active = active;
             evs.start(st);
             TRYC(launch_fwd<R>(sa, np, st));

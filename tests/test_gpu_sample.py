@@ -113,6 +113,15 @@ def test_sampling_point_on_an_eigenvalue_is_singular(rs):
     h.close()
 
 
+def test_refine_full_reaches_working_accuracy(rs):
+    prob = w.config1(s=24, N=8, L=8)
+    ref, _, _ = oracle.sample(prob)
+    h, X, eta, info = run_sample(rs, prob, rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL, 1e-10, 20)
+    assert eta.max() <= 2e-15            # refined past tol, to FP64 working accuracy
+    assert rel_err_cols(X, ref).max() < 1e-9
+    h.close()
+
+
 def test_unreachable_tolerance_reports_not_converged(rs):
     prob = w.config0(N=4, L=4, nx=9, ny=9)
     h = open_nep(rs, prob)
