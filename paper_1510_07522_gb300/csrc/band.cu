@@ -18,6 +18,27 @@ namespace rsrr {
 namespace {
 
 // ------------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async), used to stage the next block of a solve
+// while the current one is applied.  src_bytes = 0 fills the destination with zeros.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, int src_bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(cplx<R>* smem, const cplx<R>* gmem, bool valid) {
+    if (sizeof(cplx<R>) == 16) cp_async_16(smem, gmem, valid ? 16 : 0);
+    else cp_async_8(smem, gmem, valid ? 8 : 0);
+}
+
+// ------------------------------------------------------------------------------------------
 // Column accessors for apply_block (row q is relative to the block; c < CG within a group).
 // ------------------------------------------------------------------------------------------
 template <typename R, int CG>
@@ -142,12 +163,134 @@ __device__ __forceinline__ void apply_block(const cplx<R>* __restrict__ Blk, int
 }
 
 // ------------------------------------------------------------------------------------------
-// Factorisation kernel: one CTA per sampling point.
+// Factorisation kernel: one CTA per sampling point, with look-ahead.
+//   warps 0..3  (panel team): factor panel p+1 into the second shared buffer
+//   warps 4..15 (update team): during step p first update the columns of panel p+1, signal
+//                the panel team (named barrier 2: the team waits, the update warps arrive),
+//                then update the rest of step p's trailing columns.
+// Step p ends with a CTA-wide barrier, after which panel p+1 is complete in its buffer.
+// Barrier ids: 0 = __syncthreads, 1 = panel team only (128 threads), 2 = lead signal (512).
+// Every thread reaches each barrier exactly once per step, whatever the sizes.
 // ------------------------------------------------------------------------------------------
+constexpr int kPanelWarps = 4;
+constexpr int kUpdateWarps = kLuThreads / 32 - kPanelWarps;
+
+__device__ __forceinline__ void team_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kPanelWarps * 32) : "memory"); }
+__device__ __forceinline__ void lead_wait() { asm volatile("bar.sync 2, %0;" ::"n"(kLuThreads) : "memory"); }
+__device__ __forceinline__ void lead_arrive() { asm volatile("bar.arrive 2, %0;" ::"n"(kLuThreads) : "memory"); }
+
+// Panel factorisation by the panel team (kPanelWarps warps), two team barriers per column:
+//   S: rows jj and pv swapped in every panel column but jj; column jj gets the pivot and the
+//      multipliers (one thread owns rows jj and pv of that column, so no value is read after
+//      another thread overwrote it); the pivot value comes from the search warp.
+//   R: rank-1 update, warp w owning columns jj+1+w, jj+1+w+W, ... and lanes owning rows; warp 0
+//      owns column jj+1, updates it first and then searches the next pivot in it.
+// Multipliers stay in final pivot order (whole panel rows are swapped).
+template <typename R>
+__device__ __forceinline__ void pivot_search(const cplx<R>* P, int ldp, int col, int first, int last, int lane,
+                                             int* s_piv, cplx<R>* s_pval) {
+    R best = R(-1);
+    int bi = first;
+    for (int q = first + lane; q <= last; q += 32) {
+        const R v = cabs1(P[q + col * ldp]);
+        if (v > best) { best = v; bi = q; }
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const R ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+        *s_piv = bi;
+        *s_pval = P[bi + col * ldp];
+    }
+}
+
+template <typename R>
+__device__ void factor_panel(const FactorArgs<R>& a, cplx<R>* ab, cplx<R>* lp, int32_t* permg, int32_t* ipiv,
+                             int p, cplx<R>* P, int* psm, int* s_piv, cplx<R>* s_pval, int* s_info) {
+    constexpr int PT = kPanelWarps * 32;
+    const BandDims& d = a.d;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kv = d.kv, kl = d.kl, ldab = d.ldab, ldp = d.ldp, nb = d.nb, n = d.n;
+    const int k0 = p * nb;
+    const int nbe = min(nb, n - k0);
+    const int m = min(nb + kl, n - k0);
+    // stage the panel with cp.async (every load in flight at once; zero fill outside the band)
+    for (int t = warp; t < nb; t += kPanelWarps) {  // one warp per column: no index division
+        const int col = k0 + t;
+        for (int q = lane; q < ldp; q += 32) {
+            const int dq = q - t;
+            const bool valid = t < nbe && q < m && dq <= kl && dq >= -kv;
+            const cplx<R>* src = valid ? ab + (int64_t)(kv + dq) + (int64_t)col * ldab : ab;
+            cp_async_elem<R>(P + q + t * ldp, src, valid);
+        }
+    }
+    cp_async_commit();
+    for (int q = tid; q < ldp; q += PT) psm[q] = q;
+    cp_async_wait<0>();
+    team_sync();
+    if (warp == 0) pivot_search(P, ldp, 0, 0, min(kl, m - 1), lane, s_piv, s_pval);
+    team_sync();
+    for (int jj = 0; jj < nbe; ++jj) {
+        const int last = min(jj + kl, m - 1);
+        const int pv = *s_piv;
+        const cplx<R> piv = *s_pval;
+        const bool nz = !cis_zero(piv);
+        const cplx<R> rp = nz ? crecip(piv) : czero<R>();
+        // ---- S: swap (columns != jj) and column jj (pivot + multipliers) --------------------
+        if (pv != jj) {
+            for (int t = tid; t < nb; t += PT) {
+                if (t == jj) continue;
+                const cplx<R> tmp = P[jj + t * ldp];
+                P[jj + t * ldp] = P[pv + t * ldp];
+                P[pv + t * ldp] = tmp;
+            }
+        }
+        for (int q = jj + tid; q <= last; q += PT) {
+            if (q == jj) {
+                const cplx<R> old = P[jj + jj * ldp];
+                P[jj + jj * ldp] = piv;
+                if (pv != jj) P[pv + jj * ldp] = nz ? old * rp : old;
+            } else if (q != pv && nz) {
+                P[q + jj * ldp] = P[q + jj * ldp] * rp;
+            }
+        }
+        if (tid == 0) {
+            if (pv != jj) { const int tmp = psm[jj]; psm[jj] = psm[pv]; psm[pv] = tmp; }
+            ipiv[k0 + jj] = k0 + pv;
+            if (!nz && *s_info == 0) *s_info = k0 + jj + 1;
+        }
+        team_sync();
+        // ---- R: rank-1 update of columns jj+1..nbe-1 ----------------------------------------
+        if (nz) {
+            for (int c = jj + 1 + warp; c < nbe; c += kPanelWarps) {
+                const cplx<R> u = P[jj + c * ldp];
+                if (!cis_zero(u))
+                    for (int q = jj + 1 + lane; q <= last; q += 32) cfms(P[q + c * ldp], P[q + jj * ldp], u);
+                if (c == jj + 1) {  // warp 0: the next pivot column is complete
+                    __syncwarp();
+                    pivot_search(P, ldp, jj + 1, jj + 1, min(jj + 1 + kl, m - 1), lane, s_piv, s_pval);
+                }
+            }
+        } else if (warp == 0 && jj + 1 < nbe) {
+            pivot_search(P, ldp, jj + 1, jj + 1, min(jj + 1 + kl, m - 1), lane, s_piv, s_pval);
+        }
+        team_sync();
+    }
+    for (int t = warp; t < nbe; t += kPanelWarps) {  // U11 back to the band
+        for (int q = lane; q <= t; q += 32)
+            if (t - q <= kv) ab[(int64_t)(kv + q - t) + (int64_t)(k0 + t) * ldab] = P[q + t * ldp];
+    }
+    cplx<R>* lpb = lp + (int64_t)p * ldp * nb;
+    for (int idx = tid; idx < ldp * nb; idx += PT) lpb[idx] = P[idx];
+    for (int q = tid; q < ldp; q += PT) permg[(int64_t)p * ldp + q] = psm[q];
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kLuThreads) band_factor_kernel(FactorArgs<R> a) {
     constexpr int CG = BandTraits<R>::CG, CH = BandTraits<R>::CH;
-    constexpr int NW = kLuThreads / 32;
     const BandDims d = a.d;
     const int pt = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -157,89 +300,47 @@ __global__ void __launch_bounds__(kLuThreads) band_factor_kernel(FactorArgs<R> a
     int32_t* ipiv = a.ipiv + (int64_t)pt * d.n;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);
-    int* psm = reinterpret_cast<int*>(P + (size_t)d.ldp * d.nb);
-    cplx<R>* ust = reinterpret_cast<cplx<R>*>(psm + d.ldp);
+    const int blk = d.ldp * d.nb;
+    cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);                 // [2][blk]
+    int* psm = reinterpret_cast<int*>(P + 2 * (size_t)blk);            // [2][ldp]
+    cplx<R>* ust = reinterpret_cast<cplx<R>*>(psm + 2 * (size_t)d.ldp);  // [kUpdateWarps][32*CG]
     __shared__ int s_piv;
     __shared__ int s_info;
+    __shared__ cplx<R> s_pval;
     if (tid == 0) s_info = 0;
+    __syncthreads();
 
-    const int kv = d.kv, kl = d.kl, ldab = d.ldab, ldp = d.ldp, nb = d.nb, n = d.n;
+    const int kv = d.kv, ldab = d.ldab, ldp = d.ldp, nb = d.nb, n = d.n;
+    if (warp < kPanelWarps) factor_panel<R>(a, ab, lp, permg, ipiv, 0, P, psm, &s_piv, &s_pval, &s_info);
+    __syncthreads();
     for (int p = 0; p < d.npanels; ++p) {
         const int k0 = p * nb;
         const int nbe = min(nb, n - k0);
-        const int m = min(nb + kl, n - k0);
-        // ---- A: stage and factor the panel -------------------------------------------
-        for (int idx = tid; idx < ldp * nb; idx += kLuThreads) {
-            const int q = idx % ldp, t = idx / ldp;
-            cplx<R> v = czero<R>();
-            const int dq = q - t;
-            if (t < nbe && q < m && dq <= kl && dq >= -kv)
-                v = ab[(int64_t)(kv + dq) + (int64_t)(k0 + t) * ldab];
-            P[idx] = v;
-        }
-        for (int q = tid; q < ldp; q += kLuThreads) psm[q] = q;
-        __syncthreads();
-        for (int jj = 0; jj < nbe; ++jj) {
-            const int last = min(jj + kl, m - 1);
-            if (warp == 0) {
-                R best = R(-1);
-                int bi = jj;
-                for (int q = jj + lane; q <= last; q += 32) {
-                    const R v = cabs1(P[q + jj * ldp]);
-                    if (v > best) { best = v; bi = q; }
-                }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) {
-                    const R ob = __shfl_down_sync(0xffffffffu, best, off);
-                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-                }
-                if (lane == 0) s_piv = bi;
-            }
-            __syncthreads();
-            const int pv = s_piv;
-            if (pv != jj) {
-                for (int t = tid; t < nb; t += kLuThreads) {
-                    const cplx<R> tmp = P[jj + t * ldp];
-                    P[jj + t * ldp] = P[pv + t * ldp];
-                    P[pv + t * ldp] = tmp;
-                }
-                if (tid == 0) { const int tmp = psm[jj]; psm[jj] = psm[pv]; psm[pv] = tmp; }
-            }
-            __syncthreads();
-            const cplx<R> piv = P[jj + jj * ldp];
-            if (tid == 0) {
-                ipiv[k0 + jj] = k0 + pv;
-                if (cis_zero(piv) && s_info == 0) s_info = k0 + jj + 1;
-            }
-            if (!cis_zero(piv)) {
-                const cplx<R> rp = crecip(piv);
-                for (int q = jj + 1 + tid; q <= last; q += kLuThreads) P[q + jj * ldp] = P[q + jj * ldp] * rp;
-                __syncthreads();
-                const int nr = last - jj, nc = nbe - 1 - jj;
-                for (int idx = tid; idx < nr * nc; idx += kLuThreads) {
-                    const int q = jj + 1 + idx % nr, c = jj + 1 + idx / nr;
-                    cfms(P[q + c * ldp], P[q + jj * ldp], P[jj + c * ldp]);
-                }
-            }
-            __syncthreads();
-        }
-        // U11 back to the band, the whole block to lp, the permutation to perm
-        for (int idx = tid; idx < nb * nb; idx += kLuThreads) {
-            const int q = idx % nb, t = idx / nb;
-            if (t < nbe && q <= t && t - q <= kv)
-                ab[(int64_t)(kv + q - t) + (int64_t)(k0 + t) * ldab] = P[q + t * ldp];
-        }
-        cplx<R>* lpb = lp + (int64_t)p * ldp * nb;
-        for (int idx = tid; idx < ldp * nb; idx += kLuThreads) lpb[idx] = P[idx];
-        for (int q = tid; q < ldp; q += kLuThreads) permg[(int64_t)p * ldp + q] = psm[q];
-        // ---- B: trailing columns ------------------------------------------------------
+        const int m = min(nb + d.kl, n - k0);
+        const int buf = p & 1;
         const int cb = k0 + nbe, ce = min(n, k0 + nbe + kv);
-        const int ntask = (ce - cb + CG - 1) / CG;
-        for (int task = warp; task < ntask; task += NW) {
-            TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
-            apply_block<R, CG, CH, true>(P, ldp, nbe, m, psm, nullptr, ust + warp * 32 * CG, acc, lane);
+        const int ntask = max(0, (ce - cb + CG - 1) / CG);
+        const bool has_next = p + 1 < d.npanels;
+        const int nlead = has_next ? min(ntask, (nb + CG - 1) / CG) : 0;
+        if (warp >= kPanelWarps) {
+            const int uw = warp - kPanelWarps;
+            cplx<R>* Pb = P + (size_t)buf * blk;
+            int* pb = psm + (size_t)buf * ldp;
+            for (int task = uw; task < nlead; task += kUpdateWarps) {
+                TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
+                apply_block<R, CG, CH, true>(Pb, ldp, nbe, m, pb, nullptr, ust + uw * 32 * CG, acc, lane);
+            }
+            __threadfence_block();
+            lead_arrive();
+            for (int task = nlead + uw; task < ntask; task += kUpdateWarps) {
+                TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
+                apply_block<R, CG, CH, true>(Pb, ldp, nbe, m, pb, nullptr, ust + uw * 32 * CG, acc, lane);
+            }
+        } else {
+            lead_wait();
+            if (has_next)
+                factor_panel<R>(a, ab, lp, permg, ipiv, p + 1, P + (size_t)(buf ^ 1) * blk, psm + (size_t)(buf ^ 1) * ldp,
+                                &s_piv, &s_pval, &s_info);
         }
         __syncthreads();
     }
@@ -248,6 +349,8 @@ __global__ void __launch_bounds__(kLuThreads) band_factor_kernel(FactorArgs<R> a
 
 // ------------------------------------------------------------------------------------------
 // Forward solve: X <- L^{-1} P X panel by panel, one CTA per point, one warp per CG columns.
+// The next panel's L block and permutation are staged with cp.async while the current one
+// is applied (two buffers when they fit in shared memory).
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a) {
@@ -260,32 +363,53 @@ __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a)
     const cplx<R>* lp = a.lp + pt * a.lp_stride;
     const int32_t* permg = a.perm + pt * a.perm_stride;
     cplx<R>* x = a.x + pt * a.x_stride;
+    const int ldp = d.ldp, nb = d.nb, n = d.n, nbuf = d.fwd_nbuf;
+    const int blk = ldp * nb;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);
-    int* psm = reinterpret_cast<int*>(P + (size_t)d.ldp * d.nb);
-    cplx<R>* ust = reinterpret_cast<cplx<R>*>(psm + d.ldp);
-    const int ldp = d.ldp, nb = d.nb, n = d.n;
+    int* psm = reinterpret_cast<int*>(P + (size_t)nbuf * blk);
+    cplx<R>* ust = reinterpret_cast<cplx<R>*>(psm + (size_t)nbuf * ldp);
+    auto stage = [&](int p, int buf) {
+        const char* src = reinterpret_cast<const char*>(lp + (int64_t)p * blk);
+        char* dst = reinterpret_cast<char*>(P + (size_t)buf * blk);
+        const int nch = blk * (int)sizeof(cplx<R>) / 16;
+        for (int c = tid; c < nch; c += kSolveThreads) cp_async_16(dst + 16 * c, src + 16 * c, 16);
+        const char* ps = reinterpret_cast<const char*>(permg + (int64_t)p * ldp);
+        char* pd = reinterpret_cast<char*>(psm + (size_t)buf * ldp);
+        for (int c = tid; c < ldp / 4; c += kSolveThreads) cp_async_16(pd + 16 * c, ps + 16 * c, 16);
+        cp_async_commit();
+    };
     const int ntask = (a.L + CG - 1) / CG;
+    stage(0, 0);
     for (int p = 0; p < d.npanels; ++p) {
         const int k0 = p * nb;
         const int nbe = min(nb, n - k0);
         const int m = min(nb + d.kl, n - k0);
-        const cplx<R>* lpb = lp + (int64_t)p * ldp * nb;
-        for (int idx = tid; idx < ldp * nb; idx += kSolveThreads) P[idx] = lpb[idx];
-        for (int q = tid; q < ldp; q += kSolveThreads) psm[q] = permg[(int64_t)p * ldp + q];
-        __syncthreads();
-        for (int task = warp; task < ntask; task += NW) {
-            RhsCols<R, CG> acc{x, n, a.L, task * CG, k0, +1};
-            apply_block<R, CG, CH, true>(P, ldp, nbe, m, psm, nullptr, ust + warp * 32 * CG, acc, lane);
+        const bool ahead = nbuf == 2 && p + 1 < d.npanels;
+        if (ahead) {
+            stage(p + 1, (p + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const int buf = nbuf == 2 ? (p & 1) : 0;
+        for (int task = warp; task < ntask; task += NW) {
+            RhsCols<R, CG> acc{x, n, a.L, task * CG, k0, +1};
+            apply_block<R, CG, CH, true>(P + (size_t)buf * blk, ldp, nbe, m, psm + (size_t)buf * ldp, nullptr,
+                                         ust + warp * 32 * CG, acc, lane);
+        }
+        __syncthreads();
+        if (nbuf == 1 && p + 1 < d.npanels) stage(p + 1, 0);
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // Backward solve: X <- U^{-1} X from the last block up.  Rows are taken in reversed order
-// (block row k0+nbe-1 first), which turns U's block into a lower-triangular one.
+// (block row k0+nbe-1 first), which turns U's block into a lower-triangular one.  The next
+// block's U entries are gathered from the band array with cp.async (zero-filled outside the
+// band) while the current block is applied.
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a) {
@@ -297,47 +421,85 @@ __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const cplx<R>* ab = a.ab + pt * a.ab_stride;
     cplx<R>* x = a.x + pt * a.x_stride;
+    const int ldb = d.ldb, nbb = d.nbb, n = d.n, kv = d.kv, ldab = d.ldab, nbuf = d.bwd_nbuf;
+    const int blk = ldb * nbb;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* Ub = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* invd = Ub + (size_t)d.ldb * d.nbb;
+    cplx<R>* invd = Ub + (size_t)nbuf * blk;
     cplx<R>* ust = invd + 32;
-    const int ldb = d.ldb, nbb = d.nbb, n = d.n, kv = d.kv, ldab = d.ldab;
     const int nblk = (n + nbb - 1) / nbb;
-    const int ntask = (a.L + CG - 1) / CG;
-    for (int bk = nblk - 1; bk >= 0; --bk) {
+    auto stage = [&](int bk, int buf) {
         const int k0 = bk * nbb;
         const int nbe = min(nbb, n - k0);
         const int m = nbe + min(kv, k0);
-        const int top = k0 + nbe - 1;  // reversed origin
-        for (int idx = tid; idx < ldb * nbb; idx += kSolveThreads) {
+        const int top = k0 + nbe - 1;
+        cplx<R>* dst = Ub + (size_t)buf * blk;
+        for (int idx = tid; idx < blk; idx += kSolveThreads) {
             const int q = idx % ldb, t = idx / ldb;
-            cplx<R> v = czero<R>();
-            if (q < m && t < nbe) {
-                const int i = top - q, c = top - t;
-                if (i <= c && c - i <= kv) v = ab[(int64_t)(kv + i - c) + (int64_t)c * ldab];
-            }
-            Ub[idx] = v;
+            const int i = top - q, c = top - t;
+            const bool valid = q < m && t < nbe && i <= c && c - i <= kv;
+            const cplx<R>* src = valid ? ab + (int64_t)(kv + i - c) + (int64_t)c * ldab : ab;
+            cp_async_elem<R>(dst + idx, src, valid);
         }
-        for (int t = tid; t < nbe; t += kSolveThreads) {
-            const int c = top - t;
-            invd[t] = crecip(ab[(int64_t)kv + (int64_t)c * ldab]);
+        cp_async_commit();
+    };
+    const int ntask = (a.L + CG - 1) / CG;
+    stage(nblk - 1, 0);
+    for (int bk = nblk - 1, it = 0; bk >= 0; --bk, ++it) {
+        const int k0 = bk * nbb;
+        const int nbe = min(nbb, n - k0);
+        const int m = nbe + min(kv, k0);
+        const int top = k0 + nbe - 1;
+        const bool ahead = nbuf == 2 && bk > 0;
+        if (ahead) {
+            stage(bk - 1, (it + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
+        __syncthreads();
+        const int buf = nbuf == 2 ? (it & 1) : 0;
+        cplx<R>* U = Ub + (size_t)buf * blk;
+        for (int t = tid; t < nbe; t += kSolveThreads) invd[t] = crecip(U[t + t * ldb]);
         __syncthreads();
         for (int task = warp; task < ntask; task += NW) {
             RhsCols<R, CG> acc{x, n, a.L, task * CG, top, -1};
-            apply_block<R, CG, CH, false>(Ub, ldb, nbe, m, nullptr, invd, ust + warp * 32 * CG, acc, lane);
+            apply_block<R, CG, CH, false>(U, ldb, nbe, m, nullptr, invd, ust + warp * 32 * CG, acc, lane);
         }
         __syncthreads();
+        if (nbuf == 1 && bk > 0) stage(bk - 1, 0);
     }
 }
 
 }  // namespace
 
+namespace {
+// Opt a kernel into `sm` bytes of dynamic shared memory, with a readable error when the
+// request plus the kernel's static shared memory exceeds the device's per-block limit.
+template <typename K>
+int set_smem(K kernel, size_t sm, const char* name) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    if (sm + fa.sharedSizeBytes > (size_t)optin)
+        return set_error(RSRR_EUNSUPPORTED, std::string(name) + ": shared memory " + std::to_string(sm) + " + " +
+                                                std::to_string(fa.sharedSizeBytes) + " exceeds " + std::to_string(optin));
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess)
+        return set_error(RSRR_ECUDA, std::string(name) + ": cudaFuncSetAttribute(" + std::to_string(sm) + ", static " +
+                                         std::to_string(fa.sharedSizeBytes) + ", optin " + std::to_string(optin) +
+                                         "): " + cudaGetErrorString(e));
+    return RSRR_OK;
+}
+}  // namespace
+
 template <typename R>
 int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = factor_smem_bytes<R>(a.d);
-    RSRR_CUDA(cudaFuncSetAttribute(band_factor_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    RSRR_TRY(set_smem(band_factor_kernel<R>, sm, "band_factor_kernel"));
     { band_factor_kernel<R><<<npts, kLuThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
@@ -345,8 +507,8 @@ int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s) {
 
 template <typename R>
 int launch_fwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
-    const size_t sm = fwd_smem_bytes<R>(a.d);
-    RSRR_CUDA(cudaFuncSetAttribute(band_fwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm = fwd_smem_bytes<R>(a.d, a.d.fwd_nbuf);
+    RSRR_TRY(set_smem(band_fwd_kernel<R>, sm, "band_fwd_kernel"));
     { band_fwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
@@ -354,8 +516,8 @@ int launch_fwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
 
 template <typename R>
 int launch_bwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
-    const size_t sm = bwd_smem_bytes<R>(a.d);
-    RSRR_CUDA(cudaFuncSetAttribute(band_bwd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm = bwd_smem_bytes<R>(a.d, a.d.bwd_nbuf);
+    RSRR_TRY(set_smem(band_bwd_kernel<R>, sm, "band_bwd_kernel"));
     { band_bwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;

@@ -25,6 +25,7 @@ struct BandDims {
     int npanels = 0;
     int nbb = 0;   // block width of the backward solve (<= 32)
     int ldb = 0;   // rows of a backward block: multiple of 32, >= nbb + kv
+    int fwd_nbuf = 1, bwd_nbuf = 1;  // staging buffers of the solves (2 = copy-ahead)
 };
 
 template <typename R>
@@ -63,23 +64,23 @@ constexpr int kLuThreads = 512;
 constexpr int kSolveThreads = 256;
 
 template <typename R>
-size_t factor_smem_bytes(const BandDims& d) {
-    return (size_t)d.ldp * d.nb * sizeof(cplx<R>) + (size_t)d.ldp * sizeof(int) +
+size_t factor_smem_bytes(const BandDims& d) {  // two panel buffers (look-ahead) + per-warp stash
+    return 2 * ((size_t)d.ldp * d.nb * sizeof(cplx<R>) + (size_t)d.ldp * sizeof(int)) +
            (size_t)(kLuThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 template <typename R>
-size_t fwd_smem_bytes(const BandDims& d) {
-    return (size_t)d.ldp * d.nb * sizeof(cplx<R>) + (size_t)d.ldp * sizeof(int) +
+size_t fwd_smem_bytes(const BandDims& d, int nbuf) {
+    return (size_t)nbuf * ((size_t)d.ldp * d.nb * sizeof(cplx<R>) + (size_t)d.ldp * sizeof(int)) +
            (size_t)(kSolveThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 template <typename R>
-size_t bwd_smem_bytes(const BandDims& d) {
-    return (size_t)d.ldb * d.nbb * sizeof(cplx<R>) + (size_t)32 * sizeof(cplx<R>) +
+size_t bwd_smem_bytes(const BandDims& d, int nbuf) {
+    return (size_t)nbuf * d.ldb * d.nbb * sizeof(cplx<R>) + (size_t)32 * sizeof(cplx<R>) +
            (size_t)(kSolveThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 
 // Panel sizes for a band of (kl, ku) that fit the shared-memory budget.
-int pick_dims(int64_t n, int64_t kl, int64_t ku, bool c64, BandDims* d);
+int pick_dims(int64_t n, int64_t kl, int64_t ku, bool is_c64, BandDims* d);
 
 template <typename R>
 int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s);

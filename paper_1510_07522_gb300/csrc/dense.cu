@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             c128* bp = a.B + (int64_t)p * a.mb;
             c128* bq = a.B + (int64_t)q * a.mb;
             double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll 4
             for (int r = lane; r < a.mb; r += 32) {
                 const c128 x = bp[r], y = bq[r];
                 al += cnorm2(x);
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             const double zeta = (be - al) / (2.0 * g);
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+#pragma unroll 4
             for (int r = lane; r < a.mb; r += 32) {
                 const c128 x = bp[r], y = ph * bq[r];
                 bp[r] = cscale(x, c) - cscale(y, s);
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             if (a.J) {
                 c128* jp = a.J + (int64_t)p * a.kk;
                 c128* jq = a.J + (int64_t)q * a.kk;
+#pragma unroll 4
                 for (int r = lane; r < a.kk; r += 32) {
                     const c128 x = jp[r], y = ph * jq[r];
                     jp[r] = cscale(x, c) - cscale(y, s);

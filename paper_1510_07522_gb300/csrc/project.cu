@@ -7,7 +7,8 @@
 //      column); the trailing matrix is updated with the compact WY form by three ZGEMMs.
 //      After every panel the remaining trailing block is measured (Frobenius norm, then a
 //      power-iteration estimate of its 2-norm with a safety factor of 3); once its 2-norm is
-//      below 10% of delta * max_j ||s_j|| (<= 10% of delta sigma_1) the remaining rows of R are
+//      below 10% of delta * sigma_1 (sigma_1 from a power-iteration lower bound of ||S_hat||_2,
+//      so the rule errs on the side of keeping rows) the remaining rows of R are
 //      dropped: by Weyl's inequality they move no singular value by more than that, so the
 //      truncation only differs from the full SVD for sigma within 10% of the threshold.
 //   2. A second QR, of R_keep^H (m x k'), keeps only its k' x k' triangle R2; one-sided Jacobi
@@ -492,11 +493,15 @@ int project_run(rsrr_nep h, double delta) {
 
     // ---- Householder QR with early termination -----------------------------------------------
     // stop once the trailing block's 2-norm is below 0.1 delta sigma_1: dropping it moves no
-    // singular value by more than a tenth of the truncation level (Weyl)
+    // singular value by more than a tenth of the truncation level (Weyl).  sigma_1 is taken
+    // from a power-iteration estimate of ||S_hat||_2 (a lower bound, so the rule stays safe).
     HqrWork hw;
     TRYC(hw.alloc(n, m, kmax, st));
+    double s1_est = 0.0;
+    TRYC(block_norm2_est(A, n, 0, (int)n, 0, m, 30, hw.px, hw.py, hw.dnorm, st, &s1_est));
+    const double sref = std::max(smax, s1_est);
     int kk = 0, npan = 0;
-    TRYC(householder_qr(A, n, m, n, hw, 0.1 * delta * smax, &kk, &npan));
+    TRYC(householder_qr(A, n, m, n, hw, 0.1 * delta * sref, &kk, &npan));
     pc.mark();  // QR done
     // ---- SVD of R_keep (kk x m) ---------------------------------------------------------------
     // R_keep^H = Q2 R2 (a second QR, only R2 kept), so R_keep = R2^H Q2^H and the left singular
@@ -519,7 +524,7 @@ int project_run(rsrr_nep h, double delta) {
     TRYC(dalloc_n(&Jm, (size_t)kk * kk, st));
     { identity_kernel<<<(unsigned)ceil_div((int64_t)kk * kk, 256), 256, 0, st>>>(Jm, kk); note_launch(); }
     int sweeps = 0;
-    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 1e-2 * delta * smax));
+    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 1e-2 * delta * sref));
     h->jacobi_sweeps_project = sweeps;
     h->rows_kept = kk;
     dfree(colnrm, st);

@@ -177,29 +177,38 @@ __global__ void gather_rows_kernel(const c128* __restrict__ src, const int32_t* 
 
 }  // namespace
 
-int pick_dims(int64_t n, int64_t kl, int64_t ku, bool c64, BandDims* d) {
+int pick_dims(int64_t n, int64_t kl, int64_t ku, bool is_c64, BandDims* d) {
     if (kl > 2048 || ku > 2048) return set_error(RSRR_EUNSUPPORTED, "band too wide for the band kernels");
     d->n = (int)n;
     d->kl = (int)kl;
     d->ku = (int)ku;
     d->kv = d->kl + d->ku;
     d->ldab = 2 * d->kl + d->ku + 1;
-    const size_t es = c64 ? sizeof(c64) : sizeof(c128);
+    const size_t es = is_c64 ? sizeof(cplx<float>) : sizeof(cplx<double>);
     const size_t limit = 220 * 1024;
     const int64_t ubw = std::min<int64_t>(d->kv, n - 1);  // U's bandwidth cannot exceed n - 1
     for (int nb : {32, 16, 8, 4}) {
         d->nb = nb;
         d->ldp = (int)ceil_div(nb + d->kl, 32) * 32;
-        size_t s = (size_t)d->ldp * nb * es + (size_t)d->ldp * 4 + 16 * 32 * 4 * es;
+        size_t s = 2 * ((size_t)d->ldp * nb * es + (size_t)d->ldp * 4) + 16 * 32 * 4 * es;
         if (s <= limit) break;
         if (nb == 4) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory panels");
     }
-    for (int nbb : {32, 16, 8, 4}) {
-        d->nbb = nbb;
-        d->ldb = (int)ceil_div(nbb + ubw, 32) * 32;
-        size_t s = (size_t)d->ldb * nbb * es + 8 * 32 * 4 * es;
-        if (s <= limit) break;
-        if (nbb == 4) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
+    // backward blocks: prefer two staging buffers (copy-ahead), else one
+    d->bwd_nbuf = 0;
+    for (int nbuf : {2, 1}) {
+        for (int nbb : {32, 16, 8, 4}) {
+            d->nbb = nbb;
+            d->ldb = (int)ceil_div(nbb + ubw, 32) * 32;
+            size_t s = (size_t)nbuf * d->ldb * nbb * es + 8 * 32 * 4 * es + 32 * es;
+            if (s <= limit && (nbuf == 1 || nbb >= 8)) { d->bwd_nbuf = nbuf; break; }
+        }
+        if (d->bwd_nbuf) break;
+    }
+    if (!d->bwd_nbuf) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
+    {
+        const size_t one = (size_t)d->ldp * d->nb * es + (size_t)d->ldp * 4;
+        d->fwd_nbuf = (2 * one + 8 * 32 * 4 * es <= limit) ? 2 : 1;
     }
     d->npanels = (int)ceil_div(n, d->nb);
     return RSRR_OK;
