@@ -146,6 +146,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def job_value(points_per_rank, steps, ms_local, device=None):
+    """Whole-job throughput: all ranks' points over the slowest rank's time (max over ranks,
+    every rank gets the same answer).  Returns (value in points/s, max ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return points_per_rank * steps * world / (ms_max / 1e3), ms_max
+
+
 def run_ours(args):
     rank, world, local = dist_env()
     import torch
@@ -192,11 +206,7 @@ def run_ours(args):
     launches = rs.lib().rsrr_kernel_launches() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = prob.N * args.steps * world / (ms_max / 1e3)
+    value, ms_max = job_value(prob.N, args.steps, ms, device="cuda")
 
     # ---- dominant kernel and its roofline ------------------------------------------------------
     med = lambda k: statistics.median(i[k] for i in infos)
@@ -236,10 +246,8 @@ def run_ours(args):
             g.close()
         barrier()
         el = time.perf_counter() - t0
-        te = torch.tensor([el], device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": prob.N * args.steps * world / float(te.item()), "unit": UNIT,
+        e2e_value, _ = job_value(prob.N, args.steps, 1e3 * el, device="cuda")
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None

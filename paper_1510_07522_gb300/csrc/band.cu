@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kLuThreads) band_factor_kernel(FactorArgs<R> a
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a) {
-    constexpr int CG = BandTraits<R>::CG, CH = BandTraits<R>::CH;
+    constexpr int CG = SolveTraits<R>::CG, CH = SolveTraits<R>::CH;
     constexpr int NW = kSolveThreads / 32;
     const BandDims d = a.d;
     const int pt = blockIdx.x;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a)
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a) {
-    constexpr int CG = BandTraits<R>::CG, CH = BandTraits<R>::CH;
+    constexpr int CG = SolveTraits<R>::CG, CH = SolveTraits<R>::CH;
     constexpr int NW = kSolveThreads / 32;
     const BandDims d = a.d;
     const int pt = blockIdx.x;

@@ -59,9 +59,14 @@ struct SolveArgs {
 template <typename R> struct BandTraits;
 template <> struct BandTraits<float> { static constexpr int CG = 4; static constexpr int CH = 4; };
 template <> struct BandTraits<double> { static constexpr int CG = 2; static constexpr int CH = 4; };
+// The solves give each warp fewer right-hand-side columns (more warps share a block), which
+// shortens the per-block critical path of the serial triangular part.
+template <typename R> struct SolveTraits;
+template <> struct SolveTraits<float> { static constexpr int CG = 2; static constexpr int CH = 4; };
+template <> struct SolveTraits<double> { static constexpr int CG = 1; static constexpr int CH = 4; };
 
 constexpr int kLuThreads = 512;
-constexpr int kSolveThreads = 256;
+constexpr int kSolveThreads = 512;
 
 template <typename R>
 size_t factor_smem_bytes(const BandDims& d) {  // two panel buffers (look-ahead) + per-warp stash
@@ -71,12 +76,12 @@ size_t factor_smem_bytes(const BandDims& d) {  // two panel buffers (look-ahead)
 template <typename R>
 size_t fwd_smem_bytes(const BandDims& d, int nbuf) {
     return (size_t)nbuf * ((size_t)d.ldp * d.nb * sizeof(cplx<R>) + (size_t)d.ldp * sizeof(int)) +
-           (size_t)(kSolveThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
+           (size_t)(kSolveThreads / 32) * 32 * SolveTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 template <typename R>
 size_t bwd_smem_bytes(const BandDims& d, int nbuf) {
     return (size_t)nbuf * d.ldb * d.nbb * sizeof(cplx<R>) + (size_t)32 * sizeof(cplx<R>) +
-           (size_t)(kSolveThreads / 32) * 32 * BandTraits<R>::CG * sizeof(cplx<R>) + 64;
+           (size_t)(kSolveThreads / 32) * 32 * SolveTraits<R>::CG * sizeof(cplx<R>) + 64;
 }
 
 // Panel sizes for a band of (kl, ku) that fit the shared-memory budget.

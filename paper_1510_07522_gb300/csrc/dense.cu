@@ -13,13 +13,17 @@ namespace rsrr {
 // operands in shared memory so global traffic is (M + N) K / 64 elements per tile.
 // ---------------------------------------------------------------------------------------------
 namespace {
-constexpr int BM = 64, BN = 64, BK = 8;
+constexpr int BK = 8;
 
-template <int OPA, int OPB>
+// Tile BM x BN, 256 threads as TY x TX = (BM/4) x (BN/4), each owning a 4 x 4 grid of outputs
+// spaced TY rows and TX columns apart.  64 x 64 for general shapes, 32 x 128 when M <= 32.
+template <int OPA, int OPB, int BM, int BN>
 __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
+    constexpr int TY = BM / 4, TX = BN / 4;
+    static_assert(TX * TY == 256, "256 threads");
     __shared__ c128 As[BK][BM + 1];
     __shared__ c128 Bs[BK][BN + 1];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int bm = blockIdx.x * BM, bn = blockIdx.y * BN;
     const int bz = blockIdx.z, b = bz / g.ksplit, ks = bz % g.ksplit;
     const c128* A = g.A + b * g.sA;
@@ -33,7 +37,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
         for (int j = 0; j < 4; ++j) acc[i][j] = czero<double>();
     for (int k0 = k_begin; k0 < k_end; k0 += BK) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < BM * BK / 256; ++r) {
             const int idx = tid + 256 * r;
             int i, k;
             if (OPA == OP_N) { i = idx % BM; k = idx / BM; } else { k = idx % BK; i = idx / BK; }
@@ -44,13 +48,16 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
                 if (OPA == OP_C) v.im = -v.im;
             }
             As[k][i] = v;
-            int j;
+        }
+#pragma unroll
+        for (int r = 0; r < BN * BK / 256; ++r) {
+            const int idx = tid + 256 * r;
+            int j, k;
             if (OPB == OP_N) { k = idx % BK; j = idx / BK; } else { j = idx % BN; k = idx / BN; }
-            const int gj = bn + j;
-            const int gk2 = k0 + k;
+            const int gj = bn + j, gk = k0 + k;
             c128 w = czero<double>();
-            if (gj < g.N && gk2 < k_end) {
-                w = (OPB == OP_N) ? B[gk2 + (int64_t)gj * g.ldb] : B[gj + (int64_t)gk2 * g.ldb];
+            if (gj < g.N && gk < k_end) {
+                w = (OPB == OP_N) ? B[gk + (int64_t)gj * g.ldb] : B[gj + (int64_t)gk * g.ldb];
                 if (OPB == OP_C) w.im = -w.im;
             }
             Bs[k][j] = w;
@@ -60,9 +67,9 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
         for (int k = 0; k < BK; ++k) {
             c128 a[4], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty + TY * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[k][tx + TX * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -72,11 +79,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int gi = bm + ty + 16 * i;
+        const int gi = bm + ty + TY * i;
         if (gi >= g.M) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int gj = bn + tx + 16 * j;
+            const int gj = bn + tx + TX * j;
             if (gj >= g.N) continue;
             c128* c = C + gi + (int64_t)gj * g.ldc;
             const c128 v = g.alpha * acc[i][j];
@@ -102,16 +109,9 @@ __global__ void scale_kernel(c128* C, int M, int N, int64_t ldc, int64_t sC, c12
 }
 }  // namespace
 
-int zgemm(const Zgemm& g0, cudaStream_t s) {
-    Zgemm g = g0;
-    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return RSRR_OK;
+template <int BM, int BN>
+int zgemm_shape(Zgemm g, cudaStream_t s) {
     const int tm = (int)ceil_div(g.M, BM), tn = (int)ceil_div(g.N, BN);
-    if (g.K <= 0) {
-        dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
-        { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
-        RSRR_CUDA(cudaGetLastError());
-        return RSRR_OK;
-    }
     if (g.ksplit <= 0) {
         const int64_t tiles = (int64_t)tm * tn * g.batch;
         int ks = 1;
@@ -125,7 +125,7 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
         { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
     }
     dim3 grid(tm, tn, g.batch * g.ksplit);
-#define ZG(a, b) { zgemm_kernel<a, b><<<grid, 256, 0, s>>>(g, kchunk); note_launch(); }
+#define ZG(a, b) { zgemm_kernel<a, b, BM, BN><<<grid, 256, 0, s>>>(g, kchunk); note_launch(); }
     if (g.opA == OP_N && g.opB == OP_N) ZG(OP_N, OP_N)
     else if (g.opA == OP_N && g.opB == OP_T) ZG(OP_N, OP_T)
     else if (g.opA == OP_N && g.opB == OP_C) ZG(OP_N, OP_C)
@@ -137,6 +137,19 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
 #undef ZG
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
+}
+
+int zgemm(const Zgemm& g0, cudaStream_t s) {
+    Zgemm g = g0;
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return RSRR_OK;
+    if (g.K <= 0) {
+        dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
+        { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
+        RSRR_CUDA(cudaGetLastError());
+        return RSRR_OK;
+    }
+    if (g.M <= 32) return zgemm_shape<32, 128>(g, s);
+    return zgemm_shape<64, 64>(g, s);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -218,40 +231,41 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    // one CTA per column pair (CTAs loop over the pairs of a round), so every round spreads
+    // its FP64 work over all SMs
+    const int tid = threadIdx.x;
+    __shared__ double sh[4];
     for (int round = 0; round < a.npad - 1; ++round) {
-        for (int i = gw; i < a.npad / 2; i += nw) {
+        for (int i = blockIdx.x; i < a.npad / 2; i += gridDim.x) {
             int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
             if (p > q) { const int t = p; p = q; q = t; }
-            if (q >= a.kk) continue;
+            if (q >= a.kk) continue;  // uniform across the CTA
             c128* bp = a.B + (int64_t)p * a.mb;
             c128* bq = a.B + (int64_t)q * a.mb;
             double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-#pragma unroll 4
-            for (int r = lane; r < a.mb; r += 32) {
+#pragma unroll 2
+            for (int r = tid; r < a.mb; r += 256) {
                 const c128 x = bp[r], y = bq[r];
                 al += cnorm2(x);
                 be += cnorm2(y);
                 gr += x.re * y.re + x.im * y.im;  // conj(x) y
                 gi += x.re * y.im - x.im * y.re;
             }
-            al = warp_sum(al);
-            be = warp_sum(be);
-            gr = warp_sum(gr);
-            gi = warp_sum(gi);
+            al = block_sum_all(al);
+            be = block_sum_all(be);
+            gr = block_sum_all(gr);
+            gi = block_sum_all(gi);
             const double g = sqrt(gr * gr + gi * gi);
-            if (fmin(al, be) <= a.floor2 || g == 0.0) continue;
+            if (fmin(al, be) <= a.floor2 || g == 0.0) continue;  // uniform
             const double off = g / sqrt(al * be);
-            if (lane == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
-            if (off <= a.tol) continue;
+            if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
+            if (off <= a.tol) continue;  // uniform
             const c128 ph = mk<double>(gr / g, -gi / g);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
             const double zeta = (be - al) / (2.0 * g);
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-#pragma unroll 4
-            for (int r = lane; r < a.mb; r += 32) {
+#pragma unroll 2
+            for (int r = tid; r < a.mb; r += 256) {
                 const c128 x = bp[r], y = ph * bq[r];
                 bp[r] = cscale(x, c) - cscale(y, s);
                 bq[r] = cscale(x, s) + cscale(y, c);
@@ -259,22 +273,24 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             if (a.J) {
                 c128* jp = a.J + (int64_t)p * a.kk;
                 c128* jq = a.J + (int64_t)q * a.kk;
-#pragma unroll 4
-                for (int r = lane; r < a.kk; r += 32) {
+#pragma unroll 2
+                for (int r = tid; r < a.kk; r += 256) {
                     const c128 x = jp[r], y = ph * jq[r];
                     jp[r] = cscale(x, c) - cscale(y, s);
                     jq[r] = cscale(x, s) + cscale(y, c);
                 }
             }
-            if (lane == 0) atomicAdd(a.rotations, 1);
+            if (tid == 0) atomicAdd(a.rotations, 1);
+            __syncthreads();  // block_sum_all's shared slots are reused by the next pair
         }
         if (!grid_sync(a.gb)) return;
     }
+    (void)sh;
 }
 }  // namespace
 
 int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
-                         double abs_floor) {
+                         double abs_floor, double conv) {
     if (sweeps_out) *sweeps_out = 0;
     if (k < 2) return RSRR_OK;
     const int npad = k + (k & 1);
@@ -283,7 +299,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     RSRR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, 256, 0));
     if (occ < 1) return set_error(RSRR_ECUDA, "jacobi kernel cannot be resident");
-    const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 2), ceil_div(npad / 2, 8));
+    const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 4), npad / 2);
     unsigned long long* dmax = nullptr;
     int* drot = nullptr;
     unsigned* bar = nullptr;
@@ -310,9 +326,9 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         if (herr) { rc = set_error(RSRR_ETIMEOUT, "grid barrier gave up in the Jacobi sweep"); break; }
         double off;
         std::memcpy(&off, &hmax, 8);
-        // converged: no rotation left, or every pair above the floor orthogonal to 1e-12 (the
+        // converged: no rotation left, or every pair above the floor orthogonal to `conv` (the
         // remaining effect on the singular values is of second order in that number)
-        if (hrot == 0 || off <= 1e-12) { ++sweep; break; }
+        if (hrot == 0 || off <= conv) { ++sweep; break; }
     }
     dfree(dmax, s);
     dfree(drot, s);

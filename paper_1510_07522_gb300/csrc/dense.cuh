@@ -64,12 +64,12 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
         } else {
             long long spins = 0;
             while (*vgen == g) {
-                if (++spins > (1LL << 24)) {  // ~seconds: give up, report, return
+                if (++spins > (1LL << 24)) {  // bounded: give up, report, return
                     atomicExch(gb.err, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (spins > 4096) __nanosleep(32);  // tight polling first: barriers are short
             }
         }
         __threadfence();
@@ -82,10 +82,11 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
 
 // One-sided (Hestenes) Jacobi on the k columns of B (mb x k, ld mb), accumulating the
 // rotations into J (k x k, ld k, initialised to I by the caller when wanted; may be null).
-// On return the columns of B whose norms exceed abs_floor are mutually orthogonal to
-// working accuracy; columns below abs_floor are left as they are.
+// Sweeps stop once every pair of columns above abs_floor has |<b_p, b_q>| / (|b_p| |b_q|) <=
+// conv (singular values are then exact to second order in conv); columns below abs_floor are
+// not rotated.
 int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
-                         double abs_floor);
+                         double abs_floor, double conv);
 
 // Column 2-norms of B (mb x k) into out[k] (device).
 void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s);

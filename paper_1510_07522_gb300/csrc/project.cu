@@ -524,7 +524,9 @@ int project_run(rsrr_nep h, double delta) {
     TRYC(dalloc_n(&Jm, (size_t)kk * kk, st));
     { identity_kernel<<<(unsigned)ceil_div((int64_t)kk * kk, 256), 256, 0, st>>>(Jm, kk); note_launch(); }
     int sweeps = 0;
-    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 1e-2 * delta * sref));
+    // kept-subspace accuracy only needs the pairs across the truncation orthogonal; 1e-10 leaves
+    // singular values exact to ~1e-20 relative and subspace angles at ~1e-10
+    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 1e-2 * delta * sref, 1e-10));
     h->jacobi_sweeps_project = sweeps;
     h->rows_kept = kk;
     dfree(colnrm, st);

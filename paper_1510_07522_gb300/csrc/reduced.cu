@@ -461,7 +461,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         dfree(sig, st);
         sig = nullptr;
     }
-    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax));
+    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax, 1e-12));
     h->jacobi_sweeps_solve = sweeps;
     cudaEventRecord(ev[2], st);  // Hankel SVD done
     TRYC(dalloc_n(&sig, (size_t)D, st));

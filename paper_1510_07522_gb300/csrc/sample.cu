@@ -200,7 +200,7 @@ int pick_dims(int64_t n, int64_t kl, int64_t ku, bool is_c64, BandDims* d) {
         for (int nbb : {32, 16, 8, 4}) {
             d->nbb = nbb;
             d->ldb = (int)ceil_div(nbb + ubw, 32) * 32;
-            size_t s = (size_t)nbuf * d->ldb * nbb * es + 8 * 32 * 4 * es + 32 * es;
+            size_t s = (size_t)nbuf * d->ldb * nbb * es + 16 * 32 * 2 * es + 32 * es;
             if (s <= limit && (nbuf == 1 || nbb >= 8)) { d->bwd_nbuf = nbuf; break; }
         }
         if (d->bwd_nbuf) break;
@@ -208,7 +208,7 @@ int pick_dims(int64_t n, int64_t kl, int64_t ku, bool is_c64, BandDims* d) {
     if (!d->bwd_nbuf) return set_error(RSRR_EUNSUPPORTED, "band too wide for shared-memory blocks");
     {
         const size_t one = (size_t)d->ldp * d->nb * es + (size_t)d->ldp * 4;
-        d->fwd_nbuf = (2 * one + 8 * 32 * 4 * es <= limit) ? 2 : 1;
+        d->fwd_nbuf = (2 * one + 16 * 32 * 2 * es <= limit) ? 2 : 1;
     }
     d->npanels = (int)ceil_div(n, d->nb);
     return RSRR_OK;
