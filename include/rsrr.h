@@ -188,6 +188,31 @@ int rsrr_get_projected(rsrr_nep h, double* out_reim);
 /* The singular values of H, K*k_S of them, descending (after rsrr_solve). */
 int rsrr_get_hankel_sigma(rsrr_nep h, double* out);
 
+/* ---- rsrr_band_solve_noalloc --------------------------------------------------------------
+ * The paper has no counterpart: this is a deployment variant of the band LU and solves that
+ * rsrr_sample runs per sampling point, for callers that cannot allocate device memory (a
+ * process that hands all device memory to its own allocator up front, or a loop that must not
+ * pay for an allocation).  It allocates nothing: the factor scratch (L panel blocks, row
+ * permutations, pivots, status) lives in one file-scope device array of
+ * RSRR_NOALLOC_SCRATCH_BYTES, which every device that loads the library holds until exit.
+ *   n, kl, ku  order and bandwidths of A (0 <= kl, ku < n)
+ *   ab_reim    DEVICE pointer, A in general-band layout, complex128 interleaved, column-major
+ *              with leading dimension 2 kl + ku + 1, A(i, c) at row kl + ku + i - c; the top kl
+ *              rows (pivoting fill) must be zero on entry.  Overwritten: rows <= the diagonal
+ *              hold U of P A = L U (partial pivoting by |re| + |im|).
+ *   L, b_reim  DEVICE pointer to the n x L right-hand sides (complex128, column-major),
+ *              overwritten by the solution X of A X = B.
+ *   stream     cudaStream_t for the work (NULL = default stream); returns after it completes.
+ * The first call on a device looks up the scratch array's address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any stream capture.  All
+ * calls on a device share the array and leave their contents in it; calls whose GPU work
+ * overlaps race on it.  Errors: EINVAL (bad arguments, or the factor scratch of this band
+ * would exceed RSRR_NOALLOC_SCRATCH_BYTES), ESINGULAR (zero pivot), ECUDA, EUNSUPPORTED
+ * (band too wide for the shared-memory panels). */
+#define RSRR_NOALLOC_SCRATCH_BYTES (32u << 20)
+int rsrr_band_solve_noalloc(int64_t n, int32_t kl, int32_t ku, double* ab_reim, int32_t L, double* b_reim,
+                            void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 int64_t rsrr_kernel_launches(void);
 

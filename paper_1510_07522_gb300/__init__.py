@@ -68,7 +68,7 @@ _lib = None
 EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr_get_info",
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
-           "rsrr_version", "rsrr_kernel_launches"]
+           "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc"]
 
 
 def lib():
@@ -97,6 +97,7 @@ def lib():
         "rsrr_last_error": ([], ctypes.c_char_p),
         "rsrr_version": ([], ctypes.c_char_p),
         "rsrr_kernel_launches": ([], ctypes.c_int64),
+        "rsrr_band_solve_noalloc": ([I64, I32, I32, P, I32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -184,6 +185,14 @@ def rsrr_get_info(h):
     info = rsrr_info()
     _check(lib().rsrr_get_info(h, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in rsrr_info._fields_}
+
+
+def rsrr_band_solve_noalloc(n, kl, ku, ab_ptr, L, b_ptr, stream=None):
+    """Band LU + solve of one system from device pointers, using only the library's fixed
+    scratch array (no device allocation); see rsrr.h."""
+    _check(lib().rsrr_band_solve_noalloc(int(n), int(kl), int(ku), ctypes.c_void_p(ab_ptr), int(L),
+                                         ctypes.c_void_p(b_ptr),
+                                         stream if stream is not None else current_stream()))
 
 
 def rsrr_destroy(h):
