@@ -172,6 +172,8 @@ typedef struct {
     double ms_project_qr, ms_project_svd, ms_project_basis, ms_project_gemm;  /* rsrr_project parts */
     double ms_solve_inverse, ms_solve_svd, ms_solve_extract;  /* rsrr_solve parts: reduced inverses
                                    with moments and traces; Hankel SVD; count, eig, back-map */
+    double ms_zgemm;            /* device time of the FP64 complex GEMMs of the last project + solve */
+    double zgemm_gflop;         /* their algorithmic work, 8 M N K per product, in GFLOP          */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

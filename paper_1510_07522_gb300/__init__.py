@@ -61,7 +61,8 @@ class rsrr_info(ctypes.Structure):
                 ("ms_project_qr", ctypes.c_double), ("ms_project_svd", ctypes.c_double),
                 ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double),
                 ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
-                ("ms_solve_extract", ctypes.c_double)]
+                ("ms_solve_extract", ctypes.c_double), ("ms_zgemm", ctypes.c_double),
+                ("zgemm_gflop", ctypes.c_double)]
 
 
 _lib = None

@@ -241,6 +241,8 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->ms_solve_inverse = h->ms_solve_parts[0];
     o->ms_solve_svd = h->ms_solve_parts[1];
     o->ms_solve_extract = h->ms_solve_parts[2];
+    o->ms_zgemm = h->ms_zgemm_project + h->ms_zgemm_solve;
+    o->zgemm_gflop = (h->zgemm_flops_project + h->zgemm_flops_solve) * 1e-9;
     return RSRR_OK;
 }
 

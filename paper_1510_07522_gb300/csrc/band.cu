@@ -11,6 +11,8 @@
 //      in chunks, so registers do not grow with the bandwidth.
 // The forward solve reuses step B verbatim on the right-hand-side columns; the backward
 // solve runs the same routine in reversed row order with a non-unit diagonal.
+#include <cooperative_groups.h>
+
 #include "band.cuh"
 
 namespace rsrr {
@@ -348,6 +350,93 @@ __global__ void __launch_bounds__(kLuThreads) band_factor_kernel(FactorArgs<R> a
 }
 
 // ------------------------------------------------------------------------------------------
+// Cluster variant: two CTAs (one thread-block cluster) per sampling point, so a batch of N
+// points keeps 2N SMs busy.
+//   CTA 0: panel team (warps 0..3) + update team (warps 4..15), exactly as above; its update
+//          warps do the lead tasks (columns of the next panel) and a share of the rest.
+//   CTA 1: 16 update warps; at the start of each step it copies the finished panel block and
+//          its permutation from CTA 0's shared memory (distributed shared memory), then does
+//          the remaining share of the trailing columns.
+// Each step ends with a cluster barrier (release/acquire), which also orders both CTAs'
+// updates of the band in global memory before the next step reads them.  Every thread of
+// both CTAs reaches it exactly once per step and once after the prologue.
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kLuThreads) band_factor_cluster_kernel(FactorArgs<R> a) {
+    namespace cg = cooperative_groups;
+    constexpr int CG = BandTraits<R>::CG, CH = BandTraits<R>::CH;
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const BandDims d = a.d;
+    const int pt = blockIdx.x / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    cplx<R>* ab = a.ab + pt * a.ab_stride;
+    cplx<R>* lp = a.lp + pt * a.lp_stride;
+    int32_t* permg = a.perm + pt * a.perm_stride;
+    int32_t* ipiv = a.ipiv + (int64_t)pt * d.n;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int blk = d.ldp * d.nb;
+    cplx<R>* P = reinterpret_cast<cplx<R>*>(smem_raw);                 // [2][blk]
+    int* psm = reinterpret_cast<int*>(P + 2 * (size_t)blk);            // [2][ldp]
+    cplx<R>* ust = reinterpret_cast<cplx<R>*>(psm + 2 * (size_t)d.ldp);  // per update warp
+    __shared__ int s_piv;
+    __shared__ int s_info;
+    __shared__ cplx<R> s_pval;
+    if (tid == 0) s_info = 0;
+    __syncthreads();
+
+    const int kv = d.kv, ldab = d.ldab, ldp = d.ldp, nb = d.nb, n = d.n;
+    if (rank == 0 && warp < kPanelWarps) factor_panel<R>(a, ab, lp, permg, ipiv, 0, P, psm, &s_piv, &s_pval, &s_info);
+    cluster.sync();
+    for (int p = 0; p < d.npanels; ++p) {
+        const int k0 = p * nb;
+        const int nbe = min(nb, n - k0);
+        const int m = min(nb + d.kl, n - k0);
+        const int buf = p & 1;
+        const int cb = k0 + nbe, ce = min(n, k0 + nbe + kv);
+        const int ntask = max(0, (ce - cb + CG - 1) / CG);
+        const bool has_next = p + 1 < d.npanels;
+        const int nlead = has_next ? min(ntask, (nb + CG - 1) / CG) : 0;
+        const int rest = ntask - nlead;
+        const int n1 = (rest * 3) / 5;  // CTA 1's share of the non-lead columns
+        cplx<R>* Pb = P + (size_t)buf * blk;
+        int* pb = psm + (size_t)buf * ldp;
+        if (rank == 1) {
+            // copy panel p (block and permutation) from CTA 0's shared memory
+            const cplx<R>* rP = cluster.map_shared_rank(Pb, 0);
+            const int* rpb = cluster.map_shared_rank(pb, 0);
+            for (int idx = tid; idx < blk; idx += kLuThreads) Pb[idx] = rP[idx];
+            for (int q = tid; q < ldp; q += kLuThreads) pb[q] = rpb[q];
+            __syncthreads();
+            for (int task = nlead + warp; task < nlead + n1; task += kLuThreads / 32) {
+                TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
+                apply_block<R, CG, CH, true>(Pb, ldp, nbe, m, pb, nullptr, ust + warp * 32 * CG, acc, lane);
+            }
+        } else if (warp >= kPanelWarps) {
+            const int uw = warp - kPanelWarps;
+            for (int task = uw; task < nlead; task += kUpdateWarps) {
+                TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
+                apply_block<R, CG, CH, true>(Pb, ldp, nbe, m, pb, nullptr, ust + uw * 32 * CG, acc, lane);
+            }
+            __threadfence_block();
+            lead_arrive();
+            for (int task = nlead + n1 + uw; task < ntask; task += kUpdateWarps) {
+                TrailingCols<R, CG> acc{ab, ldab, kv, k0, cb + task * CG, ce};
+                apply_block<R, CG, CH, true>(Pb, ldp, nbe, m, pb, nullptr, ust + uw * 32 * CG, acc, lane);
+            }
+        } else {
+            lead_wait();
+            if (has_next)
+                factor_panel<R>(a, ab, lp, permg, ipiv, p + 1, P + (size_t)(buf ^ 1) * blk, psm + (size_t)(buf ^ 1) * ldp,
+                                &s_piv, &s_pval, &s_info);
+        }
+        cluster.sync();
+    }
+    if (rank == 0 && tid == 0) a.info[pt] = s_info;
+}
+
+// ------------------------------------------------------------------------------------------
 // Forward solve: X <- L^{-1} P X panel by panel, one CTA per point, one warp per CG columns.
 // The next panel's L block and permutation are staged with cp.async while the current one
 // is applied (two buffers when they fit in shared memory).
@@ -357,12 +446,14 @@ __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a)
     constexpr int CG = SolveTraits<R>::CG, CH = SolveTraits<R>::CH;
     constexpr int NW = kSolveThreads / 32;
     const BandDims d = a.d;
-    const int pt = blockIdx.x;
+    const int pt = blockIdx.x / a.split, part = blockIdx.x % a.split;
     if (a.active && !a.active[pt]) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const cplx<R>* lp = a.lp + pt * a.lp_stride;
     const int32_t* permg = a.perm + pt * a.perm_stride;
-    cplx<R>* x = a.x + pt * a.x_stride;
+    const int c_lo = (int)((int64_t)a.L * part / a.split), c_hi = (int)((int64_t)a.L * (part + 1) / a.split);
+    cplx<R>* x = a.x + pt * a.x_stride + (int64_t)c_lo * d.n;
+    const int Lp = c_hi - c_lo;
     const int ldp = d.ldp, nb = d.nb, n = d.n, nbuf = d.fwd_nbuf;
     const int blk = ldp * nb;
 
@@ -380,7 +471,7 @@ __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a)
         for (int c = tid; c < ldp / 4; c += kSolveThreads) cp_async_16(pd + 16 * c, ps + 16 * c, 16);
         cp_async_commit();
     };
-    const int ntask = (a.L + CG - 1) / CG;
+    const int ntask = (Lp + CG - 1) / CG;
     stage(0, 0);
     for (int p = 0; p < d.npanels; ++p) {
         const int k0 = p * nb;
@@ -396,7 +487,7 @@ __global__ void __launch_bounds__(kSolveThreads) band_fwd_kernel(SolveArgs<R> a)
         __syncthreads();
         const int buf = nbuf == 2 ? (p & 1) : 0;
         for (int task = warp; task < ntask; task += NW) {
-            RhsCols<R, CG> acc{x, n, a.L, task * CG, k0, +1};
+            RhsCols<R, CG> acc{x, n, Lp, task * CG, k0, +1};
             apply_block<R, CG, CH, true>(P + (size_t)buf * blk, ldp, nbe, m, psm + (size_t)buf * ldp, nullptr,
                                          ust + warp * 32 * CG, acc, lane);
         }
@@ -416,11 +507,13 @@ __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a)
     constexpr int CG = SolveTraits<R>::CG, CH = SolveTraits<R>::CH;
     constexpr int NW = kSolveThreads / 32;
     const BandDims d = a.d;
-    const int pt = blockIdx.x;
+    const int pt = blockIdx.x / a.split, part = blockIdx.x % a.split;
     if (a.active && !a.active[pt]) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const cplx<R>* ab = a.ab + pt * a.ab_stride;
-    cplx<R>* x = a.x + pt * a.x_stride;
+    const int c_lo = (int)((int64_t)a.L * part / a.split), c_hi = (int)((int64_t)a.L * (part + 1) / a.split);
+    cplx<R>* x = a.x + pt * a.x_stride + (int64_t)c_lo * d.n;
+    const int Lp = c_hi - c_lo;
     const int ldb = d.ldb, nbb = d.nbb, n = d.n, kv = d.kv, ldab = d.ldab, nbuf = d.bwd_nbuf;
     const int blk = ldb * nbb;
 
@@ -444,7 +537,7 @@ __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a)
         }
         cp_async_commit();
     };
-    const int ntask = (a.L + CG - 1) / CG;
+    const int ntask = (Lp + CG - 1) / CG;
     stage(nblk - 1, 0);
     for (int bk = nblk - 1, it = 0; bk >= 0; --bk, ++it) {
         const int k0 = bk * nbb;
@@ -464,7 +557,7 @@ __global__ void __launch_bounds__(kSolveThreads) band_bwd_kernel(SolveArgs<R> a)
         for (int t = tid; t < nbe; t += kSolveThreads) invd[t] = crecip(U[t + t * ldb]);
         __syncthreads();
         for (int task = warp; task < ntask; task += NW) {
-            RhsCols<R, CG> acc{x, n, a.L, task * CG, top, -1};
+            RhsCols<R, CG> acc{x, n, Lp, task * CG, top, -1};
             apply_block<R, CG, CH, false>(U, ldb, nbe, m, nullptr, invd, ust + warp * 32 * CG, acc, lane);
         }
         __syncthreads();
@@ -496,9 +589,39 @@ int set_smem(K kernel, size_t sm, const char* name) {
 }
 }  // namespace
 
+// CTAs per point for the solves: two when the doubled grid still fits one wave, so the
+// right-hand-side columns of a point are shared by two SMs.
+int solve_split(int npts, int L) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return (L >= 2 && 2 * npts <= nsm) ? 2 : 1;
+}
+
 template <typename R>
 int launch_factor(const FactorArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = factor_smem_bytes<R>(a.d);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (2 * npts <= nsm) {  // few points: two SMs per point
+        RSRR_TRY(set_smem(band_factor_cluster_kernel<R>, sm, "band_factor_cluster_kernel"));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * npts, 1, 1);
+        cfg.blockDim = dim3(kLuThreads, 1, 1);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        RSRR_CUDA(cudaLaunchKernelEx(&cfg, band_factor_cluster_kernel<R>, a));
+        note_launch();
+        return RSRR_OK;
+    }
     RSRR_TRY(set_smem(band_factor_kernel<R>, sm, "band_factor_kernel"));
     { band_factor_kernel<R><<<npts, kLuThreads, sm, s>>>(a); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
@@ -509,7 +632,9 @@ template <typename R>
 int launch_fwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = fwd_smem_bytes<R>(a.d, a.d.fwd_nbuf);
     RSRR_TRY(set_smem(band_fwd_kernel<R>, sm, "band_fwd_kernel"));
-    { band_fwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
+    SolveArgs<R> b = a;
+    b.split = solve_split(npts, a.L);
+    { band_fwd_kernel<R><<<npts * b.split, kSolveThreads, sm, s>>>(b); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
@@ -518,7 +643,9 @@ template <typename R>
 int launch_bwd(const SolveArgs<R>& a, int npts, cudaStream_t s) {
     const size_t sm = bwd_smem_bytes<R>(a.d, a.d.bwd_nbuf);
     RSRR_TRY(set_smem(band_bwd_kernel<R>, sm, "band_bwd_kernel"));
-    { band_bwd_kernel<R><<<npts, kSolveThreads, sm, s>>>(a); note_launch(); }
+    SolveArgs<R> b = a;
+    b.split = solve_split(npts, a.L);
+    { band_bwd_kernel<R><<<npts * b.split, kSolveThreads, sm, s>>>(b); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }

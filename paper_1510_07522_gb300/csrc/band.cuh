@@ -54,6 +54,7 @@ struct SolveArgs {
     int64_t x_stride;
     int L;
     const int32_t* active;  // [pts] 0 = skip this point (already converged); may be null
+    int split = 1;          // CTAs per point; CTA r of a point takes a contiguous share of the columns
 };
 
 template <typename R> struct BandTraits;
@@ -62,7 +63,7 @@ template <> struct BandTraits<double> { static constexpr int CG = 2; static cons
 // The solves give each warp fewer right-hand-side columns (more warps share a block), which
 // shortens the per-block critical path of the serial triangular part.
 template <typename R> struct SolveTraits;
-template <> struct SolveTraits<float> { static constexpr int CG = 2; static constexpr int CH = 4; };
+template <> struct SolveTraits<float> { static constexpr int CG = 1; static constexpr int CH = 4; };
 template <> struct SolveTraits<double> { static constexpr int CG = 1; static constexpr int CH = 4; };
 
 constexpr int kLuThreads = 512;

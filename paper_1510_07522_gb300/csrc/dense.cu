@@ -139,7 +139,55 @@ int zgemm_shape(Zgemm g, cudaStream_t s) {
     return RSRR_OK;
 }
 
+// ZGEMM accounting for the calling host thread: device time (events around each call) and
+// algorithmic flops 8 M N K per product, between zgemm_profile_begin and zgemm_profile_end.
+namespace {
+struct ZgemmProfile {
+    bool on = false;
+    double flops = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+};
+thread_local ZgemmProfile g_zprof;
+}  // namespace
+
+void zgemm_profile_begin() {
+    g_zprof.on = true;
+    g_zprof.flops = 0.0;
+    g_zprof.ev.clear();
+}
+
+void zgemm_profile_end(double* ms, double* flops) {
+    double t = 0.0;
+    for (auto& e : g_zprof.ev) {
+        float x = 0.f;
+        cudaEventSynchronize(e.second);
+        cudaEventElapsedTime(&x, e.first, e.second);
+        t += x;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    g_zprof.ev.clear();
+    g_zprof.on = false;
+    *ms = t;
+    *flops = g_zprof.flops;
+}
+
+static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s);
+
 int zgemm(const Zgemm& g0, cudaStream_t s) {
+    if (!g_zprof.on || g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.batch <= 0) return zgemm_dispatch(g0, s);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    const int rc = zgemm_dispatch(g0, s);
+    cudaEventRecord(b, s);
+    g_zprof.ev.emplace_back(a, b);
+    g_zprof.flops += 8.0 * g0.M * (double)g0.N * g0.K * g0.batch;
+    return rc;
+}
+
+static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s) {
     Zgemm g = g0;
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return RSRR_OK;
     if (g.K <= 0) {
@@ -219,7 +267,7 @@ struct JacobiArgs {
     c128* B;
     int mb, kk, npad;
     c128* J;
-    double tol, floor2;
+    double tol, floor2, abs_g;
     unsigned long long* max_off;
     int* rotations;
     GridBar gb;
@@ -256,7 +304,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             gr = block_sum_all(gr);
             gi = block_sum_all(gi);
             const double g = sqrt(gr * gr + gi * gi);
-            if (fmin(al, be) <= a.floor2 || g == 0.0) continue;  // uniform
+            if (fmin(al, be) <= a.floor2 || g <= a.abs_g) continue;  // uniform
             const double off = g / sqrt(al * be);
             if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
             if (off <= a.tol) continue;  // uniform
@@ -290,7 +338,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
 }  // namespace
 
 int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
-                         double abs_floor, double conv) {
+                         double abs_floor, double conv, double abs_inner) {
     if (sweeps_out) *sweeps_out = 0;
     if (k < 2) return RSRR_OK;
     const int npad = k + (k & 1);
@@ -307,7 +355,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     RSRR_TRY(dalloc_n(&drot, 1, s));
     RSRR_TRY(dalloc_n(&bar, 4, s));
     cudaMemsetAsync(bar, 0, 16, s);
-    JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor,
+    JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
                   dmax, drot, GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2)}};
     int sweep = 0, rc = RSRR_OK;
     for (; sweep < max_sweeps; ++sweep) {

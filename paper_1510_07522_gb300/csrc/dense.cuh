@@ -24,6 +24,9 @@ struct Zgemm {
     int ksplit = 0;  // 0 = choose
 };
 int zgemm(const Zgemm& g, cudaStream_t s);
+// Accounting of the ZGEMMs issued by this host thread between the two calls.
+void zgemm_profile_begin();
+void zgemm_profile_end(double* ms, double* flops);
 
 // Sum of v over a CTA (blockDim a multiple of 32, <= 1024); every thread gets the result.
 __device__ __forceinline__ double block_sum_all(double v) {
@@ -84,9 +87,9 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
 // rotations into J (k x k, ld k, initialised to I by the caller when wanted; may be null).
 // Sweeps stop once every pair of columns above abs_floor has |<b_p, b_q>| / (|b_p| |b_q|) <=
 // conv (singular values are then exact to second order in conv); columns below abs_floor are
-// not rotated.
+// not rotated, nor are pairs with |<b_p, b_q>| <= abs_inner (absolute).
 int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int max_sweeps, int* sweeps_out,
-                         double abs_floor, double conv);
+                         double abs_floor, double conv, double abs_inner);
 
 // Column 2-norms of B (mb x k) into out[k] (device).
 void column_norms(const c128* B, int mb, int k, int64_t ld, double* out, cudaStream_t s);

@@ -84,5 +84,6 @@ struct rsrr_nep_s {
     int32_t rows_kept = 0, jacobi_sweeps_project = 0, jacobi_sweeps_solve = 0;
     double ms_project_parts[4] = {0, 0, 0, 0};
     double ms_solve_parts[3] = {0, 0, 0};
+    double ms_zgemm_project = 0, zgemm_flops_project = 0, ms_zgemm_solve = 0, zgemm_flops_solve = 0;
     int64_t device_bytes = 0;
 };

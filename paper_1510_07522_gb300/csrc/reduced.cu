@@ -324,6 +324,8 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]); } } evg{ev};
     cudaEventRecord(ev[0], st);
     for (double& x : h->ms_solve_parts) x = 0.0;
+    zgemm_profile_begin();
+    struct ZpGuard { rsrr_nep h; ~ZpGuard() { zgemm_profile_end(&h->ms_zgemm_solve, &h->zgemm_flops_solve); } } zpg{h};
     const int k = h->kS, J = h->J;
     const int64_t n = h->n;
     *nC_out = 0;
@@ -461,7 +463,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         dfree(sig, st);
         sig = nullptr;
     }
-    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax, 1e-12));
+    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax, 1e-12, 0.0));
     h->jacobi_sweeps_solve = sweeps;
     cudaEventRecord(ev[2], st);  // Hankel SVD done
     TRYC(dalloc_n(&sig, (size_t)D, st));
