@@ -28,9 +28,24 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="damped quadratic NEP K + zC + z^2 M, 200x200 grid (n=40000, band 200), "
-                         "ellipse (-0.5+40i; a=2, b=30), N=64, L=32",
-                n=40000, band=200, N=64, L=32, N_S=500, K=2, delta=1e-14)
+WORKLOADS = {
+    "1": dict(workload="damped quadratic NEP K + zC + z^2 M, 200x200 grid (n=40000, band 200), "
+                       "ellipse (-0.5+40i; a=2, b=30), N=64, L=32",
+              n=40000, band=200, N=64, L=32, N_S=500, K=2, delta=1e-14, precision="c64",
+              data="synthetic (seeded generator: grid Laplacian K, lumped M = 1 + 0.1 U(0,1), C = 0.05K + 0.02M)"),
+    "0": dict(workload="gun-like sqrt NEP K - zM + i sqrt(z - s1^2) W1 + i sqrt(z - s2^2) W2, 30x30 grid "
+                       "(n=900, band 30), circle (250; 150), N=32, L=16",
+              n=900, band=30, N=32, L=16, N_S=500, K=2, delta=1e-14, precision="fp64",
+              data="synthetic (seeded generator: grid Laplacian K, M = I, boundary masks W1, W2)"),
+    "2": dict(workload="gun-like sqrt NEP, 400x250 grid (n=100000, band 250), circle (330; 300), N=64, L=48",
+              n=100000, band=250, N=64, L=48, N_S=500, K=2, delta=1e-14, precision="c64",
+              data="synthetic (seeded generator: grid Laplacian K, M = I, boundary masks W1, W2)"),
+    "3": dict(workload="batch of time-delay NEPs -zI + A0 + A1 exp(-tau z): A0 the s x s grid Laplacian, "
+                       "s ~ U{20..100} (n 400..10000), A1 5% random (dense LU), own circle each, N=32, L=8",
+              batch=32, N=32, L=8, N_S=500, K=2, delta=1e-14, precision="c64",
+              data="synthetic (seeded generator: the first members of the 256-NEP time-delay batch)"),
+}
+WORKLOAD = WORKLOADS["1"]
 METRIC = "resolvent samples/sec (LU+L-RHS solve, resid<=1e-10), full RSRR pass"
 UNIT = "samples/s"
 FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
@@ -43,9 +58,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="c64", choices=["c64", "fp64"])
+    ap.add_argument("--config", default="1", choices=sorted(WORKLOADS) + ["serve"],
+                    help="1 = the benchmark workload; 0 and 2 the smaller and larger sqrt NEPs; serve = "
+                         "Poisson request stream through the continuous-batching server")
+    ap.add_argument("--precision", default=None, choices=["c64", "fp64"], help="default: the config's own")
     ap.add_argument("--tol", type=float, default=1e-10, help="acceptance: eta <= tol per column")
-    ap.add_argument("--grid", type=int, default=200, help="grid side (200 = the benchmark workload)")
+    ap.add_argument("--grid", type=int, default=0, help="grid side override (0 = the config's own size)")
+    ap.add_argument("--rates", default="1,4,16", help="serve: Poisson arrival rates, requests/s")
+    ap.add_argument("--requests", type=int, default=12, help="serve: requests per rate")
+    ap.add_argument("--batch", type=int, default=0, help="config 3: members of the batch (0 = the config's own)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="points in the CPU baseline sample (0 = cores)")
@@ -99,9 +120,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def workload(grid):
+def workload(config, grid=0):
     import workloads
-    return workloads.config1(s=grid)
+    if config == "0":
+        return workloads.config0(nx=grid, ny=grid) if grid else workloads.config0()
+    if config == "2":
+        return workloads.config2(nx=2 * grid, ny=grid) if grid else workloads.config2()
+    return workloads.config1(s=grid) if grid else workloads.config1()
 
 
 def fns_of(p):
@@ -125,7 +150,12 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    prob = workload(args.grid)
+    if args.config == "serve":
+        print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no oracle arm; the oracle "
+                                                              "arm times configs 0-2"}), flush=True)
+        return
+    W = WORKLOADS[args.config]
+    prob = workload(args.config, args.grid)
     cores = os.cpu_count() or 1
     npts = args.cpu_points or min(prob.N, cores)
     import oracle
@@ -141,7 +171,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, parallelism="cpu threads"),
+            "data": "synthetic", "config": dict(W, parallelism="cpu threads"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -169,8 +199,10 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prob = workload(args.grid)
-    prec = (rs.RSRR_C64_IR if args.precision == "c64" else rs.RSRR_FP64) | rs.RSRR_REFINE_FULL
+    W = WORKLOADS[args.config]
+    prob = workload(args.config, args.grid)
+    precision = args.precision or W["precision"]
+    prec = (rs.RSRR_C64_IR if precision == "c64" else rs.RSRR_FP64) | rs.RSRR_REFINE_FULL
     stream = torch.cuda.current_stream()
     sp = __import__("ctypes").c_void_p(stream.cuda_stream)
 
@@ -184,8 +216,8 @@ def run_ours(args):
 
     def step(U):
         h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, U, prec, args.tol, 20)
-        h.project(WORKLOAD["delta"])
-        lam, V, res = h.solve(WORKLOAD["N_S"], WORKLOAD["K"], 1e3, 4096, True)
+        h.project(W["delta"])
+        lam, V, res = h.solve(W["N_S"], W["K"], 1e3, 4096, True)
         return h.info(), lam
 
     step(prob.U)
@@ -196,16 +228,22 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     l0 = rs.lib().rsrr_kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # Inputs smaller than L2 (config 0) get an L2 flush between steps, outside the timed events.
+    flush = None
+    if prob.n * prob.N * prob.L * 16 < 2 * 129e6:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos = []
-    e0.record(stream)
-    for _ in range(args.steps):
+    for e0, e1 in evs:
+        if flush is not None:
+            flush.random_(0, 255)
+        e0.record(stream)
         info, lam = step(None)
+        e1.record(stream)
         infos.append(info)
-    e1.record(stream)
     barrier()
     launches = rs.lib().rsrr_kernel_launches() - l0
-    ms = e0.elapsed_time(e1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     clk = clocks.stop()
     value, ms_max = job_value(prob.N, args.steps, ms, device="cuda")
 
@@ -222,10 +260,13 @@ def run_ours(args):
     flops_launch = flops_per_point * prob.N / max(1, infos[-1]["factor_launches"])
     fac_ms_launch = phases["factor_ms"] / max(1, infos[-1]["factor_launches"])
     achieved = flops_launch / (fac_ms_launch / 1e3) / 1e12 if fac_ms_launch > 0 else None
-    roof_lu = {"kernel": "band_factor_kernel<float> (complex64 band LU, CUDA-core FFMA)", "bound": "alu",
-               "achieved": achieved, "peak": FFMA_PEAK_TFLOPS, "unit": "TFLOP/s",
-               "frac": (achieved / FFMA_PEAK_TFLOPS) if achieved else None, "traffic": None,
-               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (no FP32 figure in the measured peaks)",
+    lu_peak = FFMA_PEAK_TFLOPS if precision == "c64" else FP64_PEAK_TFLOPS
+    roof_lu = {"kernel": "band_factor_kernel<%s> (%s band LU, CUDA cores)" % (
+                   ("float", "complex64") if precision == "c64" else ("double", "complex128")), "bound": "alu",
+               "achieved": achieved, "peak": lu_peak, "unit": "TFLOP/s",
+               "frac": (achieved / lu_peak) if achieved else None, "traffic": None,
+               "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (no FP32 figure in the "
+                               "measured peaks)") if precision == "c64" else "nominal FP64 rate (measured 1.19)",
                "algorithmic": f"8 n kl (kl+ku) real flops per point x {prob.N} points per launch",
                "ms_per_step": phases["factor_ms"], "ms_per_launch": fac_ms_launch}
     zg_ms = statistics.median(i["ms_zgemm"] for i in infos)
@@ -250,8 +291,8 @@ def run_ours(args):
         for _ in range(args.steps):
             g = rs.Nep(prob.n, rowptr, colind, vals, fns_of(prob), 0, sp)
             g.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, U, prec, args.tol, 20)
-            g.project(WORKLOAD["delta"])
-            lam, V, res = g.solve(WORKLOAD["N_S"], WORKLOAD["K"], 1e3, 4096, True)
+            g.project(W["delta"])
+            lam, V, res = g.solve(W["N_S"], W["K"], 1e3, 4096, True)
             d2h = lam.nbytes + (V.nbytes if V is not None else 0) + res.nbytes
             g.close()
         barrier()
@@ -273,11 +314,14 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "c64+f64" if args.precision == "c64" else "c128",
-                "data": "synthetic (seeded generator: grid Laplacian K, lumped M = 1 + 0.1 U(0,1), C = 0.05K + 0.02M)",
-                "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
-                               tol=args.tol, precision=args.precision, refine="to working accuracy",
-                               l2="inputs larger than L2 (factors 12 GB, S_hat 1.3 GB per step)"),
+                "dtype": "c64+f64" if precision == "c64" else "c128",
+                "data": W["data"],
+                "config": dict({k: v for k, v in W.items() if k != "data"},
+                               parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                               tol=args.tol, precision=precision, refine="to working accuracy",
+                               n=prob.n, N=prob.N, L=prob.L,
+                               l2="inputs larger than L2" if flush is None else
+                                  "L2 flushed between steps (256 MB write outside the timed events)"),
                 "phases_ms_median": phases, "k_S": infos[-1]["k_S"], "refine_sweeps": infos[-1]["refine_sweeps"],
                 "rows_kept": infos[-1]["rows_kept"],
                 "jacobi_sweeps": [infos[-1]["jacobi_sweeps_project"], infos[-1]["jacobi_sweeps_solve"]],
@@ -287,6 +331,239 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def batch_members(count):
+    import workloads
+    return [workloads.config3_member(i) for i in range(count)]
+
+
+def dense_lu_flops(n):
+    return 8.0 / 3.0 * float(n) ** 3
+
+
+def cpu_dense_rate(probs, seconds=15.0):
+    """The oracle's dense LU solves on the host cores, on points of the smallest members until
+    about `seconds` of work: flop rate, converted to samples/s at the batch's flop mix."""
+    import oracle
+    cores = os.cpu_count() or 1
+    small = sorted(probs, key=lambda p: p.n)
+    done_flops, t0, npts = 0.0, time.perf_counter(), 0
+    for p in small:
+        pts = list(range(min(p.N, cores)))
+        oracle.sample(p, points=pts, threads=cores, dense=True)
+        done_flops += len(pts) * dense_lu_flops(p.n)
+        npts += len(pts)
+        if time.perf_counter() - t0 > seconds:
+            break
+    el = time.perf_counter() - t0
+    rate = done_flops / el
+    mean_flops = sum(p.N * dense_lu_flops(p.n) for p in probs) / sum(p.N for p in probs)
+    return rate / mean_flops, cores, (f"oracle dense LU + L-column solves on {npts} points of the smallest members "
+                                      f"({el:.1f} s, {rate / 1e9:.2f} GFLOP/s), converted to samples/s at the batch's "
+                                      f"mean (8/3) n^3 per point")
+
+
+def run_batch(args):
+    """Config 3: one rsrr_sample_batch over all members (dense LU, persistent launches), then
+    rsrr_project and rsrr_solve per member."""
+    rank, world, local = dist_env()
+    import ctypes
+    import torch
+    import paper_1510_07522_gb300 as rs
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS["3"]
+    B = args.batch or W["batch"]
+    probs = batch_members(B)
+    precision = args.precision or W["precision"]
+    prec = (rs.RSRR_C64_IR if precision == "c64" else rs.RSRR_FP64) | rs.RSRR_REFINE_FULL
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    hs = [rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, sp) for p in probs]
+    contours = [(p.gamma, p.a, p.b) for p in probs]
+    Ns, Ls = [p.N for p in probs], [p.L for p in probs]
+
+    def step(Us):
+        rs.sample_batch(hs, contours, Ns, Ls, Us, prec, args.tol, 20)
+        counts = []
+        for h in hs:
+            h.project(W["delta"])
+            lam, _, _ = h.solve(W["N_S"], W["K"], 1e3, 4096, False)
+            counts.append(int(lam.size))
+        return counts
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    step([p.U for p in probs])
+    for _ in range(args.warmup - 1):
+        step(None)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = rs.lib().rsrr_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    for e0, e1 in evs:
+        e0.record(stream)
+        counts = step(None)
+        e1.record(stream)
+        infos.append([h.info() for h in hs])
+    barrier()
+    launches = rs.lib().rsrr_kernel_launches() - l0
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    clk = clocks.stop()
+    points = sum(Ns)
+    value, ms_max = job_value(points, args.steps, ms, device="cuda")
+    med = lambda key: statistics.median(sum(i[key] for i in step_infos) for step_infos in infos)
+    fac_ms = statistics.median(step_infos[0]["ms_factor"] for step_infos in infos)
+    launches_f = infos[-1][0]["factor_launches"]
+    flops = sum(p.N * dense_lu_flops(p.n) for p in probs)
+    achieved = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
+    roof = {"kernel": "dense_factor_kernel<%s> (persistent dense LU, one CTA per point)" % (
+                "float" if precision == "c64" else "double"), "bound": "alu",
+            "achieved": achieved, "peak": FFMA_PEAK_TFLOPS if precision == "c64" else FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if precision == "c64"
+                           else "nominal FP64 rate (measured 1.19)",
+            "algorithmic": f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
+            "ms_per_step": fac_ms}
+    roof["frac"] = achieved / roof["peak"] if achieved else None
+    phases = {"sample_ms": statistics.median(step_infos[0]["ms_sample"] for step_infos in infos),
+              "factor_ms": fac_ms,
+              "trsv_ms": statistics.median(step_infos[0]["ms_trsv"] for step_infos in infos),
+              "project_ms": med("ms_project"), "solve_ms": med("ms_solve")}
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: _pinned(torch, a)
+        host = [(pin(p.rowptr), pin(p.colind), pin(p.vals), pin(np.asfortranarray(p.U))) for p in probs]
+        h2d = sum(sum(x.nbytes for x in t) for t in host)
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            gs = [rs.Nep(p.n, t[0], t[1], t[2], fns_of(p), 0, sp) for p, t in zip(probs, host)]
+            rs.sample_batch(gs, contours, Ns, Ls, [t[3] for t in host], prec, args.tol, 20)
+            d2h = 0
+            for g in gs:
+                g.project(W["delta"])
+                lam, V, res = g.solve(W["N_S"], W["K"], 1e3, 4096, True)
+                d2h += lam.nbytes + V.nbytes + res.nbytes
+                g.close()
+        barrier()
+        e2e_value, _ = job_value(points, args.steps, 1e3 * (time.perf_counter() - t0), device="cuda")
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sample = cpu_dense_rate(probs)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    for h in hs:
+        h.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if precision == "c64" else "c128",
+                "data": W["data"],
+                "config": dict({k: v for k, v in W.items() if k != "data"}, batch=B, precision=precision,
+                               n_range=[min(p.n for p in probs), max(p.n for p in probs)],
+                               parallelism=f"replicas x{world}" if world > 1 else "1 GPU", tol=args.tol,
+                               l2="inputs larger than L2 (dense factors of GBs per step)"),
+                "phases_ms_median": phases, "eigs_inside": counts,
+                "max_eta": max(i["max_eta"] for step_infos in infos for i in step_infos),
+                "refine_sweeps": max(i["refine_sweeps"] for i in infos[-1]),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+SERVE_TYPES = ("0", "1", "2", "3")
+
+
+def serve_requests(serve, count, seed, precision_flags):
+    """`count` requests with types drawn uniformly from configs 0, 1, 2 and single members of the
+    time-delay batch (seeded), each with the config's own contour, N, L and probing block."""
+    import workloads
+    rng = np.random.default_rng([4, seed])
+    out = []
+    cache = {}
+    for i in range(count):
+        t = SERVE_TYPES[int(rng.integers(0, len(SERVE_TYPES)))]
+        if t == "3":
+            p = workloads.config3_member(int(rng.integers(0, 256)), s=int(rng.integers(20, 41)))
+        else:
+            if t not in cache:
+                cache[t] = workload(t)
+            p = cache[t]
+        prec = precision_flags(t)
+        out.append(serve.Request(rid=i, n=p.n, rowptr=p.rowptr, colind=p.colind, vals=p.vals, fns=fns_of(p),
+                                 gamma=p.gamma, a=p.a, b=p.b, N=p.N, L=p.L, U=p.U, precision=prec,
+                                 N_S=500, K=2))
+        out[-1].tag = t
+    return out
+
+
+def run_serve(args):
+    """Config 4: Poisson request streams through the continuous-batching server, then the same
+    requests one at a time in plain FP64 (the per-request path it is compared against)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_1510_07522_gb300 as rs
+    from paper_1510_07522_gb300 import serve
+    torch.cuda.set_device(local)
+    mixed = lambda t: (rs.RSRR_FP64 if t == "0" else rs.RSRR_C64_IR) | rs.RSRR_REFINE_FULL
+    plain = lambda t: rs.RSRR_FP64 | rs.RSRR_REFINE_FULL
+    rates = [float(r) for r in args.rates.split(",")]
+    # warm-up: one request of each type through a one-slot server
+    warm = serve.Server(budget_bytes=150e9, slots=1)
+    serve.replay(warm, serve_requests(serve, 4, 99, mixed), [0.0] * 4)
+    warm.close()
+    l0 = rs.lib().rsrr_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per_rate = []
+    for k, rate in enumerate(rates):
+        reqs = serve_requests(serve, args.requests, k, mixed)
+        srv = serve.Server(budget_bytes=150e9, slots=4)
+        t0 = time.perf_counter()
+        done = serve.replay(srv, reqs, serve.poisson_arrivals(rate, len(reqs), seed=1))
+        wall = time.perf_counter() - t0
+        srv.close()
+        st = serve.latency_stats(done)
+        st.update(rate=rate, wall_s=wall, peak_inflight=srv.peak_inflight,
+                  errors=sorted({r.error for r in done if r.error}),
+                  by_type={t: sum(1 for r in done if r.tag == t) for t in SERVE_TYPES})
+        per_rate.append(st)
+    # the plain FP64 per-request path: the last rate's requests, one at a time, no overlap
+    reqs = serve_requests(serve, args.requests, len(rates) - 1, plain)
+    srv = serve.Server(budget_bytes=150e9, slots=1)
+    done = serve.replay(srv, reqs, serve.poisson_arrivals(rates[-1], len(reqs), seed=1))
+    srv.close()
+    fp64 = serve.latency_stats(done)
+    fp64.update(rate=rates[-1], errors=sorted({r.error for r in done if r.error}))
+    clk = clocks.stop()
+    launches = rs.lib().rsrr_kernel_launches() - l0
+    top = per_rate[-1]
+    line = {"metric": "NEPs/s and p50/p99 latency, Poisson stream of mixed NEPs (continuous batching)",
+            "value": top["neps_per_s"], "unit": "NEPs/s", "n_gpus": 1, "steps": len(rates), "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64 (config 0 requests c128)", "data": "synthetic (seeded generators of configs 0-3)",
+            "config": {"workload": "serving: request types uniform over configs 0, 1 (c64+IR), 2 and time-delay "
+                                   "batch members (grid side 20..40, dense LU)",
+                       "requests_per_rate": args.requests, "rates": rates, "budget_GB": 150, "slots": 4,
+                       "arrivals": "Poisson, seed 1", "l2": "inputs larger than L2 for configs 1 and 2"},
+            "per_rate": per_rate, "fp64_per_request": fp64, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
 
 
 def _pinned(torch, a):
@@ -308,6 +585,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "serve":
+        run_serve(args)
+    elif args.config == "3":
+        run_batch(args)
     else:
         run_ours(args)
 

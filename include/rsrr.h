@@ -80,6 +80,9 @@ typedef struct {
 
 /* flags of rsrr_create_nep */
 #define RSRR_NATURAL_ORDER 0x1u  /* keep the caller's ordering (skip the band reordering) */
+#define RSRR_DENSE_LU      0x2u  /* factor every sampling point with the dense LU, whatever the
+                                    band (otherwise chosen when the band is wider than 768 or
+                                    than 2n/5 for n >= 128) */
 
 typedef struct rsrr_nep_s* rsrr_nep;
 
@@ -91,7 +94,7 @@ typedef struct rsrr_nep_s* rsrr_nep;
  *   colind    [nnz] column indices, each row's entries strictly increasing
  *   vals_reim [J][nnz][2] values of A_i on the union pattern (zeros where A_i has none)
  *   f         [J] the functions f_i
- *   flags     RSRR_NATURAL_ORDER or 0
+ *   flags     0, or RSRR_NATURAL_ORDER and/or RSRR_DENSE_LU
  *   stream    cudaStream_t on which all device work of this handle runs (NULL = default)
  *   out       receives the handle
  * The library picks a row/column ordering (reverse Cuthill-McKee, or the natural one if
@@ -103,8 +106,9 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
 
 /* ---- rsrr_sample ----------------------------------------------------------------------
  * Algorithm 2, Steps 1-2: for j = 0..N-1, z_j = phi(2 pi (j + 1/2) / N), factor T(z_j)
- * by band LU with partial pivoting and solve T(z_j) X_j = U; S_hat = [X_0 ... X_{N-1}]
- * (Eq. eq-hatS, n x N*L) stays on the device.
+ * by LU with partial pivoting (band LU, or dense LU when the band is too wide to pay: see
+ * RSRR_DENSE_LU) and solve T(z_j) X_j = U; S_hat = [X_0 ... X_{N-1}] (Eq. eq-hatS,
+ * n x N*L) stays on the device.
  *   C          contour
  *   N, L       sampling points (1..4096) and probing columns (1..256)
  *   U_reim     [L][n][2] the probing matrix U (n x L, column-major, caller ordering);
@@ -115,9 +119,26 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
  *   max_refine refinement sweeps allowed in RSRR_C64_IR (ignored for RSRR_FP64)
  * Errors: EINVAL, ESINGULAR (a zero pivot: some z_j is an eigenvalue),
  *         ENOTCONVERGED (eta > tol after max_refine sweeps, or > tol in FP64),
- *         ENONFINITE, ENOMEM, ECUDA, EUNSUPPORTED (band wider than 480). */
+ *         ENONFINITE, ENOMEM, ECUDA. */
 int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
                 const double* U_reim, int32_t precision, double tol, int32_t max_refine);
+
+/* ---- rsrr_sample_batch ----------------------------------------------------------------
+ * rsrr_sample on `count` handles in one call (Algorithm 2, Steps 1-2 for a batch of NEPs).
+ * The points of every NEP that takes the dense LU go into shared persistent launches (one
+ * CTA per point, largest n first, in waves sized to the free device memory); banded NEPs run
+ * one after another on the band path.  Each handle afterwards holds its own S_hat, exactly as
+ * after its own rsrr_sample, and goes on to rsrr_project / rsrr_solve independently.
+ *   hs          [count] distinct handles, all created on the same device and stream
+ *   C, N, L     [count] contour, sampling points and probing columns per handle
+ *   U_reim      [count] probing matrices as in rsrr_sample (an entry, or U_reim itself, may
+ *               be NULL to reuse each handle's resident U)
+ *   precision, tol, max_refine   as in rsrr_sample, shared by all handles
+ * Errors: as rsrr_sample (the first failing handle's); EINVAL also for mixed streams or a
+ * repeated handle.  After an error no handle of the batch counts as sampled. */
+int rsrr_sample_batch(rsrr_nep* hs, int32_t count, const rsrr_contour* C, const int32_t* N,
+                      const int32_t* L, const double* const* U_reim, int32_t precision,
+                      double tol, int32_t max_refine);
 
 /* ---- rsrr_project ---------------------------------------------------------------------
  * Algorithm 2 Step 3 and Eq. eq-Zs-expr: S_hat = Q R (Householder, FP64), R = W Sigma
@@ -163,9 +184,10 @@ typedef struct {
     double max_eta;             /* max backward error over all N*L columns                 */
     double ms_sample, ms_project, ms_solve;  /* device time of the last calls              */
     int64_t device_bytes;       /* device memory held by the handle                        */
-    double ms_factor;           /* device time of the band-LU launches of the last rsrr_sample */
+    double ms_factor;           /* device time of the LU launches of the last rsrr_sample (after
+                                   rsrr_sample_batch: of all dense-LU launches of the batch)   */
     double ms_trsv;             /* device time of its triangular-solve launches              */
-    int32_t factor_launches;    /* band-LU launches in the last rsrr_sample                  */
+    int32_t factor_launches;    /* LU launches in the last rsrr_sample                       */
     int32_t trsv_launches;      /* forward + backward solve launches in the last rsrr_sample */
     int32_t rows_kept;          /* rows of R kept by rsrr_project's early-stopped QR         */
     int32_t jacobi_sweeps_project, jacobi_sweeps_solve;  /* sweeps of the two Jacobi SVDs  */
@@ -174,6 +196,7 @@ typedef struct {
                                    with moments and traces; Hankel SVD; count, eig, back-map */
     double ms_zgemm;            /* device time of the FP64 complex GEMMs of the last project + solve */
     double zgemm_gflop;         /* their algorithmic work, 8 M N K per product, in GFLOP          */
+    int32_t dense_lu;           /* 1 if the last rsrr_sample factored with the dense LU            */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

@@ -23,6 +23,7 @@ RSRR_FP64 = 0
 RSRR_C64_IR = 1
 RSRR_REFINE_FULL = 0x100
 RSRR_NATURAL_ORDER = 0x1
+RSRR_DENSE_LU = 0x2
 
 F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL = range(6)
 
@@ -62,14 +63,14 @@ class rsrr_info(ctypes.Structure):
                 ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double),
                 ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
                 ("ms_solve_extract", ctypes.c_double), ("ms_zgemm", ctypes.c_double),
-                ("zgemm_gflop", ctypes.c_double)]
+                ("zgemm_gflop", ctypes.c_double), ("dense_lu", ctypes.c_int32)]
 
 
 _lib = None
 EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr_get_info",
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
-           "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc"]
+           "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch"]
 
 
 def lib():
@@ -99,6 +100,7 @@ def lib():
         "rsrr_version": ([], ctypes.c_char_p),
         "rsrr_kernel_launches": ([], ctypes.c_int64),
         "rsrr_band_solve_noalloc": ([I64, I32, I32, P, I32, P, P], ctypes.c_int),
+        "rsrr_sample_batch": ([P, I32, P, P, P, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -163,6 +165,29 @@ def rsrr_sample(h, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, ma
                              int(max_refine)))
 
 
+def rsrr_sample_batch(handles, contours, Ns, Ls, Us=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+    """rsrr_sample for several handles in one call (contours: list of (gamma, a, b))."""
+    count = len(handles)
+    H = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    C = (rsrr_contour * count)()
+    for i, (gamma, a, b) in enumerate(contours):
+        C[i].gamma_re, C[i].gamma_im = complex(gamma).real, complex(gamma).imag
+        C[i].a, C[i].b = float(a), float(b)
+    Narr = (ctypes.c_int32 * count)(*[int(x) for x in Ns])
+    Larr = (ctypes.c_int32 * count)(*[int(x) for x in Ls])
+    keep = []
+    Uarr = None
+    if Us is not None:
+        Uarr = (ctypes.c_void_p * count)()
+        for i, U in enumerate(Us):
+            if U is not None:
+                Uc = _c128(U)
+                keep.append(Uc)
+                Uarr[i] = Uc.ctypes.data
+    _check(lib().rsrr_sample_batch(H, count, C, Narr, Larr, Uarr, int(precision), float(tol), int(max_refine)))
+    del keep
+
+
 def rsrr_project(h, delta=1e-14):
     k = ctypes.c_int32()
     _check(lib().rsrr_project(h, float(delta), ctypes.byref(k)))
@@ -199,6 +224,13 @@ def rsrr_band_solve_noalloc(n, kl, ku, ab_ptr, L, b_ptr, stream=None):
 def rsrr_destroy(h):
     if h:
         lib().rsrr_destroy(h)
+
+
+def sample_batch(neps, contours, Ns, Ls, Us=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+    """rsrr_sample_batch over Nep objects (all created on one stream)."""
+    rsrr_sample_batch([p.h for p in neps], contours, Ns, Ls, Us, precision, tol, max_refine)
+    for p, N, L in zip(neps, Ns, Ls):
+        p.N, p.L = int(N), int(L)
 
 
 class Nep:

@@ -8,6 +8,7 @@
 
 namespace rsrr {
 int sample_run(rsrr_nep h, const double* U_reim, int max_refine);
+int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const double*>& U, int max_refine);
 int project_run(rsrr_nep h, double delta);
 int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambda_reim, double* V_reim,
               double* resid, int32_t* nC_out);
@@ -56,7 +57,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     if (n < 1 || n > (int64_t)INT32_MAX - 1) return set_error(RSRR_EINVAL, "n out of range");
     if (J < 1 || J > 16) return set_error(RSRR_EINVAL, "J must be in 1..16");
     if (!rowptr || !colind || !vals_reim || !f) return set_error(RSRR_EINVAL, "NULL input array");
-    if (flags & ~RSRR_NATURAL_ORDER) return set_error(RSRR_EINVAL, "unknown flag bits");
+    if (flags & ~(RSRR_NATURAL_ORDER | RSRR_DENSE_LU)) return set_error(RSRR_EINVAL, "unknown flag bits");
     if (rowptr[0] != 0) return set_error(RSRR_EINVAL, "rowptr[0] must be 0");
     for (int64_t r = 0; r < n; ++r) {
         if (rowptr[r + 1] < rowptr[r]) return set_error(RSRR_EINVAL, "rowptr not monotone");
@@ -84,6 +85,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
         return set_error(RSRR_ECUDA, "cudaEventCreate failed");
     }
     choose_ordering(n, rowptr, colind, (flags & RSRR_NATURAL_ORDER) != 0, &h->ord);
+    h->force_dense = (flags & RSRR_DENSE_LU) != 0;
     // permuted CSR (rows in new order, columns renumbered and sorted) and values
     std::vector<int64_t> prow(n + 1, 0);
     std::vector<int32_t> pcol(nnz), prowidx(nnz);
@@ -141,8 +143,9 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     return RSRR_OK;
 }
 
-int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const double* U_reim,
-                int32_t precision, double tol, int32_t max_refine) {
+namespace {
+int check_sample_args(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, int32_t precision, double tol,
+                      int32_t max_refine) {
     if (!h || !C) return set_error(RSRR_EINVAL, "NULL handle or contour");
     if (N < 1 || N > 4096 || L < 1 || L > 256) return set_error(RSRR_EINVAL, "N or L out of range");
     if (!(C->a > 0) || !(C->b > 0) || !std::isfinite(C->gamma_re) || !std::isfinite(C->gamma_im) ||
@@ -153,25 +156,67 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const d
         return set_error(RSRR_EINVAL, "unknown precision or flag");
     if (!(tol > 0) || max_refine < 0 || max_refine > 100) return set_error(RSRR_EINVAL, "bad tol or max_refine");
     if ((int64_t)N * L * h->n > (int64_t)1 << 34) return set_error(RSRR_ENOMEM, "S_hat too large");
-    DeviceGuard g(h->device);
+    return RSRR_OK;
+}
+
+void begin_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, int32_t precision, double tol) {
     h->C = *C;
     h->N = N;
     h->L = L;
-    h->precision = mode;
+    h->precision = precision & 0xff;
     h->refine_full = (precision & RSRR_REFINE_FULL) != 0;
     h->tol = tol;
     h->sampled = h->projected = false;
     h->kS = -1;
     h->nbar = -1;
-    Timer t(h);
-    int rc = sample_run(h, U_reim, max_refine);
-    h->ms_sample = t.stop();
-    if (rc != RSRR_OK) return rc;
-    std::vector<double> eta((size_t)N * L);
+}
+
+int finish_sample(rsrr_nep h) {
+    std::vector<double> eta((size_t)h->N * h->L);
     RSRR_CUDA(cudaMemcpy(eta.data(), h->d_eta, eta.size() * 8, cudaMemcpyDeviceToHost));
     h->max_eta = 0;
     for (double e : eta) h->max_eta = std::max(h->max_eta, e);
     h->sampled = true;
+    return RSRR_OK;
+}
+}  // namespace
+
+int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const double* U_reim,
+                int32_t precision, double tol, int32_t max_refine) {
+    RSRR_TRY(check_sample_args(h, C, N, L, precision, tol, max_refine));
+    DeviceGuard g(h->device);
+    begin_sample(h, C, N, L, precision, tol);
+    Timer t(h);
+    int rc = sample_run(h, U_reim, max_refine);
+    h->ms_sample = t.stop();
+    if (rc != RSRR_OK) return rc;
+    return finish_sample(h);
+}
+
+int rsrr_sample_batch(rsrr_nep* hs, int32_t count, const rsrr_contour* C, const int32_t* N, const int32_t* L,
+                      const double* const* U_reim, int32_t precision, double tol, int32_t max_refine) {
+    if (!hs || !C || !N || !L || count < 1 || count > 65536)
+        return set_error(RSRR_EINVAL, "rsrr_sample_batch: NULL array or count out of range");
+    for (int32_t i = 0; i < count; ++i) {
+        RSRR_TRY(check_sample_args(hs[i], &C[i], N[i], L[i], precision, tol, max_refine));
+        if (hs[i]->device != hs[0]->device || hs[i]->stream != hs[0]->stream)
+            return set_error(RSRR_EINVAL, "rsrr_sample_batch: all handles must share one device and one stream");
+        for (int32_t k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return set_error(RSRR_EINVAL, "rsrr_sample_batch: a handle appears twice");
+    }
+    DeviceGuard g(hs[0]->device);
+    std::vector<rsrr_nep> v(hs, hs + count);
+    std::vector<const double*> U(count, nullptr);
+    for (int32_t i = 0; i < count; ++i) {
+        begin_sample(hs[i], &C[i], N[i], L[i], precision, tol);
+        U[i] = U_reim ? U_reim[i] : nullptr;
+    }
+    Timer t(hs[0]);
+    int rc = sample_batch_run(v, U, max_refine);
+    const double ms = t.stop();
+    for (rsrr_nep h : v) h->ms_sample = ms;
+    if (rc != RSRR_OK) return rc;
+    for (rsrr_nep h : v) RSRR_TRY(finish_sample(h));
     return RSRR_OK;
 }
 
@@ -243,6 +288,7 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->ms_solve_extract = h->ms_solve_parts[2];
     o->ms_zgemm = h->ms_zgemm_project + h->ms_zgemm_solve;
     o->zgemm_gflop = (h->zgemm_flops_project + h->zgemm_flops_solve) * 1e-9;
+    o->dense_lu = h->dense_used ? 1 : 0;
     return RSRR_OK;
 }
 

@@ -580,7 +580,11 @@ int set_smem(K kernel, size_t sm, const char* name) {
     if (sm + fa.sharedSizeBytes > (size_t)optin)
         return set_error(RSRR_EUNSUPPORTED, std::string(name) + ": shared memory " + std::to_string(sm) + " + " +
                                                 std::to_string(fa.sharedSizeBytes) + " exceeds " + std::to_string(optin));
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // The attribute is per function and process-wide: set it to the largest allowed value (not
+    // to this launch's size), so that host threads launching the same kernel with different
+    // sizes never lower it under one another's launch.
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess)
         return set_error(RSRR_ECUDA, std::string(name) + ": cudaFuncSetAttribute(" + std::to_string(sm) + ", static " +
                                          std::to_string(fa.sharedSizeBytes) + ", optin " + std::to_string(optin) +

@@ -1,0 +1,655 @@
+// Dense complex LU with partial pivoting, one CTA per sampling point, and its block solves.
+//
+// Factorisation of one point (right-looking, panels of NB = 64 columns):
+//   1. panel: the m x 64 panel is factored as two 32-column leaves (left leaf, its
+//      interchanges and L11^{-1} applied to the right half, rank-32 update of the right half,
+//      right leaf, its interchanges applied back to the left half).  A leaf is column-by-
+//      column getf2 (pivot by cabs1 = |re| + |im|, lowest row on ties).  Panels of at most
+//      ~380 (complex64) / ~190 (complex128) rows are staged in shared memory, taller ones are
+//      factored in place in global memory.
+//   2. the panel's 64 interchanges are composed into one permutation of the <= 128 rows they
+//      touch; inv(L11) and inv(U11) of the diagonal block are formed once.
+//   3. trailing rows: per block of columns, the touched rows are gathered, permuted, and the
+//      64 pivot rows become U12 = inv(L11) * (permuted rows)  (one small product).
+//   4. trailing update A22 -= L21 * U12: 128 x 128 (complex64) or 64 x 64 (complex128) tiles,
+//      L21 tiles double-buffered in shared memory by cp.async, U12 block resident, each
+//      thread holding an 8 x 8 (4 x 4) block of the tile in registers.
+// The update is the dense contraction that carries (8/3) n^3 real flops per point; steps 1-3
+// are O(n^2 NB).
+#include <algorithm>
+#include <climits>
+#include <string>
+
+#include "dense_lu.cuh"
+
+namespace rsrr {
+
+namespace {
+
+constexpr int NB = kDenseNB;
+constexpr int NBP = NB + 1;  // padded row length of the diagonal-block arrays in shared memory
+constexpr int NT = kDenseThreads;
+constexpr int NW = NT / 32;
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename R> struct DTile;
+template <> struct DTile<float> { static constexpr int TM = 128, TN = 128, MI = 8, MJ = 8; };
+template <> struct DTile<double> { static constexpr int TM = 64, TN = 64, MI = 4, MJ = 4; };
+
+template <typename R>
+constexpr size_t gemm_smem() {
+    return (2 * (size_t)NB * DTile<R>::TM + (size_t)NB * (DTile<R>::TN + 1)) * sizeof(cplx<R>);
+}
+template <typename R>
+constexpr size_t rows_smem() {
+    return ((size_t)NB * NBP + (size_t)2 * NB * DTile<R>::TN) * sizeof(cplx<R>);
+}
+template <typename R>
+constexpr size_t inverse_smem() {
+    return (size_t)3 * NB * NBP * sizeof(cplx<R>);
+}
+template <typename R>
+constexpr size_t factor_smem() {
+    return std::max(gemm_smem<R>(), std::max(rows_smem<R>(), inverse_smem<R>()));
+}
+
+struct DShared {
+    int piv[NB];        // panel pivots, relative to the panel's first row
+    int rows[2 * NB];   // composed interchanges: row rows[e] receives row src[e]
+    int src[2 * NB];
+    int cnt;
+    int res;
+    int info;
+    int job;
+    int red_i[NW];
+    double red_v[NW];
+};
+
+// ------------------------------------------------------------------------------------------
+// cp.async element copies (src_bytes = 0 fills zeros; the source must still be a valid address)
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void cp_elem(cplx<R>* smem, const cplx<R>* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(cplx<R>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Row of the largest cabs1 in col[c..m) (lowest row on ties; c if every entry is NaN).
+template <typename R>
+__device__ int col_argmax(const cplx<R>* col, int c, int m, DShared& sh) {
+    double best = -1.0;
+    int bi = INT_MAX;
+    for (int r = c + (int)threadIdx.x; r < m; r += NT) {
+        const double a = (double)cabs1(col[r]);
+        if (a > best) { best = a; bi = r; }
+    }
+    for (int off = 16; off; off >>= 1) {
+        const double ob = __shfl_down_sync(FULL, best, off);
+        const int oi = __shfl_down_sync(FULL, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh.red_v[w] = best; sh.red_i[w] = bi; }
+    __syncthreads();
+    if (w == 0) {
+        best = lane < NW ? sh.red_v[lane] : -1.0;
+        bi = lane < NW ? sh.red_i[lane] : INT_MAX;
+        for (int off = 16; off; off >>= 1) {
+            const double ob = __shfl_down_sync(FULL, best, off);
+            const int oi = __shfl_down_sync(FULL, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) sh.res = (bi == INT_MAX) ? c : bi;
+    }
+    __syncthreads();
+    return sh.res;
+}
+
+// getf2 on the m x w block P (leading dimension ld): pivots piv[c] relative to row 0.
+template <typename R>
+__device__ void leaf_factor(cplx<R>* P, int64_t ld, int m, int w, int* piv, int col_base, DShared& sh) {
+    for (int c = 0; c < w; ++c) {
+        cplx<R>* colc = P + (int64_t)c * ld;
+        const int p = col_argmax(colc, c, m, sh);
+        if (threadIdx.x == 0) piv[c] = p;
+        if (p != c)
+            for (int q = threadIdx.x; q < w; q += NT) {
+                cplx<R>* cq = P + (int64_t)q * ld;
+                const cplx<R> t = cq[c];
+                cq[c] = cq[p];
+                cq[p] = t;
+            }
+        __syncthreads();
+        const cplx<R> pv = colc[c];
+        const bool zero = cis_zero(pv);
+        if (zero && threadIdx.x == 0 && sh.info == 0) sh.info = col_base + c + 1;
+        const cplx<R> rp = zero ? czero<R>() : crecip(pv);
+        for (int r = c + 1 + (int)threadIdx.x; r < m; r += NT) {
+            cplx<R> l = colc[r];
+            if (!zero) {
+                l = l * rp;
+                colc[r] = l;
+            }
+            for (int q = c + 1; q < w; ++q) {
+                cplx<R>* cq = P + (int64_t)q * ld;
+                cplx<R> v = cq[r];
+                cfms(v, l, cq[c]);
+                cq[r] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Factor the m x nbk panel P as two leaves of 32 columns; sh.piv[0..nbk) relative to row 0,
+// with every interchange applied to all nbk columns.
+template <typename R>
+__device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_base, DShared& sh) {
+    const int w1 = min(32, nbk);
+    leaf_factor(P, ld, m, w1, sh.piv, col_base, sh);
+    if (nbk <= w1) return;
+    const int w2 = nbk - w1;  // w1 == 32 from here on
+    cplx<R>* Rt = P + (int64_t)w1 * ld;
+    for (int q = threadIdx.x; q < w2; q += NT) {  // left interchanges on the right half
+        cplx<R>* cq = Rt + (int64_t)q * ld;
+        for (int c = 0; c < w1; ++c) {
+            const int p = sh.piv[c];
+            if (p != c) {
+                const cplx<R> t = cq[c];
+                cq[c] = cq[p];
+                cq[p] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < w2; q += NT) {  // U12 = L11^{-1} (top 32 rows of the right half)
+        cplx<R>* cq = Rt + (int64_t)q * ld;
+        for (int r = 1; r < w1; ++r) {
+            cplx<R> acc = cq[r];
+            for (int s = 0; s < r; ++s) cfms(acc, P[r + (int64_t)s * ld], cq[s]);
+            cq[r] = acc;
+        }
+    }
+    __syncthreads();
+    for (int r = w1 + (int)threadIdx.x; r < m; r += NT) {  // A22 -= L21 U12 (K = 32)
+        cplx<R> lrow[32];
+#pragma unroll
+        for (int s = 0; s < 32; ++s) lrow[s] = P[r + (int64_t)s * ld];
+        for (int q = 0; q < w2; ++q) {
+            cplx<R>* cq = Rt + (int64_t)q * ld;
+            cplx<R> acc = cq[r];
+#pragma unroll
+            for (int s = 0; s < 32; ++s) cfms(acc, lrow[s], cq[s]);
+            cq[r] = acc;
+        }
+    }
+    __syncthreads();
+    leaf_factor(Rt + w1, ld, m - w1, w2, sh.piv + w1, col_base + w1, sh);
+    if ((int)threadIdx.x < w2) sh.piv[w1 + threadIdx.x] += w1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < w1; q += NT) {  // right interchanges on the left half
+        cplx<R>* cq = P + (int64_t)q * ld;
+        for (int c = w1; c < nbk; ++c) {
+            const int p = sh.piv[c];
+            if (p != c) {
+                const cplx<R> t = cq[c];
+                cq[c] = cq[p];
+                cq[p] = t;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Compose the panel's interchanges (applied in order t = 0..nbk-1) into one permutation of the
+// rows they touch.  Entries 0..nbk-1 are the diagonal rows; further entries are pivot rows
+// below the panel's diagonal block.  Warp 0 does it; everyone waits.
+__device__ void compose_swaps(int nbk, DShared& sh) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int t = lane; t < nbk; t += 32) { sh.rows[t] = t; sh.src[t] = t; }
+        __syncwarp();
+        int cnt = nbk;
+        for (int t = 0; t < nbk; ++t) {
+            const int p = sh.piv[t];
+            if (p == t) continue;
+            int e = -1;
+            if (p < nbk) {
+                e = p;
+            } else {
+                for (int base = nbk; base < cnt && e < 0; base += 32) {
+                    const int idx = base + lane;
+                    const unsigned hit = __ballot_sync(FULL, idx < cnt && sh.rows[idx] == p);
+                    if (hit) e = base + __ffs(hit) - 1;
+                }
+                if (e < 0) {
+                    e = cnt;
+                    if (lane == 0) { sh.rows[e] = p; sh.src[e] = p; }
+                    ++cnt;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const int a = sh.src[t];
+                sh.src[t] = sh.src[e];
+                sh.src[e] = a;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) sh.cnt = cnt;
+    }
+    __syncthreads();
+}
+
+// inv(L11) and inv(U11) of the nbk x nbk diagonal block of P; shared layout (r, c) at r * NBP + c:
+// sm[0 ..) = inv(L11), then inv(U11), then a copy of the block (its padding column holds 1/U(r,r)).
+// Both go to ginv (column-major, leading dimension NB, zero outside nbk x nbk).
+template <typename R>
+__device__ void diag_inverses(const cplx<R>* P, int64_t ld, int nbk, cplx<R>* sm, cplx<R>* ginv) {
+    cplx<R>* iL = sm;
+    cplx<R>* iU = sm + NB * NBP;
+    cplx<R>* T = sm + 2 * NB * NBP;
+    const cplx<R> one = mk<R>(R(1), R(0));
+    for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
+        const int r = idx % nbk, c = idx / nbk;
+        T[r * NBP + c] = P[r + (int64_t)c * ld];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nbk; r += NT) {
+        const cplx<R> d = T[r * NBP + r];
+        T[r * NBP + NB] = cis_zero(d) ? czero<R>() : crecip(d);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < nbk) {
+        for (int r = 0; r < nbk; ++r) {
+            iL[r * NBP + t] = (r == t) ? one : czero<R>();
+            iU[r * NBP + t] = czero<R>();
+        }
+        for (int r = t + 1; r < nbk; ++r) {  // column t of inv(L11): unit lower forward substitution
+            cplx<R> a0 = czero<R>(), a1 = czero<R>();
+            int s = t;
+            for (; s + 1 < r; s += 2) {
+                cfms(a0, T[r * NBP + s], iL[s * NBP + t]);
+                cfms(a1, T[r * NBP + s + 1], iL[(s + 1) * NBP + t]);
+            }
+            if (s < r) cfms(a0, T[r * NBP + s], iL[s * NBP + t]);
+            iL[r * NBP + t] = a0 + a1;
+        }
+        iU[t * NBP + t] = T[t * NBP + NB];
+        for (int r = t - 1; r >= 0; --r) {  // column t of inv(U11): backward substitution
+            cplx<R> a0 = czero<R>(), a1 = czero<R>();
+            int s = r + 1;
+            for (; s + 1 <= t; s += 2) {
+                cfma(a0, T[r * NBP + s], iU[s * NBP + t]);
+                cfma(a1, T[r * NBP + s + 1], iU[(s + 1) * NBP + t]);
+            }
+            if (s <= t) cfma(a0, T[r * NBP + s], iU[s * NBP + t]);
+            const cplx<R> acc = a0 + a1;
+            iU[r * NBP + t] = mk<R>(-acc.re, -acc.im) * T[r * NBP + NB];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NB * NB; idx += NT) {
+        const int r = idx % NB, c = idx / NB;
+        const bool in = r < nbk && c < nbk;
+        ginv[idx] = in ? iL[r * NBP + c] : czero<R>();
+        ginv[NB * NB + idx] = in ? iU[r * NBP + c] : czero<R>();
+    }
+    __syncthreads();
+}
+
+// Trailing columns, rows of the panel: apply the composed interchanges and form
+// U12 = inv(L11) * (pivot rows), block of TN columns at a time.  sm[0..NB*NBP) = inv(L11).
+template <typename R>
+__device__ void trailing_rows(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>* sm, const DShared& sh) {
+    constexpr int TN = DTile<R>::TN;
+    const cplx<R>* iL = sm;
+    cplx<R>* g = sm + NB * NBP;  // gathered rows, g[col * 2NB + e]
+    const int cnt = sh.cnt, extra = cnt - NB;
+    for (int c0 = k0 + NB; c0 < n; c0 += TN) {
+        const int nc = min(TN, n - c0);
+        for (int idx = threadIdx.x; idx < cnt * nc; idx += NT) {
+            const int e = idx % cnt, col = idx / cnt;
+            g[col * 2 * NB + e] = A[(int64_t)(k0 + sh.src[e]) + (int64_t)(c0 + col) * lda];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < extra * nc; idx += NT) {
+            const int e = NB + idx % extra, col = idx / extra;
+            A[(int64_t)(k0 + sh.rows[e]) + (int64_t)(c0 + col) * lda] = g[col * 2 * NB + e];
+        }
+        {
+            const int t = threadIdx.x % NB, grp = threadIdx.x / NB;
+            for (int col = grp; col < nc; col += NT / NB) {
+                const cplx<R>* gc = g + col * 2 * NB;
+                cplx<R> a0 = czero<R>(), a1 = czero<R>();
+                int s = 0;
+                for (; s + 1 <= t; s += 2) {
+                    cfma(a0, iL[t * NBP + s], gc[s]);
+                    cfma(a1, iL[t * NBP + s + 1], gc[s + 1]);
+                }
+                if (s <= t) cfma(a0, iL[t * NBP + s], gc[s]);
+                A[(int64_t)(k0 + t) + (int64_t)(c0 + col) * lda] = a0 + a1;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// A22 -= L21 * U12 over rows and columns [k0 + NB, n).
+template <typename R>
+__device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>* sm) {
+    using T = DTile<R>;
+    constexpr int TM = T::TM, TN = T::TN, MI = T::MI, MJ = T::MJ, TNP = TN + 1;
+    cplx<R>* As = sm;                 // [2][NB][TM]
+    cplx<R>* Bs = sm + 2 * NB * TM;   // [NB][TNP]
+    const int tid = threadIdx.x, ty = tid % 16, tx = tid / 16;
+    const int r_begin = k0 + NB;
+    const int ntiles = (n - r_begin + TM - 1) / TM;
+    const cplx<R>* L21 = A + (int64_t)k0 * lda;  // panel columns
+    auto load_a = [&](cplx<R>* buf, int i0) {
+        for (int idx = tid; idx < NB * TM; idx += NT) {
+            const int r = idx % TM, k = idx / TM;
+            const bool ok = i0 + r < n;
+            cp_elem(&buf[k * TM + r], ok ? L21 + (i0 + r) + (int64_t)k * lda : A, ok);
+        }
+    };
+    for (int c0 = r_begin; c0 < n; c0 += TN) {
+        const int ce = min(n, c0 + TN);
+        for (int idx = tid; idx < NB * TN; idx += NT) {
+            const int k = idx % NB, c = idx / NB;
+            const bool ok = c0 + c < ce;
+            cp_elem(&Bs[k * TNP + c], ok ? A + (k0 + k) + (int64_t)(c0 + c) * lda : A, ok);
+        }
+        load_a(As, r_begin);
+        cp_commit();
+        for (int t = 0; t < ntiles; ++t) {
+            const int i0 = r_begin + t * TM;
+            if (t + 1 < ntiles) load_a(As + ((t + 1) & 1) * NB * TM, i0 + TM);
+            cp_commit();
+            cplx<R> acc[MI][MJ];
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < MJ; ++j) {
+                    const int r = i0 + ty + 16 * i, c = c0 + tx + 16 * j;
+                    acc[i][j] = (r < n && c < ce) ? A[r + (int64_t)c * lda] : czero<R>();
+                }
+            cp_wait<1>();
+            __syncthreads();
+            const cplx<R>* Ab = As + (t & 1) * NB * TM;
+#pragma unroll 2
+            for (int k = 0; k < NB; ++k) {
+                cplx<R> a[MI], b[MJ];
+#pragma unroll
+                for (int i = 0; i < MI; ++i) a[i] = Ab[k * TM + ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < MJ; ++j) b[j] = Bs[k * TNP + tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < MI; ++i)
+#pragma unroll
+                    for (int j = 0; j < MJ; ++j) cfms(acc[i][j], a[i], b[j]);
+            }
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < MJ; ++j) {
+                    const int r = i0 + ty + 16 * i, c = c0 + tx + 16 * j;
+                    if (r < n && c < ce) A[r + (int64_t)c * lda] = acc[i][j];
+                }
+            __syncthreads();
+        }
+        cp_wait<0>();
+        __syncthreads();
+    }
+}
+
+template <typename R>
+__device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh) {
+    const int n = J.n;
+    const int64_t lda = J.lda;
+    cplx<R>* A = J.a;
+    const int cap_rows = (int)(factor_smem<R>() / (NB * sizeof(cplx<R>)));
+    for (int p = 0, k0 = 0; k0 < n; ++p, k0 += NB) {
+        const int nbk = min(NB, n - k0), m = n - k0;
+        cplx<R>* Pg = A + k0 + (int64_t)k0 * lda;
+        if (m <= cap_rows) {
+            for (int idx = threadIdx.x; idx < m * nbk; idx += NT) {
+                const int r = idx % m, c = idx / m;
+                sm[r + c * m] = Pg[r + (int64_t)c * lda];
+            }
+            __syncthreads();
+            panel_factor(sm, (int64_t)m, m, nbk, k0, sh);
+            for (int idx = threadIdx.x; idx < m * nbk; idx += NT) {
+                const int r = idx % m, c = idx / m;
+                Pg[r + (int64_t)c * lda] = sm[r + c * m];
+            }
+            __syncthreads();
+        } else {
+            panel_factor(Pg, lda, m, nbk, k0, sh);
+        }
+        if ((int)threadIdx.x < nbk) J.ipiv[k0 + threadIdx.x] = k0 + sh.piv[threadIdx.x];
+        compose_swaps(nbk, sh);
+        int32_t* sw = J.swaps + (int64_t)p * kDenseSwapInts;
+        if (threadIdx.x == 0) sw[0] = sh.cnt;
+        for (int i = threadIdx.x; i < 2 * NB; i += NT) {
+            sw[1 + i] = i < sh.cnt ? sh.rows[i] : 0;
+            sw[1 + 2 * NB + i] = i < sh.cnt ? sh.src[i] : 0;
+        }
+        diag_inverses(Pg, lda, nbk, sm, J.inv + (int64_t)p * 2 * NB * NB);
+        if (k0 + nbk < n) {
+            trailing_rows(A, lda, n, k0, sm, sh);
+            trailing_update(A, lda, n, k0, sm);
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* __restrict__ jobs, int njobs,
+                                                             int32_t* __restrict__ next) {
+    extern __shared__ __align__(16) unsigned char dense_smem[];
+    cplx<R>* sm = reinterpret_cast<cplx<R>*>(dense_smem);
+    __shared__ DShared sh;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh.job = atomicAdd(next, 1);
+            sh.info = 0;
+        }
+        __syncthreads();
+        const int jb = sh.job;
+        if (jb >= njobs) return;
+        const DenseJob<R> J = jobs[jb];
+        factor_one(J, sm, sh);
+        if (threadIdx.x == 0) *J.info = sh.info;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Solves.  x (n x L, leading dimension n) <- A^{-1} x.  Forward: per panel, the composed
+// interchanges, y = inv(L11) x_top, x_below -= L21 y.  Backward: per panel from the last,
+// y = inv(U11) x_top, x_above -= U01 y.  Right-hand sides in groups of LG columns.
+// ------------------------------------------------------------------------------------------
+constexpr int LG = 32;  // right-hand-side columns per pass over the factor
+template <typename R> struct SolveChunk;
+template <> struct SolveChunk<float> { static constexpr int LC = 8; };
+template <> struct SolveChunk<double> { static constexpr int LC = 4; };
+
+template <typename R>
+constexpr size_t solve_smem() {
+    return ((size_t)NB * NBP + (size_t)2 * NB * LG + (size_t)NB * LG) * sizeof(cplx<R>);
+}
+
+// x[r, l] -= sum_k Ablk[r + k lda] y[k * LP + l]  for r in [r0, r1), l < lg
+template <typename R>
+__device__ void solve_update(const cplx<R>* __restrict__ Ablk, int64_t lda, int r0, int r1, int nbk,
+                             const cplx<R>* y, int LP, int lg, cplx<R>* __restrict__ x, int64_t ldx) {
+    constexpr int LC = SolveChunk<R>::LC;
+    for (int l0 = 0; l0 < lg; l0 += LC) {
+        for (int r = r0 + (int)threadIdx.x; r < r1; r += NT) {
+            cplx<R> acc[LC];
+#pragma unroll
+            for (int l = 0; l < LC; ++l) acc[l] = (l0 + l < lg) ? x[r + (int64_t)(l0 + l) * ldx] : czero<R>();
+#pragma unroll 8
+            for (int k = 0; k < nbk; ++k) {
+                const cplx<R> a = Ablk[r + (int64_t)k * lda];
+#pragma unroll
+                for (int l = 0; l < LC; ++l) cfms(acc[l], a, y[k * LP + l0 + l]);
+            }
+#pragma unroll
+            for (int l = 0; l < LC; ++l)
+                if (l0 + l < lg) x[r + (int64_t)(l0 + l) * ldx] = acc[l];
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) dense_solve_kernel(const DenseJob<R>* __restrict__ jobs, int njobs) {
+    constexpr int LC = SolveChunk<R>::LC;
+    extern __shared__ __align__(16) unsigned char dense_smem[];
+    cplx<R>* sinv = reinterpret_cast<cplx<R>*>(dense_smem);  // (r, c) at r * NBP + c
+    cplx<R>* g = sinv + NB * NBP;                            // [2 NB][LG]
+    cplx<R>* y = g + 2 * NB * LG;                            // [NB][LP]
+    __shared__ int s_rows[2 * NB], s_src[2 * NB];
+    __shared__ int s_cnt;
+    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+        const DenseJob<R> J = jobs[jb];
+        if (J.active && !*J.active) continue;
+        const int n = J.n;
+        const int np = (int)dense_panels(n);
+        const int64_t lda = J.lda;
+        for (int l_begin = 0; l_begin < J.L; l_begin += LG) {
+            const int lg = min(LG, J.L - l_begin);
+            const int LP = (lg + LC - 1) / LC * LC;
+            cplx<R>* x = J.x + (int64_t)l_begin * n;
+            for (int idx = threadIdx.x; idx < NB * LP; idx += NT) y[idx] = czero<R>();
+            __syncthreads();
+            for (int p = 0; p < np; ++p) {  // forward
+                const int k0 = p * NB, nbk = min(NB, n - k0);
+                const int32_t* sw = J.swaps + (int64_t)p * kDenseSwapInts;
+                const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB;
+                if (threadIdx.x == 0) s_cnt = sw[0];
+                for (int i = threadIdx.x; i < 2 * NB; i += NT) {
+                    s_rows[i] = sw[1 + i];
+                    s_src[i] = sw[1 + 2 * NB + i];
+                }
+                for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
+                    const int r = idx % nbk, c = idx / nbk;
+                    sinv[r * NBP + c] = gi[r + c * NB];
+                }
+                __syncthreads();
+                const int cnt = s_cnt;
+                for (int idx = threadIdx.x; idx < cnt * lg; idx += NT) {
+                    const int e = idx % cnt, l = idx / cnt;
+                    g[e * LG + l] = x[k0 + s_src[e] + (int64_t)l * n];
+                }
+                __syncthreads();
+                const int extra = cnt - nbk;
+                for (int idx = threadIdx.x; idx < extra * lg; idx += NT) {
+                    const int e = nbk + idx % extra, l = idx / extra;
+                    x[k0 + s_rows[e] + (int64_t)l * n] = g[e * LG + l];
+                }
+                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                    const int t = idx % nbk, l = idx / nbk;
+                    cplx<R> acc = czero<R>();
+                    for (int s = 0; s <= t; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
+                    y[t * LP + l] = acc;
+                    x[k0 + t + (int64_t)l * n] = acc;
+                }
+                __syncthreads();
+                if (k0 + nbk < n)
+                    solve_update(J.a + (int64_t)k0 * lda, lda, k0 + nbk, n, nbk, y, LP, lg, x, n);
+                __syncthreads();
+            }
+            for (int p = np - 1; p >= 0; --p) {  // backward
+                const int k0 = p * NB, nbk = min(NB, n - k0);
+                const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB + NB * NB;
+                for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
+                    const int r = idx % nbk, c = idx / nbk;
+                    sinv[r * NBP + c] = gi[r + c * NB];
+                }
+                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                    const int t = idx % nbk, l = idx / nbk;
+                    g[t * LG + l] = x[k0 + t + (int64_t)l * n];
+                }
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                    const int t = idx % nbk, l = idx / nbk;
+                    cplx<R> acc = czero<R>();
+                    for (int s = t; s < nbk; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
+                    y[t * LP + l] = acc;
+                    x[k0 + t + (int64_t)l * n] = acc;
+                }
+                __syncthreads();
+                if (k0 > 0) solve_update(J.a + (int64_t)k0 * lda, lda, 0, k0, nbk, y, LP, lg, x, n);
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// Opt a kernel into its dynamic shared memory.  The attribute is per function and process-wide,
+// so it is set to the largest allowed value rather than to this launch's size: host threads
+// launching the same kernel concurrently never lower it under one another.
+template <typename K>
+int set_smem(K kernel, size_t bytes, const char* name) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    if (bytes + fa.sharedSizeBytes > (size_t)optin)
+        return set_error(RSRR_EUNSUPPORTED, std::string(name) + ": shared memory " + std::to_string(bytes) +
+                                                " + " + std::to_string(fa.sharedSizeBytes) + " exceeds " +
+                                                std::to_string(optin));
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess)
+        return set_error(RSRR_ECUDA, std::string(name) + ": cudaFuncSetAttribute: " + cudaGetErrorString(e));
+    return RSRR_OK;
+}
+
+int sm_count() {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm > 0 ? nsm : 1;
+}
+
+}  // namespace
+
+template <typename R>
+int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int32_t* d_next, cudaStream_t s) {
+    if (njobs <= 0) return RSRR_OK;
+    const size_t sm = factor_smem<R>();
+    RSRR_TRY(set_smem(dense_factor_kernel<R>, sm, "dense_factor_kernel"));
+    RSRR_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int32_t), s));
+    const int grid = std::min(njobs, sm_count());
+    { dense_factor_kernel<R><<<grid, NT, sm, s>>>(d_jobs, njobs, d_next); note_launch(); }
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+template <typename R>
+int launch_dense_solve(const DenseJob<R>* d_jobs, int njobs, int maxL, cudaStream_t s) {
+    (void)maxL;
+    if (njobs <= 0) return RSRR_OK;
+    const size_t sm = solve_smem<R>();
+    RSRR_TRY(set_smem(dense_solve_kernel<R>, sm, "dense_solve_kernel"));
+    { dense_solve_kernel<R><<<njobs, NT, sm, s>>>(d_jobs, njobs); note_launch(); }
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+template int launch_dense_factor<float>(const DenseJob<float>*, int, int32_t*, cudaStream_t);
+template int launch_dense_factor<double>(const DenseJob<double>*, int, int32_t*, cudaStream_t);
+template int launch_dense_solve<float>(const DenseJob<float>*, int, int, cudaStream_t);
+template int launch_dense_solve<double>(const DenseJob<double>*, int, int, cudaStream_t);
+
+}  // namespace rsrr

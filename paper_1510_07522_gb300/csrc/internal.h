@@ -50,6 +50,8 @@ struct rsrr_nep_s {
     int32_t* d_rowidx = nullptr;   // [nnz] row of each entry
     rsrr::c128* d_vals = nullptr;  // [J][nnz]
     int32_t* d_perm = nullptr;     // [n] perm[new] = old
+    bool force_dense = false;      // RSRR_DENSE_LU: factor every point with the dense LU
+    bool dense_used = false;       // the last rsrr_sample factored densely
     std::vector<double> normA;     // ||A_i||_F
 
     // sampling state

@@ -530,10 +530,11 @@ int project_run(rsrr_nep h, double delta) {
     // Columns below 0.3 delta sigma_1 are rounding noise of R2 (its entries carry errors of
     // ~u sigma_1, so such columns never settle): they are not rotated.  A rotation against a
     // column of norm eps moves any other column by O(eps), and such columns stay below the
-    // truncation level.  Kept-subspace accuracy needs pairs orthogonal to ~1e-10 only, and a
-    // pair whose inner product is below 1e-18 sigma_1^2 moves no singular value or kept
-    // direction by more than ~1e-18 sigma_1, so it counts as converged.
-    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 0.3 * delta * sref, 1e-10, 1e-18 * sref * sref));
+    // truncation level.  Kept-subspace accuracy needs pairs orthogonal to ~1e-10 only.  (An
+    // absolute cut on the inner product, |<a, b>| < c sigma_1^2, stops rotating pairs of small
+    // columns before their norms separate and miscounts the singular values near delta sigma_1,
+    // so pairs are judged only relative to their own norms.)
+    TRYC(jacobi_orthogonalize(R2, kk, kk, Jm, st, 40, &sweeps, 0.3 * delta * sref, 1e-10, 0.0));
     h->jacobi_sweeps_project = sweeps;
     h->rows_kept = kk;
     dfree(colnrm, st);

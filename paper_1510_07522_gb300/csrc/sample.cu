@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "band.cuh"
+#include "dense_lu.cuh"
 #include "internal.h"
 
 namespace rsrr {
@@ -380,16 +381,262 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
     return RSRR_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Dense sampling of a set of NEPs (dense_lu.cu): every point of every NEP is one job of the
+// persistent dense-LU launch; the FP64 residual, backward error and refinement are the band
+// path's kernels, run per NEP.  Points are taken largest n first, in waves that fit the device
+// memory free at the start; a NEP may straddle two waves.
+// ---------------------------------------------------------------------------------------------
+template <typename R>
+struct DenseGroup {          // points [j0, j0 + np) of NEP hs[hi] inside one wave
+    int hi = 0, j0 = 0, np = 0;
+    cplx<R>* a = nullptr;
+    cplx<R>* x = nullptr;
+    cplx<R>* inv = nullptr;
+    int32_t *ipiv = nullptr, *info = nullptr, *swaps = nullptr, *active = nullptr;
+    c128* tvals = nullptr;
+    double *colsum = nullptr, *normT = nullptr, *rn2 = nullptr, *xn2 = nullptr, *prev_max = nullptr,
+           *un2 = nullptr;
+    bool done = false;
+    int sweeps = 0;
+};
+
+template <typename R>
+size_t dense_point_bytes(const rsrr_nep h) {
+    const int64_t n = h->n;
+    return (size_t)n * n * sizeof(cplx<R>) + (size_t)n * h->L * sizeof(cplx<R>) + (size_t)n * 4 + 16 +
+           dense_aux_bytes<R>(n) + (size_t)h->nnz * 16 + (size_t)n * 8 + (size_t)h->L * 16 + 64;
+}
+
+template <typename R>
+int sample_dense_set(const std::vector<rsrr_nep>& hs, const std::vector<c128*>& dF, int max_refine) {
+    if (hs.empty()) return RSRR_OK;
+    cudaStream_t st = hs[0]->stream;
+    std::vector<int> order(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+    size_t free_b = 0, total_b = 0;
+    RSRR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = (size_t)(0.8 * (double)free_b);
+    for (rsrr_nep h : hs) {
+        h->ms_factor = h->ms_trsv = 0;
+        h->factor_launches = h->trsv_launches = 0;
+        h->refine_sweeps = 0;
+        if (dense_point_bytes<R>(h) > budget)
+            return set_error(RSRR_ENOMEM, "one dense sampling point does not fit in device memory");
+    }
+    // The NEPs share every launch, so each handle reports the totals of the whole set.
+    double tot_factor_ms = 0, tot_trsv_ms = 0;
+    int tot_factor_launches = 0, tot_trsv_launches = 0;
+    size_t oi = 0;
+    int jnext = 0;  // next point of NEP hs[order[oi]]
+    int32_t* d_next = nullptr;
+    RSRR_TRY(dalloc_n(&d_next, 1, st));
+    int rc = RSRR_OK;
+    bool singular = false, nonfinite = false, notconv = false;
+    while (oi < order.size() && rc == RSRR_OK && !singular && !nonfinite && !notconv) {
+        // ---- the wave: largest remaining points that fit --------------------------------------
+        std::vector<DenseGroup<R>> groups;
+        size_t used = 0;
+        while (oi < order.size()) {
+            rsrr_nep h = hs[order[oi]];
+            const size_t pb = dense_point_bytes<R>(h);
+            const int fit = (int)std::min<size_t>((size_t)(h->N - jnext), (budget - used) / pb);
+            if (fit <= 0) break;
+            DenseGroup<R> g;
+            g.hi = order[oi];
+            g.j0 = jnext;
+            g.np = fit;
+            groups.push_back(g);
+            used += (size_t)fit * pb;
+            jnext += fit;
+            if (jnext == h->N) { ++oi; jnext = 0; }
+        }
+        std::vector<DenseJob<R>> jobs;
+        DenseJob<R>* d_jobs = nullptr;
+        int32_t* d_counters = nullptr;
+        auto cleanup = [&]() {
+            for (auto& g : groups) {
+                dfree(g.a, st); dfree(g.x, st); dfree(g.inv, st); dfree(g.ipiv, st); dfree(g.info, st);
+                dfree(g.swaps, st); dfree(g.active, st); dfree(g.tvals, st); dfree(g.colsum, st);
+                dfree(g.normT, st); dfree(g.rn2, st); dfree(g.xn2, st); dfree(g.prev_max, st); dfree(g.un2, st);
+            }
+            dfree(d_jobs, st);
+            dfree(d_counters, st);
+        };
+#define TRYW(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); dfree(d_next, st); return rc; } } while (0)
+#define CUDAW(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); dfree(d_next, st); return set_error(RSRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
+        const int ng = (int)groups.size();
+        TRYW(dalloc_n(&d_counters, (size_t)4 * ng, st));
+        for (auto& g : groups) {
+            rsrr_nep h = hs[g.hi];
+            const int64_t n = h->n, nnz = h->nnz, L = h->L, np = g.np;
+            const int64_t npan = dense_panels(n);
+            TRYW(dalloc_n(&g.a, (size_t)np * n * n, st));
+            TRYW(dalloc_n(&g.x, (size_t)np * n * L, st));
+            TRYW(dalloc_n(&g.inv, (size_t)np * npan * 2 * kDenseNB * kDenseNB, st));
+            TRYW(dalloc_n(&g.ipiv, (size_t)np * n, st));
+            TRYW(dalloc_n(&g.info, (size_t)np, st));
+            TRYW(dalloc_n(&g.swaps, (size_t)np * npan * kDenseSwapInts, st));
+            TRYW(dalloc_n(&g.active, (size_t)np, st));
+            TRYW(dalloc_n(&g.tvals, (size_t)np * nnz, st));
+            TRYW(dalloc_n(&g.colsum, (size_t)np * n, st));
+            TRYW(dalloc_n(&g.normT, (size_t)np, st));
+            TRYW(dalloc_n(&g.rn2, (size_t)np * L, st));
+            TRYW(dalloc_n(&g.xn2, (size_t)np * L, st));
+            TRYW(dalloc_n(&g.prev_max, (size_t)np, st));
+            TRYW(dalloc_n(&g.un2, (size_t)L, st));
+            CUDAW(cudaMemsetAsync(g.a, 0, (size_t)np * n * n * sizeof(cplx<R>), st));
+            CUDAW(cudaMemsetAsync(g.active, 1, (size_t)np * 4, st));
+            const dim3 gg((unsigned)ceil_div(nnz, 256), (unsigned)np);
+            { assemble_kernel<R><<<gg, 256, 0, st>>>(h->d_vals, h->J, nnz, h->d_rowidx, h->d_colind, dF[g.hi], g.j0,
+                                                    0, (int)(n + 1), g.tvals, g.a, n * n); note_launch(); }
+            CUDAW(cudaGetLastError());
+            CUDAW(cudaMemsetAsync(g.colsum, 0, (size_t)n * np * 8, st));
+            { colsum_kernel<<<gg, 256, 0, st>>>(g.tvals, nnz, h->d_colind, n, g.colsum); note_launch(); }
+            { max_kernel<<<(unsigned)np, 256, 0, st>>>(g.colsum, n, g.normT); note_launch(); }
+            { column_norm2_kernel<<<(unsigned)L, 256, 0, st>>>(h->d_U, n, g.un2); note_launch(); }
+            for (int k = 0; k < np; ++k) {
+                DenseJob<R> J;
+                J.a = g.a + (int64_t)k * n * n;
+                J.lda = n;
+                J.n = (int32_t)n;
+                J.L = (int32_t)L;
+                J.ipiv = g.ipiv + (int64_t)k * n;
+                J.info = g.info + k;
+                J.inv = g.inv + (int64_t)k * npan * 2 * kDenseNB * kDenseNB;
+                J.swaps = g.swaps + (int64_t)k * npan * kDenseSwapInts;
+                J.x = g.x + (int64_t)k * n * L;
+                J.active = g.active + k;
+                jobs.push_back(J);
+            }
+        }
+        const int nj = (int)jobs.size();
+        TRYW(dalloc_n(&d_jobs, (size_t)nj, st));
+        CUDAW(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)nj * sizeof(DenseJob<R>), cudaMemcpyHostToDevice, st));
+        EvPair evf, evs;
+        evf.start(st);
+        TRYW(launch_dense_factor<R>(d_jobs, nj, d_next, st));
+        evf.stop(st);
+        std::vector<int32_t> hinfo;
+        for (auto& g : groups) {
+            std::vector<int32_t> hi(g.np);
+            CUDAW(cudaMemcpyAsync(hi.data(), g.info, (size_t)g.np * 4, cudaMemcpyDeviceToHost, st));
+            CUDAW(cudaStreamSynchronize(st));
+            for (int32_t v : hi) if (v) singular = true;
+        }
+        tot_factor_ms += evf.ms();
+        tot_factor_launches += 1;
+        if (singular) { cleanup(); break; }
+        for (auto& g : groups) {
+            rsrr_nep h = hs[g.hi];
+            const int64_t nl = h->n * h->L;
+            { broadcast_rhs_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(h->d_U, nl, g.x); note_launch(); }
+        }
+        double ms_s = 0;
+        evs.start(st);
+        TRYW(launch_dense_solve<R>(d_jobs, nj, 0, st));
+        evs.stop(st);
+        bool pending = true;
+        int solves = 1;
+        for (auto& g : groups) {
+            rsrr_nep h = hs[g.hi];
+            const int64_t nl = h->n * h->L;
+            { accumulate_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(
+                  h->d_S + (int64_t)g.j0 * nl, g.x, nl, 0, nullptr); note_launch(); }
+        }
+        for (;;) {
+            for (int gi = 0; gi < ng; ++gi) {
+                auto& g = groups[gi];
+                if (g.done) continue;
+                rsrr_nep h = hs[g.hi];
+                const int64_t n = h->n, L = h->L;
+                CUDAW(cudaMemsetAsync(g.rn2, 0, (size_t)L * g.np * 8, st));
+                CUDAW(cudaMemsetAsync(g.xn2, 0, (size_t)L * g.np * 8, st));
+                CUDAW(cudaMemsetAsync(d_counters + 4 * gi, 0, 16, st));
+                { residual_kernel<R><<<dim3((unsigned)ceil_div(n, 128), (unsigned)g.np), 128, 0, st>>>(
+                      h->d_rowptr, h->d_colind, g.tvals, h->nnz, n, (int)L, h->d_U, h->d_S + (int64_t)g.j0 * n * L,
+                      g.x, g.rn2, g.xn2, g.sweeps == 0 ? nullptr : g.active); note_launch(); }
+                { eta_kernel<<<(unsigned)g.np, 32, 0, st>>>(g.rn2, g.xn2, g.un2, g.normT, g.np, (int)L, h->tol,
+                                                           h->refine_full ? 0.0 : h->tol, h->d_eta + (int64_t)g.j0 * L,
+                                                           g.active, g.prev_max, d_counters + 4 * gi,
+                                                           g.sweeps == 0 ? 1 : 0); note_launch(); }
+            }
+            std::vector<int32_t> hc((size_t)4 * ng);
+            CUDAW(cudaMemcpyAsync(hc.data(), d_counters, hc.size() * 4, cudaMemcpyDeviceToHost, st));
+            CUDAW(cudaStreamSynchronize(st));
+            if (pending) { ms_s += evs.ms(); pending = false; }
+            int active_groups = 0;
+            for (int gi = 0; gi < ng; ++gi) {
+                auto& g = groups[gi];
+                if (g.done) continue;
+                rsrr_nep h = hs[g.hi];
+                if (hc[4 * gi + 1]) nonfinite = true;
+                if (hc[4 * gi + 2]) notconv = true;
+                if (hc[4 * gi] == 0) { g.done = true; continue; }
+                if (g.sweeps >= max_refine) {
+                    std::vector<double> he((size_t)g.np * h->L);
+                    CUDAW(cudaMemcpyAsync(he.data(), h->d_eta + (int64_t)g.j0 * h->L, he.size() * 8,
+                                          cudaMemcpyDeviceToHost, st));
+                    CUDAW(cudaStreamSynchronize(st));
+                    for (double e : he) if (!(e <= h->tol)) notconv = true;
+                    CUDAW(cudaMemsetAsync(g.active, 0, (size_t)g.np * 4, st));
+                    g.done = true;
+                    continue;
+                }
+                ++active_groups;
+            }
+            if (nonfinite || notconv || active_groups == 0) break;
+            evs.start(st);
+            TRYW(launch_dense_solve<R>(d_jobs, nj, 0, st));
+            evs.stop(st);
+            pending = true;
+            ++solves;
+            for (auto& g : groups) {
+                if (g.done) continue;
+                rsrr_nep h = hs[g.hi];
+                const int64_t nl = h->n * h->L;
+                { accumulate_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(
+                      h->d_S + (int64_t)g.j0 * nl, g.x, nl, 1, g.active); note_launch(); }
+                ++g.sweeps;
+            }
+        }
+        CUDAW(cudaStreamSynchronize(st));
+        if (pending) ms_s += evs.ms();
+        tot_trsv_ms += ms_s;
+        tot_trsv_launches += solves;
+        for (auto& g : groups) hs[g.hi]->refine_sweeps = std::max(hs[g.hi]->refine_sweeps, g.sweeps);
+        cleanup();
+#undef TRYW
+#undef CUDAW
+    }
+    dfree(d_next, st);
+    RSRR_CUDA(cudaStreamSynchronize(st));
+    for (rsrr_nep h : hs) {
+        h->ms_factor = tot_factor_ms;
+        h->ms_trsv = tot_trsv_ms;
+        h->factor_launches = tot_factor_launches;
+        h->trsv_launches = tot_trsv_launches;
+    }
+    if (singular) return set_error(RSRR_ESINGULAR, "zero pivot: a sampling point is an eigenvalue of T");
+    if (nonfinite) return set_error(RSRR_ENONFINITE, "non-finite backward error in a sample solve");
+    if (notconv) return set_error(RSRR_ENOTCONVERGED, "sample solves did not reach the backward-error tolerance");
+    return rc;
+}
+
 }  // namespace
 
-int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
+// Coefficient table F (host FP64), the probing matrix on the device (permuted to the band
+// ordering) and S_hat storage for the sampling set up on h.
+int sample_prepare(rsrr_nep h, const double* U_reim, std::vector<c128>* Fout) {
     cudaStream_t st = h->stream;
     const int64_t n = h->n;
     const int N = h->N, L = h->L, J = h->J;
     // coefficient table F[j][i] = f_i(z_j) (host FP64)
     std::vector<zd> z;
     contour_nodes(h->C, N, &z, nullptr);
-    std::vector<c128> F((size_t)N * J);
+    std::vector<c128>& F = *Fout;
+    F.assign((size_t)N * J, czero<double>());
     for (int j = 0; j < N; ++j)
         for (int i = 0; i < J; ++i) {
             zd v, dv;
@@ -423,8 +670,66 @@ int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
         RSRR_TRY(dalloc_n(&h->d_eta, cols, st));
         h->S_cols_cap = cols;
     }
-    if (h->precision == RSRR_FP64) return sample_impl<double>(h, F, max_refine);
-    return sample_impl<float>(h, F, max_refine);
+    return RSRR_OK;
+}
+
+bool use_dense(const rsrr_nep h) {
+    const int64_t n = h->n, kl = h->ord.kl, ku = h->ord.ku;
+    return h->force_dense || kl > 768 || ku > 768 || (n >= 128 && 5 * (kl + ku) > 2 * n);
+}
+
+namespace {
+template <typename R>
+int dense_run(const std::vector<rsrr_nep>& hs, const std::vector<std::vector<c128>>& Fs, int max_refine) {
+    std::vector<c128*> dF(hs.size(), nullptr);
+    cudaStream_t st = hs.empty() ? nullptr : hs[0]->stream;
+    int rc = RSRR_OK;
+    for (size_t i = 0; i < hs.size() && rc == RSRR_OK; ++i) {
+        rc = dalloc_n(&dF[i], Fs[i].size(), st);
+        if (rc == RSRR_OK) {
+            cudaError_t e = cudaMemcpyAsync(dF[i], Fs[i].data(), Fs[i].size() * sizeof(c128), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) rc = set_error(RSRR_ECUDA, std::string("cudaMemcpyAsync(F): ") + cudaGetErrorString(e));
+        }
+    }
+    if (rc == RSRR_OK) rc = sample_dense_set<R>(hs, dF, max_refine);
+    for (c128* p : dF) dfree(p, st);
+    return rc;
+}
+}  // namespace
+
+int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
+    std::vector<std::vector<c128>> F(1);
+    RSRR_TRY(sample_prepare(h, U_reim, &F[0]));
+    h->dense_used = use_dense(h);
+    if (h->dense_used) {
+        std::vector<rsrr_nep> hs{h};
+        return h->precision == RSRR_FP64 ? dense_run<double>(hs, F, max_refine) : dense_run<float>(hs, F, max_refine);
+    }
+    if (h->precision == RSRR_FP64) return sample_impl<double>(h, F[0], max_refine);
+    return sample_impl<float>(h, F[0], max_refine);
+}
+
+// Several NEPs in one call: the dense ones share the persistent dense-LU launches, the banded
+// ones run one after another on the band path.  All handles use one stream and one precision.
+int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const double*>& U, int max_refine) {
+    std::vector<std::vector<c128>> F(hs.size());
+    for (size_t i = 0; i < hs.size(); ++i) RSRR_TRY(sample_prepare(hs[i], U[i], &F[i]));
+    std::vector<rsrr_nep> dh;
+    std::vector<std::vector<c128>> dFs;
+    for (size_t i = 0; i < hs.size(); ++i) {
+        hs[i]->dense_used = use_dense(hs[i]);
+        if (hs[i]->dense_used) {
+            dh.push_back(hs[i]);
+            dFs.push_back(F[i]);
+        }
+    }
+    const bool fp64 = hs[0]->precision == RSRR_FP64;
+    if (!dh.empty()) RSRR_TRY(fp64 ? dense_run<double>(dh, dFs, max_refine) : dense_run<float>(dh, dFs, max_refine));
+    for (size_t i = 0; i < hs.size(); ++i) {
+        if (use_dense(hs[i])) continue;
+        RSRR_TRY(fp64 ? sample_impl<double>(hs[i], F[i], max_refine) : sample_impl<float>(hs[i], F[i], max_refine));
+    }
+    return RSRR_OK;
 }
 
 }  // namespace rsrr

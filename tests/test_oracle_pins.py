@@ -220,3 +220,35 @@ def test_config1b_small_closed_form():
     r = o.rsrr(p, N_S=500)
     assert r["lam"].size == exact.size
     assert match(r["lam"], exact) < 1e-9
+
+
+@pytest.mark.parametrize("s,idx", [(8, 0), (10, 2), (12, 0)])
+def test_config3_shape_linear_case_matches_eig(s, idx):
+    """Time-delay batch member with tau = 0: T(z) = -zI + A0 + A1 is linear, so its eigenvalues
+    are those of A0 + A1 (numpy eig, dense); the oracle's dense path must find exactly the ones
+    inside the circle."""
+    p = w.config3_member(idx, s=s, N=32, L=8, tau=0.0)
+    ev = np.linalg.eigvals(p.term(1).toarray() + p.term(2).toarray())
+    inside = ev[o.inside_contour(ev, p.gamma, p.a, p.b)]
+    r = o.rsrr(p, dense=True)
+    assert r["lam"].size == inside.size > 0
+    assert match(r["lam"], inside) < 1e-9
+
+
+@pytest.mark.parametrize("s,idx", [(8, 0), (10, 2)])
+def test_config3_member_count_and_perturbation_bound(s, idx):
+    """Time-delay member (tau > 0): on the circle Re z > 30, so e^{-tau z} A1 is a tiny
+    perturbation of A0 and (Bauer-Fike, A0 symmetric) every eigenvalue lies within
+    |e^{-tau lambda}| ||A1||_2 of a closed-form Laplacian level; the count inside equals the
+    number of levels (with multiplicity) inside."""
+    p = w.config3_member(idx, s=s, N=32, L=8)
+    h = 1.0 / (s + 1)
+    l1 = 4.0 / h ** 2 * np.sin(np.arange(1, s + 1) * np.pi * h / 2) ** 2
+    mu = (l1[:, None] + l1[None, :]).ravel().astype(complex)
+    count = int(np.count_nonzero(o.inside_contour(mu, p.gamma, p.a, p.b)))
+    r = o.rsrr(p, dense=True)
+    assert r["lam"].size == count > 0
+    bound = np.abs(np.exp(-p.meta["tau"] * r["lam"])) * np.linalg.norm(p.term(2).toarray(), 2)
+    dist = np.min(np.abs(r["lam"][:, None] - mu[None, :]), axis=1)
+    assert np.all(dist <= bound * (1 + 1e-6) + 1e-9)
+    assert r["resid_scaled"].max() < 1e-10

@@ -1,0 +1,38 @@
+"""Admission logic of the RSRR server (host only): arrival order, bypass by smaller requests
+within the budget, and the bypass limit that prevents starvation."""
+from types import SimpleNamespace
+
+from paper_1510_07522_gb300.serve import footprint_bytes, select_admissible
+
+
+def req(fp, bypassed=0):
+    return SimpleNamespace(footprint=fp, bypassed=bypassed)
+
+
+def test_oldest_fitting_request_first():
+    q = [req(10), req(5), req(1)]
+    assert select_admissible(q, 100, 4) == 0
+
+
+def test_smaller_request_passes_a_blocked_one():
+    q = [req(80), req(10), req(5)]
+    i = select_admissible(q, 50, 4)
+    assert i == 1 and q[0].bypassed == 1 and q[1].bypassed == 0
+
+
+def test_bypass_limit_blocks_queue():
+    q = [req(80, bypassed=4), req(10)]
+    assert select_admissible(q, 50, 4) is None
+
+
+def test_nothing_fits():
+    assert select_admissible([req(80), req(90)], 50, 4) is None
+    assert select_admissible([], 50, 4) is None
+
+
+def test_footprint_grows_with_band_and_points():
+    a = footprint_bytes(40000, 200, 200, 64, 32, 200000, 3)
+    b = footprint_bytes(40000, 200, 200, 32, 32, 200000, 3)
+    c = footprint_bytes(40000, 100, 100, 64, 32, 200000, 3)
+    assert a > b and a > c
+    assert 15e9 < a < 40e9  # 64 points of a band-200 problem: ~17.5 GB of factors plus S_hat

@@ -235,12 +235,14 @@ def _laplacian_levels(s):
     return lev
 
 
-def config3_member(idx, s=None, N=32, L=8, master_seed=3):
-    """Member `idx` of the time-delay batch; A0 = (s+1)^2 * 5-point, A1 Bernoulli(0.05)."""
+def config3_member(idx, s=None, N=32, L=8, master_seed=3, tau=None):
+    """Member `idx` of the time-delay batch; A0 = (s+1)^2 * 5-point, A1 Bernoulli(0.05).
+    `tau` overrides the drawn delay (tau = 0 makes T linear: -zI + A0 + A1)."""
     rng = np.random.default_rng([master_seed, 0, idx])
     if s is None:
         s = int(rng.integers(20, 101))
-    tau = float(rng.uniform(0.5, 2.0))
+    tau_drawn = float(rng.uniform(0.5, 2.0))
+    tau = tau_drawn if tau is None else float(tau)
     n = s * s
     h = 1.0 / (s + 1)
     A0 = grid_laplacian(s, s, h, h)
