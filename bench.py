@@ -351,11 +351,12 @@ def cpu_dense_rate(probs, seconds=15.0):
     done_flops, t0, npts = 0.0, time.perf_counter(), 0
     for p in small:
         pts = list(range(min(p.N, cores)))
+        el = time.perf_counter() - t0
+        if npts and el + len(pts) * dense_lu_flops(p.n) / (done_flops / el) > seconds:
+            break  # the next member would overrun the sample's time budget
         oracle.sample(p, points=pts, threads=cores, dense=True)
         done_flops += len(pts) * dense_lu_flops(p.n)
         npts += len(pts)
-        if time.perf_counter() - t0 > seconds:
-            break
     el = time.perf_counter() - t0
     rate = done_flops / el
     mean_flops = sum(p.N * dense_lu_flops(p.n) for p in probs) / sum(p.N for p in probs)
