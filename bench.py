@@ -63,7 +63,8 @@ def parse():
                          "Poisson request stream through the continuous-batching server")
     ap.add_argument("--precision", default=None, choices=["c64", "fp64"], help="default: the config's own")
     ap.add_argument("--tol", type=float, default=1e-10, help="acceptance: eta <= tol per column")
-    ap.add_argument("--grid", type=int, default=0, help="grid side override (0 = the config's own size)")
+    ap.add_argument("--grid", type=int, default=0, help="grid side override (0 = the config's own size; config 3: "
+                                                       "every member on an s x s grid)")
     ap.add_argument("--rates", default="1,4,16", help="serve: Poisson arrival rates, requests/s")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per rate")
     ap.add_argument("--batch", type=int, default=0, help="config 3: members of the batch (0 = the config's own)")
@@ -333,9 +334,9 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def batch_members(count):
+def batch_members(count, side=0):
     import workloads
-    return [workloads.config3_member(i) for i in range(count)]
+    return [workloads.config3_member(i, s=side or None) for i in range(count)]
 
 
 def dense_lu_flops(n):
@@ -378,7 +379,7 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS["3"]
     B = args.batch or W["batch"]
-    probs = batch_members(B)
+    probs = batch_members(B, args.grid)
     precision = args.precision or W["precision"]
     prec = (rs.RSRR_C64_IR if precision == "c64" else rs.RSRR_FP64) | rs.RSRR_REFINE_FULL
     stream = torch.cuda.current_stream()

@@ -33,7 +33,7 @@ constexpr int NW = NT / 32;
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename R> struct DTile;
-template <> struct DTile<float> { static constexpr int TM = 128, TN = 128, MI = 8, MJ = 8; };
+template <> struct DTile<float> { static constexpr int TM = 128, TN = 128; };  // trailing rows only
 template <> struct DTile<double> { static constexpr int TM = 64, TN = 64, MI = 4, MJ = 4; };
 
 template <typename R>
@@ -48,9 +48,19 @@ template <typename R>
 constexpr size_t inverse_smem() {
     return (size_t)3 * NB * NBP * sizeof(cplx<R>);
 }
+// Tensor-core trailing update (complex64): an L21 tile of 128 rows and a U12 block of 32 columns,
+// each as four TF32 arrays (re hi, re lo, im hi, im lo) with K = 64 in the 128-byte-swizzled
+// K-major layout the MMA reads; two U12 buffers; +1024 B to align the operand base.
+constexpr uint32_t TC_ROWS = 128, TC_COLS = 32;
+constexpr uint32_t TC_A_FLOATS = 4 * TC_ROWS * NB;   // 32768 floats = 128 KB
+constexpr uint32_t TC_B_FLOATS = 4 * TC_COLS * NB;   // 8192 floats = 32 KB
+constexpr uint32_t TC_A_BYTES = TC_A_FLOATS * 4, TC_B_BYTES = TC_B_FLOATS * 4;
+constexpr uint32_t TC_TMEM_COLS = 128;               // two accumulator buffers of (32 re + 32 im) columns
+constexpr size_t tc_smem() { return (size_t)TC_A_BYTES + 2 * TC_B_BYTES + 1024; }
+
 template <typename R>
 constexpr size_t factor_smem() {
-    return std::max(gemm_smem<R>(), std::max(rows_smem<R>(), inverse_smem<R>()));
+    return std::max(sizeof(R) == 4 ? tc_smem() : gemm_smem<R>(), std::max(rows_smem<R>(), inverse_smem<R>()));
 }
 
 struct DShared {
@@ -410,8 +420,231 @@ __device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>*
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Complex64 trailing update on the tensor cores (tcgen05, kind::tf32).
+//
+// A22 -= L21 U12 in real arithmetic is four real products (Lr Ur, -Li Ui into the real part;
+// Lr Ui, Li Ur into the imaginary part).  Each FP32 operand x is split into TF32 hi + lo
+// (hi = round(x), lo = round(x - hi)) and a product is taken as hi*hi + hi*lo + lo*hi with FP32
+// accumulation in tensor memory, which keeps FP32-level accuracy (the dropped lo*lo is ~2^-22
+// relative); the FP64 refinement of the sample solves sits on top as for the CUDA-core path.
+//
+// Per panel the operands are split once into "images" in global memory whose bytes are exactly
+// the shared-memory layout the MMA reads (K-major, 128-byte swizzle, K = 64 as two 32-wide
+// halves): one 128 KB image per 128-row tile of L21 and one 32 KB image per 32-column block of
+// U12.  For each L21 tile the MMA issuer (thread 0) bulk-copies the tile, then walks the U12
+// blocks with two smem buffers and two TMEM accumulators, so the copy of block t+2, the MMAs of
+// block t+1 and the epilogue of block t (all 8 warps: TMEM -> registers, C -= D in global
+// memory) overlap.  Every wait is bounded; a timeout marks the job failed.
+// ------------------------------------------------------------------------------------------
+struct TcShared {
+    uint64_t bar[5];     // 0: L21 tile, 1-2: U12 buffers, 3-4: MMA completion per accumulator buffer
+    uint32_t tmem;       // tensor-memory base address
+    int fail;
+};
+struct TcPhase {
+    uint32_t a = 0, b0 = 0, b1 = 0, m0 = 0, m1 = 0;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Float index of (row r, k < 32) in a 128-byte-swizzled region of 32-float rows.
+__device__ __forceinline__ uint32_t sw128_index(int r, int k) {
+    uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + k * 4);
+    off ^= ((off >> 7) & 7) << 4;
+    return off >> 2;
+}
+// Float index of (row r, k < 64) of split array q in an operand image of `rows` rows.
+__device__ __forceinline__ uint32_t img_index(int q, int r, int k, int rows) {
+    return (uint32_t)(q * rows * NB + (k >> 5) * rows * 32) + sw128_index(r, k & 31);
+}
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void put_split(float* t, int r, int k, int rows, float re, float im) {
+    const float rh = tf32_round(re), ih = tf32_round(im);
+    t[img_index(0, r, k, rows)] = rh;
+    t[img_index(1, r, k, rows)] = tf32_round(re - rh);
+    t[img_index(2, r, k, rows)] = ih;
+    t[img_index(3, r, k, rows)] = tf32_round(im - ih);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Wait for the phase of `bar` with the given parity; gives up after ~0.1-1 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (it > 32) __nanosleep(128);
+    }
+    return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// L21 (rows k0+NB.., panel columns) -> one image per 128-row tile; rows past n are zero.
+__device__ void emit_a_image(const c64* A, int64_t lda, int n, int k0, float* img) {
+    const int r_begin = k0 + NB, m = n - r_begin;
+    const int rows_pad = (m + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
+    for (int idx = threadIdx.x; idx < rows_pad * NB; idx += NT) {
+        const int rr = idx % rows_pad, k = idx / rows_pad;
+        c64 v = czero<float>();
+        if (rr < m) v = A[(int64_t)(r_begin + rr) + (int64_t)(k0 + k) * lda];
+        put_split(img + (size_t)(rr / TC_ROWS) * TC_A_FLOATS, rr % TC_ROWS, k, TC_ROWS, v.re, v.im);
+    }
+}
+// U12 (panel rows, columns k0+NB..) -> one image per 32-column block; columns past n are zero.
+__device__ void emit_b_image(const c64* A, int64_t lda, int n, int k0, float* img) {
+    const int c_begin = k0 + NB, m = n - c_begin;
+    const int cols_pad = (m + TC_COLS - 1) / TC_COLS * TC_COLS;
+    for (int idx = threadIdx.x; idx < cols_pad * NB; idx += NT) {
+        const int k = idx % NB, cc = idx / NB;
+        c64 v = czero<float>();
+        if (cc < m) v = A[(int64_t)(k0 + k) + (int64_t)(c_begin + cc) * lda];
+        put_split(img + (size_t)(cc / TC_COLS) * TC_B_FLOATS, cc % TC_COLS, k, TC_COLS, v.re, v.im);
+    }
+}
+
+// All MMAs of one (L21 tile, U12 block) step into the accumulator pair at TMEM column dt:
+// re part at dt, im part at dt + 32.
+__device__ __forceinline__ void tc_issue(uint32_t sa, uint32_t sb, uint32_t dt) {
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((TC_COLS >> 3) << 17) | ((TC_ROWS >> 4) << 24);
+    const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pd[4] = {0, 0, 32, 32}, ng[4] = {0, 1, 0, 0};
+    uint32_t acc_r = 0, acc_i = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t id = idesc | (ng[p] ? (1u << 13) : 0u);  // negate A for -Li Ui
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {                             // hi*hi, hi*lo, lo*hi
+            const int qa = pa[p] * 2 + (s == 2 ? 1 : 0), qb = pb[p] * 2 + (s == 1 ? 1 : 0);
+#pragma unroll
+            for (int ks = 0; ks < NB / 8; ++ks) {
+                const uint32_t ao = (uint32_t)(qa * TC_ROWS * NB + (ks >> 2) * TC_ROWS * 32) * 4 + (ks & 3) * 32;
+                const uint32_t bo = (uint32_t)(qb * TC_COLS * NB + (ks >> 2) * TC_COLS * 32) * 4 + (ks & 3) * 32;
+                uint32_t& acc = pd[p] ? acc_i : acc_r;
+                tc_mma(dt + pd[p], sw128_desc(sa + ao), sw128_desc(sb + bo), id, acc);
+                acc = 1;
+            }
+        }
+    }
+}
+
+// C -= D for one 128 x 32 step: warp w reads TMEM lanes 32 (w % 4).., complex columns 16 (w / 4)..
+__device__ __forceinline__ void tc_epilogue(c64* A, int64_t lda, int n, int i0, int c0, uint32_t tbuf) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const uint32_t ta = tbuf + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 16);
+    float dr[16], di[16];
+    tc_ld16(ta, dr);
+    tc_ld16(ta + 32, di);
+    tc_wait_ld();
+    const int row = i0 + 32 * q + lane, cb = c0 + half * 16;
+    if (row < n) {
+        c64 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = (cb + c < n) ? A[row + (int64_t)(cb + c) * lda] : czero<float>();
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (cb + c < n) A[row + (int64_t)(cb + c) * lda] = mk<float>(v[c].re - dr[c], v[c].im - di[c]);
+    }
+}
+
+__device__ void trailing_update_tc(c64* A, int64_t lda, int n, int k0, unsigned char* smem_raw, const float* imgA,
+                                   const float* imgB, TcShared& ts, TcPhase& ph) {
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sB[2] = {base + TC_A_BYTES, base + TC_A_BYTES + TC_B_BYTES};
+    const int tid = threadIdx.x;
+    const int r_begin = k0 + NB, m = n - r_begin;
+    const int nrt = (m + TC_ROWS - 1) / TC_ROWS, ncb = (m + TC_COLS - 1) / TC_COLS;
+    for (int rt = 0; rt < nrt; ++rt) {
+        const int i0 = r_begin + rt * TC_ROWS;
+        if (tid == 0) {
+            mbar_expect_tx(&ts.bar[0], TC_A_BYTES);
+            for (int c = 0; c < 8; ++c)
+                bulk_g2s(base + c * (TC_A_BYTES / 8), imgA + (size_t)rt * TC_A_FLOATS + c * (TC_A_FLOATS / 8),
+                         TC_A_BYTES / 8, &ts.bar[0]);
+            mbar_expect_tx(&ts.bar[1], TC_B_BYTES);
+            bulk_g2s(sB[0], imgB, TC_B_BYTES, &ts.bar[1]);
+            if (ncb > 1) {
+                mbar_expect_tx(&ts.bar[2], TC_B_BYTES);
+                bulk_g2s(sB[1], imgB + TC_B_FLOATS, TC_B_BYTES, &ts.bar[2]);
+            }
+            const bool ok = mbar_wait(&ts.bar[0], ph.a) && mbar_wait(&ts.bar[1], ph.b0);
+            ph.a ^= 1;
+            ph.b0 ^= 1;
+            if (!ok) ts.fail = 1;
+            tc_fence_after();
+            if (!ts.fail) tc_issue(smem_u32(base), smem_u32(sB[0]), ts.tmem);
+            tc_commit(&ts.bar[3]);
+        }
+        for (int t = 0; t < ncb; ++t) {
+            const int b = t & 1;
+            if (!mbar_wait(&ts.bar[3 + b], b ? ph.m1 : ph.m0)) ts.fail = 1;
+            if (b) ph.m1 ^= 1; else ph.m0 ^= 1;
+            tc_fence_after();
+            if (tid == 0) {
+                if (t + 2 < ncb) {
+                    mbar_expect_tx(&ts.bar[1 + b], TC_B_BYTES);
+                    bulk_g2s(sB[b], imgB + (size_t)(t + 2) * TC_B_FLOATS, TC_B_BYTES, &ts.bar[1 + b]);
+                }
+                if (t + 1 < ncb) {
+                    const int nb = b ^ 1;
+                    if (!mbar_wait(&ts.bar[1 + nb], nb ? ph.b1 : ph.b0)) ts.fail = 1;
+                    if (nb) ph.b1 ^= 1; else ph.b0 ^= 1;
+                    tc_fence_after();
+                    if (!ts.fail) tc_issue(smem_u32(base), smem_u32(sB[nb]), ts.tmem + nb * 64);
+                    tc_commit(&ts.bar[3 + nb]);
+                }
+            }
+            __syncwarp();
+            tc_epilogue(A, lda, n, i0, r_begin + t * TC_COLS, ts.tmem + b * 64);
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+        }
+    }
+}
+
 template <typename R>
-__device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh) {
+__device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh, float* img, size_t img_b, TcShared* ts,
+                           TcPhase* ph) {
     const int n = J.n;
     const int64_t lda = J.lda;
     cplx<R>* A = J.a;
@@ -445,17 +678,54 @@ __device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh) {
         diag_inverses(Pg, lda, nbk, sm, J.inv + (int64_t)p * 2 * NB * NB);
         if (k0 + nbk < n) {
             trailing_rows(A, lda, n, k0, sm, sh);
-            trailing_update(A, lda, n, k0, sm);
+            if constexpr (sizeof(R) == 4) {
+                emit_a_image(A, lda, n, k0, img);
+                emit_b_image(A, lda, n, k0, img + img_b);
+                // the images (global) and the shared buffers were last touched through the generic
+                // proxy; the bulk copies and MMAs that follow go through the async proxy
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                trailing_update_tc(A, lda, n, k0, reinterpret_cast<unsigned char*>(sm), img, img + img_b, *ts, *ph);
+                if (ts->fail) {
+                    if (threadIdx.x == 0) sh.info = -1;
+                    break;
+                }
+            } else {
+                trailing_update(A, lda, n, k0, sm);
+            }
         }
     }
 }
 
+// img: per-CTA operand images (complex64 path), CTA b at img + b * img_stride, U12 images at
+// + img_b within it; unused (null) for complex128.
 template <typename R>
 __global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* __restrict__ jobs, int njobs,
-                                                             int32_t* __restrict__ next) {
+                                                             int32_t* __restrict__ next, float* img,
+                                                             size_t img_stride, size_t img_b) {
     extern __shared__ __align__(16) unsigned char dense_smem[];
     cplx<R>* sm = reinterpret_cast<cplx<R>*>(dense_smem);
     __shared__ DShared sh;
+    __shared__ __align__(8) TcShared ts;
+    TcPhase ph;
+    const bool tc = sizeof(R) == 4;
+    if (tc) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < 5; ++i) mbar_init(&ts.bar[i], 1);
+            ts.fail = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(&ts.tmem)), "r"(TC_TMEM_COLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    float* my_img = img ? img + (size_t)blockIdx.x * img_stride : nullptr;
     for (;;) {
         if (threadIdx.x == 0) {
             sh.job = atomicAdd(next, 1);
@@ -463,11 +733,21 @@ __global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* 
         }
         __syncthreads();
         const int jb = sh.job;
-        if (jb >= njobs) return;
+        if (jb >= njobs) break;
         const DenseJob<R> J = jobs[jb];
-        factor_one(J, sm, sh);
+        factor_one(J, sm, sh, my_img, img_b, &ts, &ph);
+        __syncthreads();
         if (threadIdx.x == 0) *J.info = sh.info;
         __syncthreads();
+        if (tc && ts.fail) break;
+    }
+    if (tc) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ts.tmem), "r"(TC_TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -625,13 +905,29 @@ int sm_count() {
 }  // namespace
 
 template <typename R>
-int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int32_t* d_next, cudaStream_t s) {
+int dense_factor_grid(int njobs) {
+    return std::max(1, std::min(njobs, sm_count()));
+}
+
+template <typename R>
+size_t dense_image_floats(int n_max) {
+    if (sizeof(R) != 4) return 0;
+    const size_t tiles = (size_t)(n_max + TC_ROWS - 1) / TC_ROWS, blocks = (size_t)(n_max + TC_COLS - 1) / TC_COLS;
+    return tiles * TC_A_FLOATS + blocks * TC_B_FLOATS;
+}
+
+template <typename R>
+int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int n_max, int32_t* d_next, float* d_img,
+                        cudaStream_t s) {
     if (njobs <= 0) return RSRR_OK;
+    if (sizeof(R) == 4 && !d_img) return set_error(RSRR_EINVAL, "dense factor: operand images missing");
     const size_t sm = factor_smem<R>();
     RSRR_TRY(set_smem(dense_factor_kernel<R>, sm, "dense_factor_kernel"));
     RSRR_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int32_t), s));
-    const int grid = std::min(njobs, sm_count());
-    { dense_factor_kernel<R><<<grid, NT, sm, s>>>(d_jobs, njobs, d_next); note_launch(); }
+    const int grid = dense_factor_grid<R>(njobs);
+    const size_t stride = dense_image_floats<R>(n_max);
+    const size_t img_b = sizeof(R) == 4 ? (size_t)((n_max + TC_ROWS - 1) / TC_ROWS) * TC_A_FLOATS : 0;
+    { dense_factor_kernel<R><<<grid, NT, sm, s>>>(d_jobs, njobs, d_next, d_img, stride, img_b); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
@@ -647,8 +943,12 @@ int launch_dense_solve(const DenseJob<R>* d_jobs, int njobs, int maxL, cudaStrea
     return RSRR_OK;
 }
 
-template int launch_dense_factor<float>(const DenseJob<float>*, int, int32_t*, cudaStream_t);
-template int launch_dense_factor<double>(const DenseJob<double>*, int, int32_t*, cudaStream_t);
+template int launch_dense_factor<float>(const DenseJob<float>*, int, int, int32_t*, float*, cudaStream_t);
+template int launch_dense_factor<double>(const DenseJob<double>*, int, int, int32_t*, float*, cudaStream_t);
+template int dense_factor_grid<float>(int);
+template int dense_factor_grid<double>(int);
+template size_t dense_image_floats<float>(int);
+template size_t dense_image_floats<double>(int);
 template int launch_dense_solve<float>(const DenseJob<float>*, int, int, cudaStream_t);
 template int launch_dense_solve<double>(const DenseJob<double>*, int, int, cudaStream_t);
 

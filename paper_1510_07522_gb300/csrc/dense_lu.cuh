@@ -53,8 +53,16 @@ inline size_t dense_aux_bytes(int64_t n) {
 
 // Factor every job (any order of sizes; the launcher expects them sorted largest first so
 // the last CTAs to finish hold the smallest points).  d_next: one int32 of device scratch.
+// Complex64 runs the trailing updates on the tensor cores and needs d_img: device scratch of
+// dense_factor_grid(njobs) * dense_image_floats(n_max) floats (n_max = the largest job's n);
+// complex128 ignores it.  A job whose tensor-core waits time out gets *info = -1.
 template <typename R>
-int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int32_t* d_next, cudaStream_t s);
+int dense_factor_grid(int njobs);
+template <typename R>
+size_t dense_image_floats(int n_max);
+template <typename R>
+int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int n_max, int32_t* d_next, float* d_img,
+                        cudaStream_t s);
 // X = A^{-1} X for every job (forward with the composed interchanges, then backward).
 template <typename R>
 int launch_dense_solve(const DenseJob<R>* d_jobs, int njobs, int maxL, cudaStream_t s);

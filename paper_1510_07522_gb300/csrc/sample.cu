@@ -455,7 +455,9 @@ int sample_dense_set(const std::vector<rsrr_nep>& hs, const std::vector<c128*>& 
         std::vector<DenseJob<R>> jobs;
         DenseJob<R>* d_jobs = nullptr;
         int32_t* d_counters = nullptr;
+        float* d_img = nullptr;
         auto cleanup = [&]() {
+            dfree(d_img, st);
             for (auto& g : groups) {
                 dfree(g.a, st); dfree(g.x, st); dfree(g.inv, st); dfree(g.ipiv, st); dfree(g.info, st);
                 dfree(g.swaps, st); dfree(g.active, st); dfree(g.tvals, st); dfree(g.colsum, st);
@@ -514,16 +516,30 @@ int sample_dense_set(const std::vector<rsrr_nep>& hs, const std::vector<c128*>& 
         const int nj = (int)jobs.size();
         TRYW(dalloc_n(&d_jobs, (size_t)nj, st));
         CUDAW(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)nj * sizeof(DenseJob<R>), cudaMemcpyHostToDevice, st));
+        int n_max = 0;
+        for (const auto& J : jobs) n_max = std::max(n_max, (int)J.n);
+        const size_t img_floats = (size_t)dense_factor_grid<R>(nj) * dense_image_floats<R>(n_max);
+        if (img_floats) TRYW(dalloc_n(&d_img, img_floats, st));
         EvPair evf, evs;
         evf.start(st);
-        TRYW(launch_dense_factor<R>(d_jobs, nj, d_next, st));
+        TRYW(launch_dense_factor<R>(d_jobs, nj, n_max, d_next, d_img, st));
         evf.stop(st);
-        std::vector<int32_t> hinfo;
+        bool timeout = false;
         for (auto& g : groups) {
             std::vector<int32_t> hi(g.np);
             CUDAW(cudaMemcpyAsync(hi.data(), g.info, (size_t)g.np * 4, cudaMemcpyDeviceToHost, st));
             CUDAW(cudaStreamSynchronize(st));
-            for (int32_t v : hi) if (v) singular = true;
+            for (int32_t v : hi) {
+                if (v > 0) singular = true;
+                if (v < 0) timeout = true;
+            }
+        }
+        dfree(d_img, st);
+        d_img = nullptr;
+        if (timeout) {
+            cleanup();
+            dfree(d_next, st);
+            return set_error(RSRR_ETIMEOUT, "dense LU: a tensor-core wait timed out");
         }
         tot_factor_ms += evf.ms();
         tot_factor_launches += 1;
