@@ -20,6 +20,8 @@
 #include <climits>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "dense_lu.cuh"
 
 namespace rsrr {
@@ -48,15 +50,17 @@ template <typename R>
 constexpr size_t inverse_smem() {
     return (size_t)3 * NB * NBP * sizeof(cplx<R>);
 }
-// Tensor-core trailing update (complex64): an L21 tile of 128 rows and a U12 block of 32 columns,
-// each as four TF32 arrays (re hi, re lo, im hi, im lo) with K = 64 in the 128-byte-swizzled
-// K-major layout the MMA reads; two U12 buffers; +1024 B to align the operand base.
-constexpr uint32_t TC_ROWS = 128, TC_COLS = 32;
-constexpr uint32_t TC_A_FLOATS = 4 * TC_ROWS * NB;   // 32768 floats = 128 KB
-constexpr uint32_t TC_B_FLOATS = 4 * TC_COLS * NB;   // 8192 floats = 32 KB
-constexpr uint32_t TC_A_BYTES = TC_A_FLOATS * 4, TC_B_BYTES = TC_B_FLOATS * 4;
-constexpr uint32_t TC_TMEM_COLS = 128;               // two accumulator buffers of (32 re + 32 im) columns
-constexpr size_t tc_smem() { return (size_t)TC_A_BYTES + 2 * TC_B_BYTES + 1024; }
+// Tensor-core trailing update (complex64): an L21 tile of 128 rows and a U12 block of 128
+// columns, each as six BF16 arrays (re hi, mid, lo; im hi, mid, lo) with K = 64 (one 128-byte
+// row) in the swizzled K-major layout the MMA reads; +1024 B to align the operand base.
+constexpr uint32_t TC_ROWS = 128, TC_COLS = 128;
+constexpr uint32_t TC_SPLIT = 3;                                     // bf16 pieces per FP32 value
+constexpr uint32_t TC_ARR = 2 * TC_SPLIT;                           // arrays per operand
+constexpr uint32_t TC_A_BYTES = TC_ARR * TC_ROWS * NB * 2;          // 96 KB
+constexpr uint32_t TC_B_BYTES = TC_ARR * TC_COLS * NB * 2;          // 96 KB
+constexpr uint32_t TC_A_FLOATS = TC_A_BYTES / 4, TC_B_FLOATS = TC_B_BYTES / 4;  // image sizes in 4-byte words
+constexpr uint32_t TC_TMEM_COLS = 512;               // two accumulator buffers of (128 re + 128 im) columns
+constexpr size_t tc_smem() { return (size_t)TC_A_BYTES + TC_B_BYTES + 1024; }
 
 template <typename R>
 constexpr size_t factor_smem() {
@@ -64,6 +68,7 @@ constexpr size_t factor_smem() {
 }
 
 struct DShared {
+    double2 u12[32 * 32];  // U12 of the panel's left leaf (32 x 32, complex64 or complex128)
     int piv[NB];        // panel pivots, relative to the panel's first row
     int rows[2 * NB];   // composed interchanges: row rows[e] receives row src[e]
     int src[2 * NB];
@@ -74,6 +79,9 @@ struct DShared {
     int red_i[NW];
     double red_v[NW];
 };
+
+template <typename R>
+__device__ __forceinline__ cplx<R>* sh_u12(DShared& sh) { return reinterpret_cast<cplx<R>*>(sh.u12); }
 
 // ------------------------------------------------------------------------------------------
 // cp.async element copies (src_bytes = 0 fills zeros; the source must still be a valid address)
@@ -140,17 +148,30 @@ __device__ void leaf_factor(cplx<R>* P, int64_t ld, int m, int w, int* piv, int 
         const bool zero = cis_zero(pv);
         if (zero && threadIdx.x == 0 && sh.info == 0) sh.info = col_base + c + 1;
         const cplx<R> rp = zero ? czero<R>() : crecip(pv);
+        // U row c of the leaf in shared memory (read by every thread); each row's entries are
+        // loaded in chunks before any is stored, so a tall leaf in global memory pays the memory
+        // latency once per chunk instead of once per column.
+        cplx<R>* urow = sh_u12<R>(sh);
+        if ((int)threadIdx.x < w) urow[threadIdx.x] = P[c + (int64_t)threadIdx.x * ld];
+        __syncthreads();
+        constexpr int QL = sizeof(R) == 4 ? 16 : 8;
         for (int r = c + 1 + (int)threadIdx.x; r < m; r += NT) {
             cplx<R> l = colc[r];
             if (!zero) {
                 l = l * rp;
                 colc[r] = l;
             }
-            for (int q = c + 1; q < w; ++q) {
-                cplx<R>* cq = P + (int64_t)q * ld;
-                cplx<R> v = cq[r];
-                cfms(v, l, cq[c]);
-                cq[r] = v;
+            for (int q0 = c + 1; q0 < w; q0 += QL) {
+                cplx<R> x[QL];
+#pragma unroll
+                for (int j = 0; j < QL; ++j)
+                    x[j] = (q0 + j < w) ? P[r + (int64_t)(q0 + j) * ld] : czero<R>();
+#pragma unroll
+                for (int j = 0; j < QL; ++j)
+                    if (q0 + j < w) {
+                        cfms(x[j], l, urow[q0 + j]);
+                        P[r + (int64_t)(q0 + j) * ld] = x[j];
+                    }
             }
         }
         __syncthreads();
@@ -187,16 +208,34 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
         }
     }
     __syncthreads();
-    for (int r = w1 + (int)threadIdx.x; r < m; r += NT) {  // A22 -= L21 U12 (K = 32)
+    // A22 -= L21 U12 (K = 32): U12 (32 x w2) is staged in shared memory (the caller's buffer
+    // past the panel when the panel itself is staged there); each row loads its L21 part and a
+    // chunk of its A22 part before storing anything.
+    cplx<R>* u12 = sh_u12<R>(sh);
+    for (int idx = threadIdx.x; idx < 32 * w2; idx += NT) {
+        const int s = idx % 32, q = idx / 32;
+        u12[q * 32 + s] = Rt[s + (int64_t)q * ld];
+    }
+    __syncthreads();
+    constexpr int QC = sizeof(R) == 4 ? 16 : 8;  // A22 columns per chunk
+    for (int r = w1 + (int)threadIdx.x; r < m; r += NT) {
         cplx<R> lrow[32];
 #pragma unroll
         for (int s = 0; s < 32; ++s) lrow[s] = P[r + (int64_t)s * ld];
-        for (int q = 0; q < w2; ++q) {
-            cplx<R>* cq = Rt + (int64_t)q * ld;
-            cplx<R> acc = cq[r];
+        for (int q0 = 0; q0 < w2; q0 += QC) {
+            cplx<R> x[QC];
 #pragma unroll
-            for (int s = 0; s < 32; ++s) cfms(acc, lrow[s], cq[s]);
-            cq[r] = acc;
+            for (int j = 0; j < QC; ++j)
+                x[j] = (q0 + j < w2) ? Rt[r + (int64_t)(q0 + j) * ld] : czero<R>();
+#pragma unroll
+            for (int j = 0; j < QC; ++j) {
+                if (q0 + j < w2) {
+                    const cplx<R>* uq = u12 + (q0 + j) * 32;
+#pragma unroll
+                    for (int s = 0; s < 32; ++s) cfms(x[j], lrow[s], uq[s]);
+                    Rt[r + (int64_t)(q0 + j) * ld] = x[j];
+                }
+            }
         }
     }
     __syncthreads();
@@ -421,29 +460,34 @@ __device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>*
 }
 
 // ------------------------------------------------------------------------------------------
-// Complex64 trailing update on the tensor cores (tcgen05, kind::tf32).
+// Complex64 trailing update on the tensor cores (tcgen05, kind::f16 with BF16 operands).
 //
 // A22 -= L21 U12 in real arithmetic is four real products (Lr Ur, -Li Ui into the real part;
-// Lr Ui, Li Ur into the imaginary part).  Each FP32 operand x is split into TF32 hi + lo
-// (hi = round(x), lo = round(x - hi)) and a product is taken as hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory, which keeps FP32-level accuracy (the dropped lo*lo is ~2^-22
-// relative); the FP64 refinement of the sample solves sits on top as for the CUDA-core path.
+// Lr Ui, Li Ur into the imaginary part).  Each FP32 operand x is split into three BF16 pieces
+// x = h + m + l (h = bf16(x), m = bf16(x - h), l = bf16(x - h - m): 24 significant bits), and a
+// product is taken as the six piece products of order >= 2^-16 (hh, hm, mh, hl, mm, lh) with
+// FP32 accumulation in tensor memory: FP32-level accuracy (what is dropped is ~2^-24 relative).
+// The FP64 refinement of the sample solves sits on top as for the CUDA-core path.  Against a
+// two-piece TF32 split (three products) this is the same tensor time, but the operands take
+// 12 instead of 16 bytes per complex value, which lets a 128 x 128 step fit in shared memory:
+// N = 128 per MMA keeps the operand reads per MMA within the shared-memory bandwidth.
 //
 // Per panel the operands are split once into "images" in global memory whose bytes are exactly
-// the shared-memory layout the MMA reads (K-major, 128-byte swizzle, K = 64 as two 32-wide
-// halves): one 128 KB image per 128-row tile of L21 and one 32 KB image per 32-column block of
-// U12.  For each L21 tile the MMA issuer (thread 0) bulk-copies the tile, then walks the U12
-// blocks with two smem buffers and two TMEM accumulators, so the copy of block t+2, the MMAs of
-// block t+1 and the epilogue of block t (all 8 warps: TMEM -> registers, C -= D in global
-// memory) overlap.  Every wait is bounded; a timeout marks the job failed.
+// the shared-memory layout the MMA reads (K-major, 128-byte swizzle, K = 64 = one 128-byte row):
+// one 96 KB image per 128-row tile of L21 and one per 128-column block of U12.  For each L21
+// tile the MMA issuer (thread 0) bulk-copies the tile, then walks the U12 blocks through one smem
+// buffer and two TMEM accumulator pairs: while all 8 warps run the epilogue of block t (C
+// prefetched from global memory, TMEM -> registers, C -= D), thread 0 refills the buffer with
+// block t+1 and issues its MMAs.  Every wait is bounded; a timeout marks the job failed.
 // ------------------------------------------------------------------------------------------
 struct TcShared {
-    uint64_t bar[5];     // 0: L21 tile, 1-2: U12 buffers, 3-4: MMA completion per accumulator buffer
+    // 0: L21 tile; 1: U12 buffer; 5 + b: MMAs into accumulator pair b done (2-4 unused)
+    uint64_t bar[7];
     uint32_t tmem;       // tensor-memory base address
     int fail;
 };
 struct TcPhase {
-    uint32_t a = 0, b0 = 0, b1 = 0, m0 = 0, m1 = 0;
+    uint32_t a = 0, bh[2] = {0, 0}, h0[2] = {0, 0}, d[2] = {0, 0};
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -453,27 +497,27 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// Float index of (row r, k < 32) in a 128-byte-swizzled region of 32-float rows.
-__device__ __forceinline__ uint32_t sw128_index(int r, int k) {
-    uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + k * 4);
+// Index (in 2-byte elements) of (row r, k < 64) in a 128-byte-swizzled region of 64-element rows.
+__device__ __forceinline__ uint32_t sw128_index16(int r, int k) {
+    uint32_t off = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + k * 2);
     off ^= ((off >> 7) & 7) << 4;
-    return off >> 2;
+    return off >> 1;
 }
-// Float index of (row r, k < 64) of split array q in an operand image of `rows` rows.
-__device__ __forceinline__ uint32_t img_index(int q, int r, int k, int rows) {
-    return (uint32_t)(q * rows * NB + (k >> 5) * rows * 32) + sw128_index(r, k & 31);
-}
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-__device__ __forceinline__ void put_split(float* t, int r, int k, int rows, float re, float im) {
-    const float rh = tf32_round(re), ih = tf32_round(im);
-    t[img_index(0, r, k, rows)] = rh;
-    t[img_index(1, r, k, rows)] = tf32_round(re - rh);
-    t[img_index(2, r, k, rows)] = ih;
-    t[img_index(3, r, k, rows)] = tf32_round(im - ih);
+// Write the six BF16 pieces of (re, im) at (row r, k) of an operand image with `rows` rows:
+// array q (0..2 re hi/mid/lo, 3..5 im hi/mid/lo) occupies rows * 64 elements.
+__device__ __forceinline__ void put_split(__nv_bfloat16* t, int r, int k, int rows, float re, float im) {
+    const uint32_t at = sw128_index16(r, k), stride = (uint32_t)rows * NB;
+    float x[2] = {re, im};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x[c]);
+        const float r1 = x[c] - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        t[(3 * c + 0) * stride + at] = h;
+        t[(3 * c + 1) * stride + at] = m;
+        t[(3 * c + 2) * stride + at] = l;
+    }
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -486,23 +530,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// Wait for the phase of `bar` with the given parity; gives up after ~0.1-1 s.
+// Wait for the phase of `bar` with the given parity (spin, then back off); gives up after ~0.1-1 s.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    for (uint32_t it = 0; it < (1u << 21); ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return true;
-        if (it > 32) __nanosleep(128);
+        if (it > 4096) __nanosleep(64);
     }
     return false;
+}
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                  ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -528,10 +575,11 @@ __device__ void emit_a_image(const c64* A, int64_t lda, int n, int k0, float* im
         const int rr = idx % rows_pad, k = idx / rows_pad;
         c64 v = czero<float>();
         if (rr < m) v = A[(int64_t)(r_begin + rr) + (int64_t)(k0 + k) * lda];
-        put_split(img + (size_t)(rr / TC_ROWS) * TC_A_FLOATS, rr % TC_ROWS, k, TC_ROWS, v.re, v.im);
+        put_split(reinterpret_cast<__nv_bfloat16*>(img + (size_t)(rr / TC_ROWS) * TC_A_FLOATS), rr % TC_ROWS, k,
+                  TC_ROWS, v.re, v.im);
     }
 }
-// U12 (panel rows, columns k0+NB..) -> one image per 32-column block; columns past n are zero.
+// U12 (panel rows, columns k0+NB..) -> one image per 128-column block; columns past n are zero.
 __device__ void emit_b_image(const c64* A, int64_t lda, int n, int k0, float* img) {
     const int c_begin = k0 + NB, m = n - c_begin;
     const int cols_pad = (m + TC_COLS - 1) / TC_COLS * TC_COLS;
@@ -539,102 +587,120 @@ __device__ void emit_b_image(const c64* A, int64_t lda, int n, int k0, float* im
         const int k = idx % NB, cc = idx / NB;
         c64 v = czero<float>();
         if (cc < m) v = A[(int64_t)(k0 + k) + (int64_t)(c_begin + cc) * lda];
-        put_split(img + (size_t)(cc / TC_COLS) * TC_B_FLOATS, cc % TC_COLS, k, TC_COLS, v.re, v.im);
+        put_split(reinterpret_cast<__nv_bfloat16*>(img + (size_t)(cc / TC_COLS) * TC_B_FLOATS), cc % TC_COLS, k,
+                  TC_COLS, v.re, v.im);
     }
 }
 
 // All MMAs of one (L21 tile, U12 block) step into the accumulator pair at TMEM column dt:
-// re part at dt, im part at dt + 32.
-__device__ __forceinline__ void tc_issue(uint32_t sa, uint32_t sb, uint32_t dt) {
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((TC_COLS >> 3) << 17) | ((TC_ROWS >> 4) << 24);
-    const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pd[4] = {0, 0, 32, 32}, ng[4] = {0, 1, 0, 0};
+// re part at dt, im part at dt + 128.  Descriptors are built once; an offset of o bytes inside
+// an operand buffer is + (o >> 4) on the descriptor (no carry: the buffers lie below 256 KB).
+__device__ __forceinline__ void tc_issue(uint64_t adesc, uint64_t bdesc, uint32_t dt) {
+    // kind::f16: F32 accumulate, BF16 A and B, K-major both, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_COLS >> 3) << 17) | ((TC_ROWS >> 4) << 24);
+    const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pd[4] = {0, 0, 128, 128}, ng[4] = {0, 1, 0, 0};
+    const int sa[6] = {0, 0, 1, 0, 1, 2}, sb[6] = {0, 1, 0, 2, 1, 0};  // hh hm mh hl mm lh
     uint32_t acc_r = 0, acc_i = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t id = idesc | (ng[p] ? (1u << 13) : 0u);  // negate A for -Li Ui
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {                             // hi*hi, hi*lo, lo*hi
-            const int qa = pa[p] * 2 + (s == 2 ? 1 : 0), qb = pb[p] * 2 + (s == 1 ? 1 : 0);
+        for (int s = 0; s < 6; ++s) {
+            const uint32_t qa = pa[p] * TC_SPLIT + sa[s], qb = pb[p] * TC_SPLIT + sb[s];
 #pragma unroll
-            for (int ks = 0; ks < NB / 8; ++ks) {
-                const uint32_t ao = (uint32_t)(qa * TC_ROWS * NB + (ks >> 2) * TC_ROWS * 32) * 4 + (ks & 3) * 32;
-                const uint32_t bo = (uint32_t)(qb * TC_COLS * NB + (ks >> 2) * TC_COLS * 32) * 4 + (ks & 3) * 32;
+            for (int ks = 0; ks < NB / 16; ++ks) {
+                const uint32_t ao = qa * TC_ROWS * NB * 2 + ks * 32;
+                const uint32_t bo = qb * TC_COLS * NB * 2 + ks * 32;
                 uint32_t& acc = pd[p] ? acc_i : acc_r;
-                tc_mma(dt + pd[p], sw128_desc(sa + ao), sw128_desc(sb + bo), id, acc);
+                tc_mma(dt + pd[p], adesc + (ao >> 4), bdesc + (bo >> 4), id, acc);
                 acc = 1;
             }
         }
     }
 }
 
-// C -= D for one 128 x 32 step: warp w reads TMEM lanes 32 (w % 4).., complex columns 16 (w / 4)..
-__device__ __forceinline__ void tc_epilogue(c64* A, int64_t lda, int n, int i0, int c0, uint32_t tbuf) {
+// C -= D for one 128 x 128 step: warp w reads TMEM lanes 32 (w % 4).., complex columns 64 (w / 4)..
+// in two chunks of 32.  `v` holds a chunk of C values, loaded before the TMEM data is waited for.
+__device__ __forceinline__ void tc_load_c(const c64* A, int64_t lda, int n, int i0, int c0, int chunk, c64* v) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
-    const uint32_t ta = tbuf + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 16);
-    float dr[16], di[16];
-    tc_ld16(ta, dr);
-    tc_ld16(ta + 32, di);
-    tc_wait_ld();
-    const int row = i0 + 32 * q + lane, cb = c0 + half * 16;
-    if (row < n) {
-        c64 v[16];
+    const int row = i0 + 32 * q + lane, cb = c0 + half * 64 + chunk * 32;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = (cb + c < n) ? A[row + (int64_t)(cb + c) * lda] : czero<float>();
+    for (int c = 0; c < 32; ++c)
+        v[c] = (row < n && cb + c < n) ? A[row + (int64_t)(cb + c) * lda] : czero<float>();
+}
+__device__ __forceinline__ void tc_store_c(c64* A, int64_t lda, int n, int i0, int c0, int chunk, uint32_t tbuf,
+                                           const c64* v) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+    const uint32_t ta = tbuf + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 64 + chunk * 32);
+    const int row = i0 + 32 * q + lane, cb = c0 + half * 64 + chunk * 32;
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (cb + c < n) A[row + (int64_t)(cb + c) * lda] = mk<float>(v[c].re - dr[c], v[c].im - di[c]);
+    for (int h = 0; h < 2; ++h) {
+        float dr[16], di[16];
+        tc_ld16(ta + h * 16, dr);
+        tc_ld16(ta + 128 + h * 16, di);
+        tc_wait_ld();
+        if (row < n) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int col = cb + h * 16 + c;
+                if (col < n) A[row + (int64_t)col * lda] = mk<float>(v[h * 16 + c].re - dr[c], v[h * 16 + c].im - di[c]);
+            }
+        }
     }
 }
 
 __device__ void trailing_update_tc(c64* A, int64_t lda, int n, int k0, unsigned char* smem_raw, const float* imgA,
                                    const float* imgB, TcShared& ts, TcPhase& ph) {
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sB[2] = {base + TC_A_BYTES, base + TC_A_BYTES + TC_B_BYTES};
+    unsigned char* sB = base + TC_A_BYTES;
+    const uint64_t adesc = sw128_desc(smem_u32(base)), bdesc = sw128_desc(smem_u32(sB));
     const int tid = threadIdx.x;
     const int r_begin = k0 + NB, m = n - r_begin;
     const int nrt = (m + TC_ROWS - 1) / TC_ROWS, ncb = (m + TC_COLS - 1) / TC_COLS;
+    auto copy_b = [&](int blk) {
+        mbar_expect_tx(&ts.bar[1], TC_B_BYTES);
+        const float* src = imgB + (size_t)blk * TC_B_FLOATS;
+        for (int c = 0; c < 6; ++c)
+            bulk_g2s(sB + c * (TC_B_BYTES / 6), src + c * (TC_B_FLOATS / 6), TC_B_BYTES / 6, &ts.bar[1]);
+        if (blk + 1 < ncb) prefetch_l2(src + TC_B_FLOATS, TC_B_BYTES);
+    };
+    c64 v[32];
     for (int rt = 0; rt < nrt; ++rt) {
         const int i0 = r_begin + rt * TC_ROWS;
         if (tid == 0) {
             mbar_expect_tx(&ts.bar[0], TC_A_BYTES);
-            for (int c = 0; c < 8; ++c)
-                bulk_g2s(base + c * (TC_A_BYTES / 8), imgA + (size_t)rt * TC_A_FLOATS + c * (TC_A_FLOATS / 8),
-                         TC_A_BYTES / 8, &ts.bar[0]);
-            mbar_expect_tx(&ts.bar[1], TC_B_BYTES);
-            bulk_g2s(sB[0], imgB, TC_B_BYTES, &ts.bar[1]);
-            if (ncb > 1) {
-                mbar_expect_tx(&ts.bar[2], TC_B_BYTES);
-                bulk_g2s(sB[1], imgB + TC_B_FLOATS, TC_B_BYTES, &ts.bar[2]);
-            }
-            const bool ok = mbar_wait(&ts.bar[0], ph.a) && mbar_wait(&ts.bar[1], ph.b0);
+            for (int c = 0; c < 6; ++c)
+                bulk_g2s(base + c * (TC_A_BYTES / 6), imgA + (size_t)rt * TC_A_FLOATS + c * (TC_A_FLOATS / 6),
+                         TC_A_BYTES / 6, &ts.bar[0]);
+            if (rt + 1 < nrt) prefetch_l2(imgA + (size_t)(rt + 1) * TC_A_FLOATS, TC_A_BYTES);
+            copy_b(0);
+            const bool ok = mbar_wait(&ts.bar[0], ph.a) && mbar_wait(&ts.bar[1], ph.bh[0]);
             ph.a ^= 1;
-            ph.b0 ^= 1;
+            ph.bh[0] ^= 1;
             if (!ok) ts.fail = 1;
             tc_fence_after();
-            if (!ts.fail) tc_issue(smem_u32(base), smem_u32(sB[0]), ts.tmem);
-            tc_commit(&ts.bar[3]);
+            if (!ts.fail) tc_issue(adesc, bdesc, ts.tmem);
+            tc_commit(&ts.bar[5]);
         }
         for (int t = 0; t < ncb; ++t) {
             const int b = t & 1;
-            if (!mbar_wait(&ts.bar[3 + b], b ? ph.m1 : ph.m0)) ts.fail = 1;
-            if (b) ph.m1 ^= 1; else ph.m0 ^= 1;
+            const int c0 = r_begin + t * TC_COLS;
+            tc_load_c(A, lda, n, i0, c0, 0, v);
+            if (!mbar_wait(&ts.bar[5 + b], ph.d[b])) ts.fail = 1;
+            ph.d[b] ^= 1;
             tc_fence_after();
-            if (tid == 0) {
-                if (t + 2 < ncb) {
-                    mbar_expect_tx(&ts.bar[1 + b], TC_B_BYTES);
-                    bulk_g2s(sB[b], imgB + (size_t)(t + 2) * TC_B_FLOATS, TC_B_BYTES, &ts.bar[1 + b]);
-                }
-                if (t + 1 < ncb) {
-                    const int nb = b ^ 1;
-                    if (!mbar_wait(&ts.bar[1 + nb], nb ? ph.b1 : ph.b0)) ts.fail = 1;
-                    if (nb) ph.b1 ^= 1; else ph.b0 ^= 1;
-                    tc_fence_after();
-                    if (!ts.fail) tc_issue(smem_u32(base), smem_u32(sB[nb]), ts.tmem + nb * 64);
-                    tc_commit(&ts.bar[3 + nb]);
-                }
+            if (tid == 0 && t + 1 < ncb) {  // the buffer is free: refill it and start the next block
+                copy_b(t + 1);
+                if (!mbar_wait(&ts.bar[1], ph.bh[0])) ts.fail = 1;
+                ph.bh[0] ^= 1;
+                tc_fence_after();
+                if (!ts.fail) tc_issue(adesc, bdesc, ts.tmem + (b ^ 1) * 256);
+                tc_commit(&ts.bar[5 + (b ^ 1)]);
             }
             __syncwarp();
-            tc_epilogue(A, lda, n, i0, r_begin + t * TC_COLS, ts.tmem + b * 64);
+            tc_store_c(A, lda, n, i0, c0, 0, ts.tmem + b * 256, v);
+            tc_load_c(A, lda, n, i0, c0, 1, v);
+            tc_store_c(A, lda, n, i0, c0, 1, ts.tmem + b * 256, v);
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
@@ -712,7 +778,7 @@ __global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* 
     const bool tc = sizeof(R) == 4;
     if (tc) {
         if (threadIdx.x == 0) {
-            for (int i = 0; i < 5; ++i) mbar_init(&ts.bar[i], 1);
+            for (int i = 0; i < 7; ++i) mbar_init(&ts.bar[i], 1);
             ts.fail = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
