@@ -34,6 +34,10 @@ constexpr int NT = kDenseThreads;
 constexpr int NW = NT / 32;
 constexpr unsigned FULL = 0xffffffffu;
 
+// Barrier of the NT worker threads (warps 0..7).  The complex64 factor kernel adds a ninth warp
+// that feeds the tensor cores and never takes part in the workers' barriers.
+__device__ __forceinline__ void wsync() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
+
 template <typename R> struct DTile;
 template <> struct DTile<float> { static constexpr int TM = 128, TN = 128; };  // trailing rows only
 template <> struct DTile<double> { static constexpr int TM = 64, TN = 64, MI = 4, MJ = 4; };
@@ -114,7 +118,7 @@ __device__ int col_argmax(const cplx<R>* col, int c, int m, DShared& sh) {
     }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sh.red_v[w] = best; sh.red_i[w] = bi; }
-    __syncthreads();
+    wsync();
     if (w == 0) {
         best = lane < NW ? sh.red_v[lane] : -1.0;
         bi = lane < NW ? sh.red_i[lane] : INT_MAX;
@@ -125,7 +129,7 @@ __device__ int col_argmax(const cplx<R>* col, int c, int m, DShared& sh) {
         }
         if (lane == 0) sh.res = (bi == INT_MAX) ? c : bi;
     }
-    __syncthreads();
+    wsync();
     return sh.res;
 }
 
@@ -143,7 +147,7 @@ __device__ void leaf_factor(cplx<R>* P, int64_t ld, int m, int w, int* piv, int 
                 cq[c] = cq[p];
                 cq[p] = t;
             }
-        __syncthreads();
+        wsync();
         const cplx<R> pv = colc[c];
         const bool zero = cis_zero(pv);
         if (zero && threadIdx.x == 0 && sh.info == 0) sh.info = col_base + c + 1;
@@ -153,7 +157,7 @@ __device__ void leaf_factor(cplx<R>* P, int64_t ld, int m, int w, int* piv, int 
         // latency once per chunk instead of once per column.
         cplx<R>* urow = sh_u12<R>(sh);
         if ((int)threadIdx.x < w) urow[threadIdx.x] = P[c + (int64_t)threadIdx.x * ld];
-        __syncthreads();
+        wsync();
         constexpr int QL = sizeof(R) == 4 ? 16 : 8;
         for (int r = c + 1 + (int)threadIdx.x; r < m; r += NT) {
             cplx<R> l = colc[r];
@@ -174,7 +178,7 @@ __device__ void leaf_factor(cplx<R>* P, int64_t ld, int m, int w, int* piv, int 
                     }
             }
         }
-        __syncthreads();
+        wsync();
     }
 }
 
@@ -198,7 +202,7 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
             }
         }
     }
-    __syncthreads();
+    wsync();
     for (int q = threadIdx.x; q < w2; q += NT) {  // U12 = L11^{-1} (top 32 rows of the right half)
         cplx<R>* cq = Rt + (int64_t)q * ld;
         for (int r = 1; r < w1; ++r) {
@@ -207,7 +211,7 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
             cq[r] = acc;
         }
     }
-    __syncthreads();
+    wsync();
     // A22 -= L21 U12 (K = 32): U12 (32 x w2) is staged in shared memory (the caller's buffer
     // past the panel when the panel itself is staged there); each row loads its L21 part and a
     // chunk of its A22 part before storing anything.
@@ -216,7 +220,7 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
         const int s = idx % 32, q = idx / 32;
         u12[q * 32 + s] = Rt[s + (int64_t)q * ld];
     }
-    __syncthreads();
+    wsync();
     constexpr int QC = sizeof(R) == 4 ? 16 : 8;  // A22 columns per chunk
     for (int r = w1 + (int)threadIdx.x; r < m; r += NT) {
         cplx<R> lrow[32];
@@ -238,10 +242,10 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
             }
         }
     }
-    __syncthreads();
+    wsync();
     leaf_factor(Rt + w1, ld, m - w1, w2, sh.piv + w1, col_base + w1, sh);
     if ((int)threadIdx.x < w2) sh.piv[w1 + threadIdx.x] += w1;
-    __syncthreads();
+    wsync();
     for (int q = threadIdx.x; q < w1; q += NT) {  // right interchanges on the left half
         cplx<R>* cq = P + (int64_t)q * ld;
         for (int c = w1; c < nbk; ++c) {
@@ -253,7 +257,7 @@ __device__ void panel_factor(cplx<R>* P, int64_t ld, int m, int nbk, int col_bas
             }
         }
     }
-    __syncthreads();
+    wsync();
 }
 
 // Compose the panel's interchanges (applied in order t = 0..nbk-1) into one permutation of the
@@ -293,7 +297,7 @@ __device__ void compose_swaps(int nbk, DShared& sh) {
         }
         if (lane == 0) sh.cnt = cnt;
     }
-    __syncthreads();
+    wsync();
 }
 
 // inv(L11) and inv(U11) of the nbk x nbk diagonal block of P; shared layout (r, c) at r * NBP + c:
@@ -309,12 +313,12 @@ __device__ void diag_inverses(const cplx<R>* P, int64_t ld, int nbk, cplx<R>* sm
         const int r = idx % nbk, c = idx / nbk;
         T[r * NBP + c] = P[r + (int64_t)c * ld];
     }
-    __syncthreads();
+    wsync();
     for (int r = threadIdx.x; r < nbk; r += NT) {
         const cplx<R> d = T[r * NBP + r];
         T[r * NBP + NB] = cis_zero(d) ? czero<R>() : crecip(d);
     }
-    __syncthreads();
+    wsync();
     const int t = threadIdx.x;
     if (t < nbk) {
         for (int r = 0; r < nbk; ++r) {
@@ -344,14 +348,14 @@ __device__ void diag_inverses(const cplx<R>* P, int64_t ld, int nbk, cplx<R>* sm
             iU[r * NBP + t] = mk<R>(-acc.re, -acc.im) * T[r * NBP + NB];
         }
     }
-    __syncthreads();
+    wsync();
     for (int idx = threadIdx.x; idx < NB * NB; idx += NT) {
         const int r = idx % NB, c = idx / NB;
         const bool in = r < nbk && c < nbk;
         ginv[idx] = in ? iL[r * NBP + c] : czero<R>();
         ginv[NB * NB + idx] = in ? iU[r * NBP + c] : czero<R>();
     }
-    __syncthreads();
+    wsync();
 }
 
 // Trailing columns, rows of the panel: apply the composed interchanges and form
@@ -368,7 +372,7 @@ __device__ void trailing_rows(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>* s
             const int e = idx % cnt, col = idx / cnt;
             g[col * 2 * NB + e] = A[(int64_t)(k0 + sh.src[e]) + (int64_t)(c0 + col) * lda];
         }
-        __syncthreads();
+        wsync();
         for (int idx = threadIdx.x; idx < extra * nc; idx += NT) {
             const int e = NB + idx % extra, col = idx / extra;
             A[(int64_t)(k0 + sh.rows[e]) + (int64_t)(c0 + col) * lda] = g[col * 2 * NB + e];
@@ -387,7 +391,7 @@ __device__ void trailing_rows(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>* s
                 A[(int64_t)(k0 + t) + (int64_t)(c0 + col) * lda] = a0 + a1;
             }
         }
-        __syncthreads();
+        wsync();
     }
 }
 
@@ -431,7 +435,7 @@ __device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>*
                     acc[i][j] = (r < n && c < ce) ? A[r + (int64_t)c * lda] : czero<R>();
                 }
             cp_wait<1>();
-            __syncthreads();
+            wsync();
             const cplx<R>* Ab = As + (t & 1) * NB * TM;
 #pragma unroll 2
             for (int k = 0; k < NB; ++k) {
@@ -452,10 +456,10 @@ __device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>*
                     const int r = i0 + ty + 16 * i, c = c0 + tx + 16 * j;
                     if (r < n && c < ce) A[r + (int64_t)c * lda] = acc[i][j];
                 }
-            __syncthreads();
+            wsync();
         }
         cp_wait<0>();
-        __syncthreads();
+        wsync();
     }
 }
 
@@ -481,16 +485,24 @@ __device__ void trailing_update(cplx<R>* A, int64_t lda, int n, int k0, cplx<R>*
 // block t+1 and issues its MMAs.  Every wait is bounded; a timeout marks the job failed.
 // ------------------------------------------------------------------------------------------
 struct TcShared {
-    // 0: L21 tile; 1: U12 buffer; 5 + b: MMAs into accumulator pair b done (2-4 unused)
+    // 0: L21 tile; 1: U12 buffer; 2: command to the producer warp; 3 + b: epilogue of accumulator
+    // pair b done (one arrival per worker warp); 5 + b: MMAs into accumulator pair b done
     uint64_t bar[7];
     uint32_t tmem;       // tensor-memory base address
-    int fail;
+    int fail;            // set by any thread whose bounded wait ran out
+    int stop;            // the workers' common view of `fail`, written by worker thread 0 between barriers
+    int cmd;             // 1: run a trailing update with the parameters below, 2: exit
+    int n, k0;
+    int64_t lda;
+    const float* imgA;
+    const float* imgB;
 };
 struct TcPhase {
-    uint32_t a = 0, bh[2] = {0, 0}, h0[2] = {0, 0}, d[2] = {0, 0};
+    uint32_t a = 0, b = 0, go = 0, e[2] = {0, 0}, d[2] = {0, 0};
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool failed(const TcShared& ts) { return *(const volatile int*)&ts.fail != 0; }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -522,6 +534,9 @@ __device__ __forceinline__ void put_split(__nv_bfloat16* t, int r, int k, int ro
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -649,62 +664,107 @@ __device__ __forceinline__ void tc_store_c(c64* A, int64_t lda, int n, int i0, i
     }
 }
 
-__device__ void trailing_update_tc(c64* A, int64_t lda, int n, int k0, unsigned char* smem_raw, const float* imgA,
-                                   const float* imgB, TcShared& ts, TcPhase& ph) {
+// Worker side (warps 0..7) of one panel's trailing update: hand the parameters to the producer
+// warp, then for every (L21 tile, U12 block) step in order: prefetch C, wait for the step's
+// MMAs, read the accumulators, release them to the producer, write C back.
+__device__ void trailing_update_tc(c64* A, int64_t lda, int n, int k0, const float* imgA, const float* imgB,
+                                   TcShared& ts, TcPhase& ph) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int r_begin = k0 + NB, m = n - r_begin;
+    const int ncb = (m + TC_COLS - 1) / TC_COLS, steps = (m + TC_ROWS - 1) / TC_ROWS * ncb;
+    if (tid == 0) {
+        ts.n = n;
+        ts.k0 = k0;
+        ts.lda = lda;
+        ts.imgA = imgA;
+        ts.imgB = imgB;
+        ts.cmd = 1;
+        mbar_arrive(&ts.bar[2]);  // release: the producer reads the parameters after its wait
+    }
+    c64 v[32];
+    for (int g = 0; g < steps && !failed(ts); ++g) {
+        const int b = g & 1;
+        const int i0 = r_begin + (g / ncb) * TC_ROWS, c0 = r_begin + (g % ncb) * TC_COLS;
+        const uint32_t tb = ts.tmem + b * 256;
+        tc_load_c(A, lda, n, i0, c0, 0, v);
+        if (!mbar_wait(&ts.bar[5 + b], ph.d[b])) ts.fail = 1;
+        ph.d[b] ^= 1;
+        tc_fence_after();
+        tc_store_c(A, lda, n, i0, c0, 0, tb, v);
+        tc_load_c(A, lda, n, i0, c0, 1, v);
+        tc_store_c(A, lda, n, i0, c0, 1, tb, v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ts.bar[3 + b]);
+    }
+    wsync();  // warps may leave the loop at different steps after a timeout; all meet here
+    if (tid == 0) ts.stop = failed(ts) ? 1 : 0;
+    wsync();
+}
+
+// Producer warp (warp 8; lane 0 issues): per trailing update, bulk-copy each L21 tile and U12
+// block into shared memory and issue the step's MMAs into accumulator pair g % 2 once the
+// workers have released it.  Runs until the exit command.
+__device__ void tc_producer(unsigned char* smem_raw, TcShared& ts) {
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sB = base + TC_A_BYTES;
     const uint64_t adesc = sw128_desc(smem_u32(base)), bdesc = sw128_desc(smem_u32(sB));
-    const int tid = threadIdx.x;
-    const int r_begin = k0 + NB, m = n - r_begin;
-    const int nrt = (m + TC_ROWS - 1) / TC_ROWS, ncb = (m + TC_COLS - 1) / TC_COLS;
-    auto copy_b = [&](int blk) {
-        mbar_expect_tx(&ts.bar[1], TC_B_BYTES);
-        const float* src = imgB + (size_t)blk * TC_B_FLOATS;
-        for (int c = 0; c < 6; ++c)
-            bulk_g2s(sB + c * (TC_B_BYTES / 6), src + c * (TC_B_FLOATS / 6), TC_B_BYTES / 6, &ts.bar[1]);
-        if (blk + 1 < ncb) prefetch_l2(src + TC_B_FLOATS, TC_B_BYTES);
+    const bool leader = (threadIdx.x & 31) == 0;
+    uint32_t pa = 0, pb = 0, pgo = 0, pm[2] = {0, 0}, pe[2] = {0, 0};
+    auto wait = [&](uint64_t* bar, uint32_t& par) {
+        if (!failed(ts) && !mbar_wait(bar, par)) ts.fail = 1;
+        par ^= 1;
     };
-    c64 v[32];
-    for (int rt = 0; rt < nrt; ++rt) {
-        const int i0 = r_begin + rt * TC_ROWS;
-        if (tid == 0) {
-            mbar_expect_tx(&ts.bar[0], TC_A_BYTES);
-            for (int c = 0; c < 6; ++c)
-                bulk_g2s(base + c * (TC_A_BYTES / 6), imgA + (size_t)rt * TC_A_FLOATS + c * (TC_A_FLOATS / 6),
-                         TC_A_BYTES / 6, &ts.bar[0]);
-            if (rt + 1 < nrt) prefetch_l2(imgA + (size_t)(rt + 1) * TC_A_FLOATS, TC_A_BYTES);
-            copy_b(0);
-            const bool ok = mbar_wait(&ts.bar[0], ph.a) && mbar_wait(&ts.bar[1], ph.bh[0]);
-            ph.a ^= 1;
-            ph.bh[0] ^= 1;
-            if (!ok) ts.fail = 1;
-            tc_fence_after();
-            if (!ts.fail) tc_issue(adesc, bdesc, ts.tmem);
-            tc_commit(&ts.bar[5]);
+    for (;;) {
+        // the command barrier completes once per command; the workers factor a panel in between,
+        // so one bounded wait may run out: retry a bounded number of times, then give up
+        int got = 0;
+        if (leader)
+            for (int tries = 0; tries < 64 && !got; ++tries) got = mbar_wait(&ts.bar[2], pgo) ? 1 : 0;
+        got = __shfl_sync(FULL, got, 0);  // one decision for the whole warp
+        if (!got) {
+            ts.fail = 1;
+            return;
         }
-        for (int t = 0; t < ncb; ++t) {
-            const int b = t & 1;
-            const int c0 = r_begin + t * TC_COLS;
-            tc_load_c(A, lda, n, i0, c0, 0, v);
-            if (!mbar_wait(&ts.bar[5 + b], ph.d[b])) ts.fail = 1;
-            ph.d[b] ^= 1;
-            tc_fence_after();
-            if (tid == 0 && t + 1 < ncb) {  // the buffer is free: refill it and start the next block
-                copy_b(t + 1);
-                if (!mbar_wait(&ts.bar[1], ph.bh[0])) ts.fail = 1;
-                ph.bh[0] ^= 1;
-                tc_fence_after();
-                if (!ts.fail) tc_issue(adesc, bdesc, ts.tmem + (b ^ 1) * 256);
-                tc_commit(&ts.bar[5 + (b ^ 1)]);
+        pgo ^= 1;
+        if (*(volatile int*)&ts.cmd != 1) break;
+        const int n = *(volatile int*)&ts.n, k0 = *(volatile int*)&ts.k0;
+        const float* imgA = *(const float* volatile*)&ts.imgA;
+        const float* imgB = *(const float* volatile*)&ts.imgB;
+        const int r_begin = k0 + NB, m = n - r_begin;
+        const int ncb = (m + TC_COLS - 1) / TC_COLS, steps = (m + TC_ROWS - 1) / TC_ROWS * ncb;
+        for (int g = 0; g < steps; ++g) {
+            const int rt = g / ncb, t = g % ncb, b = g & 1;
+            if (g > 0) wait(&ts.bar[5 + ((g - 1) & 1)], pm[(g - 1) & 1]);  // the operand buffers are free
+            if (leader && !failed(ts)) {
+                if (t == 0) {
+                    mbar_expect_tx(&ts.bar[0], TC_A_BYTES);
+                    for (int c = 0; c < 6; ++c)
+                        bulk_g2s(base + c * (TC_A_BYTES / 6), imgA + (size_t)rt * TC_A_FLOATS + c * (TC_A_FLOATS / 6),
+                                 TC_A_BYTES / 6, &ts.bar[0]);
+                }
+                mbar_expect_tx(&ts.bar[1], TC_B_BYTES);
+                const float* src = imgB + (size_t)t * TC_B_FLOATS;
+                for (int c = 0; c < 6; ++c)
+                    bulk_g2s(sB + c * (TC_B_BYTES / 6), src + c * (TC_B_FLOATS / 6), TC_B_BYTES / 6, &ts.bar[1]);
+                if (t + 1 < ncb) prefetch_l2(src + TC_B_FLOATS, TC_B_BYTES);
+                else if ((rt + 1) * TC_ROWS < m) prefetch_l2(imgA + (size_t)(rt + 1) * TC_A_FLOATS, TC_A_BYTES);
             }
             __syncwarp();
-            tc_store_c(A, lda, n, i0, c0, 0, ts.tmem + b * 256, v);
-            tc_load_c(A, lda, n, i0, c0, 1, v);
-            tc_store_c(A, lda, n, i0, c0, 1, ts.tmem + b * 256, v);
-            tc_fence_before();
-            __syncthreads();
+            if (t == 0) wait(&ts.bar[0], pa);
+            wait(&ts.bar[1], pb);
+            if (g >= 2) wait(&ts.bar[3 + b], pe[b]);  // the workers have read accumulator pair b
             tc_fence_after();
+            if (leader) {
+                if (!failed(ts)) tc_issue(adesc, bdesc, ts.tmem + b * 256);
+                tc_commit(&ts.bar[5 + b]);
+            }
+            __syncwarp();
         }
+        // consume the completions not waited for above, so every barrier's phase stays in step
+        if (steps > 0) wait(&ts.bar[5 + ((steps - 1) & 1)], pm[(steps - 1) & 1]);
+        if (steps > 1) wait(&ts.bar[3 + ((steps - 2) & 1)], pe[(steps - 2) & 1]);
+        if (steps > 0) wait(&ts.bar[3 + ((steps - 1) & 1)], pe[(steps - 1) & 1]);
     }
 }
 
@@ -723,13 +783,13 @@ __device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh, float
                 const int r = idx % m, c = idx / m;
                 sm[r + c * m] = Pg[r + (int64_t)c * lda];
             }
-            __syncthreads();
+            wsync();
             panel_factor(sm, (int64_t)m, m, nbk, k0, sh);
             for (int idx = threadIdx.x; idx < m * nbk; idx += NT) {
                 const int r = idx % m, c = idx / m;
                 Pg[r + (int64_t)c * lda] = sm[r + c * m];
             }
-            __syncthreads();
+            wsync();
         } else {
             panel_factor(Pg, lda, m, nbk, k0, sh);
         }
@@ -751,9 +811,9 @@ __device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh, float
                 // proxy; the bulk copies and MMAs that follow go through the async proxy
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                trailing_update_tc(A, lda, n, k0, reinterpret_cast<unsigned char*>(sm), img, img + img_b, *ts, *ph);
-                if (ts->fail) {
+                wsync();
+                trailing_update_tc(A, lda, n, k0, img, img + img_b, *ts, *ph);
+                if (ts->stop) {  // uniform: written by thread 0 between two worker barriers
                     if (threadIdx.x == 0) sh.info = -1;
                     break;
                 }
@@ -765,21 +825,24 @@ __device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh, float
 }
 
 // img: per-CTA operand images (complex64 path), CTA b at img + b * img_stride, U12 images at
-// + img_b within it; unused (null) for complex128.
+// + img_b within it; unused (null) for complex128.  Complex64 launches NT + 32 threads: warps
+// 0..7 factor, warp 8 feeds the tensor cores; complex128 launches NT.
 template <typename R>
-__global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* __restrict__ jobs, int njobs,
-                                                             int32_t* __restrict__ next, float* img,
-                                                             size_t img_stride, size_t img_b) {
+__global__ void __launch_bounds__(sizeof(R) == 4 ? NT + 32 : NT, 1) dense_factor_kernel(const DenseJob<R>* __restrict__ jobs, int njobs,
+                                                                  int32_t* __restrict__ next, float* img,
+                                                                  size_t img_stride, size_t img_b) {
     extern __shared__ __align__(16) unsigned char dense_smem[];
     cplx<R>* sm = reinterpret_cast<cplx<R>*>(dense_smem);
     __shared__ DShared sh;
     __shared__ __align__(8) TcShared ts;
     TcPhase ph;
-    const bool tc = sizeof(R) == 4;
+    constexpr bool tc = sizeof(R) == 4;
     if (tc) {
         if (threadIdx.x == 0) {
-            for (int i = 0; i < 7; ++i) mbar_init(&ts.bar[i], 1);
+            for (int i = 0; i < 7; ++i) mbar_init(&ts.bar[i], i == 3 || i == 4 ? NT / 32 : 1);
             ts.fail = 0;
+            ts.stop = 0;
+            ts.cmd = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         if (threadIdx.x < 32) {
@@ -790,22 +853,30 @@ __global__ void __launch_bounds__(NT, 1) dense_factor_kernel(const DenseJob<R>* 
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-    }
-    float* my_img = img ? img + (size_t)blockIdx.x * img_stride : nullptr;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            sh.job = atomicAdd(next, 1);
-            sh.info = 0;
+        if (threadIdx.x >= NT) {
+            tc_producer(dense_smem, ts);
         }
-        __syncthreads();
-        const int jb = sh.job;
-        if (jb >= njobs) break;
-        const DenseJob<R> J = jobs[jb];
-        factor_one(J, sm, sh, my_img, img_b, &ts, &ph);
-        __syncthreads();
-        if (threadIdx.x == 0) *J.info = sh.info;
-        __syncthreads();
-        if (tc && ts.fail) break;
+    }
+    if (threadIdx.x < NT) {
+        float* my_img = img ? img + (size_t)blockIdx.x * img_stride : nullptr;
+        for (;;) {
+            if (threadIdx.x == 0) {  // after a tensor-core timeout no further job is taken
+                sh.job = (tc && ts.stop) ? njobs : atomicAdd(next, 1);
+                sh.info = 0;
+            }
+            wsync();
+            const int jb = sh.job;
+            if (jb >= njobs) break;
+            const DenseJob<R> J = jobs[jb];
+            factor_one(J, sm, sh, my_img, img_b, &ts, &ph);
+            wsync();
+            if (threadIdx.x == 0) *J.info = sh.info;
+            wsync();
+        }
+        if (tc && threadIdx.x == 0) {
+            ts.cmd = 2;
+            mbar_arrive(&ts.bar[2]);
+        }
     }
     if (tc) {
         tc_fence_before();
@@ -993,7 +1064,8 @@ int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int n_max, int32_t
     const int grid = dense_factor_grid<R>(njobs);
     const size_t stride = dense_image_floats<R>(n_max);
     const size_t img_b = sizeof(R) == 4 ? (size_t)((n_max + TC_ROWS - 1) / TC_ROWS) * TC_A_FLOATS : 0;
-    { dense_factor_kernel<R><<<grid, NT, sm, s>>>(d_jobs, njobs, d_next, d_img, stride, img_b); note_launch(); }
+    const int threads = sizeof(R) == 4 ? NT + 32 : NT;
+    { dense_factor_kernel<R><<<grid, threads, sm, s>>>(d_jobs, njobs, d_next, d_img, stride, img_b); note_launch(); }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
