@@ -52,6 +52,17 @@ FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 x max 
 FP64_PEAK_TFLOPS = 1.25                              # nominal FP64 rate of this part (measured 1.19)
 
 
+def measured_peaks():
+    """BF16 tensor TFLOP/s and HBM GB/s measured on this machine (MEASURED_PEAKS.json), else the
+    earlier GB300 measurement used as fallback; returns (bf16, hbm, source)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 6800.0, "fallback (no measured peaks file)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,15 +440,23 @@ def run_batch(args):
     launches_f = infos[-1][0]["factor_launches"]
     flops = sum(p.N * dense_lu_flops(p.n) for p in probs)
     achieved = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
-    roof = {"kernel": "dense_factor_kernel<%s> (persistent dense LU, one CTA per point)" % (
-                "float" if precision == "c64" else "double"), "bound": "alu",
-            "achieved": achieved, "peak": FFMA_PEAK_TFLOPS if precision == "c64" else FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if precision == "c64"
-                           else "nominal FP64 rate (measured 1.19)",
-            "algorithmic": f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
-            "ms_per_step": fac_ms}
+    bf16, _, src = measured_peaks()
+    if precision == "c64":
+        roof = {"kernel": "dense_factor_kernel<float> (persistent dense LU, one CTA per point; trailing update "
+                          "on tcgen05 BF16 tensor cores)", "bound": "tensor", "achieved": achieved, "peak": bf16,
+                "unit": "TFLOP/s", "traffic": None, "peak_source": "BF16 dense, " + src,
+                "split_ceiling": bf16 / 6.0,
+                "split_note": "each real product is 6 BF16 piece products (3-piece split), so the algorithmic "
+                              "ceiling is peak / 6"}
+    else:
+        roof = {"kernel": "dense_factor_kernel<double> (persistent dense LU, CUDA-core FP64)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal FP64 rate (measured 1.19)"}
+    roof.update({"algorithmic": f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
+                 "ms_per_step": fac_ms})
     roof["frac"] = achieved / roof["peak"] if achieved else None
+    if "split_ceiling" in roof and achieved:
+        roof["frac_of_split_ceiling"] = achieved / roof["split_ceiling"]
     phases = {"sample_ms": statistics.median(step_infos[0]["ms_sample"] for step_infos in infos),
               "factor_ms": fac_ms,
               "trsv_ms": statistics.median(step_infos[0]["ms_trsv"] for step_infos in infos),

@@ -824,70 +824,6 @@ __device__ void factor_one(const DenseJob<R>& J, cplx<R>* sm, DShared& sh, float
     }
 }
 
-// img: per-CTA operand images (complex64 path), CTA b at img + b * img_stride, U12 images at
-// + img_b within it; unused (null) for complex128.  Complex64 launches NT + 32 threads: warps
-// 0..7 factor, warp 8 feeds the tensor cores; complex128 launches NT.
-template <typename R>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? NT + 32 : NT, 1) dense_factor_kernel(const DenseJob<R>* __restrict__ jobs, int njobs,
-                                                                  int32_t* __restrict__ next, float* img,
-                                                                  size_t img_stride, size_t img_b) {
-    extern __shared__ __align__(16) unsigned char dense_smem[];
-    cplx<R>* sm = reinterpret_cast<cplx<R>*>(dense_smem);
-    __shared__ DShared sh;
-    __shared__ __align__(8) TcShared ts;
-    TcPhase ph;
-    constexpr bool tc = sizeof(R) == 4;
-    if (tc) {
-        if (threadIdx.x == 0) {
-            for (int i = 0; i < 7; ++i) mbar_init(&ts.bar[i], i == 3 || i == 4 ? NT / 32 : 1);
-            ts.fail = 0;
-            ts.stop = 0;
-            ts.cmd = 0;
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        if (threadIdx.x < 32) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                         ::"r"(smem_u32(&ts.tmem)), "r"(TC_TMEM_COLS) : "memory");
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (threadIdx.x >= NT) {
-            tc_producer(dense_smem, ts);
-        }
-    }
-    if (threadIdx.x < NT) {
-        float* my_img = img ? img + (size_t)blockIdx.x * img_stride : nullptr;
-        for (;;) {
-            if (threadIdx.x == 0) {  // after a tensor-core timeout no further job is taken
-                sh.job = (tc && ts.stop) ? njobs : atomicAdd(next, 1);
-                sh.info = 0;
-            }
-            wsync();
-            const int jb = sh.job;
-            if (jb >= njobs) break;
-            const DenseJob<R> J = jobs[jb];
-            factor_one(J, sm, sh, my_img, img_b, &ts, &ph);
-            wsync();
-            if (threadIdx.x == 0) *J.info = sh.info;
-            wsync();
-        }
-        if (tc && threadIdx.x == 0) {
-            ts.cmd = 2;
-            mbar_arrive(&ts.bar[2]);
-        }
-    }
-    if (tc) {
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        if (threadIdx.x < 32)
-            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ts.tmem), "r"(TC_TMEM_COLS)
-                         : "memory");
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // Solves.  x (n x L, leading dimension n) <- A^{-1} x.  Forward: per panel, the composed
 // interchanges, y = inv(L11) x_top, x_below -= L21 y.  Backward: per panel from the last,
@@ -926,88 +862,351 @@ __device__ void solve_update(const cplx<R>* __restrict__ Ablk, int64_t lda, int 
     }
 }
 
+// x <- A^{-1} x for one factored point (all J.L columns), by the NT worker threads.
+// smem: solve_smem<R>() bytes; rows/src/cnt: 2 NB + 2 NB + 1 ints of shared scratch.
 template <typename R>
-__global__ void __launch_bounds__(NT) dense_solve_kernel(const DenseJob<R>* __restrict__ jobs, int njobs) {
+__device__ void solve_one(const DenseJob<R>& J, unsigned char* smem, int* s_rows, int* s_src, int* s_cnt) {
     constexpr int LC = SolveChunk<R>::LC;
-    extern __shared__ __align__(16) unsigned char dense_smem[];
-    cplx<R>* sinv = reinterpret_cast<cplx<R>*>(dense_smem);  // (r, c) at r * NBP + c
-    cplx<R>* g = sinv + NB * NBP;                            // [2 NB][LG]
-    cplx<R>* y = g + 2 * NB * LG;                            // [NB][LP]
-    __shared__ int s_rows[2 * NB], s_src[2 * NB];
-    __shared__ int s_cnt;
-    for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
-        const DenseJob<R> J = jobs[jb];
-        if (J.active && !*J.active) continue;
-        const int n = J.n;
-        const int np = (int)dense_panels(n);
-        const int64_t lda = J.lda;
-        for (int l_begin = 0; l_begin < J.L; l_begin += LG) {
-            const int lg = min(LG, J.L - l_begin);
-            const int LP = (lg + LC - 1) / LC * LC;
-            cplx<R>* x = J.x + (int64_t)l_begin * n;
-            for (int idx = threadIdx.x; idx < NB * LP; idx += NT) y[idx] = czero<R>();
-            __syncthreads();
-            for (int p = 0; p < np; ++p) {  // forward
-                const int k0 = p * NB, nbk = min(NB, n - k0);
-                const int32_t* sw = J.swaps + (int64_t)p * kDenseSwapInts;
-                const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB;
-                if (threadIdx.x == 0) s_cnt = sw[0];
-                for (int i = threadIdx.x; i < 2 * NB; i += NT) {
-                    s_rows[i] = sw[1 + i];
-                    s_src[i] = sw[1 + 2 * NB + i];
-                }
-                for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
-                    const int r = idx % nbk, c = idx / nbk;
-                    sinv[r * NBP + c] = gi[r + c * NB];
-                }
-                __syncthreads();
-                const int cnt = s_cnt;
-                for (int idx = threadIdx.x; idx < cnt * lg; idx += NT) {
-                    const int e = idx % cnt, l = idx / cnt;
-                    g[e * LG + l] = x[k0 + s_src[e] + (int64_t)l * n];
-                }
-                __syncthreads();
-                const int extra = cnt - nbk;
-                for (int idx = threadIdx.x; idx < extra * lg; idx += NT) {
-                    const int e = nbk + idx % extra, l = idx / extra;
-                    x[k0 + s_rows[e] + (int64_t)l * n] = g[e * LG + l];
-                }
-                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
-                    const int t = idx % nbk, l = idx / nbk;
-                    cplx<R> acc = czero<R>();
-                    for (int s = 0; s <= t; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
-                    y[t * LP + l] = acc;
-                    x[k0 + t + (int64_t)l * n] = acc;
-                }
-                __syncthreads();
-                if (k0 + nbk < n)
-                    solve_update(J.a + (int64_t)k0 * lda, lda, k0 + nbk, n, nbk, y, LP, lg, x, n);
-                __syncthreads();
+    cplx<R>* sinv = reinterpret_cast<cplx<R>*>(smem);  // (r, c) at r * NBP + c
+    cplx<R>* g = sinv + NB * NBP;                      // [2 NB][LG]
+    cplx<R>* y = g + 2 * NB * LG;                      // [NB][LP]
+    const int n = J.n;
+    const int np = (int)dense_panels(n);
+    const int64_t lda = J.lda;
+    for (int l_begin = 0; l_begin < J.L; l_begin += LG) {
+        const int lg = min(LG, J.L - l_begin);
+        const int LP = (lg + LC - 1) / LC * LC;
+        cplx<R>* x = J.x + (int64_t)l_begin * n;
+        for (int idx = threadIdx.x; idx < NB * LP; idx += NT) y[idx] = czero<R>();
+        wsync();
+        for (int p = 0; p < np; ++p) {  // forward
+            const int k0 = p * NB, nbk = min(NB, n - k0);
+            const int32_t* sw = J.swaps + (int64_t)p * kDenseSwapInts;
+            const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB;
+            if (threadIdx.x == 0) *s_cnt = sw[0];
+            for (int i = threadIdx.x; i < 2 * NB; i += NT) {
+                s_rows[i] = sw[1 + i];
+                s_src[i] = sw[1 + 2 * NB + i];
             }
-            for (int p = np - 1; p >= 0; --p) {  // backward
-                const int k0 = p * NB, nbk = min(NB, n - k0);
-                const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB + NB * NB;
-                for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
-                    const int r = idx % nbk, c = idx / nbk;
-                    sinv[r * NBP + c] = gi[r + c * NB];
+            for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
+                const int r = idx % nbk, c = idx / nbk;
+                sinv[r * NBP + c] = gi[r + c * NB];
+            }
+            wsync();
+            const int cnt = *s_cnt;
+            for (int idx = threadIdx.x; idx < cnt * lg; idx += NT) {
+                const int e = idx % cnt, l = idx / cnt;
+                g[e * LG + l] = x[k0 + s_src[e] + (int64_t)l * n];
+            }
+            wsync();
+            const int extra = cnt - nbk;
+            for (int idx = threadIdx.x; idx < extra * lg; idx += NT) {
+                const int e = nbk + idx % extra, l = idx / extra;
+                x[k0 + s_rows[e] + (int64_t)l * n] = g[e * LG + l];
+            }
+            for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                const int t = idx % nbk, l = idx / nbk;
+                cplx<R> acc = czero<R>();
+                for (int s = 0; s <= t; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
+                y[t * LP + l] = acc;
+                x[k0 + t + (int64_t)l * n] = acc;
+            }
+            wsync();
+            if (k0 + nbk < n) solve_update(J.a + (int64_t)k0 * lda, lda, k0 + nbk, n, nbk, y, LP, lg, x, n);
+            wsync();
+        }
+        for (int p = np - 1; p >= 0; --p) {  // backward
+            const int k0 = p * NB, nbk = min(NB, n - k0);
+            const cplx<R>* gi = J.inv + (int64_t)p * 2 * NB * NB + NB * NB;
+            for (int idx = threadIdx.x; idx < nbk * nbk; idx += NT) {
+                const int r = idx % nbk, c = idx / nbk;
+                sinv[r * NBP + c] = gi[r + c * NB];
+            }
+            for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                const int t = idx % nbk, l = idx / nbk;
+                g[t * LG + l] = x[k0 + t + (int64_t)l * n];
+            }
+            wsync();
+            for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
+                const int t = idx % nbk, l = idx / nbk;
+                cplx<R> acc = czero<R>();
+                for (int s = t; s < nbk; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
+                y[t * LP + l] = acc;
+                x[k0 + t + (int64_t)l * n] = acc;
+            }
+            wsync();
+            if (k0 > 0) solve_update(J.a + (int64_t)k0 * lda, lda, 0, k0, nbk, y, LP, lg, x, n);
+            wsync();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused dense sampling.  Per job (point j of NEP E), in the CTA's slot:
+//   zero the matrix, scatter T(z_j) = sum_i f_i(z_j) A_i (precision R) and the FP64 column
+//   sums |T| (for ||T||_1); factor; x = U; solve; X = x in S_hat (FP64); then
+//   r = U - T X in FP64 from the CSR values (T recomputed from the f_i), eta per column,
+//   and refinement X += (LU)^{-1} r while the stopping rule of the band path asks for it.
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxL = 256;
+
+struct SampleShared {
+    double rn2[kMaxL], xn2[kMaxL];
+    double red[NW];
+    double normT, mx;
+    int action;
+};
+
+template <typename R>
+struct Slot {
+    cplx<R>* a;
+    cplx<R>* x;
+    int32_t* ipiv;
+    cplx<R>* inv;
+    int32_t* swaps;
+    double* colsum;
+};
+
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename R>
+__host__ __device__ inline size_t slot_bytes(int n_max, int L_max) {
+    const size_t np = (size_t)dense_panels(n_max);
+    return align256((size_t)n_max * n_max * sizeof(cplx<R>)) + align256((size_t)n_max * L_max * sizeof(cplx<R>)) +
+           align256((size_t)n_max * 4) + align256(np * 2 * NB * NB * sizeof(cplx<R>)) +
+           align256(np * kDenseSwapInts * 4) + align256((size_t)n_max * 8);
+}
+
+template <typename R>
+__device__ Slot<R> slot_at(unsigned char* base, int n_max, int L_max) {
+    const size_t np = (size_t)dense_panels(n_max);
+    Slot<R> t;
+    unsigned char* p = base;
+    t.a = reinterpret_cast<cplx<R>*>(p);
+    p += align256((size_t)n_max * n_max * sizeof(cplx<R>));
+    t.x = reinterpret_cast<cplx<R>*>(p);
+    p += align256((size_t)n_max * L_max * sizeof(cplx<R>));
+    t.ipiv = reinterpret_cast<int32_t*>(p);
+    p += align256((size_t)n_max * 4);
+    t.inv = reinterpret_cast<cplx<R>*>(p);
+    p += align256(np * 2 * NB * NB * sizeof(cplx<R>));
+    t.swaps = reinterpret_cast<int32_t*>(p);
+    p += align256(np * kDenseSwapInts * 4);
+    t.colsum = reinterpret_cast<double*>(p);
+    return t;
+}
+
+// Block-wide max of one double per thread (workers only); every worker gets the result.
+__device__ double worker_max(double v, SampleShared& ss) {
+    for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_down_sync(FULL, v, off));
+    if ((threadIdx.x & 31) == 0) ss.red[threadIdx.x >> 5] = v;
+    wsync();
+    double m = ss.red[0];
+    for (int w = 1; w < NW; ++w) m = fmax(m, ss.red[w]);
+    wsync();
+    return m;
+}
+
+// r = U - T X (FP64, T from the CSR values and f_i(z_j)); x = r in precision R; per-column
+// ||r||^2 and ||X||^2 into ss.rn2 / ss.xn2.
+template <typename R>
+__device__ void residual_one(const DenseNep& E, int j, const c128* X, cplx<R>* x, SampleShared& ss) {
+    constexpr int LC = 8;
+    const int n = E.n, L = E.L, J = E.J;
+    const int64_t nnz = E.nnz;
+    const c128* f = E.F + (int64_t)j * J;
+    for (int l = threadIdx.x; l < L; l += NT) ss.rn2[l] = ss.xn2[l] = 0.0;
+    wsync();
+    for (int l0 = 0; l0 < L; l0 += LC) {
+        double pr[LC], px[LC];
+#pragma unroll
+        for (int l = 0; l < LC; ++l) pr[l] = px[l] = 0.0;
+        for (int r = threadIdx.x; r < n; r += NT) {
+            c128 acc[LC];
+#pragma unroll
+            for (int l = 0; l < LC; ++l) acc[l] = (l0 + l < L) ? E.U[r + (int64_t)(l0 + l) * n] : czero<double>();
+            for (int64_t k = E.rowptr[r]; k < E.rowptr[r + 1]; ++k) {
+                c128 t = czero<double>();
+                for (int i = 0; i < J; ++i) cfma(t, f[i], E.vals[(int64_t)i * nnz + k]);
+                const int64_t c = E.colind[k];
+#pragma unroll
+                for (int l = 0; l < LC; ++l)
+                    if (l0 + l < L) cfms(acc[l], t, X[c + (int64_t)(l0 + l) * n]);
+            }
+#pragma unroll
+            for (int l = 0; l < LC; ++l)
+                if (l0 + l < L) {
+                    x[r + (int64_t)(l0 + l) * n] = ccast<R>(acc[l]);
+                    pr[l] += cnorm2(acc[l]);
+                    px[l] += cnorm2(X[r + (int64_t)(l0 + l) * n]);
                 }
-                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
-                    const int t = idx % nbk, l = idx / nbk;
-                    g[t * LG + l] = x[k0 + t + (int64_t)l * n];
-                }
-                __syncthreads();
-                for (int idx = threadIdx.x; idx < nbk * lg; idx += NT) {
-                    const int t = idx % nbk, l = idx / nbk;
-                    cplx<R> acc = czero<R>();
-                    for (int s = t; s < nbk; ++s) cfma(acc, sinv[t * NBP + s], g[s * LG + l]);
-                    y[t * LP + l] = acc;
-                    x[k0 + t + (int64_t)l * n] = acc;
-                }
-                __syncthreads();
-                if (k0 > 0) solve_update(J.a + (int64_t)k0 * lda, lda, 0, k0, nbk, y, LP, lg, x, n);
-                __syncthreads();
+        }
+#pragma unroll
+        for (int l = 0; l < LC; ++l) {
+            double a = pr[l], b = px[l];
+            for (int off = 16; off; off >>= 1) {
+                a += __shfl_down_sync(FULL, a, off);
+                b += __shfl_down_sync(FULL, b, off);
+            }
+            if ((threadIdx.x & 31) == 0 && l0 + l < L) {
+                atomicAdd(&ss.rn2[l0 + l], a);
+                atomicAdd(&ss.xn2[l0 + l], b);
             }
         }
+    }
+    wsync();
+}
+
+template <typename R>
+__device__ void sample_one(const DenseNep& E, int j, const Slot<R>& sl, cplx<R>* sm, DShared& sh, SampleShared& ss,
+                           float* img, size_t img_b, TcShared* ts, TcPhase* ph, const DenseSampleCfg& cfg) {
+    const int n = E.n, L = E.L, J = E.J;
+    const int64_t nnz = E.nnz, nl = (int64_t)n * L;
+    cplx<R>* A = sl.a;
+    // assemble T(z_j) (precision R) and its FP64 column sums
+    {
+        const int64_t nn = (int64_t)n * n;
+        for (int64_t idx = threadIdx.x; idx < nn; idx += NT) A[idx] = czero<R>();
+        for (int c = threadIdx.x; c < n; c += NT) sl.colsum[c] = 0.0;
+        wsync();
+        const c128* f = E.F + (int64_t)j * J;
+        for (int64_t k = threadIdx.x; k < nnz; k += NT) {
+            c128 t = czero<double>();
+            for (int i = 0; i < J; ++i) cfma(t, f[i], E.vals[(int64_t)i * nnz + k]);
+            const int c = E.colind[k];
+            A[E.rowidx[k] + (int64_t)c * n] = ccast<R>(t);
+            atomicAdd(&sl.colsum[c], sqrt(cnorm2(t)));
+        }
+        wsync();
+        double m = 0.0;
+        for (int c = threadIdx.x; c < n; c += NT) m = fmax(m, sl.colsum[c]);
+        m = worker_max(m, ss);
+        if (threadIdx.x == 0) ss.normT = m;
+    }
+    DenseJob<R> Jb;
+    Jb.a = A;
+    Jb.lda = n;
+    Jb.n = n;
+    Jb.L = L;
+    Jb.ipiv = sl.ipiv;
+    Jb.inv = sl.inv;
+    Jb.swaps = sl.swaps;
+    Jb.x = sl.x;
+    if (threadIdx.x == 0) sh.info = 0;
+    wsync();
+    factor_one(Jb, sm, sh, img, img_b, ts, ph);
+    wsync();
+    const int info = sh.info;
+    if (info != 0) {
+        if (threadIdx.x == 0) {
+            E.status[j] = info;
+            E.sweeps[j] = 0;
+        }
+        wsync();
+        return;
+    }
+    c128* X = E.S + (int64_t)j * nl;
+    for (int64_t idx = threadIdx.x; idx < nl; idx += NT) sl.x[idx] = ccast<R>(E.U[idx]);
+    wsync();
+    unsigned char* smb = reinterpret_cast<unsigned char*>(sm);
+    solve_one(Jb, smb, sh.rows, sh.src, &sh.cnt);
+    for (int64_t idx = threadIdx.x; idx < nl; idx += NT) X[idx] = ccast<double>(sl.x[idx]);
+    wsync();
+    double prev = 0.0;
+    int sweeps = 0;
+    for (;;) {
+        residual_one(E, j, X, sl.x, ss);
+        // backward error per column and the decision (one thread decides, all follow)
+        double mx = 0.0;
+        int nonfinite = 0;
+        for (int l = threadIdx.x; l < L; l += NT) {
+            const double e = sqrt(ss.rn2[l]) / (ss.normT * sqrt(ss.xn2[l]) + sqrt(E.un2[l]));
+            E.eta[(int64_t)j * L + l] = e;
+            if (!isfinite(e)) nonfinite = 1;
+            mx = fmax(mx, e);
+        }
+        mx = worker_max(nonfinite ? INFINITY : mx, ss);
+        if (threadIdx.x == 0) {
+            int action;                                          // 0 done, 1 refine, < 0 failed
+            const bool improving = sweeps == 0 || mx < 0.5 * prev;
+            if (!isfinite(mx)) action = -2;
+            else if (!(mx <= cfg.target) && improving) action = sweeps >= cfg.max_refine ? (mx <= cfg.tol ? 0 : -3) : 1;
+            else action = (mx <= cfg.tol) ? 0 : -3;
+            ss.action = action;
+        }
+        prev = mx;
+        wsync();
+        const int action = ss.action;
+        if (action != 1) {
+            if (threadIdx.x == 0) {
+                E.status[j] = action;
+                E.sweeps[j] = sweeps;
+            }
+            break;
+        }
+        solve_one(Jb, smb, sh.rows, sh.src, &sh.cnt);
+        for (int64_t idx = threadIdx.x; idx < nl; idx += NT) X[idx] = X[idx] + ccast<double>(sl.x[idx]);
+        wsync();
+        ++sweeps;
+    }
+    wsync();
+}
+
+// Complex64 launches NT + 32 threads: warps 0..7 work, warp 8 feeds the tensor cores;
+// complex128 launches NT.  CTA b uses slot b and (complex64) image block b.
+template <typename R>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? NT + 32 : NT, 1)
+    dense_sample_kernel(const DenseNep* __restrict__ neps, const DenseSampleJob* __restrict__ jobs, int njobs,
+                        int n_max, int L_max, unsigned char* slots, size_t slot_stride, float* img, size_t img_stride,
+                        size_t img_b, int32_t* __restrict__ next, DenseSampleCfg cfg) {
+    extern __shared__ __align__(16) unsigned char dense_smem[];
+    cplx<R>* sm = reinterpret_cast<cplx<R>*>(dense_smem);
+    __shared__ DShared sh;
+    __shared__ SampleShared ss;
+    __shared__ __align__(8) TcShared ts;
+    TcPhase ph;
+    constexpr bool tc = sizeof(R) == 4;
+    if (tc) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < 7; ++i) mbar_init(&ts.bar[i], i == 3 || i == 4 ? NT / 32 : 1);
+            ts.fail = 0;
+            ts.stop = 0;
+            ts.cmd = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(&ts.tmem)), "r"(TC_TMEM_COLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x >= NT) tc_producer(dense_smem, ts);
+    }
+    if (threadIdx.x < NT) {
+        const Slot<R> sl = slot_at<R>(slots + (size_t)blockIdx.x * slot_stride, n_max, L_max);
+        float* my_img = img ? img + (size_t)blockIdx.x * img_stride : nullptr;
+        for (;;) {
+            if (threadIdx.x == 0) sh.job = (tc && ts.stop) ? njobs : atomicAdd(next, 1);  // no new job after a timeout
+            wsync();
+            const int jb = sh.job;
+            if (jb >= njobs) break;
+            const DenseSampleJob job = jobs[jb];
+            sample_one<R>(neps[job.nep], job.j, sl, sm, sh, ss, my_img, img_b, &ts, &ph, cfg);
+        }
+        if (tc && threadIdx.x == 0) {
+            ts.cmd = 2;
+            mbar_arrive(&ts.bar[2]);
+        }
+    }
+    if (tc) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(ts.tmem), "r"(TC_TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -1041,53 +1240,50 @@ int sm_count() {
 
 }  // namespace
 
+int dense_sample_grid(int njobs) { return std::max(1, std::min(njobs, sm_count())); }
+
 template <typename R>
-int dense_factor_grid(int njobs) {
-    return std::max(1, std::min(njobs, sm_count()));
+size_t dense_slot_bytes(int n_max, int L_max) {
+    return slot_bytes<R>(n_max, L_max);
 }
 
 template <typename R>
-size_t dense_image_floats(int n_max) {
+size_t dense_image_bytes(int n_max) {
     if (sizeof(R) != 4) return 0;
     const size_t tiles = (size_t)(n_max + TC_ROWS - 1) / TC_ROWS, blocks = (size_t)(n_max + TC_COLS - 1) / TC_COLS;
-    return tiles * TC_A_FLOATS + blocks * TC_B_FLOATS;
+    return (tiles * TC_A_FLOATS + blocks * TC_B_FLOATS) * 4;
 }
 
 template <typename R>
-int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int n_max, int32_t* d_next, float* d_img,
-                        cudaStream_t s) {
+int launch_dense_sample(const DenseNep* d_neps, const DenseSampleJob* d_jobs, int njobs, int n_max, int L_max,
+                        int grid, void* d_slots, void* d_img, int32_t* d_next, DenseSampleCfg cfg, cudaStream_t s) {
     if (njobs <= 0) return RSRR_OK;
-    if (sizeof(R) == 4 && !d_img) return set_error(RSRR_EINVAL, "dense factor: operand images missing");
-    const size_t sm = factor_smem<R>();
-    RSRR_TRY(set_smem(dense_factor_kernel<R>, sm, "dense_factor_kernel"));
+    if (L_max > kMaxL) return set_error(RSRR_EINVAL, "dense sampling: L above 256");
+    if (sizeof(R) == 4 && !d_img) return set_error(RSRR_EINVAL, "dense sampling: operand images missing");
+    const size_t sm = std::max(factor_smem<R>(), solve_smem<R>());
+    RSRR_TRY(set_smem(dense_sample_kernel<R>, sm, "dense_sample_kernel"));
     RSRR_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int32_t), s));
-    const int grid = dense_factor_grid<R>(njobs);
-    const size_t stride = dense_image_floats<R>(n_max);
-    const size_t img_b = sizeof(R) == 4 ? (size_t)((n_max + TC_ROWS - 1) / TC_ROWS) * TC_A_FLOATS : 0;
     const int threads = sizeof(R) == 4 ? NT + 32 : NT;
-    { dense_factor_kernel<R><<<grid, threads, sm, s>>>(d_jobs, njobs, d_next, d_img, stride, img_b); note_launch(); }
+    const size_t img_stride = dense_image_bytes<R>(n_max) / 4;
+    const size_t img_b = sizeof(R) == 4 ? (size_t)((n_max + TC_ROWS - 1) / TC_ROWS) * TC_A_FLOATS : 0;
+    {
+        dense_sample_kernel<R><<<grid, threads, sm, s>>>(d_neps, d_jobs, njobs, n_max, L_max,
+                                                         static_cast<unsigned char*>(d_slots),
+                                                         dense_slot_bytes<R>(n_max, L_max), static_cast<float*>(d_img),
+                                                         img_stride, img_b, d_next, cfg);
+        note_launch();
+    }
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;
 }
 
-template <typename R>
-int launch_dense_solve(const DenseJob<R>* d_jobs, int njobs, int maxL, cudaStream_t s) {
-    (void)maxL;
-    if (njobs <= 0) return RSRR_OK;
-    const size_t sm = solve_smem<R>();
-    RSRR_TRY(set_smem(dense_solve_kernel<R>, sm, "dense_solve_kernel"));
-    { dense_solve_kernel<R><<<njobs, NT, sm, s>>>(d_jobs, njobs); note_launch(); }
-    RSRR_CUDA(cudaGetLastError());
-    return RSRR_OK;
-}
-
-template int launch_dense_factor<float>(const DenseJob<float>*, int, int, int32_t*, float*, cudaStream_t);
-template int launch_dense_factor<double>(const DenseJob<double>*, int, int, int32_t*, float*, cudaStream_t);
-template int dense_factor_grid<float>(int);
-template int dense_factor_grid<double>(int);
-template size_t dense_image_floats<float>(int);
-template size_t dense_image_floats<double>(int);
-template int launch_dense_solve<float>(const DenseJob<float>*, int, int, cudaStream_t);
-template int launch_dense_solve<double>(const DenseJob<double>*, int, int, cudaStream_t);
+template size_t dense_slot_bytes<float>(int, int);
+template size_t dense_slot_bytes<double>(int, int);
+template size_t dense_image_bytes<float>(int);
+template size_t dense_image_bytes<double>(int);
+template int launch_dense_sample<float>(const DenseNep*, const DenseSampleJob*, int, int, int, int, void*, void*,
+                                        int32_t*, DenseSampleCfg, cudaStream_t);
+template int launch_dense_sample<double>(const DenseNep*, const DenseSampleJob*, int, int, int, int, void*, void*,
+                                         int32_t*, DenseSampleCfg, cudaStream_t);
 
 }  // namespace rsrr

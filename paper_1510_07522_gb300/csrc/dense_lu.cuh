@@ -31,6 +31,7 @@ constexpr int kDenseSwapInts = 1 + 4 * kDenseNB;
 
 __host__ __device__ inline int64_t dense_panels(int64_t n) { return (n + kDenseNB - 1) / kDenseNB; }
 
+// The factor and solve of one point (one CTA's slot).
 template <typename R>
 struct DenseJob {
     cplx<R>* a;              // [n][lda] column-major
@@ -38,33 +39,51 @@ struct DenseJob {
     int32_t n;
     int32_t L;               // right-hand sides (solve)
     int32_t* ipiv;           // [n]
-    int32_t* info;           // [1]: first zero pivot (1-based), 0 if none
     cplx<R>* inv;            // [npanels][2][NB * NB]
     int32_t* swaps;          // [npanels][kDenseSwapInts]
     cplx<R>* x;              // [L][n] right-hand sides, overwritten by the solution (solve)
-    const int32_t* active;   // solve: the point is skipped when *active == 0 (may be null)
 };
 
-// Device bytes of the per-point work arrays besides a, x and ipiv.
-template <typename R>
-inline size_t dense_aux_bytes(int64_t n) {
-    return (size_t)dense_panels(n) * (2 * kDenseNB * kDenseNB * sizeof(cplx<R>) + kDenseSwapInts * 4);
-}
+// ---- fused dense sampling: one persistent launch for all points of a set of NEPs --------------
+// Each CTA takes (NEP, point) jobs largest n first and, in a memory slot of its own, assembles
+// T(z_j), factors it, solves T X = U, computes the FP64 residual and backward error and refines
+// until the stopping rule of the band path holds, writing X into the NEP's S_hat.
+struct DenseNep {
+    int32_t n, J, L, N;
+    int64_t nnz;
+    const int64_t* rowptr;   // CSR of the union pattern (band ordering)
+    const int32_t* colind;
+    const int32_t* rowidx;
+    const c128* vals;        // [J][nnz]
+    const c128* F;           // [N][J] f_i(z_j)
+    const c128* U;           // [L][n] probing matrix (band ordering)
+    const double* un2;       // [L] squared column norms of U
+    c128* S;                 // [N][L][n] S_hat
+    double* eta;             // [N][L] backward errors
+    int32_t* status;         // [N] 0 ok, > 0 first zero pivot (1-based), -1 tensor-core timeout,
+                             //     -2 non-finite backward error, -3 tolerance not reached
+    int32_t* sweeps;         // [N] refinement sweeps
+};
+struct DenseSampleJob {
+    int32_t nep, j;
+};
+struct DenseSampleCfg {
+    double tol;              // acceptance: eta <= tol per column
+    double target;           // keep refining while eta > target and still halving (0 = working accuracy)
+    int32_t max_refine;
+};
 
-// Factor every job (any order of sizes; the launcher expects them sorted largest first so
-// the last CTAs to finish hold the smallest points).  d_next: one int32 of device scratch.
-// Complex64 runs the trailing updates on the tensor cores and needs d_img: device scratch of
-// dense_factor_grid(njobs) * dense_image_floats(n_max) floats (n_max = the largest job's n);
-// complex128 ignores it.  A job whose tensor-core waits time out gets *info = -1.
+// Device bytes of one CTA's slot for n <= n_max, L <= L_max.
 template <typename R>
-int dense_factor_grid(int njobs);
+size_t dense_slot_bytes(int n_max, int L_max);
+// Largest CTA count worth launching for njobs jobs (one per SM at most).
+int dense_sample_grid(int njobs);
+// Device bytes of one CTA's tensor-core operand images (complex64; 0 for complex128).
 template <typename R>
-size_t dense_image_floats(int n_max);
+size_t dense_image_bytes(int n_max);
+// d_slots: grid * dense_slot_bytes; d_img: grid * dense_image_bytes; d_next: one int32.
 template <typename R>
-int launch_dense_factor(const DenseJob<R>* d_jobs, int njobs, int n_max, int32_t* d_next, float* d_img,
-                        cudaStream_t s);
-// X = A^{-1} X for every job (forward with the composed interchanges, then backward).
-template <typename R>
-int launch_dense_solve(const DenseJob<R>* d_jobs, int njobs, int maxL, cudaStream_t s);
+int launch_dense_sample(const DenseNep* d_neps, const DenseSampleJob* d_jobs, int njobs, int n_max, int L_max,
+                        int grid, void* d_slots, void* d_img, int32_t* d_next, DenseSampleCfg cfg, cudaStream_t s);
 
 }  // namespace rsrr

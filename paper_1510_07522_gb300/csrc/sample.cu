@@ -382,262 +382,123 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Dense sampling of a set of NEPs (dense_lu.cu): every point of every NEP is one job of the
-// persistent dense-LU launch; the FP64 residual, backward error and refinement are the band
-// path's kernels, run per NEP.  Points are taken largest n first, in waves that fit the device
-// memory free at the start; a NEP may straddle two waves.
+// Dense sampling of a set of NEPs (dense_lu.cu): every point of every NEP is one job of a single
+// persistent launch that assembles, factors, solves and refines the point in a per-CTA memory
+// slot (largest n first), so uneven NEPs share the GPU with no host round trip between stages.
 // ---------------------------------------------------------------------------------------------
-template <typename R>
-struct DenseGroup {          // points [j0, j0 + np) of NEP hs[hi] inside one wave
-    int hi = 0, j0 = 0, np = 0;
-    cplx<R>* a = nullptr;
-    cplx<R>* x = nullptr;
-    cplx<R>* inv = nullptr;
-    int32_t *ipiv = nullptr, *info = nullptr, *swaps = nullptr, *active = nullptr;
-    c128* tvals = nullptr;
-    double *colsum = nullptr, *normT = nullptr, *rn2 = nullptr, *xn2 = nullptr, *prev_max = nullptr,
-           *un2 = nullptr;
-    bool done = false;
-    int sweeps = 0;
-};
-
-template <typename R>
-size_t dense_point_bytes(const rsrr_nep h) {
-    const int64_t n = h->n;
-    return (size_t)n * n * sizeof(cplx<R>) + (size_t)n * h->L * sizeof(cplx<R>) + (size_t)n * 4 + 16 +
-           dense_aux_bytes<R>(n) + (size_t)h->nnz * 16 + (size_t)n * 8 + (size_t)h->L * 16 + 64;
-}
-
 template <typename R>
 int sample_dense_set(const std::vector<rsrr_nep>& hs, const std::vector<c128*>& dF, int max_refine) {
     if (hs.empty()) return RSRR_OK;
     cudaStream_t st = hs[0]->stream;
-    std::vector<int> order(hs.size());
-    for (size_t i = 0; i < hs.size(); ++i) order[i] = (int)i;
+    const int nh = (int)hs.size();
+    int n_max = 0, L_max = 0;
+    int64_t total_points = 0;
+    for (rsrr_nep h : hs) {
+        n_max = std::max<int>(n_max, (int)h->n);
+        L_max = std::max<int>(L_max, h->L);
+        total_points += h->N;
+        h->refine_sweeps = 0;
+    }
+    // jobs, largest n first
+    std::vector<DenseSampleJob> jobs;
+    jobs.reserve((size_t)total_points);
+    std::vector<int> order(nh);
+    for (int i = 0; i < nh; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+    for (int i : order)
+        for (int j = 0; j < hs[i]->N; ++j) jobs.push_back(DenseSampleJob{i, j});
+    const int njobs = (int)jobs.size();
+    // CTAs: one per SM at most, and no more slots than the free memory holds
     size_t free_b = 0, total_b = 0;
     RSRR_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_cta = dense_slot_bytes<R>(n_max, L_max) + dense_image_bytes<R>(n_max);
     const size_t budget = (size_t)(0.8 * (double)free_b);
-    for (rsrr_nep h : hs) {
-        h->ms_factor = h->ms_trsv = 0;
-        h->factor_launches = h->trsv_launches = 0;
-        h->refine_sweeps = 0;
-        if (dense_point_bytes<R>(h) > budget)
-            return set_error(RSRR_ENOMEM, "one dense sampling point does not fit in device memory");
-    }
-    // The NEPs share every launch, so each handle reports the totals of the whole set.
-    double tot_factor_ms = 0, tot_trsv_ms = 0;
-    int tot_factor_launches = 0, tot_trsv_launches = 0;
-    size_t oi = 0;
-    int jnext = 0;  // next point of NEP hs[order[oi]]
+    const int grid = (int)std::min<size_t>((size_t)dense_sample_grid(njobs), budget / per_cta);
+    if (grid < 1) return set_error(RSRR_ENOMEM, "one dense sampling slot does not fit in device memory");
+
+    std::vector<DenseNep> neps(nh);
+    std::vector<double*> un2(nh, nullptr);
+    std::vector<int32_t*> status(nh, nullptr), sweeps(nh, nullptr);
+    DenseNep* d_neps = nullptr;
+    DenseSampleJob* d_jobs = nullptr;
     int32_t* d_next = nullptr;
-    RSRR_TRY(dalloc_n(&d_next, 1, st));
-    int rc = RSRR_OK;
-    bool singular = false, nonfinite = false, notconv = false;
-    while (oi < order.size() && rc == RSRR_OK && !singular && !nonfinite && !notconv) {
-        // ---- the wave: largest remaining points that fit --------------------------------------
-        std::vector<DenseGroup<R>> groups;
-        size_t used = 0;
-        while (oi < order.size()) {
-            rsrr_nep h = hs[order[oi]];
-            const size_t pb = dense_point_bytes<R>(h);
-            const int fit = (int)std::min<size_t>((size_t)(h->N - jnext), (budget - used) / pb);
-            if (fit <= 0) break;
-            DenseGroup<R> g;
-            g.hi = order[oi];
-            g.j0 = jnext;
-            g.np = fit;
-            groups.push_back(g);
-            used += (size_t)fit * pb;
-            jnext += fit;
-            if (jnext == h->N) { ++oi; jnext = 0; }
-        }
-        std::vector<DenseJob<R>> jobs;
-        DenseJob<R>* d_jobs = nullptr;
-        int32_t* d_counters = nullptr;
-        float* d_img = nullptr;
-        auto cleanup = [&]() {
-            dfree(d_img, st);
-            for (auto& g : groups) {
-                dfree(g.a, st); dfree(g.x, st); dfree(g.inv, st); dfree(g.ipiv, st); dfree(g.info, st);
-                dfree(g.swaps, st); dfree(g.active, st); dfree(g.tvals, st); dfree(g.colsum, st);
-                dfree(g.normT, st); dfree(g.rn2, st); dfree(g.xn2, st); dfree(g.prev_max, st); dfree(g.un2, st);
-            }
-            dfree(d_jobs, st);
-            dfree(d_counters, st);
-        };
-#define TRYW(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); dfree(d_next, st); return rc; } } while (0)
-#define CUDAW(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); dfree(d_next, st); return set_error(RSRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
-        const int ng = (int)groups.size();
-        TRYW(dalloc_n(&d_counters, (size_t)4 * ng, st));
-        for (auto& g : groups) {
-            rsrr_nep h = hs[g.hi];
-            const int64_t n = h->n, nnz = h->nnz, L = h->L, np = g.np;
-            const int64_t npan = dense_panels(n);
-            TRYW(dalloc_n(&g.a, (size_t)np * n * n, st));
-            TRYW(dalloc_n(&g.x, (size_t)np * n * L, st));
-            TRYW(dalloc_n(&g.inv, (size_t)np * npan * 2 * kDenseNB * kDenseNB, st));
-            TRYW(dalloc_n(&g.ipiv, (size_t)np * n, st));
-            TRYW(dalloc_n(&g.info, (size_t)np, st));
-            TRYW(dalloc_n(&g.swaps, (size_t)np * npan * kDenseSwapInts, st));
-            TRYW(dalloc_n(&g.active, (size_t)np, st));
-            TRYW(dalloc_n(&g.tvals, (size_t)np * nnz, st));
-            TRYW(dalloc_n(&g.colsum, (size_t)np * n, st));
-            TRYW(dalloc_n(&g.normT, (size_t)np, st));
-            TRYW(dalloc_n(&g.rn2, (size_t)np * L, st));
-            TRYW(dalloc_n(&g.xn2, (size_t)np * L, st));
-            TRYW(dalloc_n(&g.prev_max, (size_t)np, st));
-            TRYW(dalloc_n(&g.un2, (size_t)L, st));
-            CUDAW(cudaMemsetAsync(g.a, 0, (size_t)np * n * n * sizeof(cplx<R>), st));
-            CUDAW(cudaMemsetAsync(g.active, 1, (size_t)np * 4, st));
-            const dim3 gg((unsigned)ceil_div(nnz, 256), (unsigned)np);
-            { assemble_kernel<R><<<gg, 256, 0, st>>>(h->d_vals, h->J, nnz, h->d_rowidx, h->d_colind, dF[g.hi], g.j0,
-                                                    0, (int)(n + 1), g.tvals, g.a, n * n); note_launch(); }
-            CUDAW(cudaGetLastError());
-            CUDAW(cudaMemsetAsync(g.colsum, 0, (size_t)n * np * 8, st));
-            { colsum_kernel<<<gg, 256, 0, st>>>(g.tvals, nnz, h->d_colind, n, g.colsum); note_launch(); }
-            { max_kernel<<<(unsigned)np, 256, 0, st>>>(g.colsum, n, g.normT); note_launch(); }
-            { column_norm2_kernel<<<(unsigned)L, 256, 0, st>>>(h->d_U, n, g.un2); note_launch(); }
-            for (int k = 0; k < np; ++k) {
-                DenseJob<R> J;
-                J.a = g.a + (int64_t)k * n * n;
-                J.lda = n;
-                J.n = (int32_t)n;
-                J.L = (int32_t)L;
-                J.ipiv = g.ipiv + (int64_t)k * n;
-                J.info = g.info + k;
-                J.inv = g.inv + (int64_t)k * npan * 2 * kDenseNB * kDenseNB;
-                J.swaps = g.swaps + (int64_t)k * npan * kDenseSwapInts;
-                J.x = g.x + (int64_t)k * n * L;
-                J.active = g.active + k;
-                jobs.push_back(J);
-            }
-        }
-        const int nj = (int)jobs.size();
-        TRYW(dalloc_n(&d_jobs, (size_t)nj, st));
-        CUDAW(cudaMemcpyAsync(d_jobs, jobs.data(), (size_t)nj * sizeof(DenseJob<R>), cudaMemcpyHostToDevice, st));
-        int n_max = 0;
-        for (const auto& J : jobs) n_max = std::max(n_max, (int)J.n);
-        const size_t img_floats = (size_t)dense_factor_grid<R>(nj) * dense_image_floats<R>(n_max);
-        if (img_floats) TRYW(dalloc_n(&d_img, img_floats, st));
-        EvPair evf, evs;
-        evf.start(st);
-        TRYW(launch_dense_factor<R>(d_jobs, nj, n_max, d_next, d_img, st));
-        evf.stop(st);
-        bool timeout = false;
-        for (auto& g : groups) {
-            std::vector<int32_t> hi(g.np);
-            CUDAW(cudaMemcpyAsync(hi.data(), g.info, (size_t)g.np * 4, cudaMemcpyDeviceToHost, st));
-            CUDAW(cudaStreamSynchronize(st));
-            for (int32_t v : hi) {
-                if (v > 0) singular = true;
-                if (v < 0) timeout = true;
-            }
-        }
-        dfree(d_img, st);
-        d_img = nullptr;
-        if (timeout) {
-            cleanup();
-            dfree(d_next, st);
-            return set_error(RSRR_ETIMEOUT, "dense LU: a tensor-core wait timed out");
-        }
-        tot_factor_ms += evf.ms();
-        tot_factor_launches += 1;
-        if (singular) { cleanup(); break; }
-        for (auto& g : groups) {
-            rsrr_nep h = hs[g.hi];
-            const int64_t nl = h->n * h->L;
-            { broadcast_rhs_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(h->d_U, nl, g.x); note_launch(); }
-        }
-        double ms_s = 0;
-        evs.start(st);
-        TRYW(launch_dense_solve<R>(d_jobs, nj, 0, st));
-        evs.stop(st);
-        bool pending = true;
-        int solves = 1;
-        for (auto& g : groups) {
-            rsrr_nep h = hs[g.hi];
-            const int64_t nl = h->n * h->L;
-            { accumulate_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(
-                  h->d_S + (int64_t)g.j0 * nl, g.x, nl, 0, nullptr); note_launch(); }
-        }
-        for (;;) {
-            for (int gi = 0; gi < ng; ++gi) {
-                auto& g = groups[gi];
-                if (g.done) continue;
-                rsrr_nep h = hs[g.hi];
-                const int64_t n = h->n, L = h->L;
-                CUDAW(cudaMemsetAsync(g.rn2, 0, (size_t)L * g.np * 8, st));
-                CUDAW(cudaMemsetAsync(g.xn2, 0, (size_t)L * g.np * 8, st));
-                CUDAW(cudaMemsetAsync(d_counters + 4 * gi, 0, 16, st));
-                { residual_kernel<R><<<dim3((unsigned)ceil_div(n, 128), (unsigned)g.np), 128, 0, st>>>(
-                      h->d_rowptr, h->d_colind, g.tvals, h->nnz, n, (int)L, h->d_U, h->d_S + (int64_t)g.j0 * n * L,
-                      g.x, g.rn2, g.xn2, g.sweeps == 0 ? nullptr : g.active); note_launch(); }
-                { eta_kernel<<<(unsigned)g.np, 32, 0, st>>>(g.rn2, g.xn2, g.un2, g.normT, g.np, (int)L, h->tol,
-                                                           h->refine_full ? 0.0 : h->tol, h->d_eta + (int64_t)g.j0 * L,
-                                                           g.active, g.prev_max, d_counters + 4 * gi,
-                                                           g.sweeps == 0 ? 1 : 0); note_launch(); }
-            }
-            std::vector<int32_t> hc((size_t)4 * ng);
-            CUDAW(cudaMemcpyAsync(hc.data(), d_counters, hc.size() * 4, cudaMemcpyDeviceToHost, st));
-            CUDAW(cudaStreamSynchronize(st));
-            if (pending) { ms_s += evs.ms(); pending = false; }
-            int active_groups = 0;
-            for (int gi = 0; gi < ng; ++gi) {
-                auto& g = groups[gi];
-                if (g.done) continue;
-                rsrr_nep h = hs[g.hi];
-                if (hc[4 * gi + 1]) nonfinite = true;
-                if (hc[4 * gi + 2]) notconv = true;
-                if (hc[4 * gi] == 0) { g.done = true; continue; }
-                if (g.sweeps >= max_refine) {
-                    std::vector<double> he((size_t)g.np * h->L);
-                    CUDAW(cudaMemcpyAsync(he.data(), h->d_eta + (int64_t)g.j0 * h->L, he.size() * 8,
-                                          cudaMemcpyDeviceToHost, st));
-                    CUDAW(cudaStreamSynchronize(st));
-                    for (double e : he) if (!(e <= h->tol)) notconv = true;
-                    CUDAW(cudaMemsetAsync(g.active, 0, (size_t)g.np * 4, st));
-                    g.done = true;
-                    continue;
-                }
-                ++active_groups;
-            }
-            if (nonfinite || notconv || active_groups == 0) break;
-            evs.start(st);
-            TRYW(launch_dense_solve<R>(d_jobs, nj, 0, st));
-            evs.stop(st);
-            pending = true;
-            ++solves;
-            for (auto& g : groups) {
-                if (g.done) continue;
-                rsrr_nep h = hs[g.hi];
-                const int64_t nl = h->n * h->L;
-                { accumulate_kernel<R><<<dim3((unsigned)ceil_div(nl, 256), (unsigned)g.np), 256, 0, st>>>(
-                      h->d_S + (int64_t)g.j0 * nl, g.x, nl, 1, g.active); note_launch(); }
-                ++g.sweeps;
-            }
-        }
-        CUDAW(cudaStreamSynchronize(st));
-        if (pending) ms_s += evs.ms();
-        tot_trsv_ms += ms_s;
-        tot_trsv_launches += solves;
-        for (auto& g : groups) hs[g.hi]->refine_sweeps = std::max(hs[g.hi]->refine_sweeps, g.sweeps);
-        cleanup();
-#undef TRYW
-#undef CUDAW
+    void* d_slots = nullptr;
+    void* d_img = nullptr;
+    auto cleanup = [&]() {
+        for (int i = 0; i < nh; ++i) { dfree(un2[i], st); dfree(status[i], st); dfree(sweeps[i], st); }
+        dfree(d_neps, st); dfree(d_jobs, st); dfree(d_next, st); dfree(d_slots, st); dfree(d_img, st);
+    };
+#define TRYD(expr) do { int rc_ = (expr); if (rc_ != RSRR_OK) { cleanup(); return rc_; } } while (0)
+#define CUDAD(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) { cleanup(); return set_error(RSRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); } } while (0)
+    for (int i = 0; i < nh; ++i) {
+        rsrr_nep h = hs[i];
+        TRYD(dalloc_n(&un2[i], (size_t)h->L, st));
+        TRYD(dalloc_n(&status[i], (size_t)h->N, st));
+        TRYD(dalloc_n(&sweeps[i], (size_t)h->N, st));
+        { column_norm2_kernel<<<(unsigned)h->L, 256, 0, st>>>(h->d_U, h->n, un2[i]); note_launch(); }
+        CUDAD(cudaGetLastError());
+        DenseNep& E = neps[i];
+        E.n = (int32_t)h->n;
+        E.J = h->J;
+        E.L = h->L;
+        E.N = h->N;
+        E.nnz = h->nnz;
+        E.rowptr = h->d_rowptr;
+        E.colind = h->d_colind;
+        E.rowidx = h->d_rowidx;
+        E.vals = h->d_vals;
+        E.F = dF[i];
+        E.U = h->d_U;
+        E.un2 = un2[i];
+        E.S = h->d_S;
+        E.eta = h->d_eta;
+        E.status = status[i];
+        E.sweeps = sweeps[i];
     }
-    dfree(d_next, st);
-    RSRR_CUDA(cudaStreamSynchronize(st));
-    for (rsrr_nep h : hs) {
-        h->ms_factor = tot_factor_ms;
-        h->ms_trsv = tot_trsv_ms;
-        h->factor_launches = tot_factor_launches;
-        h->trsv_launches = tot_trsv_launches;
+    TRYD(dalloc_n(&d_neps, (size_t)nh, st));
+    TRYD(dalloc_n(&d_jobs, (size_t)njobs, st));
+    TRYD(dalloc_n(&d_next, 1, st));
+    TRYD(dalloc(&d_slots, (size_t)grid * dense_slot_bytes<R>(n_max, L_max), st));
+    if (dense_image_bytes<R>(n_max)) TRYD(dalloc(&d_img, (size_t)grid * dense_image_bytes<R>(n_max), st));
+    CUDAD(cudaMemcpyAsync(d_neps, neps.data(), neps.size() * sizeof(DenseNep), cudaMemcpyHostToDevice, st));
+    CUDAD(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(DenseSampleJob), cudaMemcpyHostToDevice, st));
+    DenseSampleCfg cfg;
+    cfg.tol = hs[0]->tol;
+    cfg.target = hs[0]->refine_full ? 0.0 : hs[0]->tol;
+    cfg.max_refine = max_refine;
+    EvPair ev;
+    ev.start(st);
+    TRYD(launch_dense_sample<R>(d_neps, d_jobs, njobs, n_max, L_max, grid, d_slots, d_img, d_next, cfg, st));
+    ev.stop(st);
+    bool singular = false, timeout = false, nonfinite = false, notconv = false;
+    for (int i = 0; i < nh; ++i) {
+        std::vector<int32_t> hst(hs[i]->N), hsw(hs[i]->N);
+        CUDAD(cudaMemcpyAsync(hst.data(), status[i], hst.size() * 4, cudaMemcpyDeviceToHost, st));
+        CUDAD(cudaMemcpyAsync(hsw.data(), sweeps[i], hsw.size() * 4, cudaMemcpyDeviceToHost, st));
+        CUDAD(cudaStreamSynchronize(st));
+        for (int j = 0; j < hs[i]->N; ++j) {
+            if (hst[j] > 0) singular = true;
+            if (hst[j] == -1) timeout = true;
+            if (hst[j] == -2) nonfinite = true;
+            if (hst[j] == -3) notconv = true;
+            hs[i]->refine_sweeps = std::max(hs[i]->refine_sweeps, hsw[j]);
+        }
     }
+    const double ms = ev.ms();
+    for (rsrr_nep h : hs) {  // one launch serves the whole set: each handle reports it
+        h->ms_factor = ms;
+        h->ms_trsv = 0;
+        h->factor_launches = 1;
+        h->trsv_launches = 0;
+    }
+    cleanup();
+#undef TRYD
+#undef CUDAD
+    if (timeout) return set_error(RSRR_ETIMEOUT, "dense LU: a tensor-core wait timed out");
     if (singular) return set_error(RSRR_ESINGULAR, "zero pivot: a sampling point is an eigenvalue of T");
     if (nonfinite) return set_error(RSRR_ENONFINITE, "non-finite backward error in a sample solve");
     if (notconv) return set_error(RSRR_ENOTCONVERGED, "sample solves did not reach the backward-error tolerance");
-    return rc;
+    return RSRR_OK;
 }
 
 }  // namespace
