@@ -345,6 +345,9 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+SOLVE_STREAMS = 4  # config 3: streams (and host threads) for the per-NEP project / solve calls
+
+
 def batch_members(count, side=0):
     import workloads
     return [workloads.config3_member(i, s=side or None) for i in range(count)]
@@ -395,18 +398,36 @@ def run_batch(args):
     prec = (rs.RSRR_C64_IR if precision == "c64" else rs.RSRR_FP64) | rs.RSRR_REFINE_FULL
     stream = torch.cuda.current_stream()
     sp = ctypes.c_void_p(stream.cuda_stream)
-    hs = [rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, sp) for p in probs]
+    # the handles are spread over a few streams: one batched sampling call, then each stream's
+    # handles go through rsrr_project / rsrr_solve in a host thread of their own
+    streams = [torch.cuda.Stream() for _ in range(SOLVE_STREAMS)]
+    sps = [ctypes.c_void_p(st.cuda_stream) for st in streams]
+    hs = [rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, sps[i % len(sps)]) for i, p in enumerate(probs)]
     contours = [(p.gamma, p.a, p.b) for p in probs]
     Ns, Ls = [p.N for p in probs], [p.L for p in probs]
 
+    def finish(handles, vectors=False):
+        """rsrr_project + rsrr_solve of every handle, one host thread per stream; eigenvalue counts."""
+        counts = [0] * len(handles)
+        out = {}
+
+        def work(slot):
+            for i in range(slot, len(handles), len(sps)):
+                h = handles[i]
+                h.project(W["delta"])
+                lam, V, res = h.solve(W["N_S"], W["K"], 1e3, 4096, vectors)
+                counts[i] = int(lam.size)
+                out[i] = (lam, V, res)
+        threads = [threading.Thread(target=work, args=(k,)) for k in range(len(sps))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        return counts, out
+
     def step(Us):
         rs.sample_batch(hs, contours, Ns, Ls, Us, prec, args.tol, 20)
-        counts = []
-        for h in hs:
-            h.project(W["delta"])
-            lam, _, _ = h.solve(W["N_S"], W["K"], 1e3, 4096, False)
-            counts.append(int(lam.size))
-        return counts
+        return finish(hs)[0]
 
     def barrier():
         torch.cuda.synchronize()
@@ -470,13 +491,12 @@ def run_batch(args):
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
-            gs = [rs.Nep(p.n, t[0], t[1], t[2], fns_of(p), 0, sp) for p, t in zip(probs, host)]
+            gs = [rs.Nep(p.n, t[0], t[1], t[2], fns_of(p), 0, sps[i % len(sps)])
+                  for i, (p, t) in enumerate(zip(probs, host))]
             rs.sample_batch(gs, contours, Ns, Ls, [t[3] for t in host], prec, args.tol, 20)
-            d2h = 0
+            _, out = finish(gs, vectors=True)
+            d2h = sum(lam.nbytes + V.nbytes + res.nbytes for lam, V, res in out.values())
             for g in gs:
-                g.project(W["delta"])
-                lam, V, res = g.solve(W["N_S"], W["K"], 1e3, 4096, True)
-                d2h += lam.nbytes + V.nbytes + res.nbytes
                 g.close()
         barrier()
         e2e_value, _ = job_value(points, args.steps, 1e3 * (time.perf_counter() - t0), device="cuda")

@@ -125,16 +125,19 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
 
 /* ---- rsrr_sample_batch ----------------------------------------------------------------
  * rsrr_sample on `count` handles in one call (Algorithm 2, Steps 1-2 for a batch of NEPs).
- * The points of every NEP that takes the dense LU go into shared persistent launches (one
- * CTA per point, largest n first, in waves sized to the free device memory); banded NEPs run
- * one after another on the band path.  Each handle afterwards holds its own S_hat, exactly as
- * after its own rsrr_sample, and goes on to rsrr_project / rsrr_solve independently.
- *   hs          [count] distinct handles, all created on the same device and stream
+ * The points of every NEP that takes the dense LU go into one persistent launch (one CTA per
+ * point at a time, largest n first, each CTA in a memory slot of its own) on the stream of the
+ * first such handle, ordered after the work already queued on the other handles' streams;
+ * banded NEPs run one after another on the band path, each on its own stream.  Each handle
+ * afterwards holds its own S_hat, exactly as after its own rsrr_sample, and goes on to
+ * rsrr_project / rsrr_solve independently (on its own stream, so several can run at once).
+ * Returns after all of it has completed.
+ *   hs          [count] distinct handles, all created on the same device
  *   C, N, L     [count] contour, sampling points and probing columns per handle
  *   U_reim      [count] probing matrices as in rsrr_sample (an entry, or U_reim itself, may
  *               be NULL to reuse each handle's resident U)
  *   precision, tol, max_refine   as in rsrr_sample, shared by all handles
- * Errors: as rsrr_sample (the first failing handle's); EINVAL also for mixed streams or a
+ * Errors: as rsrr_sample (the first failing handle's); EINVAL also for mixed devices or a
  * repeated handle.  After an error no handle of the batch counts as sampled. */
 int rsrr_sample_batch(rsrr_nep* hs, int32_t count, const rsrr_contour* C, const int32_t* N,
                       const int32_t* L, const double* const* U_reim, int32_t precision,

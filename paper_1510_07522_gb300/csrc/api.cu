@@ -199,8 +199,8 @@ int rsrr_sample_batch(rsrr_nep* hs, int32_t count, const rsrr_contour* C, const 
         return set_error(RSRR_EINVAL, "rsrr_sample_batch: NULL array or count out of range");
     for (int32_t i = 0; i < count; ++i) {
         RSRR_TRY(check_sample_args(hs[i], &C[i], N[i], L[i], precision, tol, max_refine));
-        if (hs[i]->device != hs[0]->device || hs[i]->stream != hs[0]->stream)
-            return set_error(RSRR_EINVAL, "rsrr_sample_batch: all handles must share one device and one stream");
+        if (hs[i]->device != hs[0]->device)
+            return set_error(RSRR_EINVAL, "rsrr_sample_batch: all handles must be on one device");
         for (int32_t k = 0; k < i; ++k)
             if (hs[k] == hs[i]) return set_error(RSRR_EINVAL, "rsrr_sample_batch: a handle appears twice");
     }

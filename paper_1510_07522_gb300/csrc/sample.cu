@@ -586,8 +586,8 @@ int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
     return sample_impl<float>(h, F[0], max_refine);
 }
 
-// Several NEPs in one call: the dense ones share the persistent dense-LU launches, the banded
-// ones run one after another on the band path.  All handles use one stream and one precision.
+// Several NEPs in one call: the dense ones share one fused dense launch, the banded ones run one
+// after another on the band path, each on its own stream.  All handles use one precision.
 int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const double*>& U, int max_refine) {
     std::vector<std::vector<c128>> F(hs.size());
     for (size_t i = 0; i < hs.size(); ++i) RSRR_TRY(sample_prepare(hs[i], U[i], &F[i]));
@@ -601,11 +601,31 @@ int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const do
         }
     }
     const bool fp64 = hs[0]->precision == RSRR_FP64;
-    if (!dh.empty()) RSRR_TRY(fp64 ? dense_run<double>(dh, dFs, max_refine) : dense_run<float>(dh, dFs, max_refine));
+    if (!dh.empty()) {
+        // The dense NEPs share one launch on the first one's stream: it waits for the work already
+        // queued on the other handles' streams (their probing matrices and S_hat storage), and
+        // those streams wait for it in turn.
+        cudaStream_t s0 = dh[0]->stream;
+        cudaEvent_t ev = nullptr;
+        RSRR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        int rc = RSRR_OK;
+        for (rsrr_nep h : dh) {
+            if (h->stream == s0 || rc != RSRR_OK) continue;
+            if (cudaEventRecord(ev, h->stream) != cudaSuccess || cudaStreamWaitEvent(s0, ev, 0) != cudaSuccess)
+                rc = set_error(RSRR_ECUDA, "rsrr_sample_batch: stream ordering failed");
+        }
+        if (rc == RSRR_OK) rc = fp64 ? dense_run<double>(dh, dFs, max_refine) : dense_run<float>(dh, dFs, max_refine);
+        if (cudaEventRecord(ev, s0) == cudaSuccess)
+            for (rsrr_nep h : dh)
+                if (h->stream != s0) cudaStreamWaitEvent(h->stream, ev, 0);
+        cudaEventDestroy(ev);
+        RSRR_TRY(rc);
+    }
     for (size_t i = 0; i < hs.size(); ++i) {
         if (use_dense(hs[i])) continue;
         RSRR_TRY(fp64 ? sample_impl<double>(hs[i], F[i], max_refine) : sample_impl<float>(hs[i], F[i], max_refine));
     }
+    for (rsrr_nep h : hs) RSRR_CUDA(cudaStreamSynchronize(h->stream));
     return RSRR_OK;
 }
 

@@ -144,19 +144,27 @@ def test_batch_then_project_and_solve(rs):
         h.close()
 
 
-def test_batch_rejects_mixed_streams_and_repeats(rs):
-    import torch
-    p = w.config3_member(0, s=9, N=4, L=2)
-    a = open_nep(rs, p)
-    s2 = torch.cuda.Stream()
+def test_batch_across_streams_and_repeats(rs):
+    """Handles on different streams: the batch orders itself after each stream's queued work and
+    every handle gets the same samples as in a one-stream batch; a repeated handle is refused."""
     import ctypes
-    b = rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, ctypes.c_void_p(s2.cuda_stream))
-    args = ([(p.gamma, p.a, p.b)] * 2, [p.N] * 2, [p.L] * 2, [p.U] * 2, rs.RSRR_FP64, 1e-10, 5)
+    import torch
+    probs = [w.config3_member(i, s=s, N=6, L=4) for i, s in [(0, 14), (1, 12), (2, 9)]]
+    mode = rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL
+    args = lambda ps: ([(p.gamma, p.a, p.b) for p in ps], [p.N for p in ps], [p.L for p in ps], [p.U for p in ps],
+                       mode, 1e-10, 20)
+    one = [open_nep(rs, p) for p in probs]
+    rs.sample_batch(one, *args(probs))
+    ref = [h.samples() for h in one]
+    streams = [torch.cuda.Stream() for _ in probs]
+    many = [rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, ctypes.c_void_p(st.cuda_stream))
+            for p, st in zip(probs, streams)]
+    rs.sample_batch(many, *args(probs))
+    for h, X in zip(many, ref):
+        assert rel_err_cols(h.samples(), X).max() < 1e-10
+        h.project(1e-14)  # each handle goes on on its own stream
     with pytest.raises(rs.RsrrError) as e:
-        rs.sample_batch([a, b], *args)
+        rs.sample_batch([one[0], one[0]], *args(probs[:1] * 2))
     assert e.value.name == "EINVAL"
-    with pytest.raises(rs.RsrrError) as e:
-        rs.sample_batch([a, a], *args)
-    assert e.value.name == "EINVAL"
-    a.close()
-    b.close()
+    for h in one + many:
+        h.close()
