@@ -299,10 +299,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
                 gr += x.re * y.re + x.im * y.im;  // conj(x) y
                 gi += x.re * y.im - x.im * y.re;
             }
-            al = block_sum_all(al);
-            be = block_sum_all(be);
-            gr = block_sum_all(gr);
-            gi = block_sum_all(gi);
+            block_sum4(al, be, gr, gi);
             const double g = sqrt(gr * gr + gi * gi);
             if (fmin(al, be) <= a.floor2 || g <= a.abs_g) continue;  // uniform
             const double off = g / sqrt(al * be);
@@ -329,7 +326,7 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
                 }
             }
             if (tid == 0) atomicAdd(a.rotations, 1);
-            __syncthreads();  // block_sum_all's shared slots are reused by the next pair
+            __syncthreads();
         }
         if (!grid_sync(a.gb)) return;
     }

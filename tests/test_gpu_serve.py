@@ -19,7 +19,8 @@ def rs():
 
 def make_requests(rs, serve):
     probs = [w.config0(N=16, L=8, nx=12, ny=10), w.planted_sqrt(), w.tiny_qep(),
-             w.config1b(s=16, N=24, L=8), w.planted_delay(), w.config0_linear(N=16, L=8, nx=14, ny=11)]
+             w.config1b(s=16, N=24, L=8), w.planted_delay(), w.config0_linear(N=16, L=8, nx=14, ny=11),
+             w.config3_member(2, s=12, N=16, L=8)]  # the last one takes the dense LU
     out = []
     for i, p in enumerate(probs):
         K = 4 if p.name == "tiny_qep" else 2
@@ -38,7 +39,7 @@ def test_results_same_alone_and_in_mix(rs):
         alone[r.rid] = [d for d in done if d.rid == r.rid][0]
     srv.close()
     srv = serve.Server(budget_bytes=64e9, slots=4)
-    mix = serve.replay(srv, make_requests(rs, serve), np.zeros(6))
+    mix = serve.replay(srv, make_requests(rs, serve), np.zeros(7))
     srv.close()
     assert srv.peak_inflight > 1  # requests really overlapped
     for r in mix:
