@@ -55,13 +55,23 @@ typedef enum {
                                p1 = 1: continued branch -sqrt(p0 - z), holomorphic off
                                [p0, +inf) (gun-type problems, Section 7.2)               */
     RSRR_F_EXP_DELAY = 4,   /* f = exp(-p0 z)                                            */
-    RSRR_F_RATIONAL = 5     /* f = p0 z / (z + p1)  (Biot / loaded-string terms)         */
+    RSRR_F_RATIONAL = 5,    /* f = p0 z / (z + p1)  (Biot / loaded-string terms)         */
+    RSRR_F_CALLBACK = 6     /* f and f' from the caller's function `cb` (any analytic f) */
 } rsrr_fkind;
+
+/* Caller-supplied scalar function (RSRR_F_CALLBACK): for k < m, write f(z_k) and f'(z_k) to
+ * f_reim[2k..2k+1] and df_reim[2k..2k+1] (z_reim[2k] + i z_reim[2k+1]).  It must be analytic
+ * inside and on the contour (Section 6: T(z) = sum_i f_i(z) A_i); f' is used by the winding
+ * number (Eq. eq-ncs).  Called on the host, from the thread that runs rsrr_sample / rsrr_solve,
+ * for as long as the handle lives. */
+typedef void (*rsrr_fn_cb)(void* user, int64_t m, const double* z_reim, double* f_reim, double* df_reim);
 
 typedef struct {
     int32_t kind;           /* an rsrr_fkind                                             */
     int32_t reserved;       /* must be 0                                                 */
     double p[4];            /* parameters, meaning per kind above                        */
+    rsrr_fn_cb cb;          /* RSRR_F_CALLBACK: the function; otherwise ignored (NULL)   */
+    void* user;             /* passed to cb unchanged                                    */
 } rsrr_fn;
 
 /* Elliptic contour phi(t) = gamma + a cos t + i b sin t (Eq. eq-contour).  The N
@@ -123,6 +133,19 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
 int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
                 const double* U_reim, int32_t precision, double tol, int32_t max_refine);
 
+/* ---- rsrr_sample_points ---------------------------------------------------------------
+ * rsrr_sample at sampling points the caller chooses.  The sampling scheme needs only the
+ * solutions T(z_j)^{-1} U at some points z_j (Eq. eq-hatS): nothing ties them to a quadrature
+ * rule on the contour, and points inside the contour can serve too (Section 3.2).  The contour C
+ * is still the one Algorithm 1 integrates over in rsrr_solve.
+ *   C           contour used by rsrr_solve (and for nothing else here)
+ *   N, z_reim   the N sampling points, [N][2] (re, im); none may be an eigenvalue
+ *   L, U_reim, precision, tol, max_refine   as in rsrr_sample
+ * rsrr_project_moments refuses a handle sampled this way (its weights are the contour's).
+ * Errors: as rsrr_sample; EINVAL also for a NULL or non-finite point. */
+int rsrr_sample_points(rsrr_nep h, const rsrr_contour* C, int32_t N, const double* z_reim, int32_t L,
+                       const double* U_reim, int32_t precision, double tol, int32_t max_refine);
+
 /* ---- rsrr_sample_batch ----------------------------------------------------------------
  * rsrr_sample on `count` handles in one call (Algorithm 2, Steps 1-2 for a batch of NEPs).
  * The points of every NEP that takes the dense LU go into one persistent launch (one CTA per
@@ -151,6 +174,19 @@ int rsrr_sample_batch(rsrr_nep* hs, int32_t count, const rsrr_contour* C, const 
  *   k_S_out receives k_S
  * Errors: EORDER, EINVAL, ENOMEM, ECUDA, ENONFINITE. */
 int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out);
+
+/* ---- rsrr_project_moments -------------------------------------------------------------
+ * rsrr_project with the moment scheme of SSRR (Section 3.1) in place of the sampling scheme:
+ * Step 3 factors M_hat = [M_0 ... M_{K'-1}] (Eq. eq-hatM), the quadrature moments
+ * M_alpha = sum_i w_i zeta_i^alpha T(z_i)^{-1} U of the samples already on the device
+ * (Eq. eq-malpha-qud, trapezoid weights w_i = phi'(theta_i) / (i N) of the contour), i.e.
+ * M_hat = S_hat D Z (Eq. eq-hatMS).  zeta_i = (z_i - gamma) / max(a, b): the shifted and scaled
+ * monomials span the same space as z_i^alpha.  Everything after (truncation at delta, P_i,
+ * rsrr_solve) is unchanged, so the two schemes can be compared on the same samples.
+ *   Kp       moment order K', 1 <= K' <= N (K' = N spans the same space as S_hat when Z has
+ *            full rank)
+ * Errors: as rsrr_project; EINVAL for K' outside 1..N. */
+int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out);
 
 /* ---- rsrr_solve -----------------------------------------------------------------------
  * Algorithm 1 on T_S(z) = sum_i f_i(z) P_i with the same contour as rsrr_sample:
@@ -200,6 +236,8 @@ typedef struct {
     double ms_zgemm;            /* device time of the FP64 complex GEMMs of the last project + solve */
     double zgemm_gflop;         /* their algorithmic work, 8 M N K per product, in GFLOP          */
     int32_t dense_lu;           /* 1 if the last rsrr_sample factored with the dense LU            */
+    int32_t proj_cols;          /* columns of the matrix the last projection factored: N*L
+                                   (rsrr_project) or K'*L (rsrr_project_moments)                 */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);
@@ -207,7 +245,8 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* out);
 int rsrr_get_samples(rsrr_nep h, int32_t j0, int32_t j1, double* out_reim);
 /* Backward errors eta of all N*L columns (column jL + l is point j, probe l). */
 int rsrr_get_eta(rsrr_nep h, double* out);
-/* The min(n, N*L) singular values of S_hat, descending (after rsrr_project). */
+/* The min(n, proj_cols) singular values of S_hat (or M_hat after rsrr_project_moments),
+ * descending. */
 int rsrr_get_sigma(rsrr_nep h, double* out);
 /* The orthonormal basis S, n x k_S, caller ordering (after rsrr_project). */
 int rsrr_get_basis(rsrr_nep h, double* out_reim);

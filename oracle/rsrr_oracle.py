@@ -226,6 +226,27 @@ def truncated_basis(Shat, delta=1e-14):
 
 
 # ----------------------------------------------------------------------------------------
+# The moment scheme of SSRR (Section 3.1, Eqs. eq-malpha-qud and eq-hatM): the projection space
+# is spanned by the quadrature moments M_alpha = sum_i w_i z_i^alpha T(z_i)^{-1} U, alpha < K',
+# instead of by the samples themselves.  w_i = phi'(theta_i) / (i N) are the trapezoid weights
+# of (1 / 2 pi i) oint dz on the ellipse.  The monomials are taken in the shifted and scaled
+# variable (z - gamma) / rho with rho = max(a, b): a polynomial change of basis of degree < K',
+# so span(M_hat) is the same, with better-scaled columns.
+# ----------------------------------------------------------------------------------------
+def moment_matrix(prob, Shat, Kp):
+    z, dphi, _ = contour_points(prob.gamma, prob.a, prob.b, prob.N)
+    rho = max(prob.a, prob.b)
+    w = dphi / (1j * prob.N)
+    zeta = (z - prob.gamma) / rho
+    L = prob.L
+    M = np.zeros((prob.n, Kp * L), dtype=np.complex128, order="F")
+    for al in range(Kp):
+        for i in range(prob.N):
+            M[:, al * L:(al + 1) * L] += w[i] * zeta[i] ** al * Shat[:, i * L:(i + 1) * L]
+    return M
+
+
+# ----------------------------------------------------------------------------------------
 # Algorithm 2, Step 4 (first half), Eq. eq-Zs-expr: P_i = S^H A_i S.
 # ----------------------------------------------------------------------------------------
 def project(prob, S):
@@ -325,10 +346,14 @@ def eigen_residuals(prob, lam, V):
     return np.array(raw), np.array(scaled)
 
 
-def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False):
-    """Algorithm 2 end to end; eigenvalues strictly inside the ellipse, sorted by |lam|."""
-    Shat, infos, eta = sample(prob, threads=threads, dense=dense)
-    S, sigma, k_S = truncated_basis(Shat, delta)
+def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False, moments=0, z=None):
+    """Algorithm 2 end to end; eigenvalues strictly inside the ellipse, sorted by |lam|.
+    moments = K' > 0: the SSRR moment scheme (Step 3 on M_hat of K' moments instead of S_hat).
+    z: sampling points other than the contour's nodes (Section 3.2 allows any points in the
+    domain; the ellipse still bounds Algorithm 1)."""
+    assert not (moments and z is not None), "the moment scheme needs the contour's nodes"
+    Shat, infos, eta = sample(prob, threads=threads, dense=dense, z=z)
+    S, sigma, k_S = truncated_basis(moment_matrix(prob, Shat, moments) if moments else Shat, delta)
     P = project(prob, S)
     lam, g, diag = reduced_ss(P, prob.fns, prob.gamma, prob.a, prob.b, N_S, K, tol_gap,
                               return_diag=True)

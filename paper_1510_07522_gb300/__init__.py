@@ -25,7 +25,7 @@ RSRR_REFINE_FULL = 0x100
 RSRR_NATURAL_ORDER = 0x1
 RSRR_DENSE_LU = 0x2
 
-F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL = range(6)
+F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL, F_CALLBACK = range(7)
 
 
 class RsrrError(RuntimeError):
@@ -35,8 +35,27 @@ class RsrrError(RuntimeError):
         self.name = ERRORS.get(code, str(code))
 
 
+# f(z) and f'(z) for m points: (user, m, z_reim, f_reim, df_reim)
+RSRR_FN_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+
+
 class rsrr_fn(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p", ctypes.c_double * 4)]
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p", ctypes.c_double * 4),
+                ("cb", RSRR_FN_CB), ("user", ctypes.c_void_p)]
+
+
+def callback_fn(f, df):
+    """A RSRR_F_CALLBACK term from Python callables f(z) and df(z) on complex scalars.  Returns the
+    (kind, params) pair that rsrr_create_nep / Nep take; the wrapper lives with the returned
+    object, which the handle keeps."""
+    def cb(user, m, z, fo, dfo):
+        for k in range(m):
+            zz = complex(z[2 * k], z[2 * k + 1])
+            v, d = complex(f(zz)), complex(df(zz))
+            fo[2 * k], fo[2 * k + 1] = v.real, v.imag
+            dfo[2 * k], dfo[2 * k + 1] = d.real, d.imag
+    return (F_CALLBACK, RSRR_FN_CB(cb))
 
 
 class rsrr_contour(ctypes.Structure):
@@ -63,14 +82,16 @@ class rsrr_info(ctypes.Structure):
                 ("ms_project_basis", ctypes.c_double), ("ms_project_gemm", ctypes.c_double),
                 ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
                 ("ms_solve_extract", ctypes.c_double), ("ms_zgemm", ctypes.c_double),
-                ("zgemm_gflop", ctypes.c_double), ("dense_lu", ctypes.c_int32)]
+                ("zgemm_gflop", ctypes.c_double), ("dense_lu", ctypes.c_int32),
+                ("proj_cols", ctypes.c_int32)]
 
 
 _lib = None
 EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr_get_info",
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
-           "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch"]
+           "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
+           "rsrr_project_moments", "rsrr_sample_points"]
 
 
 def lib():
@@ -101,6 +122,8 @@ def lib():
         "rsrr_kernel_launches": ([], ctypes.c_int64),
         "rsrr_band_solve_noalloc": ([I64, I32, I32, P, I32, P, P], ctypes.c_int),
         "rsrr_sample_batch": ([P, I32, P, P, P, P, I32, D, I32], ctypes.c_int),
+        "rsrr_project_moments": ([P, I32, D, P], ctypes.c_int),
+        "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -148,6 +171,9 @@ def rsrr_create_nep(n, rowptr, colind, vals, fns, flags=0, stream=None):
     for i, (kind, params) in enumerate(fns):
         farr[i].kind = int(kind)
         farr[i].reserved = 0
+        if int(kind) == F_CALLBACK:
+            farr[i].cb = params  # an RSRR_FN_CB from callback_fn
+            continue
         p = list(params) + [0.0] * 4
         for t in range(4):
             farr[i].p[t] = float(p[t])
@@ -186,6 +212,21 @@ def rsrr_sample_batch(handles, contours, Ns, Ls, Us=None, precision=RSRR_FP64, t
                 Uarr[i] = Uc.ctypes.data
     _check(lib().rsrr_sample_batch(H, count, C, Narr, Larr, Uarr, int(precision), float(tol), int(max_refine)))
     del keep
+
+
+def rsrr_sample_points(h, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+    """rsrr_sample at the points z (complex array); (gamma, a, b) is the contour for rsrr_solve."""
+    C = rsrr_contour(complex(gamma).real, complex(gamma).imag, float(a), float(b))
+    zr = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    Uc = None if U is None else _c128(U)
+    _check(lib().rsrr_sample_points(h, ctypes.byref(C), int(zr.size), _ptr(zr), int(L), _ptr(Uc), int(precision),
+                                    float(tol), int(max_refine)))
+
+
+def rsrr_project_moments(h, Kp, delta=1e-14):
+    k = ctypes.c_int32()
+    _check(lib().rsrr_project_moments(h, int(Kp), float(delta), ctypes.byref(k)))
+    return k.value
 
 
 def rsrr_project(h, delta=1e-14):
@@ -239,7 +280,8 @@ class Nep:
     def __init__(self, n, rowptr, colind, vals, fns, flags=0, stream=None):
         self.n = int(n)
         self.J = int(np.asarray(vals).shape[0])
-        self.h = rsrr_create_nep(n, rowptr, colind, vals, fns, flags, stream)
+        self._fns = list(fns)  # keeps RSRR_F_CALLBACK wrappers alive as long as the handle
+        self.h = rsrr_create_nep(n, rowptr, colind, vals, self._fns, flags, stream)
 
     def sample(self, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
         self.N, self.L = int(N), int(L)
@@ -247,6 +289,16 @@ class Nep:
 
     def project(self, delta=1e-14):
         self.kS = rsrr_project(self.h, delta)
+        return self.kS
+
+    def sample_points(self, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+        """rsrr_sample_points: sample at the points z, keep (gamma, a, b) for rsrr_solve."""
+        self.N, self.L = int(np.asarray(z).size), int(L)
+        rsrr_sample_points(self.h, gamma, a, b, z, L, U, precision, tol, max_refine)
+
+    def project_moments(self, Kp, delta=1e-14):
+        """The SSRR moment scheme: rsrr_project on K' quadrature moments of the samples."""
+        self.kS = rsrr_project_moments(self.h, Kp, delta)
         return self.kS
 
     def solve(self, N_S=500, K=2, tol_gap=1e3, cap=4096, vectors=True):
@@ -267,7 +319,7 @@ class Nep:
         return out
 
     def sigma(self):
-        out = np.zeros(min(self.n, self.N * self.L))
+        out = np.zeros(min(self.n, self.info()["proj_cols"]))
         _check(lib().rsrr_get_sigma(self.h, _ptr(out)))
         return out
 

@@ -161,6 +161,7 @@ int check_sample_args(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, i
 
 void begin_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, int32_t precision, double tol) {
     h->C = *C;
+    h->points.clear();
     h->N = N;
     h->L = L;
     h->precision = precision & 0xff;
@@ -186,6 +187,26 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const d
     RSRR_TRY(check_sample_args(h, C, N, L, precision, tol, max_refine));
     DeviceGuard g(h->device);
     begin_sample(h, C, N, L, precision, tol);
+    Timer t(h);
+    int rc = sample_run(h, U_reim, max_refine);
+    h->ms_sample = t.stop();
+    if (rc != RSRR_OK) return rc;
+    return finish_sample(h);
+}
+
+int rsrr_sample_points(rsrr_nep h, const rsrr_contour* C, int32_t N, const double* z_reim, int32_t L,
+                       const double* U_reim, int32_t precision, double tol, int32_t max_refine) {
+    RSRR_TRY(check_sample_args(h, C, N, L, precision, tol, max_refine));
+    if (!z_reim) return set_error(RSRR_EINVAL, "rsrr_sample_points: NULL point array");
+    std::vector<zd> pts(N);
+    for (int32_t j = 0; j < N; ++j) {
+        pts[j] = zd(z_reim[2 * j], z_reim[2 * j + 1]);
+        if (!std::isfinite(pts[j].real()) || !std::isfinite(pts[j].imag()))
+            return set_error(RSRR_EINVAL, "rsrr_sample_points: non-finite point");
+    }
+    DeviceGuard g(h->device);
+    begin_sample(h, C, N, L, precision, tol);
+    h->points = pts;
     Timer t(h);
     int rc = sample_run(h, U_reim, max_refine);
     h->ms_sample = t.stop();
@@ -232,6 +253,18 @@ int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out) {
     h->projected = true;
     if (k_S_out) *k_S_out = h->kS;
     return RSRR_OK;
+}
+
+int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out) {
+    if (!h) return set_error(RSRR_EINVAL, "NULL handle");
+    if (!h->sampled) return set_error(RSRR_EORDER, "rsrr_project_moments needs a successful rsrr_sample");
+    if (Kp < 1 || Kp > h->N) return set_error(RSRR_EINVAL, "moment order K' must be in 1..N");
+    if (!h->points.empty())
+        return set_error(RSRR_EINVAL, "the moment scheme needs the contour's quadrature nodes, not rsrr_sample_points");
+    h->moment_order = Kp;
+    const int rc = rsrr_project(h, delta, k_S_out);
+    h->moment_order = 0;
+    return rc;
 }
 
 int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, double* lambda_reim,
@@ -289,6 +322,7 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->ms_zgemm = h->ms_zgemm_project + h->ms_zgemm_solve;
     o->zgemm_gflop = (h->zgemm_flops_project + h->zgemm_flops_solve) * 1e-9;
     o->dense_lu = h->dense_used ? 1 : 0;
+    o->proj_cols = h->proj_cols;
     return RSRR_OK;
 }
 

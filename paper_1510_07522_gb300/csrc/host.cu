@@ -56,8 +56,9 @@ void dfree(void* p, cudaStream_t s) {
 
 // ---- scalar functions ----------------------------------------------------------------------
 int check_fn(const rsrr_fn& f) {
-    if (f.kind < RSRR_F_CONST || f.kind > RSRR_F_RATIONAL)
+    if (f.kind < RSRR_F_CONST || f.kind > RSRR_F_CALLBACK)
         return set_error(RSRR_EINVAL, "unknown function kind " + std::to_string(f.kind));
+    if (f.kind == RSRR_F_CALLBACK && !f.cb) return set_error(RSRR_EINVAL, "RSRR_F_CALLBACK without a function");
     for (double v : f.p)
         if (!std::isfinite(v)) return set_error(RSRR_ENONFINITE, "non-finite function parameter");
     if (f.kind == RSRR_F_ISQRT_SHIFT && f.p[1] != 0.0 && f.p[1] != 1.0)
@@ -92,6 +93,14 @@ void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv) {
             zd d = z + f.p[1];
             *val = f.p[0] * z / d;
             *deriv = f.p[0] * f.p[1] / (d * d);
+            break;
+        }
+        case RSRR_F_CALLBACK: {
+            const double zr[2] = {z.real(), z.imag()};
+            double fr[2] = {0.0, 0.0}, dr[2] = {0.0, 0.0};
+            f.cb(f.user, 1, zr, fr, dr);
+            *val = zd(fr[0], fr[1]);
+            *deriv = zd(dr[0], dr[1]);
             break;
         }
         default: *val = 0.0; *deriv = 0.0;

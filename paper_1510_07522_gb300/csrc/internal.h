@@ -56,6 +56,7 @@ struct rsrr_nep_s {
 
     // sampling state
     int32_t N = 0, L = 0, precision = 0;
+    std::vector<std::complex<double>> points;  // caller's sampling points (empty: the contour's nodes)
     bool refine_full = false;
     rsrr_contour C{};
     double tol = 0;
@@ -69,6 +70,8 @@ struct rsrr_nep_s {
     size_t S_cols_cap = 0;
 
     // projection state
+    int32_t moment_order = 0;      // > 0: the next rsrr_project uses K' quadrature moments (SSRR)
+    int32_t proj_cols = 0;         // columns of the matrix the last projection factored
     bool projected = false;
     int32_t kS = -1;
     rsrr::c128* d_Q = nullptr;     // [kS][n] orthonormal basis S (permuted rows)

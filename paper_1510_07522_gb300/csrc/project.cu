@@ -14,7 +14,8 @@
 //   2. A second QR, of R_keep^H (m x k'), keeps only its k' x k' triangle R2; one-sided Jacobi
 //      on R2 with the rotations accumulated gives R2^H = J Sigma W^H, and the left singular
 //      vectors of R_keep = R2^H Q2^H are the columns of J.
-//   3. S = Q [J(:, 1:k_S); 0] by applying the panels' reflectors in reverse.
+//   3. S = Q [J(:, 1:k_S); 0] by applying the panels' reflectors in reverse, after one
+//      Newton-Schulz step on J(:, 1:k_S) against the rounding its rotations accumulated.
 //   4. P_i = S^H (A_i S): CSR SpMM, then ZGEMM.
 #include <algorithm>
 #include <cmath>
@@ -446,8 +447,10 @@ int project_run(rsrr_nep h, double delta) {
     zgemm_profile_begin();
     const int64_t n = h->n;
     const int N = h->N, L = h->L, J = h->J;
-    const int m = N * L;
+    const int Kp = h->moment_order;
+    const int m = Kp > 0 ? Kp * L : N * L;
     const int kmax = (int)std::min<int64_t>(n, m);
+    h->proj_cols = m;
     dfree(h->d_Q, st);
     dfree(h->d_P, st);
     h->d_Q = nullptr;
@@ -455,7 +458,7 @@ int project_run(rsrr_nep h, double delta) {
 
     c128 *A = nullptr, *V = nullptr, *W = nullptr, *W2 = nullptr, *tau = nullptr, *Tall = nullptr,
          *alpha = nullptr, *part2 = nullptr, *part3 = nullptr, *Yb = nullptr, *B = nullptr, *Jm = nullptr,
-         *Ybuf = nullptr, *Z = nullptr, *Z2 = nullptr, *AY = nullptr;
+         *Ybuf = nullptr, *Z = nullptr, *Z2 = nullptr, *AY = nullptr, *Eg = nullptr, *Jn = nullptr;
     double *part = nullptr, *dnorm = nullptr, *colnrm = nullptr;
     unsigned* bar = nullptr;
     int *order_d = nullptr, *cols_d = nullptr;
@@ -465,7 +468,7 @@ int project_run(rsrr_nep h, double delta) {
         zgemm_profile_end(&zm, &zf);
         for (void* p : {(void*)A, (void*)V, (void*)W, (void*)W2, (void*)tau, (void*)Tall, (void*)alpha,
                         (void*)part2, (void*)part3, (void*)Yb, (void*)B, (void*)Jm, (void*)Ybuf, (void*)Z,
-                        (void*)Z2, (void*)AY, (void*)part, (void*)dnorm, (void*)colnrm, (void*)bar,
+                        (void*)Z2, (void*)AY, (void*)Eg, (void*)Jn, (void*)part, (void*)dnorm, (void*)colnrm, (void*)bar,
                         (void*)order_d, (void*)cols_d})
             dfree(p, st);
     };
@@ -479,12 +482,41 @@ int project_run(rsrr_nep h, double delta) {
     if (occ < 1) { cleanup(); return set_error(RSRR_ECUDA, "panel kernel cannot be resident"); }
     const int G = nsm;
 
-    // ---- work copy of S_hat with point blocks in bit-reversed order --------------------------
-    std::vector<int> order = bit_reversed_order(N);
     TRYC(dalloc_n(&A, (size_t)n * m, st));
-    TRYC(dalloc_n(&order_d, (size_t)N, st));
-    CUDAC(cudaMemcpyAsync(order_d, order.data(), N * 4, cudaMemcpyHostToDevice, st));
-    { gather_blocks_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(h->d_S, n, L, order_d, m, A); note_launch(); }
+    if (Kp > 0) {
+        // ---- SSRR moment scheme (Eqs. eq-malpha-qud, eq-hatM, eq-hatMS): M_hat = S_hat D Z ------
+        // Column block alpha is sum_i w_i zeta_i^alpha X_i with the trapezoid weights
+        // w_i = phi'(theta_i) / (i N) of (1 / 2 pi i) oint dz and zeta_i = (z_i - gamma) / rho,
+        // rho = max(a, b) (a change of polynomial basis: the same span as z_i^alpha, better scaled).
+        // D Z is block diagonal in the probe index, so it is one NL x K'L matrix and one ZGEMM.
+        std::vector<zd> z, dphi;
+        contour_nodes(h->C, N, &z, &dphi);
+        const zd gamma(h->C.gamma_re, h->C.gamma_im);
+        const double rho = std::max(h->C.a, h->C.b);
+        std::vector<c128> Wt((size_t)N * L * m, czero<double>());
+        for (int i = 0; i < N; ++i) {
+            const zd wi = dphi[i] / (zd(0.0, 1.0) * (double)N), zeta = (z[i] - gamma) / rho;
+            zd p = wi;
+            for (int al = 0; al < Kp; ++al, p *= zeta)
+                for (int l = 0; l < L; ++l) Wt[(size_t)(i * L + l) + (size_t)(al * L + l) * N * L] = fromstd(p);
+        }
+        TRYC(dalloc_n(&Z, Wt.size(), st));
+        CUDAC(cudaMemcpyAsync(Z, Wt.data(), Wt.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
+        Zgemm gm;
+        gm.opA = OP_N; gm.opB = OP_N; gm.M = (int)n; gm.N = m; gm.K = N * L;
+        gm.A = h->d_S; gm.lda = n; gm.B = Z; gm.ldb = N * L; gm.C = A; gm.ldc = n;
+        gm.ksplit = 1;
+        TRYC(zgemm(gm, st));
+        CUDAC(cudaStreamSynchronize(st));
+        dfree(Z, st);
+        Z = nullptr;
+    } else {
+        // ---- work copy of S_hat with point blocks in bit-reversed order --------------------------
+        std::vector<int> order = bit_reversed_order(N);
+        TRYC(dalloc_n(&order_d, (size_t)N, st));
+        CUDAC(cudaMemcpyAsync(order_d, order.data(), N * 4, cudaMemcpyHostToDevice, st));
+        { gather_blocks_kernel<<<(unsigned)ceil_div(n * m, 256), 256, 0, st>>>(h->d_S, n, L, order_d, m, A); note_launch(); }
+    }
     // reference size for the stopping rule: max column norm of S_hat (<= sigma_1)
     TRYC(dalloc_n(&colnrm, (size_t)m, st));
     column_norms(A, (int)n, m, n, colnrm, st);
@@ -563,6 +595,27 @@ int project_run(rsrr_nep h, double delta) {
         CUDAC(cudaMemcpyAsync(cols_d, idx.data(), kS * 4, cudaMemcpyHostToDevice, st));
         TRYC(dalloc_n(&Ybuf, (size_t)n * kS, st));
         { init_y_kernel<<<(unsigned)ceil_div(n * kS, 256), 256, 0, st>>>(Jm, kk, cols_d, kS, n, Ybuf); note_launch(); }
+        // J is a product of many thousands of plane rotations, and its columns drift from
+        // orthonormal by about sqrt(rotations) u each (1e-13 in the 2-norm after tens of sweeps
+        // over a few hundred columns).  One Newton-Schulz step, J <- J (I - E / 2) with
+        // E = J^H J - I, makes them orthonormal to O(|E|^2) and leaves span(J) unchanged.
+        TRYC(dalloc_n(&Eg, (size_t)kS * kS, st));
+        { identity_kernel<<<(unsigned)ceil_div((int64_t)kS * kS, 256), 256, 0, st>>>(Eg, kS); note_launch(); }
+        Zgemm ge;
+        ge.opA = OP_C; ge.opB = OP_N; ge.M = kS; ge.N = kS; ge.K = kk;
+        ge.beta = mk<double>(-1.0, 0.0);
+        ge.A = Ybuf; ge.lda = n; ge.B = Ybuf; ge.ldb = n; ge.C = Eg; ge.ldc = kS;
+        TRYC(zgemm(ge, st));
+        TRYC(dalloc_n(&Jn, (size_t)kk * kS, st));
+        CUDAC(cudaMemcpy2DAsync(Jn, (size_t)kk * sizeof(c128), Ybuf, (size_t)n * sizeof(c128), (size_t)kk * sizeof(c128),
+                                kS, cudaMemcpyDeviceToDevice, st));
+        Zgemm gn;
+        gn.M = kk; gn.N = kS; gn.K = kS;
+        gn.alpha = mk<double>(-0.5, 0.0); gn.beta = mk<double>(1.0, 0.0);
+        gn.A = Ybuf; gn.lda = n; gn.B = Eg; gn.ldb = kS; gn.C = Jn; gn.ldc = kk; gn.ksplit = 1;
+        TRYC(zgemm(gn, st));
+        CUDAC(cudaMemcpy2DAsync(Ybuf, (size_t)n * sizeof(c128), Jn, (size_t)kk * sizeof(c128), (size_t)kk * sizeof(c128),
+                                kS, cudaMemcpyDeviceToDevice, st));
         TRYC(dalloc_n(&Z, (size_t)kPB * kS, st));
         TRYC(dalloc_n(&Z2, (size_t)kPB * kS, st));
         for (int p = npan - 1; p >= 0; --p) {

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import workloads as w
-from gpu_util import match, open_nep
+from gpu_util import match, open_nep, rel_err_cols
 
 pytestmark = pytest.mark.gpu
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_pins.json")))
@@ -54,7 +54,7 @@ def check_projection(rs, prob, g, delta=1e-14):
     ref_S, ref_sig, ref_k = oracle.truncated_basis(g["Shat"], delta)
     S = g["S"]
     # S orthonormal, captures S_hat down to the truncation level, same rank up to near-ties
-    assert np.linalg.norm(S.conj().T @ S - np.eye(g["kS"])) < 1e-11
+    assert np.linalg.norm(S.conj().T @ S - np.eye(g["kS"])) < 1e-12
     resid = np.linalg.norm(g["Shat"] - S @ (S.conj().T @ g["Shat"]), 2)
     assert resid <= 20 * delta * ref_sig[0] + 1e-15 * np.linalg.norm(g["Shat"])
     assert abs(g["kS"] - ref_k) <= near_threshold(ref_sig, delta)
@@ -164,3 +164,111 @@ def test_hankel_singular_values_match_oracle(rs):
     assert g["info"]["n_winding"] == diag["n_winding"]
     assert abs(complex(g["info"]["winding_re"], g["info"]["winding_im"]) - diag["winding"]) < 1e-8
     assert ref["lam"].size == g["lam"].size
+
+
+def test_callback_function_kind_matches_builtin(rs):
+    """RSRR_F_CALLBACK: the same NEP with its z^2 (quadratic) and i sqrt(z) (planted sqrt) terms
+    supplied as host callbacks gives the built-in kinds' eigenvalues."""
+    import cmath
+    for name, K in (("tiny_qep", 4), ("planted_sqrt", 2)):
+        prob = w.by_name(name)
+        builtin = gpu_rsrr(rs, prob, K=K)
+        fns = []
+        for f in prob.fns:
+            if f.kind == w.FN_Z2:
+                fns.append(rs.callback_fn(lambda z: z * z, lambda z: 2 * z))
+            elif f.kind == w.FN_ISQRT_SHIFT and f.params()[1] == 0.0:
+                s = f.params()[0]
+                fns.append(rs.callback_fn(lambda z, s=s: 1j * cmath.sqrt(z - s),
+                                          lambda z, s=s: 0.5j / cmath.sqrt(z - s)))
+            else:
+                fns.append((f.kind, f.params()))
+        assert any(k == rs.F_CALLBACK for k, _ in fns)
+        h = rs.Nep(prob.n, prob.rowptr, prob.colind, prob.vals, fns)
+        h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12)
+        h.project(1e-14)
+        lam, V, res = h.solve(500, K, 1e3, 4096, True)
+        assert lam.size == builtin["lam"].size > 0
+        assert match(lam, builtin["lam"]) < 1e-12
+        h.close()
+
+
+@pytest.mark.parametrize("name,Kp", [("config0_linear", 32), ("config0_linear", 12), ("config0", 16)])
+def test_moment_scheme_matches_oracle(rs, name, Kp):
+    """rsrr_project_moments (SSRR moment scheme, Eqs. eq-malpha-qud, eq-hatMS) on the device
+    against the oracle's moment scheme on the same samples: the truncation of M_hat, the
+    projected matrices and the eigenvalues."""
+    prob = w.by_name(name)
+    h = open_nep(rs, prob)
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    Shat = h.samples()
+    kS = h.project_moments(Kp)
+    assert h.info()["proj_cols"] == Kp * prob.L
+    S, P, sig = h.basis(), h.projected(), h.sigma()
+    lam, V, res = h.solve(500, 2, 1e3, 4096, True)
+    h.close()
+    M = oracle.moment_matrix(prob, Shat, Kp)
+    ref_S, ref_sig, ref_k = oracle.truncated_basis(M, 1e-14)
+    assert abs(kS - ref_k) <= near_threshold(ref_sig, 1e-14)
+    assert np.linalg.norm(S.conj().T @ S - np.eye(kS)) < 1e-12
+    resid = np.linalg.norm(M - S @ (S.conj().T @ M), 2)
+    assert resid <= 20 * 1e-14 * ref_sig[0] + 1e-15 * np.linalg.norm(M)
+    top = ref_sig[ref_sig > 1e-6 * ref_sig[0]]
+    assert np.allclose(sig[:top.size], top, rtol=1e-9, atol=1e-13 * ref_sig[0])
+    assert np.allclose(P, oracle.project(prob, S), rtol=0, atol=1e-11 * np.abs(P).max())
+    ref = oracle.rsrr(prob, moments=Kp)
+    assert lam.size == ref["lam"].size > 0
+    assert match(lam, ref["lam"]) < 1e-9
+    if name == "config0_linear":
+        assert match(lam, exact_eigs(name, prob)) < 1e-9
+
+
+def interior_points(prob, N, seed=5, rmax=0.8):
+    rng = np.random.default_rng(seed)
+    r, ph = np.sqrt(rng.uniform(0, rmax, N)), rng.uniform(0, 2 * np.pi, N)
+    return prob.gamma + r * (prob.a * np.cos(ph) + 1j * prob.b * np.sin(ph))
+
+
+@pytest.mark.parametrize("name,prec", [("config0_linear", "fp64"), ("config0", "c64"), ("tiny_qep", "fp64")])
+def test_sample_points_matches_oracle(rs, name, prec):
+    """rsrr_sample_points (Section 3.2: sampling points anywhere in the domain): samples at interior
+    points equal the oracle's solves at the same points, and the eigenvalues inside the ellipse
+    equal the oracle's (and the closed form where there is one)."""
+    prob = w.by_name(name)
+    z = interior_points(prob, prob.N)
+    mode = rs.RSRR_FP64 if prec == "fp64" else rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL
+    h = open_nep(rs, prob)
+    h.sample_points(prob.gamma, prob.a, prob.b, z, prob.L, prob.U, mode, 1e-12 if prec == "fp64" else 1e-10, 20)
+    X = h.samples()
+    ref, infos, _ = oracle.sample(prob, z=z)
+    assert np.all(infos == 0)
+    assert rel_err_cols(X, ref).max() < 1e-8
+    with pytest.raises(rs.RsrrError) as e:
+        h.project_moments(4)
+    assert e.value.name == "EINVAL"
+    h.project(1e-14)
+    K = 4 if name == "tiny_qep" else 2
+    lam, V, res = h.solve(500, K, 1e3, 4096, True)
+    h.close()
+    refr = oracle.rsrr(prob, K=K, z=z)
+    assert lam.size == refr["lam"].size > 0
+    assert match(lam, refr["lam"]) < 1e-9
+    assert scaled(prob, lam, res).max() < 1e-10
+    if name in CLOSED:
+        assert match(lam, exact_eigs(name, prob)) < 1e-9
+
+
+def test_sample_points_at_contour_nodes_equals_sample(rs):
+    """With the contour's own trapezoid nodes, rsrr_sample_points gives rsrr_sample's samples."""
+    prob = w.config0()
+    h = open_nep(rs, prob)
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    X0 = h.samples()
+    th = 2 * np.pi * (np.arange(prob.N) + 0.5) / prob.N
+    z = prob.gamma + prob.a * np.cos(th) + 1j * prob.b * np.sin(th)
+    h.sample_points(prob.gamma, prob.a, prob.b, z, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    assert rel_err_cols(h.samples(), X0).max() < 1e-13
+    with pytest.raises(rs.RsrrError) as e:
+        h.sample_points(prob.gamma, prob.a, prob.b, np.array([np.nan]), prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    assert e.value.name == "EINVAL"
+    h.close()

@@ -252,3 +252,47 @@ def test_config3_member_count_and_perturbation_bound(s, idx):
     dist = np.min(np.abs(r["lam"][:, None] - mu[None, :]), axis=1)
     assert np.all(dist <= bound * (1 + 1e-6) + 1e-9)
     assert r["resid_scaled"].max() < 1e-10
+
+
+def test_moment_scheme_closed_form():
+    """SSRR moment scheme (Eqs. eq-malpha-qud, eq-hatM) on T = K - zI: with K' = N the moments span
+    the same space as the samples (Eq. eq-hatMS with Z invertible), and for K' = N and smaller K'
+    the eigenvalues are the closed-form Laplacian ones inside the circle."""
+    p = w.config0_linear(N=32, L=16)
+    h = 1.0 / 31
+    k = np.arange(1, 31)
+    lam1 = 4.0 / h ** 2 * np.sin(k * np.pi * h / 2) ** 2
+    mu = (lam1[:, None] + lam1[None, :]).ravel().astype(complex)
+    exact = mu[o.inside_contour(mu, p.gamma, p.a, p.b)]
+    samp = o.rsrr(p)
+    for Kp in (32, 12):
+        r = o.rsrr(p, moments=Kp)
+        assert r["lam"].size == exact.size == 22
+        assert match(r["lam"], exact) < 1e-9
+        if Kp == p.N:
+            assert r["k_S"] == samp["k_S"]
+        else:
+            assert r["k_S"] < samp["k_S"]
+
+
+def test_interior_sampling_points_closed_form():
+    """Sampling at points that are not the contour's nodes (Section 3.2: any points of the domain
+    serve, the ones inside the contour included): the samples solve T(z_j) X_j = U at the given
+    points, and the eigenvalues inside the ellipse are still the closed-form Laplacian ones."""
+    p = w.config0_linear(N=32, L=16)
+    assert [f.kind for f in p.fns] == [w.FN_CONST, w.FN_Z]
+    h = 1.0 / 31
+    lam1 = 4.0 / h ** 2 * np.sin(np.arange(1, 31) * np.pi * h / 2) ** 2
+    mu = (lam1[:, None] + lam1[None, :]).ravel().astype(complex)
+    exact = mu[o.inside_contour(mu, p.gamma, p.a, p.b)]
+    rng = np.random.default_rng(5)
+    r, ph = np.sqrt(rng.uniform(0, 0.8, 32)), rng.uniform(0, 2 * np.pi, 32)
+    z = p.gamma + r * (p.a * np.cos(ph) + 1j * p.b * np.sin(ph))
+    Shat, infos, eta = o.sample(p, z=z)
+    for j in (0, 7, 31):
+        T = p.term(0) + z[j] * p.term(1)
+        X = Shat[:, j * p.L:(j + 1) * p.L]
+        assert np.linalg.norm(T @ X - p.U) < 1e-12 * np.linalg.norm(p.U)
+    res = o.rsrr(p, z=z)
+    assert res["lam"].size == exact.size == 22
+    assert match(res["lam"], exact) < 1e-9
