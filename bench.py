@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="1", choices=sorted(WORKLOADS) + ["serve"],
+    ap.add_argument("--config", default="1", choices=sorted(WORKLOADS) + ["serve", "compare"],
                     help="1 = the benchmark workload; 0 and 2 the smaller and larger sqrt NEPs; serve = "
                          "Poisson request stream through the continuous-batching server")
     ap.add_argument("--precision", default=None, choices=["c64", "fp64"], help="default: the config's own")
@@ -162,9 +162,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    if args.config == "serve":
-        print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no oracle arm; the oracle "
-                                                              "arm times configs 0-2"}), flush=True)
+    if args.config in ("serve", "compare"):
+        print(json.dumps({"impl": "reference", "unavailable": "the serving stream and the scheme comparison have "
+                                                              "no oracle arm; the oracle arm times configs 0-3"}),
+              flush=True)
         return
     W = WORKLOADS[args.config]
     prob = workload(args.config, args.grid)
@@ -607,6 +608,44 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_compare(args):
+    """Sampling scheme against the SSRR moment scheme (K' = N and N/2) on the paper's two small
+    examples with its parameters: k_S, the singular value of the projection matrix at the
+    eigenvalue count, the count found and the largest eigen-residual ||T(l) v|| / ||v||."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_1510_07522_gb300 as rs
+    import workloads as w
+    torch.cuda.set_device(local)
+    cases = [("loaded_string", dict(n=5000, N=100, L=1), 1000, 8, 32),
+             ("acoustic_1d", dict(), 1000, 2, 40)]
+    out = []
+    for name, kw, NS, K, count in cases:
+        prob = w.by_name(name, **kw)
+        for Kp in (0, prob.N, prob.N // 2):
+            fns = [(f.kind, f.params()) for f in prob.fns]
+            h = rs.Nep(prob.n, prob.rowptr, prob.colind, prob.vals, fns)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+            kS = h.project_moments(Kp) if Kp else h.project(1e-14)
+            lam, V, res = h.solve(NS, K, 1e3, 4096, True)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t0)
+            sig = h.sigma()
+            h.close()
+            out.append({"problem": name, "n": prob.n, "N": prob.N, "L": prob.L,
+                        "scheme": "sampling" if Kp == 0 else "moments K'=%d" % Kp, "k_S": int(kS),
+                        "sigma_count_over_sigma1": float(sig[count - 1] / sig[0]) if sig.size >= count else 0.0,
+                        "eigenvalues": int(lam.size), "max_residual": float(res.max()) if res.size else None,
+                        "ms": round(ms, 1)})
+    print(json.dumps({"metric": "sampling vs moment scheme (k_S, sigma at the count, residuals)",
+                      "data": "the paper's loaded string and Acoustic-1D examples (printed matrices)",
+                      "results": out}), flush=True)
+
+
 def _pinned(torch, a):
     a = np.asarray(a)
     t = torch.empty(a.shape[::-1] if a.flags["F_CONTIGUOUS"] and not a.flags["C_CONTIGUOUS"] else a.shape,
@@ -628,6 +667,8 @@ def main():
         run_reference(args)
     elif args.config == "serve":
         run_serve(args)
+    elif args.config == "compare":
+        run_compare(args)
     elif args.config == "3":
         run_batch(args)
     else:

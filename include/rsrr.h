@@ -74,11 +74,24 @@ typedef struct {
     void* user;             /* passed to cb unchanged                                    */
 } rsrr_fn;
 
-/* Elliptic contour phi(t) = gamma + a cos t + i b sin t (Eq. eq-contour).  The N
- * sampling points are the trapezoid nodes t_j = 2 pi (j + 1/2) / N (Eq. eq-Ap-num). */
+/* The contour C enclosing the wanted eigenvalues, and the quadrature rule on it.
+ *   RSRR_CONTOUR_ELLIPSE    phi(t) = gamma + a cos t + i b sin t (Eq. eq-contour); N points at the
+ *                           trapezoid nodes t_j = 2 pi (j + 1/2) / N (Eq. eq-Ap-num).
+ *   RSRR_CONTOUR_RECTANGLE  the rectangle gamma + [-a, a] + i [-b, b], run counter-clockwise from
+ *                           its lower-left corner (bottom, right, top, left side), with a
+ *                           Gauss-Legendre rule on each side (Section 7.2, the gun example).  N is
+ *                           even; each horizontal side gets side_nodes points and each vertical
+ *                           side N/2 - side_nodes (the paper's "10-5" for N = 30 is side_nodes =
+ *                           10 when a > b).  side_nodes = 0 splits in proportion to the side
+ *                           lengths; rsrr_solve always splits its N_S points that way.
+ * A zero-initialised struct with gamma, a, b set is an ellipse. */
+#define RSRR_CONTOUR_ELLIPSE   0
+#define RSRR_CONTOUR_RECTANGLE 1
 typedef struct {
-    double gamma_re, gamma_im;  /* centre                                                */
-    double a, b;                /* semi-axes along re and im, both > 0                   */
+    double gamma_re, gamma_im;  /* centre                                                  */
+    double a, b;                /* semi-axes (ellipse) or half-sides (rectangle), both > 0  */
+    int32_t shape;              /* RSRR_CONTOUR_ELLIPSE or RSRR_CONTOUR_RECTANGLE           */
+    int32_t side_nodes;         /* rectangle: points per horizontal side (0 = proportional) */
 } rsrr_contour;
 
 /* precision of the sample solves (rsrr_sample) */
@@ -195,8 +208,11 @@ int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out)
  * (Eq. eq-gap, gaps over the whole SVD), A = V_0^H H^< W_0 Sigma_0^{-1} (Eq. eq-A), its
  * eigenpairs, lambda = rho lambda' + gamma, g (Eq. eq-eigens); then v = S g / ||S g||
  * (Algorithm 2 Step 5) and the residual ||T(lambda) v||_2 (||v|| = 1, Section 7.1).
- * Only eigenvalues strictly inside the ellipse are returned, sorted by |lambda|.
- *   N_S, K      quadrature points and Hankel block count (the paper: 500..1000, 2..8)
+ * The quadrature is the contour's rule with N_S points (trapezoid on an ellipse,
+ * Gauss-Legendre on a rectangle's sides, split in proportion to the side lengths).
+ * Only eigenvalues strictly inside the contour are returned, sorted by |lambda|.
+ *   N_S, K      quadrature points (even for a rectangle) and Hankel block count (the paper:
+ *               500..1000, 2..8)
  *   tol_gap     gap acceptance threshold (the paper: 1e3)
  *   cap         capacity of the output arrays
  *   lambda_reim [cap][2] eigenvalues

@@ -90,9 +90,47 @@ def contour_points(gamma, a, b, N):
     return z, dphi, theta
 
 
-def inside_contour(lam, gamma, a, b):
+def rectangle_split(N, a, b, side_nodes=0):
+    """Points per horizontal and per vertical side of a rectangle with N (even) points."""
+    half = N // 2
+    nh = side_nodes if side_nodes else int(np.floor(half * a / (a + b) + 0.5))
+    nh = min(max(nh, 1), half - 1)
+    return nh, half - nh
+
+
+def contour_rule(gamma, a, b, N, shape="ellipse", side_nodes=0):
+    """Nodes z_j and weights w_j with (1 / 2 pi i) oint g(z) dz ~ sum_j w_j g(z_j).
+
+    ellipse:   the trapezoid rule of Eq. eq-Ap-num, w_j = phi'(theta_j) / (i N).
+    rectangle: gamma + [-a, a] + i [-b, b] counter-clockwise from the lower-left corner
+               (bottom, right, top, left), an m-point Gauss-Legendre rule on each side
+               (Section 7.2, the gun example); on a side from P to Q, z = P + (Q - P)(t + 1)/2
+               and dz = (Q - P)/2 dt.
+    """
+    if shape == "ellipse":
+        z, dphi, _ = contour_points(gamma, a, b, N)
+        return z, dphi / (1j * N)
+    assert shape == "rectangle" and N % 2 == 0 and N >= 4
+    nh, nv = rectangle_split(N, a, b, side_nodes)
+    corners = [gamma - a - 1j * b, gamma + a - 1j * b, gamma + a + 1j * b, gamma - a + 1j * b]
+    zs, ws = [], []
+    for side in range(4):
+        P, Q = corners[side], corners[(side + 1) % 4]
+        t, om = np.polynomial.legendre.leggauss(nh if side % 2 == 0 else nv)
+        zs.append(P + (Q - P) * (t + 1) / 2)
+        ws.append(om * (Q - P) / 2 / (2j * np.pi))
+    return np.concatenate(zs), np.concatenate(ws)
+
+
+def inside_contour(lam, gamma, a, b, shape="ellipse"):
     w = np.asarray(lam) - gamma
+    if shape == "rectangle":
+        return (np.abs(w.real) < a) & (np.abs(w.imag) < b)
     return (w.real / a) ** 2 + (w.imag / b) ** 2 < 1.0
+
+
+def _shape(prob):
+    return getattr(prob, "shape", "ellipse"), getattr(prob, "side_nodes", 0)
 
 
 # ----------------------------------------------------------------------------------------
@@ -193,7 +231,8 @@ def sample(prob, points=None, threads=None, dense=False, z=None):
     column blocks).  Returns (S_hat [n, len(points) L], info per point, eta per column).
     """
     if z is None:
-        z, _, _ = contour_points(prob.gamma, prob.a, prob.b, prob.N)
+        shape, side_nodes = _shape(prob)
+        z, _ = contour_rule(prob.gamma, prob.a, prob.b, prob.N, shape, side_nodes)
     pts = list(range(len(z))) if points is None else list(points)
     F, _ = coefficients(prob.fns, z)
     kl, ku = bandwidths(prob)
@@ -234,9 +273,9 @@ def truncated_basis(Shat, delta=1e-14):
 # so span(M_hat) is the same, with better-scaled columns.
 # ----------------------------------------------------------------------------------------
 def moment_matrix(prob, Shat, Kp):
-    z, dphi, _ = contour_points(prob.gamma, prob.a, prob.b, prob.N)
+    shape, side_nodes = _shape(prob)
+    z, w = contour_rule(prob.gamma, prob.a, prob.b, prob.N, shape, side_nodes)
     rho = max(prob.a, prob.b)
-    w = dphi / (1j * prob.N)
     zeta = (z - prob.gamma) / rho
     L = prob.L
     M = np.zeros((prob.n, Kp * L), dtype=np.complex128, order="F")
@@ -260,17 +299,19 @@ def _reduced_T(P, Frow):
     return np.tensordot(Frow, P, axes=(0, 0))
 
 
-def reduced_ss(P, fns, gamma, a, b, N_S=500, K=2, tol_gap=1e3, return_diag=False):
+def reduced_ss(P, fns, gamma, a, b, N_S=500, K=2, tol_gap=1e3, return_diag=False, shape="ellipse"):
     """Returns (lam [nbar], g [k_S, nbar]) plus diagnostics if requested.
 
-    Step 2: moments A_alpha (Eq. eq-Ap-num, rho = max(a, b)) and H, H^< (Eq. eq-HH).
+    Step 2: moments A_alpha (Eq. eq-Ap-num, rho = max(a, b); on a rectangle the Gauss-Legendre
+            rule of contour_rule with N_S points split in proportion to the sides) and
+            H, H^< (Eq. eq-HH).
     Step 3: SVD of H (Eq. eq-svdH) and nbar from the winding number (Eq. eq-ncs) and the
             singular-value gap (Eq. eq-gap), combined as Section 4.3 suggests.
     Step 4: A = V_0^H H^< W_0 Sigma_0^{-1} (Eq. eq-A), eig, then Eq. eq-eigens.
     """
     k = P.shape[1]
     rho = max(a, b)
-    z, dphi, _ = contour_points(gamma, a, b, N_S)
+    z, wq = contour_rule(gamma, a, b, N_S, shape)
     F, dF = coefficients(fns, z)
     moments = np.zeros((2 * K, k, k), dtype=np.complex128)
     wind = 0.0 + 0.0j
@@ -278,12 +319,10 @@ def reduced_ss(P, fns, gamma, a, b, N_S=500, K=2, tol_gap=1e3, return_diag=False
         Ts = _reduced_T(P, F[j])
         Tinv = np.linalg.solve(Ts, np.eye(k))
         dTs = _reduced_T(P, dF[j])
-        wind += np.trace(Tinv @ dTs) * dphi[j]
+        wind += np.trace(Tinv @ dTs) * wq[j]
         w = (z[j] - gamma) / rho
         for al in range(2 * K):
-            moments[al] += (w ** al) * dphi[j] * Tinv
-    moments /= 1j * N_S
-    wind /= 1j * N_S
+            moments[al] += (w ** al) * wq[j] * Tinv
     H = np.block([[moments[r + c] for c in range(K)] for r in range(K)])
     Hl = np.block([[moments[r + c + 1] for c in range(K)] for r in range(K)])
     V, sig, Wh = np.linalg.svd(H)
@@ -355,9 +394,10 @@ def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False
     Shat, infos, eta = sample(prob, threads=threads, dense=dense, z=z)
     S, sigma, k_S = truncated_basis(moment_matrix(prob, Shat, moments) if moments else Shat, delta)
     P = project(prob, S)
+    shape, _ = _shape(prob)
     lam, g, diag = reduced_ss(P, prob.fns, prob.gamma, prob.a, prob.b, N_S, K, tol_gap,
-                              return_diag=True)
-    keep = inside_contour(lam, prob.gamma, prob.a, prob.b)
+                              return_diag=True, shape=shape)
+    keep = inside_contour(lam, prob.gamma, prob.a, prob.b, shape)
     lam, g = lam[keep], g[:, keep]
     order = np.argsort(np.abs(lam), kind="stable")
     lam, g = lam[order], g[:, order]

@@ -60,7 +60,15 @@ def callback_fn(f, df):
 
 class rsrr_contour(ctypes.Structure):
     _fields_ = [("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
-                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+                ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("shape", ctypes.c_int32), ("side_nodes", ctypes.c_int32)]
+
+
+RSRR_CONTOUR_ELLIPSE, RSRR_CONTOUR_RECTANGLE = 0, 1
+
+
+def _contour(gamma, a, b, shape=RSRR_CONTOUR_ELLIPSE, side_nodes=0):
+    return rsrr_contour(complex(gamma).real, complex(gamma).imag, float(a), float(b), int(shape), int(side_nodes))
 
 
 class rsrr_info(ctypes.Structure):
@@ -184,21 +192,22 @@ def rsrr_create_nep(n, rowptr, colind, vals, fns, flags=0, stream=None):
     return h
 
 
-def rsrr_sample(h, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
-    C = rsrr_contour(complex(gamma).real, complex(gamma).imag, float(a), float(b))
+def rsrr_sample(h, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10,
+                shape=RSRR_CONTOUR_ELLIPSE, side_nodes=0):
+    C = _contour(gamma, a, b, shape, side_nodes)
     Uc = None if U is None else _c128(U)
     _check(lib().rsrr_sample(h, ctypes.byref(C), int(N), int(L), _ptr(Uc), int(precision), float(tol),
                              int(max_refine)))
 
 
 def rsrr_sample_batch(handles, contours, Ns, Ls, Us=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
-    """rsrr_sample for several handles in one call (contours: list of (gamma, a, b))."""
+    """rsrr_sample for several handles in one call (contours: list of (gamma, a, b) or
+    (gamma, a, b, shape, side_nodes))."""
     count = len(handles)
     H = (ctypes.c_void_p * count)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     C = (rsrr_contour * count)()
-    for i, (gamma, a, b) in enumerate(contours):
-        C[i].gamma_re, C[i].gamma_im = complex(gamma).real, complex(gamma).imag
-        C[i].a, C[i].b = float(a), float(b)
+    for i, c in enumerate(contours):
+        C[i] = _contour(*c)
     Narr = (ctypes.c_int32 * count)(*[int(x) for x in Ns])
     Larr = (ctypes.c_int32 * count)(*[int(x) for x in Ls])
     keep = []
@@ -214,9 +223,10 @@ def rsrr_sample_batch(handles, contours, Ns, Ls, Us=None, precision=RSRR_FP64, t
     del keep
 
 
-def rsrr_sample_points(h, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
-    """rsrr_sample at the points z (complex array); (gamma, a, b) is the contour for rsrr_solve."""
-    C = rsrr_contour(complex(gamma).real, complex(gamma).imag, float(a), float(b))
+def rsrr_sample_points(h, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10,
+                       shape=RSRR_CONTOUR_ELLIPSE):
+    """rsrr_sample at the points z (complex array); (gamma, a, b, shape) is the contour for rsrr_solve."""
+    C = _contour(gamma, a, b, shape)
     zr = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
     Uc = None if U is None else _c128(U)
     _check(lib().rsrr_sample_points(h, ctypes.byref(C), int(zr.size), _ptr(zr), int(L), _ptr(Uc), int(precision),
@@ -283,18 +293,20 @@ class Nep:
         self._fns = list(fns)  # keeps RSRR_F_CALLBACK wrappers alive as long as the handle
         self.h = rsrr_create_nep(n, rowptr, colind, vals, self._fns, flags, stream)
 
-    def sample(self, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
+    def sample(self, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10,
+               shape=RSRR_CONTOUR_ELLIPSE, side_nodes=0):
         self.N, self.L = int(N), int(L)
-        rsrr_sample(self.h, gamma, a, b, N, L, U, precision, tol, max_refine)
+        rsrr_sample(self.h, gamma, a, b, N, L, U, precision, tol, max_refine, shape, side_nodes)
 
     def project(self, delta=1e-14):
         self.kS = rsrr_project(self.h, delta)
         return self.kS
 
-    def sample_points(self, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10):
-        """rsrr_sample_points: sample at the points z, keep (gamma, a, b) for rsrr_solve."""
+    def sample_points(self, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10,
+                      shape=RSRR_CONTOUR_ELLIPSE):
+        """rsrr_sample_points: sample at the points z, keep the contour for rsrr_solve."""
         self.N, self.L = int(np.asarray(z).size), int(L)
-        rsrr_sample_points(self.h, gamma, a, b, z, L, U, precision, tol, max_refine)
+        rsrr_sample_points(self.h, gamma, a, b, z, L, U, precision, tol, max_refine, shape)
 
     def project_moments(self, Kp, delta=1e-14):
         """The SSRR moment scheme: rsrr_project on K' quadrature moments of the samples."""

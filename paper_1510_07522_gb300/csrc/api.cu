@@ -144,13 +144,28 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
 }
 
 namespace {
-int check_sample_args(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, int32_t precision, double tol,
-                      int32_t max_refine) {
-    if (!h || !C) return set_error(RSRR_EINVAL, "NULL handle or contour");
-    if (N < 1 || N > 4096 || L < 1 || L > 256) return set_error(RSRR_EINVAL, "N or L out of range");
+// N < 0: the contour serves rsrr_solve only (its own N_S is checked there).
+int check_contour(const rsrr_contour* C, int32_t N) {
     if (!(C->a > 0) || !(C->b > 0) || !std::isfinite(C->gamma_re) || !std::isfinite(C->gamma_im) ||
         !std::isfinite(C->a) || !std::isfinite(C->b))
         return set_error(RSRR_EINVAL, "bad contour");
+    if (C->shape != RSRR_CONTOUR_ELLIPSE && C->shape != RSRR_CONTOUR_RECTANGLE)
+        return set_error(RSRR_EINVAL, "unknown contour shape");
+    if (C->shape == RSRR_CONTOUR_RECTANGLE) {
+        if (N >= 0 && (N < 4 || N % 2)) return set_error(RSRR_EINVAL, "a rectangle needs an even N >= 4");
+        if (C->side_nodes < 0 || (N >= 0 && C->side_nodes > N / 2 - 1))
+            return set_error(RSRR_EINVAL, "side_nodes must be in 0..N/2-1");
+    } else if (C->side_nodes != 0) {
+        return set_error(RSRR_EINVAL, "side_nodes is for rectangles only");
+    }
+    return RSRR_OK;
+}
+
+int check_sample_args(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, int32_t precision, double tol,
+                      int32_t max_refine, bool own_points = false) {
+    if (!h || !C) return set_error(RSRR_EINVAL, "NULL handle or contour");
+    if (N < 1 || N > 4096 || L < 1 || L > 256) return set_error(RSRR_EINVAL, "N or L out of range");
+    RSRR_TRY(check_contour(C, own_points ? -1 : N));
     const int mode = precision & 0xff;
     if ((mode != RSRR_FP64 && mode != RSRR_C64_IR) || (precision & ~(0xff | RSRR_REFINE_FULL)))
         return set_error(RSRR_EINVAL, "unknown precision or flag");
@@ -196,7 +211,7 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, const d
 
 int rsrr_sample_points(rsrr_nep h, const rsrr_contour* C, int32_t N, const double* z_reim, int32_t L,
                        const double* U_reim, int32_t precision, double tol, int32_t max_refine) {
-    RSRR_TRY(check_sample_args(h, C, N, L, precision, tol, max_refine));
+    RSRR_TRY(check_sample_args(h, C, N, L, precision, tol, max_refine, true));
     if (!z_reim) return set_error(RSRR_EINVAL, "rsrr_sample_points: NULL point array");
     std::vector<zd> pts(N);
     for (int32_t j = 0; j < N; ++j) {
@@ -274,6 +289,8 @@ int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, 
     if (N_S < 4 || N_S > 100000 || K < 1 || K > 64 || !(tol_gap > 1) || cap < 0 || !nC_out ||
         (cap > 0 && !lambda_reim))
         return set_error(RSRR_EINVAL, "bad rsrr_solve arguments");
+    if (h->C.shape == RSRR_CONTOUR_RECTANGLE && N_S % 2)
+        return set_error(RSRR_EINVAL, "a rectangular contour needs an even N_S");
     DeviceGuard g(h->device);
     Timer t(h);
     int rc = solve_run(h, N_S, K, tol_gap, cap, lambda_reim, V_reim, resid, nC_out);

@@ -107,15 +107,88 @@ void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv) {
     }
 }
 
-void contour_nodes(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* dphi) {
-    z->resize(N);
-    if (dphi) dphi->resize(N);
+// m-point Gauss-Legendre rule on [-1, 1], nodes increasing: Newton's method on P_m from the
+// asymptotic first guesses cos(pi (k + 3/4) / (m + 1/2)), P_m and P_m' by the three-term
+// recurrence; w_k = 2 / ((1 - x_k^2) P_m'(x_k)^2).
+void gauss_legendre(int m, std::vector<double>* x, std::vector<double>* w) {
+    x->assign(m, 0.0);
+    w->assign(m, 0.0);
     const double pi = 3.14159265358979323846;
-    for (int j = 0; j < N; ++j) {
-        double t = 2.0 * pi * (j + 0.5) / N;
-        (*z)[j] = zd(C.gamma_re + C.a * std::cos(t), C.gamma_im + C.b * std::sin(t));
-        if (dphi) (*dphi)[j] = zd(-C.a * std::sin(t), C.b * std::cos(t));
+    for (int k = 0; k < (m + 1) / 2; ++k) {
+        double t = std::cos(pi * (k + 0.75) / (m + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int j = 1; j < m; ++j) {
+                const double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            if (m == 1) { p1 = t; p0 = 1.0; }
+            dp = m * (t * p1 - p0) / (t * t - 1.0);
+            const double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) <= 4e-16 * std::fabs(t) + 1e-300) break;
+        }
+        // one more evaluation at the converged node for the weight
+        double p0 = 1.0, p1 = t;
+        for (int j = 1; j < m; ++j) {
+            const double p2 = ((2.0 * j + 1.0) * t * p1 - j * p0) / (j + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = (m == 1) ? 1.0 : m * (t * p1 - p0) / (t * t - 1.0);
+        const double wk = 2.0 / ((1.0 - t * t) * dp * dp);
+        (*x)[m - 1 - k] = t;
+        (*x)[k] = -t;
+        (*w)[m - 1 - k] = wk;
+        (*w)[k] = wk;
     }
+    if (m % 2 == 1) (*x)[m / 2] = 0.0;
+}
+
+void rectangle_split(const rsrr_contour& C, int N, int side_nodes, int* nh, int* nv) {
+    const int half = N / 2;
+    int h = side_nodes > 0 ? side_nodes : (int)std::lround(half * C.a / (C.a + C.b));
+    h = std::min(std::max(h, 1), half - 1);
+    *nh = h;
+    *nv = half - h;
+}
+
+void contour_rule(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* w, int side_nodes) {
+    z->resize(N);
+    if (w) w->resize(N);
+    const double pi = 3.14159265358979323846;
+    const zd gamma(C.gamma_re, C.gamma_im);
+    if (C.shape != RSRR_CONTOUR_RECTANGLE) {
+        // trapezoid rule in t on phi(t): (1 / 2 pi i) oint g dz ~ sum_j phi'(t_j) g(z_j) / (i N)
+        for (int j = 0; j < N; ++j) {
+            const double t = 2.0 * pi * (j + 0.5) / N;
+            (*z)[j] = gamma + zd(C.a * std::cos(t), C.b * std::sin(t));
+            if (w) (*w)[j] = zd(-C.a * std::sin(t), C.b * std::cos(t)) / (zd(0.0, 1.0) * (double)N);
+        }
+        return;
+    }
+    int nh = 0, nv = 0;
+    rectangle_split(C, N, side_nodes, &nh, &nv);
+    const zd corner[4] = {gamma + zd(-C.a, -C.b), gamma + zd(C.a, -C.b), gamma + zd(C.a, C.b),
+                          gamma + zd(-C.a, C.b)};
+    int j = 0;
+    for (int side = 0; side < 4; ++side) {
+        const zd P = corner[side], Q = corner[(side + 1) % 4], half = 0.5 * (Q - P);
+        std::vector<double> x, om;
+        gauss_legendre(side % 2 == 0 ? nh : nv, &x, &om);
+        for (size_t k = 0; k < x.size(); ++k, ++j) {
+            (*z)[j] = P + half * (x[k] + 1.0);
+            if (w) (*w)[j] = om[k] * half / zd(0.0, 2.0 * pi);
+        }
+    }
+}
+
+bool inside_contour(const rsrr_contour& C, zd z) {
+    const zd d = z - zd(C.gamma_re, C.gamma_im);
+    if (C.shape == RSRR_CONTOUR_RECTANGLE) return std::fabs(d.real()) < C.a && std::fabs(d.imag()) < C.b;
+    const double q = std::pow(d.real() / C.a, 2) + std::pow(d.imag() / C.b, 2);
+    return q < 1.0 && std::isfinite(q);
 }
 
 // ---- ordering --------------------------------------------------------------------------------

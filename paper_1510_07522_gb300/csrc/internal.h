@@ -16,7 +16,12 @@ int check_fn(const rsrr_fn& f);
 void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv);
 
 // ---- host: contour nodes (Eq. eq-contour, Eq. eq-Ap-num) --------------------------------
-void contour_nodes(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* dphi);
+// Nodes z_j and weights w_j of the contour's rule: (1 / 2 pi i) oint g(z) dz ~ sum_j w_j g(z_j).
+// side_nodes: points per horizontal side of a rectangle (0 = in proportion to the side lengths).
+void contour_rule(const rsrr_contour& C, int N, std::vector<zd>* z, std::vector<zd>* w, int side_nodes = 0);
+void gauss_legendre(int m, std::vector<double>* x, std::vector<double>* w);
+// strictly inside C (Algorithm 1 keeps only those eigenvalues)
+bool inside_contour(const rsrr_contour& C, zd z);
 
 // ---- host: band-reducing ordering ---------------------------------------------------------
 struct Ordering {

@@ -485,17 +485,18 @@ int project_run(rsrr_nep h, double delta) {
     TRYC(dalloc_n(&A, (size_t)n * m, st));
     if (Kp > 0) {
         // ---- SSRR moment scheme (Eqs. eq-malpha-qud, eq-hatM, eq-hatMS): M_hat = S_hat D Z ------
-        // Column block alpha is sum_i w_i zeta_i^alpha X_i with the trapezoid weights
-        // w_i = phi'(theta_i) / (i N) of (1 / 2 pi i) oint dz and zeta_i = (z_i - gamma) / rho,
-        // rho = max(a, b) (a change of polynomial basis: the same span as z_i^alpha, better scaled).
+        // Column block alpha is sum_i w_i zeta_i^alpha X_i with the contour rule's weights w_i of
+        // (1 / 2 pi i) oint dz (trapezoid on the ellipse: phi'(theta_i) / (i N); Gauss-Legendre on
+        // a rectangle's sides) and zeta_i = (z_i - gamma) / rho, rho = max(a, b) (a change of
+        // polynomial basis: the same span as z_i^alpha, better scaled).
         // D Z is block diagonal in the probe index, so it is one NL x K'L matrix and one ZGEMM.
-        std::vector<zd> z, dphi;
-        contour_nodes(h->C, N, &z, &dphi);
+        std::vector<zd> z, wq;
+        contour_rule(h->C, N, &z, &wq, h->C.side_nodes);
         const zd gamma(h->C.gamma_re, h->C.gamma_im);
         const double rho = std::max(h->C.a, h->C.b);
         std::vector<c128> Wt((size_t)N * L * m, czero<double>());
         for (int i = 0; i < N; ++i) {
-            const zd wi = dphi[i] / (zd(0.0, 1.0) * (double)N), zeta = (z[i] - gamma) / rho;
+            const zd wi = wq[i], zeta = (z[i] - gamma) / rho;
             zd p = wi;
             for (int al = 0; al < Kp; ++al, p *= zeta)
                 for (int l = 0; l < L; ++l) Wt[(size_t)(i * L + l) + (size_t)(al * L + l) * N * L] = fromstd(p);

@@ -337,8 +337,8 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     if (k <= 0) return RSRR_OK;
     const double rho = std::max(h->C.a, h->C.b);
     const zd gamma(h->C.gamma_re, h->C.gamma_im);
-    std::vector<zd> z, dphi;
-    contour_nodes(h->C, N_S, &z, &dphi);
+    std::vector<zd> z, wq;
+    contour_rule(h->C, N_S, &z, &wq);
     std::vector<c128> F((size_t)N_S * J), dF((size_t)N_S * J), Wt((size_t)N_S * 2 * K);
     for (int j = 0; j < N_S; ++j) {
         for (int i = 0; i < J; ++i) {
@@ -350,7 +350,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
             dF[(size_t)j * J + i] = fromstd(d);
         }
         const zd w = (z[j] - gamma) / rho;
-        zd p = dphi[j] / (zd(0, 1) * (double)N_S);
+        zd p = wq[j];
         for (int al = 0; al < 2 * K; ++al) {
             Wt[(size_t)j + (size_t)al * N_S] = fromstd(p);  // N_S x 2K, column al
             p *= w;
@@ -438,9 +438,8 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     for (int j = 0; j < N_S; ++j) {
         zd t = 0.0;
         for (int i = 0; i < J; ++i) t += tostd(dF[(size_t)j * J + i]) * tostd(htr[(size_t)j + (size_t)i * N_S]);
-        wind += t * dphi[j];
+        wind += t * wq[j];
     }
-    wind /= zd(0, 1) * (double)N_S;
     h->winding = wind;
     // ---- Hankel matrices and the SVD of H ------------------------------------------------------
     const int D = K * k;
@@ -607,13 +606,10 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     nbar = std::min(nbar, D);
     h->nbar = nbar;
     TRYC(extract(nbar));
-    // keep eigenvalues strictly inside the ellipse, sorted by |lambda|
+    // keep eigenvalues strictly inside the contour, sorted by |lambda|
     std::vector<int> keep;
-    for (int t = 0; t < nbar; ++t) {
-        const zd w = lam_h[t] - gamma;
-        const double q = std::pow(w.real() / h->C.a, 2) + std::pow(w.imag() / h->C.b, 2);
-        if (q < 1.0 && std::isfinite(q)) keep.push_back(t);
-    }
+    for (int t = 0; t < nbar; ++t)
+        if (inside_contour(h->C, lam_h[t])) keep.push_back(t);
     std::stable_sort(keep.begin(), keep.end(), [&](int x, int y) { return std::abs(lam_h[x]) < std::abs(lam_h[y]); });
     const int nk = (int)keep.size();
     *nC_out = nk;

@@ -511,7 +511,7 @@ int sample_prepare(rsrr_nep h, const double* U_reim, std::vector<c128>* Fout) {
     const int N = h->N, L = h->L, J = h->J;
     // coefficient table F[j][i] = f_i(z_j) (host FP64)
     std::vector<zd> z;
-    if (h->points.empty()) contour_nodes(h->C, N, &z, nullptr);
+    if (h->points.empty()) contour_rule(h->C, N, &z, nullptr, h->C.side_nodes);
     else z = h->points;
     std::vector<c128>& F = *Fout;
     F.assign((size_t)N * J, czero<double>());

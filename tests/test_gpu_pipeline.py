@@ -272,3 +272,97 @@ def test_sample_points_at_contour_nodes_equals_sample(rs):
         h.sample_points(prob.gamma, prob.a, prob.b, np.array([np.nan]), prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
     assert e.value.name == "EINVAL"
     h.close()
+
+
+def test_sampling_vs_moment_scheme_on_string(rs):
+    """The paper's comparison (Sections 3.1, 6.1) on the device: on the loaded string with K' = N
+    the device's M_hat is numerically rank deficient where S_hat is not, the truncation of each
+    matches the oracle's, and the moment scheme's eigenpairs are far less accurate."""
+    G = GOLD["loaded_string"]
+    prob = w.by_name("loaded_string", n=G["n"], N=G["N"], L=G["L"])
+    out = {}
+    for Kp in (0, G["N"]):
+        h = open_nep(rs, prob)
+        h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+        Shat = h.samples()
+        kS = h.project_moments(Kp) if Kp else h.project(1e-14)
+        sig = h.sigma()
+        lam, V, res = h.solve(G["N_S"], G["K"], 1e3, 4096, True)
+        h.close()
+        M = oracle.moment_matrix(prob, Shat, Kp) if Kp else Shat
+        _, ref_sig, ref_k = oracle.truncated_basis(M, 1e-14)
+        assert abs(kS - ref_k) <= near_threshold(ref_sig, 1e-14)
+        out[Kp] = (kS, sig, lam, scaled(prob, lam, res))
+    c = G["count"]
+    (k0, s0, l0, r0), (k1, s1, l1, r1) = out[0], out[G["N"]]
+    assert l0.size == l1.size == c
+    assert s0[c - 1] / s0[0] > 1e-4 and s1[c - 1] / s1[0] < 1e-9
+    assert k0 > k1
+    assert r0.max() < 1e-10 and r1.max() > 1e3 * r0.max()
+
+
+def sample_rect(rs, prob, h, precision=None, tol=1e-12):
+    precision = rs.RSRR_FP64 if precision is None else precision
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, precision, tol, 20,
+             shape=rs.RSRR_CONTOUR_RECTANGLE, side_nodes=prob.side_nodes)
+
+
+@pytest.mark.parametrize("linear", [True, False])
+def test_rectangle_contour_matches_oracle(rs, linear):
+    """Rectangle contour with Gauss-Legendre points ("10-5", Section 7.2): the samples at the
+    rule's nodes, the winding number, the eigenvalues (closed form for T = K - zI) and the
+    residuals against the oracle's run on the same rectangle."""
+    prob = w.config0_rect(linear=linear)
+    ref = oracle.rsrr(prob)
+    h = open_nep(rs, prob)
+    sample_rect(rs, prob, h)
+    X = h.samples()
+    assert rel_err_cols(X, ref["Shat"]).max() < 1e-8
+    h.project(1e-14)
+    lam, V, res = h.solve(500, 2, 1e3, 4096, True)
+    info = h.info()
+    h.close()
+    assert info["n_winding"] == ref["n_winding"] == 14
+    assert abs(complex(info["winding_re"], info["winding_im"]) - ref["winding"]) < 1e-7
+    assert lam.size == ref["lam"].size == 14
+    assert match(lam, ref["lam"]) < 1e-9
+    assert scaled(prob, lam, res).max() < 1e-10
+    if linear:
+        h_ = 1.0 / 31
+        l1 = 4 / h_ ** 2 * np.sin(np.arange(1, 31) * np.pi * h_ / 2) ** 2
+        mu = (l1[:, None] + l1[None, :]).ravel()
+        assert match(lam, mu[oracle.inside_contour(mu, prob.gamma, prob.a, prob.b, "rectangle")]) < 1e-9
+
+
+def test_rectangle_moments_and_argument_checks(rs):
+    """The moment scheme with the rectangle's Gauss-Legendre weights against the oracle, and
+    the argument checks of rectangular contours."""
+    prob = w.config0_rect(N=36, side_nodes=12)
+    h = open_nep(rs, prob)
+    sample_rect(rs, prob, h, rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL, 1e-10)
+    Shat = h.samples()
+    kS = h.project_moments(18)
+    S, P = h.basis(), h.projected()
+    lam, V, res = h.solve(500, 2, 1e3, 4096, True)
+    M = oracle.moment_matrix(prob, Shat, 18)
+    ref_S, ref_sig, ref_k = oracle.truncated_basis(M, 1e-14)
+    assert abs(kS - ref_k) <= near_threshold(ref_sig, 1e-14)
+    assert np.linalg.norm(M - S @ (S.conj().T @ M), 2) <= 20 * 1e-14 * ref_sig[0] + 1e-15 * np.linalg.norm(M)
+    ref = oracle.rsrr(prob, moments=18)
+    assert lam.size == ref["lam"].size == 14
+    assert match(lam, ref["lam"]) < 1e-9
+    for kw in (dict(N=31), dict(side_nodes=18), dict(side_nodes=-1)):
+        N = kw.get("N", prob.N)
+        with pytest.raises(rs.RsrrError) as e:
+            h.sample(prob.gamma, prob.a, prob.b, N, prob.L, prob.U[:, :prob.L], rs.RSRR_FP64, 1e-12, 12,
+                     shape=rs.RSRR_CONTOUR_RECTANGLE, side_nodes=kw.get("side_nodes", 0))
+        assert e.value.name == "EINVAL"
+    with pytest.raises(rs.RsrrError) as e:
+        h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12, shape=7)
+    assert e.value.name == "EINVAL"
+    sample_rect(rs, prob, h)
+    h.project(1e-14)
+    with pytest.raises(rs.RsrrError) as e:
+        h.solve(501, 2, 1e3, 4096, True)
+    assert e.value.name == "EINVAL"
+    h.close()

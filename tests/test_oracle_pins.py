@@ -296,3 +296,76 @@ def test_interior_sampling_points_closed_form():
     res = o.rsrr(p, z=z)
     assert res["lam"].size == exact.size == 22
     assert match(res["lam"], exact) < 1e-9
+
+
+def test_sampling_scheme_outranks_moment_scheme_on_string():
+    """Sections 3.1 and 6.1: with high-order moments M_hat becomes numerically rank deficient
+    while S_hat keeps a clear gap after the eigenvalue count.  On the loaded string (L = 1,
+    N = 100, the paper's contour, K' = N) the 32nd singular value of M_hat sits at the rounding
+    floor, that of S_hat two decades below sigma_1, and the moment scheme's eigenpairs are
+    orders of magnitude less accurate, as the paper's residual plots show."""
+    G = GOLD["loaded_string"]
+    p = w.by_name("loaded_string", n=G["n"], N=G["N"], L=G["L"])
+    r = o.rsrr(p, N_S=G["N_S"], K=G["K"])
+    rm = o.rsrr(p, N_S=G["N_S"], K=G["K"], moments=G["N"])
+    c = G["count"]
+    assert r["lam"].size == rm["lam"].size == c
+    assert r["sigma"][c - 1] / r["sigma"][0] > 1e-4
+    assert rm["sigma"][c - 1] / rm["sigma"][0] < 1e-9
+    assert r["k_S"] > rm["k_S"]
+    assert r["resid_scaled"].max() < 1e-10
+    assert rm["resid_scaled"].max() > 1e3 * r["resid_scaled"].max()
+
+
+def test_rectangle_rule():
+    """The rectangle's Gauss-Legendre rule (Section 7.2, the gun example): each side's m-point
+    rule integrates t^k exactly for k < 2m, so the contour integral of any polynomial of
+    degree < 2 min(m) vanishes; the Cauchy integral of 1/(z - c) is 1 inside, 0 outside
+    (counter-clockwise orientation); the paper's "10-5" split for N = 30."""
+    for m in (1, 5, 10, 51):
+        t, om = np.polynomial.legendre.leggauss(m)
+        for k in range(2 * m):
+            assert abs(om @ t ** k - (2.0 / (k + 1) if k % 2 == 0 else 0.0)) < 1e-14
+    g, a, b = 237.7 + 20j, 97.7, 25.0
+    assert o.rectangle_split(30, a, b, 10) == (10, 5)
+    assert o.rectangle_split(36, a, b, 12) == (12, 6)
+    assert o.rectangle_split(500, a, b) == (199, 51)
+    z, wq = o.contour_rule(g, a, b, 30, "rectangle", 10)
+    d = z - g
+    on_side = np.minimum(np.abs(np.abs(d.real) - a), np.abs(np.abs(d.imag) - b))
+    assert z.size == 30 and on_side.max() < 1e-12 * a
+    assert np.allclose(z[:10].imag, g.imag - b) and np.all(np.diff(z[:10].real) > 0)  # bottom, left to right
+    u = (z - g) / a
+    for k in range(10):
+        assert abs(wq @ u ** k) < 1e-13
+    z, wq = o.contour_rule(g, a, b, 400, "rectangle")
+    for c, want in ((g, 1.0), (g + 50 - 10j, 1.0), (g + 150, 0.0), (g + 60j, 0.0)):
+        assert abs(wq @ (1.0 / (z - c)) - want) < 1e-10
+    # the ellipse's rule is the trapezoid one of Eq. eq-Ap-num
+    z, wq = o.contour_rule(1 + 2j, 3.0, 0.5, 256)
+    ze, dphi, _ = o.contour_points(1 + 2j, 3.0, 0.5, 256)
+    assert np.allclose(z, ze) and np.allclose(wq, dphi / (256j))
+    assert abs(wq @ (1.0 / (z - (1.5 + 2.1j))) - 1) < 1e-12
+
+
+def test_rectangle_contour_closed_form():
+    """RSRR with the rectangle contour and Gauss-Legendre sampling points: on T = K - zI the
+    eigenvalues inside the rectangle are the closed-form Laplacian ones, the winding number
+    counts them, and on the gun-like NEP the rectangle finds the same eigenvalues as the
+    ellipse run inside the rectangle."""
+    p = w.config0_rect(linear=True)
+    h = 1.0 / 31
+    lam1 = 4.0 / h ** 2 * np.sin(np.arange(1, 31) * np.pi * h / 2) ** 2
+    mu = (lam1[:, None] + lam1[None, :]).ravel().astype(complex)
+    exact = mu[o.inside_contour(mu, p.gamma, p.a, p.b, "rectangle")]
+    r = o.rsrr(p)
+    assert r["lam"].size == exact.size == 14
+    assert r["n_winding"] == 14 and abs(r["winding"] - 14) < 1e-6
+    assert match(r["lam"], exact) < 1e-9
+    q = w.config0_rect()
+    rq = o.rsrr(q)
+    re = o.rsrr(w.config0())
+    ref = re["lam"][o.inside_contour(re["lam"], q.gamma, q.a, q.b, "rectangle")]
+    assert rq["lam"].size == ref.size == 14
+    assert match(rq["lam"], ref) < 1e-9
+    assert rq["resid_scaled"].max() < 1e-10

@@ -54,6 +54,8 @@ class Problem:
     U: np.ndarray               # complex128 [n, L] (Fortran order)
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    shape: str = "ellipse"      # or "rectangle": gamma + [-a, a] + i [-b, b]
+    side_nodes: int = 0         # rectangle: sampling points per horizontal side (0 = proportional)
 
     @property
     def J(self) -> int:
@@ -154,6 +156,18 @@ def config0_linear(N=32, L=16, nx=30, ny=30):
     """config0 without the masks: T(z) = K - z I, eigenvalues in closed form."""
     return _gun_like("config0_linear", nx, ny, 1.0 / (nx + 1), 1.0 / (ny + 1), 250.0, 150.0,
                      N, L, with_masks=False)
+
+
+def config0_rect(N=30, L=4, side_nodes=10, linear=False):
+    """config0's NEP (or its linear part) with the paper's gun-example contour shape: a
+    rectangle of 195.4 x 50 (lower-left 140 - 5i, upper-right 335.4 + 45i; shifted 5 below
+    the real axis, which the eigenvalues here lie just above) with N Gauss-Legendre points,
+    side_nodes on each long side ("10-5" for N = 30)."""
+    p = config0_linear(N=N, L=L) if linear else config0(N=N, L=L)
+    p.name = "config0_rect_linear" if linear else "config0_rect"
+    p.gamma, p.a, p.b = complex(237.7, 20.0), 97.7, 25.0
+    p.shape, p.side_nodes = "rectangle", int(side_nodes)
+    return p
 
 
 def config2(N=64, L=48, nx=400, ny=250, gamma=330.0, radius=300.0):
@@ -380,5 +394,5 @@ def by_name(name: str, **kw) -> Problem:
     table = dict(config0=config0, config0_linear=config0_linear, config1=config1,
                  config1b=config1b, config2=config2, planted_sqrt=planted_sqrt,
                  planted_delay=planted_delay, tiny_qep=tiny_qep, loaded_string=loaded_string,
-                 acoustic_1d=acoustic_1d)
+                 acoustic_1d=acoustic_1d, config0_rect=config0_rect)
     return table[name](**kw)
