@@ -56,7 +56,10 @@ typedef enum {
                                [p0, +inf) (gun-type problems, Section 7.2)               */
     RSRR_F_EXP_DELAY = 4,   /* f = exp(-p0 z)                                            */
     RSRR_F_RATIONAL = 5,    /* f = p0 z / (z + p1)  (Biot / loaded-string terms)         */
-    RSRR_F_CALLBACK = 6     /* f and f' from the caller's function `cb` (any analytic f) */
+    RSRR_F_CALLBACK = 6,    /* f and f' from the caller's function `cb` (any analytic f) */
+    RSRR_F_CHEBYSHEV = 7    /* f = tau_m((2z - p1 - p2) / (p2 - p1)), the Chebyshev polynomial
+                               of the first kind of degree m = p0 (an integer, 0..1024) on the
+                               interval [p1, p2], p1 < p2 (Section 6.2, Eq. eq-T-interp)   */
 } rsrr_fkind;
 
 /* Caller-supplied scalar function (RSRR_F_CALLBACK): for k < m, write f(z_k) and f'(z_k) to
@@ -201,6 +204,25 @@ int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out);
  * Errors: as rsrr_project; EINVAL for K' outside 1..N. */
 int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out);
 
+/* ---- rsrr_project_chebyshev ------------------------------------------------------------
+ * rsrr_project (Step 3: S from the truncated SVD), then the reduced NEP is replaced by its
+ * Chebyshev interpolant of degree d on the real interval [x_lo, x_hi] (Section 6.2,
+ * Eqs. eq-T-interp, eq-Ts-interp, eq-Ts-coefs):
+ *   x_k = c + r cos(theta_k), theta_k = (k + 1/2) pi / (d + 1), k = 0..d, c, r the interval's
+ *   centre and half-width;  P_hat_j = (2 / (d + 1)) sum_k [S^H T(x_k) S] cos(j theta_k), with
+ *   P_hat_0 halved (the standard first-kind interpolant: it reproduces every polynomial of
+ *   degree <= d);  T_S(z) ~ sum_j P_hat_j tau_j((z - c) / r).
+ * rsrr_solve then runs Algorithm 1 on this polynomial NEP; its residuals ||T(lambda) v|| are
+ * still those of the true T.  rsrr_get_projected returns the d + 1 matrices P_hat_j and
+ * rsrr_info.red_terms is d + 1.  Useful when T is costly to project term by term (a BEM
+ * matrix) or has many terms; the interpolation error decays exponentially in d when T is
+ * holomorphic near the interval.
+ *   d           degree, 0 <= d <= 256
+ *   x_lo, x_hi  the interval, x_lo < x_hi (typically the contour's extent on the real axis)
+ * Errors: as rsrr_project; EINVAL for bad d or interval, ENONFINITE if some f_i is not
+ *         finite at a Chebyshev point. */
+int rsrr_project_chebyshev(rsrr_nep h, int32_t d, double x_lo, double x_hi, double delta, int32_t* k_S_out);
+
 /* ---- rsrr_solve -----------------------------------------------------------------------
  * Algorithm 1 on T_S(z) = sum_i f_i(z) P_i with the same contour as rsrr_sample:
  * moments A_alpha (Eq. eq-Ap-num, rho = max(a, b)), block Hankel H, H^< (Eq. eq-HH),
@@ -252,6 +274,8 @@ typedef struct {
     double ms_zgemm;            /* device time of the FP64 complex GEMMs of the last project + solve */
     double zgemm_gflop;         /* their algorithmic work, 8 M N K per product, in GFLOP          */
     int32_t dense_lu;           /* 1 if the last rsrr_sample factored with the dense LU            */
+    int32_t red_terms;          /* terms of the reduced NEP: J, or d + 1 after
+                                   rsrr_project_chebyshev                                   */
     int32_t proj_cols;          /* columns of the matrix the last projection factored: N*L
                                    (rsrr_project) or K'*L (rsrr_project_moments)                 */
 } rsrr_info;

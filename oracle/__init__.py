@@ -9,5 +9,5 @@ from .rsrr_oracle import (  # noqa: F401
     coefficients, contour_points, assemble_dense, assemble_band, band_lu, band_solve,
     dense_lu, dense_solve, sample, backward_error, truncated_basis, numerical_rank,
     project, reduced_ss, backmap, eigen_residuals, inside_contour, rsrr, moment_matrix,
-    contour_rule, rectangle_split,
+    contour_rule, rectangle_split, chebyshev_reduce,
 )

@@ -76,6 +76,13 @@ def coefficients(fns, z):
         elif k == 5:
             F[..., i] = p[0] * z / (z + p[1])
             dF[..., i] = p[0] * p[1] / (z + p[1]) ** 2
+        elif k == 7:                   # Chebyshev polynomial tau_m on [p1, p2] (numpy's chebval)
+            m, lo, hi = int(p[0]), p[1], p[2]
+            e = np.zeros(m + 1)
+            e[m] = 1.0
+            x = (2.0 * z - (lo + hi)) / (hi - lo)
+            F[..., i] = np.polynomial.chebyshev.chebval(x, e)
+            dF[..., i] = np.polynomial.chebyshev.chebval(x, np.polynomial.chebyshev.chebder(e)) * 2.0 / (hi - lo)
         else:
             raise ValueError(f"unknown function kind {k}")
     return F, dF
@@ -286,6 +293,43 @@ def moment_matrix(prob, Shat, Kp):
 
 
 # ----------------------------------------------------------------------------------------
+# Section 6.2 (Eqs. eq-T-interp, eq-T-coefs, eq-Ts-interp, eq-Ts-coefs): the reduced NEP as a
+# Chebyshev interpolant of degree d on the real interval [lo, hi].  The paper states the rule
+# on [-1, 1]; x = c + r t maps it (c, r the centre and half-width).  Its coefficient formula
+# read literally doubles the constant term; the first-kind interpolant takes half of it for
+# j = 0 (the reading that reproduces polynomials of degree <= d exactly).
+# ----------------------------------------------------------------------------------------
+def chebyshev_reduce(prob, S, d, lo, hi):
+    """Returns (P_hat [d+1, k, k], fns): T_S(z) ~ sum_j P_hat_j tau_j((2z - lo - hi)/(hi - lo))."""
+    m = d + 1
+    c, r = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    theta = (np.arange(m) + 0.5) * np.pi / m
+    x = c + r * np.cos(theta)
+    F, _ = coefficients(prob.fns, x)
+    Q = []
+    for k in range(m):
+        Tk = sum(F[k, i] * prob.term(i) for i in range(prob.J))
+        Q.append(S.conj().T @ (Tk @ S))
+    Phat = np.zeros((m,) + Q[0].shape, dtype=np.complex128)
+    for j in range(m):
+        for k in range(m):
+            Phat[j] += (2.0 / m) * np.cos(j * theta[k]) * Q[k]
+    Phat[0] *= 0.5
+    fns = [_Fn(7, (float(j), float(lo), float(hi))) for j in range(m)]
+    return Phat, fns
+
+
+class _Fn:
+    """A function descriptor of the reduced NEP (kind and parameters, as in the workloads)."""
+    def __init__(self, kind, p):
+        self.kind, self.p = kind, tuple(p)
+
+    def params(self):
+        q = list(self.p) + [0.0] * 4
+        return [float(v) for v in q[:4]]
+
+
+# ----------------------------------------------------------------------------------------
 # Algorithm 2, Step 4 (first half), Eq. eq-Zs-expr: P_i = S^H A_i S.
 # ----------------------------------------------------------------------------------------
 def project(prob, S):
@@ -385,17 +429,22 @@ def eigen_residuals(prob, lam, V):
     return np.array(raw), np.array(scaled)
 
 
-def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False, moments=0, z=None):
+def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False, moments=0, z=None,
+         chebyshev=None):
     """Algorithm 2 end to end; eigenvalues strictly inside the ellipse, sorted by |lam|.
     moments = K' > 0: the SSRR moment scheme (Step 3 on M_hat of K' moments instead of S_hat).
     z: sampling points other than the contour's nodes (Section 3.2 allows any points in the
-    domain; the ellipse still bounds Algorithm 1)."""
+    domain; the ellipse still bounds Algorithm 1).
+    chebyshev = (d, lo, hi): the reduced NEP as its Chebyshev interpolant (Section 6.2)."""
     assert not (moments and z is not None), "the moment scheme needs the contour's nodes"
     Shat, infos, eta = sample(prob, threads=threads, dense=dense, z=z)
     S, sigma, k_S = truncated_basis(moment_matrix(prob, Shat, moments) if moments else Shat, delta)
-    P = project(prob, S)
+    if chebyshev is None:
+        P, rfns = project(prob, S), prob.fns
+    else:
+        P, rfns = chebyshev_reduce(prob, S, *chebyshev)
     shape, _ = _shape(prob)
-    lam, g, diag = reduced_ss(P, prob.fns, prob.gamma, prob.a, prob.b, N_S, K, tol_gap,
+    lam, g, diag = reduced_ss(P, rfns, prob.gamma, prob.a, prob.b, N_S, K, tol_gap,
                               return_diag=True, shape=shape)
     keep = inside_contour(lam, prob.gamma, prob.a, prob.b, shape)
     lam, g = lam[keep], g[:, keep]

@@ -25,7 +25,7 @@ RSRR_REFINE_FULL = 0x100
 RSRR_NATURAL_ORDER = 0x1
 RSRR_DENSE_LU = 0x2
 
-F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL, F_CALLBACK = range(7)
+F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL, F_CALLBACK, F_CHEBYSHEV = range(8)
 
 
 class RsrrError(RuntimeError):
@@ -91,7 +91,7 @@ class rsrr_info(ctypes.Structure):
                 ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
                 ("ms_solve_extract", ctypes.c_double), ("ms_zgemm", ctypes.c_double),
                 ("zgemm_gflop", ctypes.c_double), ("dense_lu", ctypes.c_int32),
-                ("proj_cols", ctypes.c_int32)]
+                ("red_terms", ctypes.c_int32), ("proj_cols", ctypes.c_int32)]
 
 
 _lib = None
@@ -99,7 +99,7 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
-           "rsrr_project_moments", "rsrr_sample_points"]
+           "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev"]
 
 
 def lib():
@@ -131,6 +131,7 @@ def lib():
         "rsrr_band_solve_noalloc": ([I64, I32, I32, P, I32, P, P], ctypes.c_int),
         "rsrr_sample_batch": ([P, I32, P, P, P, P, I32, D, I32], ctypes.c_int),
         "rsrr_project_moments": ([P, I32, D, P], ctypes.c_int),
+        "rsrr_project_chebyshev": ([P, I32, D, D, D, P], ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -233,6 +234,12 @@ def rsrr_sample_points(h, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e
                                     float(tol), int(max_refine)))
 
 
+def rsrr_project_chebyshev(h, d, x_lo, x_hi, delta=1e-14):
+    k = ctypes.c_int32()
+    _check(lib().rsrr_project_chebyshev(h, int(d), float(x_lo), float(x_hi), float(delta), ctypes.byref(k)))
+    return k.value
+
+
 def rsrr_project_moments(h, Kp, delta=1e-14):
     k = ctypes.c_int32()
     _check(lib().rsrr_project_moments(h, int(Kp), float(delta), ctypes.byref(k)))
@@ -313,6 +320,11 @@ class Nep:
         self.kS = rsrr_project_moments(self.h, Kp, delta)
         return self.kS
 
+    def project_chebyshev(self, d, x_lo, x_hi, delta=1e-14):
+        """rsrr_project, then the reduced NEP as its degree-d Chebyshev interpolant on [x_lo, x_hi]."""
+        self.kS = rsrr_project_chebyshev(self.h, d, x_lo, x_hi, delta)
+        return self.kS
+
     def solve(self, N_S=500, K=2, tol_gap=1e3, cap=4096, vectors=True):
         return rsrr_solve(self.h, N_S, K, tol_gap, cap, self.n, vectors)
 
@@ -341,7 +353,7 @@ class Nep:
         return out
 
     def projected(self):
-        out = np.zeros((self.J, self.kS, self.kS), dtype=np.complex128)
+        out = np.zeros((self.info()["red_terms"], self.kS, self.kS), dtype=np.complex128)
         _check(lib().rsrr_get_projected(self.h, _ptr(out)))
         # stored column-major per term
         return np.ascontiguousarray(np.transpose(out, (0, 2, 1)))

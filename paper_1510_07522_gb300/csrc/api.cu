@@ -10,6 +10,7 @@ namespace rsrr {
 int sample_run(rsrr_nep h, const double* U_reim, int max_refine);
 int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const double*>& U, int max_refine);
 int project_run(rsrr_nep h, double delta);
+int chebyshev_reduce(rsrr_nep h, int d, double lo, double hi);
 int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambda_reim, double* V_reim,
               double* resid, int32_t* nC_out);
 
@@ -261,6 +262,7 @@ int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out) {
     if (!h->sampled) return set_error(RSRR_EORDER, "rsrr_project needs a successful rsrr_sample");
     if (!(delta >= 0) || !(delta < 1)) return set_error(RSRR_EINVAL, "delta must be in [0, 1)");
     DeviceGuard g(h->device);
+    h->projected = false;
     Timer t(h);
     int rc = project_run(h, delta);
     h->ms_project = t.stop();
@@ -268,6 +270,17 @@ int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out) {
     h->projected = true;
     if (k_S_out) *k_S_out = h->kS;
     return RSRR_OK;
+}
+
+int rsrr_project_chebyshev(rsrr_nep h, int32_t d, double x_lo, double x_hi, double delta, int32_t* k_S_out) {
+    if (!h) return set_error(RSRR_EINVAL, "NULL handle");
+    if (d < 0 || d > 256 || !std::isfinite(x_lo) || !std::isfinite(x_hi) || !(x_lo < x_hi))
+        return set_error(RSRR_EINVAL, "Chebyshev degree must be in 0..256 and x_lo < x_hi");
+    RSRR_TRY(rsrr_project(h, delta, k_S_out));
+    DeviceGuard g(h->device);
+    const int rc = chebyshev_reduce(h, d, x_lo, x_hi);
+    if (rc != RSRR_OK) h->projected = false;
+    return rc;
 }
 
 int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out) {
@@ -340,6 +353,7 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->zgemm_gflop = (h->zgemm_flops_project + h->zgemm_flops_solve) * 1e-9;
     o->dense_lu = h->dense_used ? 1 : 0;
     o->proj_cols = h->proj_cols;
+    o->red_terms = h->red_J;
     return RSRR_OK;
 }
 
@@ -399,7 +413,7 @@ int rsrr_get_projected(rsrr_nep h, double* out_reim) {
     if (!h || !out_reim) return set_error(RSRR_EINVAL, "NULL argument");
     if (!h->projected) return set_error(RSRR_EORDER, "no projection");
     DeviceGuard g(h->device);
-    const size_t cnt = (size_t)h->J * h->kS * h->kS;
+    const size_t cnt = (size_t)h->red_J * h->kS * h->kS;
     if (cnt) RSRR_CUDA(cudaMemcpy(out_reim, h->d_P, cnt * sizeof(c128), cudaMemcpyDeviceToHost));
     return RSRR_OK;
 }

@@ -56,13 +56,16 @@ void dfree(void* p, cudaStream_t s) {
 
 // ---- scalar functions ----------------------------------------------------------------------
 int check_fn(const rsrr_fn& f) {
-    if (f.kind < RSRR_F_CONST || f.kind > RSRR_F_CALLBACK)
+    if (f.kind < RSRR_F_CONST || f.kind > RSRR_F_CHEBYSHEV)
         return set_error(RSRR_EINVAL, "unknown function kind " + std::to_string(f.kind));
     if (f.kind == RSRR_F_CALLBACK && !f.cb) return set_error(RSRR_EINVAL, "RSRR_F_CALLBACK without a function");
     for (double v : f.p)
         if (!std::isfinite(v)) return set_error(RSRR_ENONFINITE, "non-finite function parameter");
     if (f.kind == RSRR_F_ISQRT_SHIFT && f.p[1] != 0.0 && f.p[1] != 1.0)
         return set_error(RSRR_EINVAL, "sqrt branch flag must be 0 or 1");
+    if (f.kind == RSRR_F_CHEBYSHEV &&
+        (f.p[0] < 0 || f.p[0] > 1024 || f.p[0] != std::floor(f.p[0]) || !(f.p[1] < f.p[2])))
+        return set_error(RSRR_EINVAL, "Chebyshev kind needs an integer degree 0..1024 and p1 < p2");
     return RSRR_OK;
 }
 
@@ -101,6 +104,22 @@ void eval_fn(const rsrr_fn& f, zd z, zd* val, zd* deriv) {
             f.cb(f.user, 1, zr, fr, dr);
             *val = zd(fr[0], fr[1]);
             *deriv = zd(dr[0], dr[1]);
+            break;
+        }
+        case RSRR_F_CHEBYSHEV: {
+            // three-term recurrences tau_{k+1} = 2x tau_k - tau_{k-1} and, differentiated,
+            // tau'_{k+1} = 2 tau_k + 2x tau'_k - tau'_{k-1}, at x = (2z - p1 - p2) / (p2 - p1)
+            const int m = (int)f.p[0];
+            const double w = f.p[2] - f.p[1];
+            const zd x = (2.0 * z - (f.p[1] + f.p[2])) / w;
+            zd t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
+            if (m == 0) { *val = 1.0; *deriv = 0.0; break; }
+            for (int k = 1; k < m; ++k) {
+                const zd t2 = 2.0 * x * t1 - t0, d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
+                t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+            }
+            *val = t1;
+            *deriv = d1 * (2.0 / w);
             break;
         }
         default: *val = 0.0; *deriv = 0.0;

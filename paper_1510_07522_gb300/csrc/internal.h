@@ -80,7 +80,9 @@ struct rsrr_nep_s {
     bool projected = false;
     int32_t kS = -1;
     rsrr::c128* d_Q = nullptr;     // [kS][n] orthonormal basis S (permuted rows)
-    rsrr::c128* d_P = nullptr;     // [J][kS][kS]
+    rsrr::c128* d_P = nullptr;     // [red_J][kS][kS]
+    std::vector<rsrr_fn> red_fns;  // functions of the reduced NEP T_S(z) = sum_i red_fns[i](z) P_i:
+    int32_t red_J = 0;             // fns (rsrr_project) or Chebyshev polynomials (rsrr_project_chebyshev)
     std::vector<double> sigma;     // singular values of S_hat
 
     // reduced solve state

@@ -455,6 +455,8 @@ int project_run(rsrr_nep h, double delta) {
     dfree(h->d_P, st);
     h->d_Q = nullptr;
     h->d_P = nullptr;
+    h->red_fns = h->fns;  // the reduced NEP keeps T's own functions: P_i = S^H A_i S
+    h->red_J = J;
 
     c128 *A = nullptr, *V = nullptr, *W = nullptr, *W2 = nullptr, *tau = nullptr, *Tall = nullptr,
          *alpha = nullptr, *part2 = nullptr, *part3 = nullptr, *Yb = nullptr, *B = nullptr, *Jm = nullptr,
@@ -657,6 +659,64 @@ int project_run(rsrr_nep h, double delta) {
     cleanup();
 #undef TRYC
 #undef CUDAC
+    return RSRR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Section 6.2 (Eqs. eq-T-interp, eq-Ts-interp, eq-Ts-coefs): the reduced NEP replaced by its
+// degree-d Chebyshev interpolant on [lo, hi].  With T = sum_i f_i A_i, S^H T(x_k) S is
+// sum_i f_i(x_k) P_i, so P_hat_j = sum_i W[i][j] P_i with W[i][j] = sum_k f_i(x_k) c_kj and
+// c_kj = (2 / (d + 1)) cos(j theta_k) (halved for j = 0): one ZGEMM of the k_S^2 x J matrix of
+// the P_i against the J x (d + 1) matrix W.
+// ---------------------------------------------------------------------------------------------
+int chebyshev_reduce(rsrr_nep h, int d, double lo, double hi) {
+    cudaStream_t st = h->stream;
+    const int J = h->J, k = h->kS, m = d + 1;
+    const double pi = 3.14159265358979323846, c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+    std::vector<zd> W((size_t)J * m, zd(0.0, 0.0));
+    for (int kx = 0; kx < m; ++kx) {
+        const double th = (kx + 0.5) * pi / m, x = c + r * std::cos(th);
+        for (int i = 0; i < J; ++i) {
+            zd f, df;
+            eval_fn(h->fns[i], zd(x, 0.0), &f, &df);
+            if (!std::isfinite(std::abs(f)))
+                return set_error(RSRR_ENONFINITE, "f_i is not finite at a Chebyshev point");
+            for (int j = 0; j < m; ++j) {
+                const double cj = (2.0 / m) * std::cos(j * th) * (j == 0 ? 0.5 : 1.0);
+                W[(size_t)i + (size_t)j * J] += f * cj;
+            }
+        }
+    }
+    std::vector<rsrr_fn> fns(m);
+    for (int j = 0; j < m; ++j) {
+        fns[j] = rsrr_fn{};
+        fns[j].kind = RSRR_F_CHEBYSHEV;
+        fns[j].p[0] = j;
+        fns[j].p[1] = lo;
+        fns[j].p[2] = hi;
+    }
+    if (k > 0) {
+        const int64_t kk = (int64_t)k * k;
+        c128 *Wd = nullptr, *Pn = nullptr;
+        RSRR_TRY(dalloc_n(&Wd, (size_t)J * m, st));
+        int rc = dalloc_n(&Pn, (size_t)kk * m, st);
+        if (rc != RSRR_OK) { dfree(Wd, st); return rc; }
+        std::vector<c128> Wh(W.size());
+        for (size_t e = 0; e < W.size(); ++e) Wh[e] = fromstd(W[e]);
+        cudaMemcpyAsync(Wd, Wh.data(), Wh.size() * sizeof(c128), cudaMemcpyHostToDevice, st);
+        Zgemm g;
+        g.M = (int)kk; g.N = m; g.K = J;
+        g.A = h->d_P; g.lda = kk; g.B = Wd; g.ldb = J; g.C = Pn; g.ldc = kk; g.ksplit = 1;
+        rc = zgemm(g, st);
+        if (rc == RSRR_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_error(RSRR_ECUDA, "Chebyshev coefficients");
+        dfree(Wd, st);
+        if (rc != RSRR_OK) { dfree(Pn, st); return rc; }
+        dfree(h->d_P, st);
+        h->d_P = Pn;
+    }
+    h->red_fns = fns;
+    h->red_J = m;
     return RSRR_OK;
 }
 

@@ -326,7 +326,10 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     for (double& x : h->ms_solve_parts) x = 0.0;
     zgemm_profile_begin();
     struct ZpGuard { rsrr_nep h; ~ZpGuard() { zgemm_profile_end(&h->ms_zgemm_solve, &h->zgemm_flops_solve); } } zpg{h};
-    const int k = h->kS, J = h->J;
+    // J, fns: the reduced NEP's terms (T's own, or Chebyshev polynomials); the final residual
+    // uses T itself (h->J, h->fns, the CSR values)
+    const int k = h->kS, J = h->red_J;
+    const std::vector<rsrr_fn>& fns = h->red_fns;
     const int64_t n = h->n;
     *nC_out = 0;
     h->nbar = 0;
@@ -343,7 +346,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     for (int j = 0; j < N_S; ++j) {
         for (int i = 0; i < J; ++i) {
             zd v, d;
-            eval_fn(h->fns[i], z[j], &v, &d);
+            eval_fn(fns[i], z[j], &v, &d);
             if (!std::isfinite(std::abs(v)) || !std::isfinite(std::abs(d)))
                 return set_error(RSRR_ENONFINITE, "f_i is not finite at a quadrature point");
             F[(size_t)j * J + i] = fromstd(v);
@@ -556,15 +559,16 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     // max over pairs of ||T_S(lambda) g|| / ||g|| for the pairs currently in (lam_h, G)
     TRYC(dalloc_n(&PG, (size_t)J * k * D, st));
     TRYC(dalloc_n(&RG, (size_t)k * D, st));
-    TRYC(dalloc_n(&Fl, (size_t)D * J, st));
+    TRYC(dalloc_n(&Fl, (size_t)D * std::max(J, h->J), st));
     TRYC(dalloc_n(&rn, (size_t)2 * D, st));
-    auto coef_upload = [&](const std::vector<zd>& lams) -> int {
-        std::vector<c128> fl(lams.size() * J);
+    auto coef_upload = [&](const std::vector<zd>& lams, const std::vector<rsrr_fn>& fs) -> int {
+        const int nf = (int)fs.size();
+        std::vector<c128> fl(lams.size() * nf);
         for (size_t t = 0; t < lams.size(); ++t)
-            for (int i = 0; i < J; ++i) {
+            for (int i = 0; i < nf; ++i) {
                 zd v, dv;
-                eval_fn(h->fns[i], lams[t], &v, &dv);
-                fl[t * J + i] = fromstd(v);
+                eval_fn(fs[i], lams[t], &v, &dv);
+                fl[t * nf + i] = fromstd(v);
             }
         if (!fl.empty())
             RSRR_CUDA(cudaMemcpyAsync(Fl, fl.data(), fl.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
@@ -573,7 +577,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     auto reduced_residual = [&](int nb, double* out) -> int {
         *out = 0.0;
         if (nb <= 0) return RSRR_OK;
-        RSRR_TRY(coef_upload(lam_h));
+        RSRR_TRY(coef_upload(lam_h, fns));
         Zgemm gp;
         gp.opA = OP_N; gp.opB = OP_N; gp.M = k; gp.N = nb; gp.K = k;
         gp.A = h->d_P; gp.lda = k; gp.sA = kk; gp.B = G; gp.ldb = k; gp.sB = 0;
@@ -627,10 +631,10 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         { scale_cols_kernel<<<(unsigned)ceil_div(n * nk, 256), 256, 0, st>>>(Vfull, n, nk, n, rn, 1); note_launch(); }
         std::vector<zd> lk(nk);
         for (int t = 0; t < nk; ++t) lk[t] = lam_h[keep[t]];
-        TRYC(coef_upload(lk));
+        TRYC(coef_upload(lk, h->fns));
         CUDAC(cudaMemsetAsync(rn, 0, nk * 8, st));
         dim3 gr((unsigned)ceil_div(n, 128), nk);
-        { csr_residual_kernel<<<gr, 128, 0, st>>>(h->d_rowptr, h->d_colind, h->d_vals, h->nnz, n, J, Fl, Vfull, nk, rn); note_launch(); }
+        { csr_residual_kernel<<<gr, 128, 0, st>>>(h->d_rowptr, h->d_colind, h->d_vals, h->nnz, n, h->J, Fl, Vfull, nk, rn); note_launch(); }
         std::vector<double> hres(nk);
         CUDAC(cudaMemcpyAsync(hres.data(), rn, nk * 8, cudaMemcpyDeviceToHost, st));
         std::vector<c128> hv;

@@ -366,3 +366,53 @@ def test_rectangle_moments_and_argument_checks(rs):
         h.solve(501, 2, 1e3, 4096, True)
     assert e.value.name == "EINVAL"
     h.close()
+
+
+@pytest.mark.parametrize("name,d", [("tiny_qep", 2), ("config0_flat", 20)])
+def test_chebyshev_projection_matches_oracle(rs, name, d):
+    """rsrr_project_chebyshev (Section 6.2, Eqs. eq-Ts-interp, eq-Ts-coefs): the d + 1
+    interpolant coefficients P_hat_j against the oracle's on the device's basis, and the
+    eigenvalues against the oracle's Chebyshev route, the direct route and (quadratic NEP) the
+    companion linearisation; residuals are those of the true T."""
+    if name == "config0_flat":
+        prob = w.config0()
+        prob.b = 10.0
+        lo, hi, K = 100.0, 400.0, 2
+    else:
+        prob = w.by_name(name)
+        lo, hi, K = prob.gamma.real - prob.a, prob.gamma.real + prob.a, 4
+    h = open_nep(rs, prob)
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    kS = h.project_chebyshev(d, lo, hi)
+    assert h.info()["red_terms"] == d + 1
+    S, Ph = h.basis(), h.projected()
+    lam, V, res = h.solve(500, K, 1e3, 4096, True)
+    h.close()
+    ref_Ph, _ = oracle.chebyshev_reduce(prob, S, d, lo, hi)
+    assert np.abs(Ph - ref_Ph).max() < 1e-11 * np.abs(ref_Ph).max()
+    ref = oracle.rsrr(prob, K=K, chebyshev=(d, lo, hi))
+    assert lam.size == ref["lam"].size > 0
+    assert match(lam, ref["lam"]) < 1e-9
+    assert scaled(prob, lam, res).max() < 1e-10
+    direct = oracle.rsrr(prob, K=K)
+    assert match(lam, direct["lam"]) < 1e-9
+    if name == "tiny_qep":
+        assert match(lam, exact_eigs(name, prob)) < 1e-9
+
+
+def test_chebyshev_argument_checks(rs):
+    prob = w.tiny_qep()
+    h = open_nep(rs, prob)
+    with pytest.raises(rs.RsrrError) as e:
+        h.project_chebyshev(4, -1.0, 1.0)
+    assert e.value.name == "EORDER"
+    h.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, rs.RSRR_FP64, 1e-12, 12)
+    for d, lo, hi in ((-1, -1.0, 1.0), (257, -1.0, 1.0), (4, 1.0, 1.0), (4, 2.0, -1.0)):
+        with pytest.raises(rs.RsrrError) as e:
+            h.project_chebyshev(d, lo, hi)
+        assert e.value.name == "EINVAL"
+    # a Chebyshev term can also be one of T's own functions
+    fns = [(w.FN_CHEBYSHEV, [2, -1.6, 1.6]) if f.kind == w.FN_Z2 else (f.kind, f.params()) for f in prob.fns]
+    h.close()
+    h2 = rs.Nep(prob.n, prob.rowptr, prob.colind, prob.vals, fns)
+    h2.close()

@@ -369,3 +369,62 @@ def test_rectangle_contour_closed_form():
     assert rq["lam"].size == ref.size == 14
     assert match(rq["lam"], ref) < 1e-9
     assert rq["resid_scaled"].max() < 1e-10
+
+
+def test_chebyshev_kind():
+    """The Chebyshev function kind: tau_m(cos t) = cos(m t) and tau_m'(cos t) = m sin(m t)/sin t,
+    on an interval [lo, hi] mapped to [-1, 1]."""
+    lo, hi = 100.0, 400.0
+    t = np.linspace(0.1, 3.0, 7)
+    z = 0.5 * (lo + hi) + 0.5 * (hi - lo) * np.cos(t)
+    for m in (0, 1, 2, 7, 30):
+        F, dF = o.coefficients([w.Fn(w.FN_CHEBYSHEV, (m, lo, hi))], z)
+        assert np.allclose(F[:, 0], np.cos(m * t), atol=1e-12)
+        assert np.allclose(dF[:, 0], m * np.sin(m * t) / np.sin(t) * 2.0 / (hi - lo), atol=1e-10)
+
+
+def test_chebyshev_interpolant_reproduces_polynomial_nep():
+    """Section 6.2: a degree-d Chebyshev interpolant reproduces any T of degree <= d, so for the
+    quadratic NEP the reduced interpolant equals sum_i f_i(z) P_i at any z when d >= 2 (and not
+    for d = 1), and the eigenvalues are the companion linearisation's.  This decides the j = 0
+    weight: with the constant term not halved the d = 2 interpolant misses by P_hat_0."""
+    p = w.tiny_qep()
+    Shat, _, _ = o.sample(p)
+    S, _, _ = o.truncated_basis(Shat, 1e-14)
+    P = o.project(p, S)
+    lo, hi = p.gamma.real - p.a, p.gamma.real + p.a
+    rng = np.random.default_rng(7)
+    zs = rng.normal(size=5) * 2 + 1j * rng.normal(size=5)
+    F, _ = o.coefficients(p.fns, zs)
+    for d, exact in ((1, False), (2, True), (5, True)):
+        Ph, fns = o.chebyshev_reduce(p, S, d, lo, hi)
+        Fc, _ = o.coefficients(fns, zs)
+        err = max(np.linalg.norm(np.tensordot(Fc[t], Ph, 1) - np.tensordot(F[t], P, 1)) /
+                  np.linalg.norm(np.tensordot(F[t], P, 1)) for t in range(zs.size))
+        assert (err < 1e-12) == exact
+    K, C, M = (p.term(i).toarray() for i in range(3))
+    n = p.n
+    A = np.block([[np.zeros((n, n)), np.eye(n)], [-K, -C]])
+    B = np.block([[np.eye(n), np.zeros((n, n))], [np.zeros((n, n)), M]])
+    ev = np.linalg.eigvals(np.linalg.solve(B, A))
+    ev = ev[o.inside_contour(ev, p.gamma, p.a, p.b)]
+    r = o.rsrr(p, K=4, chebyshev=(2, lo, hi))
+    assert r["lam"].size == ev.size > 0
+    assert match(r["lam"], ev) < 1e-9
+
+
+def test_chebyshev_route_converges_on_sqrt_nep():
+    """Section 6.2: for T holomorphic near the interval the interpolant's error decays
+    exponentially in d.  Gun-like sqrt NEP (branch points at 0 and 108.8^2), flat ellipse
+    (250; 150, 10) around the interval [100, 400]: d = 10 and d = 20 approach the eigenvalues of
+    the direct reduced NEP geometrically; residuals are judged on the true T."""
+    q = w.config0()
+    q.b = 10.0
+    ref = o.rsrr(q)
+    errs = []
+    for d in (10, 20):
+        r = o.rsrr(q, chebyshev=(d, 100.0, 400.0))
+        assert r["lam"].size == ref["lam"].size == 22
+        errs.append(match(r["lam"], ref["lam"]))
+        assert r["resid_scaled"].max() < (1e-10 if d == 20 else 1e-8)
+    assert errs[0] < 1e-8 and errs[1] < 1e-13 and errs[1] < 1e-3 * errs[0]

@@ -25,6 +25,7 @@ FN_Z2 = 2           # f = z^2
 FN_ISQRT_SHIFT = 3  # f = i*sqrt(z - p0); p1 = 0 principal branch, p1 = 1 continued branch -sqrt(p0 - z)
 FN_EXP_DELAY = 4    # f = exp(-p0 z)
 FN_RATIONAL = 5     # f = p0 z / (z + p1)
+FN_CHEBYSHEV = 7    # f = tau_{p0}((2z - p1 - p2) / (p2 - p1)), Chebyshev polynomial on [p1, p2]
 
 
 @dataclass
