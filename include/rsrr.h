@@ -130,6 +130,24 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
                     const double* vals_reim, const rsrr_fn* f, uint32_t flags,
                     void* stream, rsrr_nep* out);
 
+/* ---- rsrr_create_nep_tz ---------------------------------------------------------------
+ * A handle for a T(z) known only through its values (Section 6: T need not be affine, e.g. a
+ * BEM matrix whose entries depend on z through the kernel).  The library calls
+ *   tz(user, m, z_reim, vals_reim)
+ * on the host to get T(z_k) on the fixed pattern for m points at once:
+ *   z_reim    [m][2] the points
+ *   vals_reim [m][nnz][2] to fill, entry order of rowptr/colind (the caller's ordering)
+ * It is called for the sampling points (rsrr_sample), the Chebyshev points
+ * (rsrr_project_chebyshev) and the eigenvalues (the residuals of rsrr_solve), from the thread
+ * that makes those calls, for as long as the handle lives.  Such a handle is projected with
+ * rsrr_project_chebyshev only (there are no A_i for rsrr_project or rsrr_project_moments).
+ * Arguments otherwise as rsrr_create_nep.
+ * Errors: EINVAL (NULL tz, bad pattern), ENOMEM, ECUDA; later calls report ENONFINITE if tz
+ *         returns a non-finite value. */
+typedef void (*rsrr_tz_cb)(void* user, int64_t m, const double* z_reim, double* vals_reim);
+int rsrr_create_nep_tz(int64_t n, const int64_t* rowptr, const int32_t* colind, rsrr_tz_cb tz, void* user,
+                       uint32_t flags, void* stream, rsrr_nep* out);
+
 /* ---- rsrr_sample ----------------------------------------------------------------------
  * Algorithm 2, Steps 1-2: for j = 0..N-1, z_j = phi(2 pi (j + 1/2) / N), factor T(z_j)
  * by LU with partial pivoting (band LU, or dense LU when the band is too wide to pay: see
@@ -219,8 +237,10 @@ int rsrr_project_moments(rsrr_nep h, int32_t Kp, double delta, int32_t* k_S_out)
  * holomorphic near the interval.
  *   d           degree, 0 <= d <= 256
  *   x_lo, x_hi  the interval, x_lo < x_hi (typically the contour's extent on the real axis)
- * Errors: as rsrr_project; EINVAL for bad d or interval, ENONFINITE if some f_i is not
- *         finite at a Chebyshev point. */
+ * For a handle from rsrr_create_nep_tz, S^H T(x_k) S is formed from the values T(x_k)
+ * (SpMM, then ZGEMM), exactly as Eq. eq-Ts-coefs writes it.
+ * Errors: as rsrr_project; EINVAL for bad d or interval, ENONFINITE if some f_i (or T) is
+ *         not finite at a Chebyshev point. */
 int rsrr_project_chebyshev(rsrr_nep h, int32_t d, double x_lo, double x_hi, double delta, int32_t* k_S_out);
 
 /* ---- rsrr_solve -----------------------------------------------------------------------

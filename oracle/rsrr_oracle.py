@@ -18,6 +18,7 @@ design notes):
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 from concurrent.futures import ThreadPoolExecutor
 
@@ -136,6 +137,20 @@ def inside_contour(lam, gamma, a, b, shape="ellipse"):
     return (w.real / a) ** 2 + (w.imag / b) ** 2 < 1.0
 
 
+def _is_tz(prob):
+    return getattr(prob, "tz", None) is not None
+
+
+def _T_at(prob, z):
+    """T(z) as a sparse matrix on the pattern (from the values of a tz problem, or sum f_i A_i)."""
+    if _is_tz(prob):
+        v = prob.tz(z)
+    else:
+        F, _ = coefficients(prob.fns, np.array([z]))
+        v = F[0] @ prob.vals
+    return sp.csr_matrix((v, prob.colind, prob.rowptr), shape=(prob.n, prob.n))
+
+
 def _shape(prob):
     return getattr(prob, "shape", "ellipse"), getattr(prob, "side_nodes", 0)
 
@@ -241,7 +256,12 @@ def sample(prob, points=None, threads=None, dense=False, z=None):
         shape, side_nodes = _shape(prob)
         z, _ = contour_rule(prob.gamma, prob.a, prob.b, prob.N, shape, side_nodes)
     pts = list(range(len(z))) if points is None else list(points)
-    F, _ = coefficients(prob.fns, z)
+    if _is_tz(prob):
+        # T known by its values: T(z_j) of each sampling point as its own term, coefficients I
+        prob = dataclasses.replace(prob, vals=np.stack([prob.tz(zz) for zz in z]), fns=[])
+        F = np.eye(len(z), dtype=np.complex128)
+    else:
+        F, _ = coefficients(prob.fns, z)
     kl, ku = bandwidths(prob)
     threads = threads or os.cpu_count() or 1
     with ThreadPoolExecutor(threads) as ex:
@@ -305,10 +325,9 @@ def chebyshev_reduce(prob, S, d, lo, hi):
     c, r = 0.5 * (lo + hi), 0.5 * (hi - lo)
     theta = (np.arange(m) + 0.5) * np.pi / m
     x = c + r * np.cos(theta)
-    F, _ = coefficients(prob.fns, x)
     Q = []
     for k in range(m):
-        Tk = sum(F[k, i] * prob.term(i) for i in range(prob.J))
+        Tk = _T_at(prob, x[k])
         Q.append(S.conj().T @ (Tk @ S))
     Phat = np.zeros((m,) + Q[0].shape, dtype=np.complex128)
     for j in range(m):
@@ -417,15 +436,19 @@ def backmap(S, g):
 
 
 def eigen_residuals(prob, lam, V):
-    """(raw ||T(lam) v|| / ||v||, scaled raw / sum_i |f_i(lam)| ||A_i||_F) per pair."""
-    F, _ = coefficients(prob.fns, lam)
-    normA = np.array([np.linalg.norm(prob.vals[i]) for i in range(prob.J)])
+    """(raw ||T(lam) v|| / ||v||, scaled raw / sum_i |f_i(lam)| ||A_i||_F) per pair; for a tz
+    problem (no A_i) the scale is ||T(lam)||_F."""
     raw, scaled = [], []
     for t in range(len(lam)):
-        T = sp.csr_matrix((F[t] @ prob.vals, prob.colind, prob.rowptr), shape=(prob.n, prob.n))
+        T = _T_at(prob, lam[t])
         r = np.linalg.norm(T @ V[:, t]) / np.linalg.norm(V[:, t])
         raw.append(r)
-        scaled.append(r / float(np.abs(F[t]) @ normA))
+        if _is_tz(prob):
+            scaled.append(r / np.linalg.norm(T.data))
+        else:
+            F, _ = coefficients(prob.fns, np.array([lam[t]]))
+            normA = np.array([np.linalg.norm(prob.vals[i]) for i in range(prob.J)])
+            scaled.append(r / float(np.abs(F[0]) @ normA))
     return np.array(raw), np.array(scaled)
 
 
@@ -440,6 +463,7 @@ def rsrr(prob, delta=1e-14, N_S=500, K=2, tol_gap=1e3, threads=None, dense=False
     Shat, infos, eta = sample(prob, threads=threads, dense=dense, z=z)
     S, sigma, k_S = truncated_basis(moment_matrix(prob, Shat, moments) if moments else Shat, delta)
     if chebyshev is None:
+        assert not _is_tz(prob), "a tz problem has no A_i: use the Chebyshev route"
         P, rfns = project(prob, S), prob.fns
     else:
         P, rfns = chebyshev_reduce(prob, S, *chebyshev)

@@ -99,7 +99,7 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
-           "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev"]
+           "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz"]
 
 
 def lib():
@@ -132,6 +132,7 @@ def lib():
         "rsrr_sample_batch": ([P, I32, P, P, P, P, I32, D, I32], ctypes.c_int),
         "rsrr_project_moments": ([P, I32, D, P], ctypes.c_int),
         "rsrr_project_chebyshev": ([P, I32, D, D, D, P], ctypes.c_int),
+        "rsrr_create_nep_tz": ([I64, P, P, RSRR_TZ_CB, P, U32, P, P], ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -190,6 +191,30 @@ def rsrr_create_nep(n, rowptr, colind, vals, fns, flags=0, stream=None):
     _check(lib().rsrr_create_nep(int(n), int(J), _ptr(rowptr), _ptr(colind), _ptr(vals), farr,
                                  int(flags), stream if stream is not None else current_stream(),
                                  ctypes.byref(h)))
+    return h
+
+
+# T(z) values for m points: (user, m, z_reim, vals_reim [m][nnz][2])
+RSRR_TZ_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double))
+
+
+def tz_callback(tz, nnz):
+    """An RSRR_TZ_CB from a Python callable tz(z) -> complex values [nnz] of T(z) on the pattern."""
+    def cb(user, m, z, out):
+        buf = np.ctypeslib.as_array(out, shape=(int(m) * nnz * 2,)).view(np.complex128).reshape(int(m), nnz)
+        for k in range(m):
+            buf[k] = tz(complex(z[2 * k], z[2 * k + 1]))
+    return RSRR_TZ_CB(cb)
+
+
+def rsrr_create_nep_tz(n, rowptr, colind, cb, flags=0, stream=None):
+    """cb: an RSRR_TZ_CB (see tz_callback); the caller keeps it alive with the handle."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().rsrr_create_nep_tz(int(n), _ptr(rowptr), _ptr(colind), cb, None, int(flags),
+                                    stream if stream is not None else current_stream(), ctypes.byref(h)))
     return h
 
 
@@ -299,6 +324,15 @@ class Nep:
         self.J = int(np.asarray(vals).shape[0])
         self._fns = list(fns)  # keeps RSRR_F_CALLBACK wrappers alive as long as the handle
         self.h = rsrr_create_nep(n, rowptr, colind, vals, self._fns, flags, stream)
+
+    @classmethod
+    def from_tz(cls, n, rowptr, colind, tz, flags=0, stream=None):
+        """rsrr_create_nep_tz: T known only by tz(z) -> complex values [nnz] on the pattern."""
+        self = cls.__new__(cls)
+        self.n, self.J = int(n), 0
+        self._fns = [tz_callback(tz, int(np.asarray(colind).size))]
+        self.h = rsrr_create_nep_tz(n, rowptr, colind, self._fns[0], flags, stream)
+        return self
 
     def sample(self, gamma, a, b, N, L, U=None, precision=RSRR_FP64, tol=1e-10, max_refine=10,
                shape=RSRR_CONTOUR_ELLIPSE, side_nodes=0):

@@ -14,6 +14,34 @@ int chebyshev_reduce(rsrr_nep h, int d, double lo, double hi);
 int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambda_reim, double* V_reim,
               double* resid, int32_t* nC_out);
 
+int tz_values(rsrr_nep_s* h, const std::vector<zd>& z, c128** d_vals) {
+    const int64_t m = (int64_t)z.size(), nnz = h->nnz;
+    *d_vals = nullptr;
+    if (m == 0) return RSRR_OK;
+    std::vector<double> zr(2 * m), raw((size_t)2 * m * nnz, 0.0);
+    for (int64_t k = 0; k < m; ++k) {
+        zr[2 * k] = z[k].real();
+        zr[2 * k + 1] = z[k].imag();
+    }
+    h->tz(h->tz_user, m, zr.data(), raw.data());
+    std::vector<c128> pv((size_t)m * nnz);
+    for (int64_t k = 0; k < m; ++k)
+        for (int64_t e = 0; e < nnz; ++e) {
+            const double* v = raw.data() + 2 * (k * nnz + h->vsrc[e]);
+            if (!std::isfinite(v[0]) || !std::isfinite(v[1]))
+                return set_error(RSRR_ENONFINITE, "T(z) from the tz callback is not finite");
+            pv[(size_t)k * nnz + e] = mk<double>(v[0], v[1]);
+        }
+    RSRR_TRY(dalloc_n(d_vals, pv.size(), h->stream));
+    if (cudaMemcpyAsync(*d_vals, pv.data(), pv.size() * sizeof(c128), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        dfree(*d_vals, h->stream);
+        *d_vals = nullptr;
+        return set_error(RSRR_ECUDA, "upload of T(z) values");
+    }
+    return RSRR_OK;
+}
+
 namespace {
 struct DeviceGuard {
     int prev = -1;
@@ -50,14 +78,18 @@ const char* rsrr_last_error(void) { return rsrr::last_error(); }
 const char* rsrr_version(void) { return "rsrr-gb300 0.1 (sm_103a)"; }
 int64_t rsrr_kernel_launches(void) { return rsrr::launches_total(); }
 
-int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
-                    const double* vals_reim, const rsrr_fn* f, uint32_t flags, void* stream,
-                    rsrr_nep* out) {
+}  // extern "C"
+
+namespace {
+// Shared by rsrr_create_nep (J terms with values) and rsrr_create_nep_tz (J = 0, tz given).
+int create_impl(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
+                const double* vals_reim, const rsrr_fn* f, rsrr_tz_cb tz, void* tz_user, uint32_t flags,
+                void* stream, rsrr_nep* out) {
     if (!out) return set_error(RSRR_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > (int64_t)INT32_MAX - 1) return set_error(RSRR_EINVAL, "n out of range");
-    if (J < 1 || J > 16) return set_error(RSRR_EINVAL, "J must be in 1..16");
-    if (!rowptr || !colind || !vals_reim || !f) return set_error(RSRR_EINVAL, "NULL input array");
+    if (tz ? J != 0 : (J < 1 || J > 16)) return set_error(RSRR_EINVAL, "J must be in 1..16");
+    if (!rowptr || !colind || (!tz && (!vals_reim || !f))) return set_error(RSRR_EINVAL, "NULL input array");
     if (flags & ~(RSRR_NATURAL_ORDER | RSRR_DENSE_LU)) return set_error(RSRR_EINVAL, "unknown flag bits");
     if (rowptr[0] != 0) return set_error(RSRR_EINVAL, "rowptr[0] must be 0");
     for (int64_t r = 0; r < n; ++r) {
@@ -80,7 +112,9 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     h->n = n;
     h->nnz = nnz;
     h->J = J;
-    h->fns.assign(f, f + J);
+    if (J) h->fns.assign(f, f + J);
+    h->tz = tz;
+    h->tz_user = tz_user;
     if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
         delete h;
         return set_error(RSRR_ECUDA, "cudaEventCreate failed");
@@ -108,6 +142,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
             prow[rn + 1] = pos;
         }
     }
+    h->vsrc = src;
     std::vector<c128> pv((size_t)J * nnz);
     h->normA.assign(J, 0.0);
     for (int i = 0; i < J; ++i) {
@@ -123,7 +158,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     cudaStream_t st = h->stream;
     int rc = RSRR_OK;
     if ((rc = dalloc_n(&h->d_rowptr, n + 1, st)) || (rc = dalloc_n(&h->d_colind, nnz, st)) ||
-        (rc = dalloc_n(&h->d_rowidx, nnz, st)) || (rc = dalloc_n(&h->d_vals, (size_t)J * nnz, st)) ||
+        (rc = dalloc_n(&h->d_rowidx, nnz, st)) || (J && (rc = dalloc_n(&h->d_vals, (size_t)J * nnz, st))) ||
         (rc = dalloc_n(&h->d_perm, n, st))) {
         rsrr_destroy(h);
         return rc;
@@ -132,7 +167,7 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_rowptr, prow.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_colind, pcol.data(), nnz * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_rowidx, prowidx.data(), nnz * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_vals, pv.data(), pv.size() * sizeof(c128), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && J) e = cudaMemcpyAsync(h->d_vals, pv.data(), pv.size() * sizeof(c128), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_perm, h->ord.perm.data(), n * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -142,6 +177,22 @@ int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* 
     h->device_bytes = (n + 1) * 8 + nnz * 8 + (int64_t)pv.size() * 16 + n * 4;
     *out = h;
     return RSRR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int rsrr_create_nep(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* colind,
+                    const double* vals_reim, const rsrr_fn* f, uint32_t flags, void* stream,
+                    rsrr_nep* out) {
+    if (!vals_reim || !f) return set_error(RSRR_EINVAL, "NULL input array");
+    return create_impl(n, J, rowptr, colind, vals_reim, f, nullptr, nullptr, flags, stream, out);
+}
+
+int rsrr_create_nep_tz(int64_t n, const int64_t* rowptr, const int32_t* colind, rsrr_tz_cb tz, void* user,
+                       uint32_t flags, void* stream, rsrr_nep* out) {
+    if (!tz) return set_error(RSRR_EINVAL, "tz is NULL");
+    return create_impl(n, 0, rowptr, colind, nullptr, nullptr, tz, user, flags, stream, out);
 }
 
 namespace {
@@ -261,6 +312,8 @@ int rsrr_project(rsrr_nep h, double delta, int32_t* k_S_out) {
     if (!h) return set_error(RSRR_EINVAL, "NULL handle");
     if (!h->sampled) return set_error(RSRR_EORDER, "rsrr_project needs a successful rsrr_sample");
     if (!(delta >= 0) || !(delta < 1)) return set_error(RSRR_EINVAL, "delta must be in [0, 1)");
+    if (h->tz && !h->tz_basis_only)
+        return set_error(RSRR_EINVAL, "a handle of rsrr_create_nep_tz is projected with rsrr_project_chebyshev");
     DeviceGuard g(h->device);
     h->projected = false;
     Timer t(h);
@@ -276,7 +329,10 @@ int rsrr_project_chebyshev(rsrr_nep h, int32_t d, double x_lo, double x_hi, doub
     if (!h) return set_error(RSRR_EINVAL, "NULL handle");
     if (d < 0 || d > 256 || !std::isfinite(x_lo) || !std::isfinite(x_hi) || !(x_lo < x_hi))
         return set_error(RSRR_EINVAL, "Chebyshev degree must be in 0..256 and x_lo < x_hi");
-    RSRR_TRY(rsrr_project(h, delta, k_S_out));
+    h->tz_basis_only = true;
+    const int rp = rsrr_project(h, delta, k_S_out);
+    h->tz_basis_only = false;
+    RSRR_TRY(rp);
     DeviceGuard g(h->device);
     const int rc = chebyshev_reduce(h, d, x_lo, x_hi);
     if (rc != RSRR_OK) h->projected = false;
@@ -299,6 +355,7 @@ int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, 
                double* V_reim, double* resid, int32_t* nC_out) {
     if (!h) return set_error(RSRR_EINVAL, "NULL handle");
     if (!h->projected) return set_error(RSRR_EORDER, "rsrr_solve needs a successful rsrr_project");
+    if (h->red_J < 1) return set_error(RSRR_EORDER, "no reduced NEP (a tz handle needs rsrr_project_chebyshev)");
     if (N_S < 4 || N_S > 100000 || K < 1 || K > 64 || !(tol_gap > 1) || cap < 0 || !nC_out ||
         (cap > 0 && !lambda_reim))
         return set_error(RSRR_EINVAL, "bad rsrr_solve arguments");

@@ -39,6 +39,13 @@ void choose_ordering(int64_t n, const int64_t* rowptr, const int32_t* colind, bo
 struct SampleWork;  // defined in sample.cu
 
 }  // namespace rsrr
+struct rsrr_nep_s;
+namespace rsrr {
+// T(z_k) values of a tz handle for m points, permuted to the device's entry order and uploaded
+// to *d_vals ([m][nnz], allocated here, freed by the caller).
+int tz_values(rsrr_nep_s* h, const std::vector<zd>& z, c128** d_vals);
+
+}  // namespace rsrr
 
 struct rsrr_nep_s {
     int device = 0;
@@ -58,6 +65,11 @@ struct rsrr_nep_s {
     bool force_dense = false;      // RSRR_DENSE_LU: factor every point with the dense LU
     bool dense_used = false;       // the last rsrr_sample factored densely
     std::vector<double> normA;     // ||A_i||_F
+    rsrr_tz_cb tz = nullptr;       // T known by its values (rsrr_create_nep_tz): the library calls
+    void* tz_user = nullptr;       // tz for T(z) at the points it needs; d_vals then holds T(z_j)
+                                   // of the sampling points as J = N "terms" with F = I
+    std::vector<int64_t> vsrc;     // device entry e holds the caller's entry vsrc[e]
+    bool tz_basis_only = false;    // rsrr_project_chebyshev's inner rsrr_project on a tz handle
 
     // sampling state
     int32_t N = 0, L = 0, precision = 0;

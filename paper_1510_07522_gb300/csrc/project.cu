@@ -456,7 +456,7 @@ int project_run(rsrr_nep h, double delta) {
     h->d_Q = nullptr;
     h->d_P = nullptr;
     h->red_fns = h->fns;  // the reduced NEP keeps T's own functions: P_i = S^H A_i S
-    h->red_J = J;
+    h->red_J = h->tz ? 0 : J;  // a tz handle has no A_i: its reduced NEP comes from chebyshev_reduce
 
     c128 *A = nullptr, *V = nullptr, *W = nullptr, *W2 = nullptr, *tau = nullptr, *Tall = nullptr,
          *alpha = nullptr, *part2 = nullptr, *part3 = nullptr, *Yb = nullptr, *B = nullptr, *Jm = nullptr,
@@ -639,6 +639,16 @@ int project_run(rsrr_nep h, double delta) {
             TRYC(zgemm(g3, st));
         }
         pc.mark();  // basis done
+        if (h->tz) {  // no A_i: rsrr_project_chebyshev forms the reduced NEP from T(x_k)
+            h->d_Q = Ybuf;
+            Ybuf = nullptr;
+            pc.mark();
+            CUDAC(cudaStreamSynchronize(st));
+            for (int i = 0; i < 4; ++i) h->ms_project_parts[i] = pc.ms(i);
+            zgemm_profile_end(&h->ms_zgemm_project, &h->zgemm_flops_project);
+            cleanup();
+            return RSRR_OK;
+        }
         // ---- P_i = S^H (A_i S) ---------------------------------------------------------------
         TRYC(dalloc_n(&AY, (size_t)J * n * kS, st));
         dim3 gs((unsigned)ceil_div(n * kS, 256), J);
@@ -669,7 +679,66 @@ int project_run(rsrr_nep h, double delta) {
 // c_kj = (2 / (d + 1)) cos(j theta_k) (halved for j = 0): one ZGEMM of the k_S^2 x J matrix of
 // the P_i against the J x (d + 1) matrix W.
 // ---------------------------------------------------------------------------------------------
+// A tz handle has no P_i: Q_k = S^H T(x_k) S is formed from T's values at the Chebyshev points
+// (SpMM, batched ZGEMM), then P_hat_j = sum_k c_kj Q_k is one more ZGEMM, as Eq. eq-Ts-coefs.
+int chebyshev_reduce_tz(rsrr_nep h, int d, double lo, double hi) {
+    cudaStream_t st = h->stream;
+    const int k = h->kS, m = d + 1;
+    const int64_t n = h->n, kk = (int64_t)k * k;
+    const double pi = 3.14159265358979323846, c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+    std::vector<zd> x(m);
+    std::vector<c128> Cm((size_t)m * m);
+    for (int kx = 0; kx < m; ++kx) {
+        const double th = (kx + 0.5) * pi / m;
+        x[kx] = zd(c + r * std::cos(th), 0.0);
+        for (int j = 0; j < m; ++j)
+            Cm[(size_t)kx + (size_t)j * m] = mk<double>((2.0 / m) * std::cos(j * th) * (j == 0 ? 0.5 : 1.0), 0.0);
+    }
+    std::vector<rsrr_fn> fns(m);
+    for (int j = 0; j < m; ++j) {
+        fns[j] = rsrr_fn{};
+        fns[j].kind = RSRR_F_CHEBYSHEV;
+        fns[j].p[0] = j;
+        fns[j].p[1] = lo;
+        fns[j].p[2] = hi;
+    }
+    if (k > 0) {
+        c128 *vals = nullptr, *AY = nullptr, *Q = nullptr, *Cd = nullptr, *Pn = nullptr;
+        auto release = [&]() { for (c128* p : {vals, AY, Q, Cd}) dfree(p, st); };
+        int rc = tz_values(h, x, &vals);
+        if (rc == RSRR_OK) rc = dalloc_n(&AY, (size_t)m * n * k, st);
+        if (rc == RSRR_OK) rc = dalloc_n(&Q, (size_t)m * kk, st);
+        if (rc == RSRR_OK) rc = dalloc_n(&Cd, Cm.size(), st);
+        if (rc == RSRR_OK) rc = dalloc_n(&Pn, (size_t)m * kk, st);
+        if (rc != RSRR_OK) { release(); dfree(Pn, st); return rc; }
+        cudaMemcpyAsync(Cd, Cm.data(), Cm.size() * sizeof(c128), cudaMemcpyHostToDevice, st);
+        dim3 gs((unsigned)ceil_div(n * k, 256), m);
+        { spmm_terms_kernel<<<gs, 256, 0, st>>>(h->d_rowptr, h->d_colind, vals, h->nnz, n, h->d_Q, k, AY); note_launch(); }
+        Zgemm gq;  // Q_k = S^H (T(x_k) S)
+        gq.opA = OP_C; gq.opB = OP_N; gq.M = k; gq.N = k; gq.K = (int)n;
+        gq.A = h->d_Q; gq.lda = n; gq.sA = 0; gq.B = AY; gq.ldb = n; gq.sB = n * k;
+        gq.C = Q; gq.ldc = k; gq.sC = kk; gq.batch = m;
+        rc = zgemm(gq, st);
+        if (rc == RSRR_OK) {
+            Zgemm gc;  // P_hat = [Q_0 .. Q_d] C
+            gc.M = (int)kk; gc.N = m; gc.K = m;
+            gc.A = Q; gc.lda = kk; gc.B = Cd; gc.ldb = m; gc.C = Pn; gc.ldc = kk; gc.ksplit = 1;
+            rc = zgemm(gc, st);
+        }
+        if (rc == RSRR_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_error(RSRR_ECUDA, "Chebyshev coefficients");
+        release();
+        if (rc != RSRR_OK) { dfree(Pn, st); return rc; }
+        dfree(h->d_P, st);
+        h->d_P = Pn;
+    }
+    h->red_fns = fns;
+    h->red_J = m;
+    return RSRR_OK;
+}
+
 int chebyshev_reduce(rsrr_nep h, int d, double lo, double hi) {
+    if (h->tz) return chebyshev_reduce_tz(h, d, lo, hi);
     cudaStream_t st = h->stream;
     const int J = h->J, k = h->kS, m = d + 1;
     const double pi = 3.14159265358979323846, c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);

@@ -372,7 +372,8 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     c128 *dFt = nullptr, *dWt = nullptr, *ab = nullptr, *lp = nullptr, *X = nullptr, *mom = nullptr,
          *Pt = nullptr, *trc = nullptr, *H = nullptr, *Hl = nullptr, *Jm = nullptr, *V0 = nullptr, *W0 = nullptr,
          *T1 = nullptr, *Am = nullptr, *Zs = nullptr, *vt = nullptr, *lam_d = nullptr, *Xe = nullptr,
-         *G = nullptr, *Hr = nullptr, *T2 = nullptr, *PG = nullptr, *RG = nullptr, *Fl = nullptr, *Vfull = nullptr;
+         *G = nullptr, *Hr = nullptr, *T2 = nullptr, *PG = nullptr, *RG = nullptr, *Fl = nullptr, *Vfull = nullptr,
+         *Tz = nullptr;
     int32_t *perm = nullptr, *ipiv = nullptr, *info = nullptr, *cols = nullptr, *est = nullptr;
     double *sig = nullptr, *rn = nullptr, *sigs = nullptr, *sigsafe = nullptr;
     int rc = RSRR_OK;
@@ -380,7 +381,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         for (void* p : {(void*)dFt, (void*)dWt, (void*)ab, (void*)lp, (void*)X, (void*)mom, (void*)Pt, (void*)trc,
                         (void*)H, (void*)Hl, (void*)Jm, (void*)V0, (void*)W0, (void*)T1, (void*)Am, (void*)Zs,
                         (void*)vt, (void*)lam_d, (void*)Xe, (void*)G, (void*)Hr, (void*)T2, (void*)PG, (void*)RG,
-                        (void*)Fl, (void*)Vfull, (void*)perm, (void*)ipiv, (void*)info, (void*)cols, (void*)est,
+                        (void*)Fl, (void*)Vfull, (void*)Tz, (void*)perm, (void*)ipiv, (void*)info, (void*)cols, (void*)est,
                         (void*)sig, (void*)rn, (void*)sigs, (void*)sigsafe})
             dfree(p, st);
     };
@@ -631,10 +632,25 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         { scale_cols_kernel<<<(unsigned)ceil_div(n * nk, 256), 256, 0, st>>>(Vfull, n, nk, n, rn, 1); note_launch(); }
         std::vector<zd> lk(nk);
         for (int t = 0; t < nk; ++t) lk[t] = lam_h[keep[t]];
-        TRYC(coef_upload(lk, h->fns));
+        const c128* tvals = h->d_vals;
+        int tJ = h->J;
+        if (h->tz) {
+            // T(lambda_t) from the caller's values: nk terms with coefficients F = I
+            TRYC(tz_values(h, lk, &Tz));
+            tvals = Tz;
+            tJ = nk;
+            std::vector<c128> eye((size_t)nk * nk, czero<double>());
+            for (int t = 0; t < nk; ++t) eye[(size_t)t * nk + t] = mk<double>(1.0, 0.0);
+            dfree(Fl, st);
+            Fl = nullptr;
+            TRYC(dalloc_n(&Fl, eye.size(), st));
+            CUDAC(cudaMemcpyAsync(Fl, eye.data(), eye.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
+        } else {
+            TRYC(coef_upload(lk, h->fns));
+        }
         CUDAC(cudaMemsetAsync(rn, 0, nk * 8, st));
         dim3 gr((unsigned)ceil_div(n, 128), nk);
-        { csr_residual_kernel<<<gr, 128, 0, st>>>(h->d_rowptr, h->d_colind, h->d_vals, h->nnz, n, h->J, Fl, Vfull, nk, rn); note_launch(); }
+        { csr_residual_kernel<<<gr, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, h->nnz, n, tJ, Fl, Vfull, nk, rn); note_launch(); }
         std::vector<double> hres(nk);
         CUDAC(cudaMemcpyAsync(hres.data(), rn, nk * 8, cudaMemcpyDeviceToHost, st));
         std::vector<c128> hv;

@@ -508,21 +508,33 @@ int sample_dense_set(const std::vector<rsrr_nep>& hs, const std::vector<c128*>& 
 int sample_prepare(rsrr_nep h, const double* U_reim, std::vector<c128>* Fout) {
     cudaStream_t st = h->stream;
     const int64_t n = h->n;
-    const int N = h->N, L = h->L, J = h->J;
-    // coefficient table F[j][i] = f_i(z_j) (host FP64)
+    const int N = h->N, L = h->L;
     std::vector<zd> z;
     if (h->points.empty()) contour_rule(h->C, N, &z, nullptr, h->C.side_nodes);
     else z = h->points;
     std::vector<c128>& F = *Fout;
-    F.assign((size_t)N * J, czero<double>());
-    for (int j = 0; j < N; ++j)
-        for (int i = 0; i < J; ++i) {
-            zd v, dv;
-            eval_fn(h->fns[i], z[j], &v, &dv);
-            if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
-                return set_error(RSRR_ENONFINITE, "f_i(z_j) is not finite (a sampling point at a pole?)");
-            F[(size_t)j * J + i] = fromstd(v);
-        }
+    if (h->tz) {
+        // T known by its values: T(z_j) for every sampling point become the J = N terms, F = I
+        c128* v = nullptr;
+        RSRR_TRY(tz_values(h, z, &v));
+        dfree(h->d_vals, st);
+        h->d_vals = v;
+        h->J = N;
+        F.assign((size_t)N * N, czero<double>());
+        for (int j = 0; j < N; ++j) F[(size_t)j * N + j] = mk<double>(1.0, 0.0);
+    } else {
+        // coefficient table F[j][i] = f_i(z_j) (host FP64)
+        const int J = h->J;
+        F.assign((size_t)N * J, czero<double>());
+        for (int j = 0; j < N; ++j)
+            for (int i = 0; i < J; ++i) {
+                zd v, dv;
+                eval_fn(h->fns[i], z[j], &v, &dv);
+                if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+                    return set_error(RSRR_ENONFINITE, "f_i(z_j) is not finite (a sampling point at a pole?)");
+                F[(size_t)j * J + i] = fromstd(v);
+            }
+    }
     // probing matrix: upload and permute to the band ordering
     if (U_reim) {
         if (h->d_U && h->U_L != L) { dfree(h->d_U, st); h->d_U = nullptr; }

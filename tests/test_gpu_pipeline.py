@@ -416,3 +416,63 @@ def test_chebyshev_argument_checks(rs):
     h.close()
     h2 = rs.Nep(prob.n, prob.rowptr, prob.colind, prob.vals, fns)
     h2.close()
+
+
+def tz_handle(rs, prob, tz):
+    return rs.Nep.from_tz(prob.n, prob.rowptr, prob.colind, tz)
+
+
+def test_tz_handle_equals_affine_handle(rs):
+    """rsrr_create_nep_tz with T(z) = sum_i f_i(z) A_i supplied as values: the samples equal the
+    affine handle's, and rsrr_project_chebyshev gives the affine handle's Chebyshev eigenvalues."""
+    p = w.config0()
+    p.b = 10.0
+    F = lambda z: oracle.coefficients(p.fns, np.array([z]))[0][0]
+    ha = open_nep(rs, p)
+    hb = tz_handle(rs, p, lambda z: F(z) @ p.vals)
+    out = []
+    for h in (ha, hb):
+        h.sample(p.gamma, p.a, p.b, p.N, p.L, p.U, rs.RSRR_FP64, 1e-12, 12)
+        X = h.samples()
+        h.project_chebyshev(16, 100.0, 400.0)
+        lam, V, res = h.solve(500, 2, 1e3, 4096, True)
+        out.append((X, lam, res))
+        h.close()
+    assert rel_err_cols(out[1][0], out[0][0]).max() < 1e-12
+    assert out[1][1].size == out[0][1].size == 22
+    assert match(out[1][1], out[0][1]) < 1e-11
+    for X, lam, res in out:
+        assert scaled(p, lam, res).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "c64"])
+def test_distributed_delay_tz_matches_oracle(rs, prec):
+    """A NEP known only by its values (one delay per coupling, Section 6's situation): samples,
+    Chebyshev coefficients and eigenvalues against the oracle; residuals of the true T scaled
+    by ||T(lambda)||_F; the tz handle refuses the term-by-term projections."""
+    p = w.distributed_delay()
+    lo, hi = p.gamma.real - p.a, p.gamma.real + p.a
+    h = tz_handle(rs, p, p.tz)
+    mode = rs.RSRR_FP64 if prec == "fp64" else rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL
+    h.sample(p.gamma, p.a, p.b, p.N, p.L, p.U, mode, 1e-12 if prec == "fp64" else 1e-10, 20)
+    X = h.samples()
+    ref_X, infos, _ = oracle.sample(p)
+    assert rel_err_cols(X, ref_X).max() < 1e-8
+    for call in (lambda: h.project(1e-14), lambda: h.project_moments(8)):
+        with pytest.raises(rs.RsrrError) as e:
+            call()
+        assert e.value.name == "EINVAL"
+    with pytest.raises(rs.RsrrError) as e:
+        h.solve(500, 2, 1e3, 4096, True)
+    assert e.value.name == "EORDER"
+    h.project_chebyshev(16, lo, hi)
+    S, Ph = h.basis(), h.projected()
+    ref_Ph, _ = oracle.chebyshev_reduce(p, S, 16, lo, hi)
+    assert np.abs(Ph - ref_Ph).max() < 1e-11 * np.abs(ref_Ph).max()
+    lam, V, res = h.solve(500, 2, 1e3, 4096, True)
+    h.close()
+    ref = oracle.rsrr(p, chebyshev=(16, lo, hi))
+    assert lam.size == ref["lam"].size == 28
+    assert match(lam, ref["lam"]) < 1e-9
+    for t in range(lam.size):
+        assert res[t] / np.linalg.norm(p.tz(lam[t])) < 1e-10

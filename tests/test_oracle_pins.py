@@ -428,3 +428,46 @@ def test_chebyshev_route_converges_on_sqrt_nep():
         errs.append(match(r["lam"], ref["lam"]))
         assert r["resid_scaled"].max() < (1e-10 if d == 20 else 1e-8)
     assert errs[0] < 1e-8 and errs[1] < 1e-13 and errs[1] < 1e-3 * errs[0]
+
+
+def test_tz_route_equals_affine_route():
+    """A NEP given by its values T(z) (no affine form; Section 6) goes through the same steps:
+    built from config 0's sum_i f_i(z) A_i it yields the same samples and the same Chebyshev
+    eigenvalues as the affine description."""
+    p = w.config0()
+    p.b = 10.0
+    F = lambda z: o.coefficients(p.fns, np.array([z]))[0][0]
+    q = w.TzProblem(name="config0_tz", n=p.n, rowptr=p.rowptr, colind=p.colind,
+                    vals=np.zeros((0, p.nnz), np.complex128), fns=[], gamma=p.gamma, a=p.a, b=p.b,
+                    N=p.N, L=p.L, U=p.U, tz=lambda z: F(z) @ p.vals)
+    Sp, _, _ = o.sample(p)
+    Sq, _, _ = o.sample(q)
+    assert np.abs(Sp - Sq).max() <= 1e-13 * np.abs(Sp).max()
+    rp = o.rsrr(p, chebyshev=(16, 100.0, 400.0))
+    rq = o.rsrr(q, chebyshev=(16, 100.0, 400.0))
+    assert rq["lam"].size == rp["lam"].size == 22
+    assert match(rq["lam"], rp["lam"]) < 1e-12
+
+
+def test_distributed_delay_count_by_argument_principle():
+    """The distributed-delay NEP (one delay per coupling, known only by its values): the count
+    inside the contour from the argument principle on det T(z) (dense log-determinants along
+    the ellipse, independent of the method) is the Chebyshev route's count, and each
+    eigenvalue makes T(lambda) singular to working accuracy."""
+    p = w.distributed_delay()
+    th = 2 * np.pi * (np.arange(3000) + 0.5) / 3000
+    zc = p.gamma + p.a * np.cos(th) + 1j * p.b * np.sin(th)
+    def logdet(z):
+        T = np.zeros((p.n, p.n), np.complex128)
+        T[np.repeat(np.arange(p.n), np.diff(p.rowptr)), p.colind] = p.tz(z)
+        sgn, ld = np.linalg.slogdet(T)
+        return np.angle(sgn)
+    ph = np.unwrap([logdet(z) for z in zc])
+    count = int(np.rint((ph[-1] - ph[0] + (ph[1] - ph[0])) / (2 * np.pi)))
+    r = o.rsrr(p, chebyshev=(16, p.gamma.real - p.a, p.gamma.real + p.a))
+    assert count == r["lam"].size == 28
+    for lam in r["lam"][:5]:
+        T = np.zeros((p.n, p.n), np.complex128)
+        T[np.repeat(np.arange(p.n), np.diff(p.rowptr)), p.colind] = p.tz(lam)
+        sv = np.linalg.svd(T, compute_uv=False)
+        assert sv[-1] < 1e-12 * sv[0]

@@ -10,5 +10,5 @@ from .problems import (  # noqa: F401
     Fn, FN_CONST, FN_Z, FN_Z2, FN_ISQRT_SHIFT, FN_EXP_DELAY, FN_RATIONAL, FN_CHEBYSHEV,
     Problem, probe_matrix, grid_laplacian, config0, config0_linear, config0_rect, config1,
     config1b, config2, config3_member, config3_batch, planted_sqrt,
-    planted_delay, tiny_qep, loaded_string, acoustic_1d, by_name,
+    planted_delay, tiny_qep, loaded_string, acoustic_1d, by_name, TzProblem, distributed_delay,
 )

@@ -75,6 +75,14 @@ class Problem:
         return np.ascontiguousarray(self.vals).view(np.float64).reshape(self.J, self.nnz, 2)
 
 
+@dataclass
+class TzProblem(Problem):
+    """A NEP known only by its values: tz(z) -> complex [nnz], T(z) on the pattern.  vals is
+    empty (J = 0) and fns too; tz is the problem's definition, as a BEM assembly routine would
+    be, not a step of the method."""
+    tz: Optional[object] = None
+
+
 def probe_matrix(n: int, L: int, seed: int) -> np.ndarray:
     """Random complex Gaussian U (n x L): re, im iid N(0,1)/sqrt(2) (Algorithm 2, Step 1)."""
     g = np.random.default_rng(seed).standard_normal((L, n, 2))
@@ -391,9 +399,44 @@ def acoustic_1d(n=1000, N=100, L=2, zeta=1.0):
                  9.9 + 0.8j, 10.1, 1.01, N, L, 0, dict(band=1, expected_count=40))
 
 
+# --------------------------------------------------------------------------------------
+# Distributed-delay NEP, known only by its values: each coupling has its own delay,
+#   T(z)_ij = K_ij - z delta_ij + B_ij exp(-tau_ij z),
+# so T is not of the form sum_i f_i(z) A_i with few terms (the situation of Section 6, where T
+# is a BEM matrix).  K is the unscaled 5-point Laplacian on an s x s grid (spectrum in (0, 8)),
+# B and tau symmetric on K's off-diagonal pattern, |B_ij| <= beta, tau_ij ~ U(0.5, 2).
+# --------------------------------------------------------------------------------------
+def distributed_delay(s=16, N=48, L=4, beta=0.3, gamma=1.507, a=0.53, b=0.1, seed=0):
+    """Default contour: the flat ellipse over [0.977, 2.037], whose ends sit in spectral gaps
+    of width 0.11 and 0.13; 28 eigenvalues inside (all real: T(x) is real symmetric)."""
+    K = grid_laplacian(s, s, 1.0, 1.0)
+    n = s * s
+    rowptr, colind, kv = _union([K])
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    rng = np.random.default_rng([5, 0])
+    lo_ = np.minimum(rows, colind)
+    hi_ = np.maximum(rows, colind)
+    key = lo_ * n + hi_                     # one draw per unordered pair keeps B, tau symmetric
+    uk, inv = np.unique(key, return_inverse=True)
+    bvals = beta * rng.uniform(-1.0, 1.0, uk.size)[inv]
+    taus = rng.uniform(0.5, 2.0, uk.size)[inv]
+    off = rows != colind
+    bvals[~off] = 0.0
+    diag = (~off).astype(np.float64)
+    k0 = kv[0].real.copy()
+
+    def tz(z):
+        return k0 - z * diag + bvals * np.exp(-taus * z)
+
+    return TzProblem(name="distributed_delay", n=n, rowptr=rowptr, colind=colind,
+                     vals=np.zeros((0, colind.size), dtype=np.complex128), fns=[],
+                     gamma=complex(gamma), a=float(a), b=float(b), N=int(N), L=int(L),
+                     U=probe_matrix(n, L, seed), seed=seed, meta=dict(s=s, beta=beta), tz=tz)
+
+
 def by_name(name: str, **kw) -> Problem:
     table = dict(config0=config0, config0_linear=config0_linear, config1=config1,
                  config1b=config1b, config2=config2, planted_sqrt=planted_sqrt,
                  planted_delay=planted_delay, tiny_qep=tiny_qep, loaded_string=loaded_string,
-                 acoustic_1d=acoustic_1d, config0_rect=config0_rect)
+                 acoustic_1d=acoustic_1d, config0_rect=config0_rect, distributed_delay=distributed_delay)
     return table[name](**kw)
