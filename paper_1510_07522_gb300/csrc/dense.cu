@@ -309,20 +309,27 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             const double zeta = (be - al) / (2.0 * g);
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+            // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q), the phase folded
+            // into the two complex coefficients (12 FP64 operations per row)
+            const c128 sp = cscale(ph, s), cp = cscale(ph, c);
 #pragma unroll 2
             for (int r = tid; r < a.mb; r += 256) {
-                const c128 x = bp[r], y = ph * bq[r];
-                bp[r] = cscale(x, c) - cscale(y, s);
-                bq[r] = cscale(x, s) + cscale(y, c);
+                const c128 x = bp[r], y = bq[r];
+                bp[r] = mk<double>(fma(-sp.re, y.re, fma(sp.im, y.im, c * x.re)),
+                                   fma(-sp.re, y.im, fma(-sp.im, y.re, c * x.im)));
+                bq[r] = mk<double>(fma(cp.re, y.re, fma(-cp.im, y.im, s * x.re)),
+                                   fma(cp.re, y.im, fma(cp.im, y.re, s * x.im)));
             }
             if (a.J) {
                 c128* jp = a.J + (int64_t)p * a.kk;
                 c128* jq = a.J + (int64_t)q * a.kk;
 #pragma unroll 2
                 for (int r = tid; r < a.kk; r += 256) {
-                    const c128 x = jp[r], y = ph * jq[r];
-                    jp[r] = cscale(x, c) - cscale(y, s);
-                    jq[r] = cscale(x, s) + cscale(y, c);
+                    const c128 x = jp[r], y = jq[r];
+                    jp[r] = mk<double>(fma(-sp.re, y.re, fma(sp.im, y.im, c * x.re)),
+                                       fma(-sp.re, y.im, fma(-sp.im, y.re, c * x.im)));
+                    jq[r] = mk<double>(fma(cp.re, y.re, fma(-cp.im, y.im, s * x.re)),
+                                       fma(cp.re, y.im, fma(cp.im, y.re, s * x.im)));
                 }
             }
             if (tid == 0) atomicAdd(a.rotations, 1);
@@ -361,10 +368,10 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     unsigned* bar = nullptr;
     RSRR_TRY(dalloc_n(&dmax, 1, s));
     RSRR_TRY(dalloc_n(&drot, 1, s));
-    RSRR_TRY(dalloc_n(&bar, 4, s));
-    cudaMemsetAsync(bar, 0, 16, s);
+    RSRR_TRY(dalloc_n(&bar, kGridBarWords, s));
+    cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s);
     JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
-                  dmax, drot, GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2)}};
+                  dmax, drot, grid_bar_at(bar)};
     // Before each sweep the columns (and J's with them) are put in order of decreasing norm: the
     // round-robin pairs then meet in an order that converges in fewer sweeps, and the caller,
     // which sorts the final column norms itself, sees no difference.
@@ -404,7 +411,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         int hrot = 0, herr = 0;
         unsigned long long hmax = 0;
         cudaMemcpyAsync(&hrot, drot, 4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&herr, bar + 2, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&herr, bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
         if (herr) { rc = set_error(RSRR_ETIMEOUT, "grid barrier gave up in the Jacobi sweep"); break; }

@@ -73,6 +73,11 @@ struct GridBar {
     unsigned* gen;
     int* err;
 };
+// The three words sit on separate 128-byte lines: the arrival atomics on `count` must not
+// queue behind hundreds of CTAs polling `gen` in the same L2 line.
+constexpr int kGridBarWords = 96;  // allocation size in unsigned words
+inline GridBar grid_bar_at(unsigned* base) { return GridBar{base, base + 32, reinterpret_cast<int*>(base + 64)}; }
+constexpr int kGridBarErrWord = 64;
 __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
     __shared__ int s_ok;
     __syncthreads();
@@ -88,13 +93,17 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
             atomicAdd(gb.gen, 1u);
         } else {
             long long spins = 0;
+            unsigned backoff = 8;
             while (*vgen == g) {
                 if (++spins > (1LL << 24)) {  // bounded: give up, report, return
                     atomicExch(gb.err, 1);
                     ok = 0;
                     break;
                 }
-                if (spins > 4096) __nanosleep(32);  // tight polling first: barriers are short
+                // short backoff from the first miss, so that a few hundred pollers do not
+                // saturate the line the releasing CTA has to write
+                __nanosleep(backoff);
+                if (backoff < 128) backoff <<= 1;
             }
         }
         __threadfence();

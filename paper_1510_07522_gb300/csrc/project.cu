@@ -269,11 +269,11 @@ struct HqrWork {
         RSRR_TRY(dalloc_n(&part2, (size_t)G * kPB, s));
         RSRR_TRY(dalloc_n(&part3, (size_t)G * kPB * kPB, s));
         RSRR_TRY(dalloc_n(&Yb, (size_t)kPB * kPB, s));
-        RSRR_TRY(dalloc_n(&bar, 4, s));
+        RSRR_TRY(dalloc_n(&bar, kGridBarWords, s));
         RSRR_TRY(dalloc_n(&dnorm, 1, s));
         RSRR_TRY(dalloc_n(&px, (size_t)cols, s));
         RSRR_TRY(dalloc_n(&py, (size_t)rows, s));
-        RSRR_CUDA(cudaMemsetAsync(bar, 0, 16, s));
+        RSRR_CUDA(cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s));
         return RSRR_OK;
     }
     ~HqrWork() {
@@ -297,7 +297,7 @@ int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, dou
     for (int kb = 0; kb < kmax; kb += kPB) {
         const int bw = std::min(kPB, kmax - kb);
         PanelArgs pa{A, lda, (int)rows, kb, bw, w.tau, w.Tall + (int64_t)npan * kPB * kPB, w.part, w.alpha,
-                     w.part2, w.part3, w.Yb, GridBar{w.bar, w.bar + 1, reinterpret_cast<int*>(w.bar + 2)}};
+                     w.part2, w.part3, w.Yb, grid_bar_at(w.bar)};
         void* args[] = {&pa};
         RSRR_CUDA(cudaLaunchCooperativeKernel((void*)hqr_panel_kernel, w.G, 256, args, 0, st));
         note_launch();
@@ -329,7 +329,7 @@ int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, dou
             block_norm2(A, lda, kk, (int)rows, kk, cols, w.dnorm, st);
             RSRR_CUDA(cudaMemcpyAsync(&tn2, w.dnorm, 8, cudaMemcpyDeviceToHost, st));
         }
-        RSRR_CUDA(cudaMemcpyAsync(&berr, w.bar + 2, 4, cudaMemcpyDeviceToHost, st));
+        RSRR_CUDA(cudaMemcpyAsync(&berr, w.bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, st));
         RSRR_CUDA(cudaStreamSynchronize(st));
         if (berr) return set_error(RSRR_ETIMEOUT, "grid barrier gave up in the panel kernel");
         if (!std::isfinite(tn2)) return set_error(RSRR_ENONFINITE, "non-finite QR");
