@@ -266,6 +266,21 @@ int rsrr_project_chebyshev(rsrr_nep h, int32_t d, double x_lo, double x_hi, doub
 int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap,
                double* lambda_reim, double* V_reim, double* resid, int32_t* nC_out);
 
+/* ---- rsrr_zgemm (diagnostics) ----------------------------------------------------------
+ * The library's complex GEMM on caller device memory, C = alpha op(A) op(B) + beta C for each
+ * of `batch` problems (column-major, complex128 as [2] doubles; op 0 = as stored, 1 =
+ * transpose, 2 = conjugate transpose; sA, sB, sC element strides between problems).  It is
+ * the GEMM the projection and the reduced solve use, exported to test its two paths against a
+ * reference: path 0 = chosen by shape (as inside the library), 1 = FP64 on the CUDA cores,
+ * 2 = FP64-accurate emulation on the tensor cores (exact BF16 digit products with FP32
+ * accumulation, combined in FP64) for any shape.  Runs on `stream` (NULL = default) and
+ * returns after the work is queued, or after it finished for path 2.  The paper has no
+ * counterpart (it leaves dense algebra to its host libraries).
+ * Errors: EINVAL (bad sizes, op or path), ENOMEM, ETIMEOUT (a tensor-core wait gave up), ECUDA. */
+int rsrr_zgemm(int32_t path, int32_t opA, int32_t opB, int32_t M, int32_t N, int32_t K, const double* alpha_reim,
+               const void* A, int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB,
+               const double* beta_reim, void* C, int64_t ldc, int64_t sC, int32_t batch, void* stream);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------------ */
 typedef struct {
     int64_t n, nnz;

@@ -99,7 +99,8 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_samples", "rsrr_get_eta", "rsrr_get_sigma", "rsrr_get_basis",
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
-           "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz"]
+           "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz",
+           "rsrr_zgemm"]
 
 
 def lib():
@@ -133,6 +134,8 @@ def lib():
         "rsrr_project_moments": ([P, I32, D, P], ctypes.c_int),
         "rsrr_project_chebyshev": ([P, I32, D, D, D, P], ctypes.c_int),
         "rsrr_create_nep_tz": ([I64, P, P, RSRR_TZ_CB, P, U32, P, P], ctypes.c_int),
+        "rsrr_zgemm": ([I32, I32, I32, I32, I32, I32, P, P, I64, I64, P, I64, I64, P, P, I64, I64, I32, P],
+                       ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -257,6 +260,20 @@ def rsrr_sample_points(h, gamma, a, b, z, L, U=None, precision=RSRR_FP64, tol=1e
     Uc = None if U is None else _c128(U)
     _check(lib().rsrr_sample_points(h, ctypes.byref(C), int(zr.size), _ptr(zr), int(L), _ptr(Uc), int(precision),
                                     float(tol), int(max_refine)))
+
+
+def zgemm(path, A, B, C, opA=0, opB=0, alpha=1.0, beta=0.0, M=None, N=None, K=None, batch=1, strides=(0, 0, 0),
+          lds=None, stream=None):
+    """rsrr_zgemm on device buffers A, B, C (objects with data_ptr(), complex128, column-major with
+    leading dimensions `lds` = (lda, ldb, ldc)); C = alpha op(A) op(B) + beta C."""
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    lda, ldb, ldc = lds
+    _check(lib().rsrr_zgemm(int(path), int(opA), int(opB), int(M), int(N), int(K), al,
+                            ctypes.c_void_p(A.data_ptr()), int(lda), int(strides[0]),
+                            ctypes.c_void_p(B.data_ptr()), int(ldb), int(strides[1]), be,
+                            ctypes.c_void_p(C.data_ptr()), int(ldc), int(strides[2]), int(batch),
+                            stream if stream is not None else current_stream()))
 
 
 def rsrr_project_chebyshev(h, d, x_lo, x_hi, delta=1e-14):

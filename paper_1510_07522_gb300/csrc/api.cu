@@ -4,6 +4,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dense.cuh"
 #include "internal.h"
 
 namespace rsrr {
@@ -365,6 +366,29 @@ int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, 
     Timer t(h);
     int rc = solve_run(h, N_S, K, tol_gap, cap, lambda_reim, V_reim, resid, nC_out);
     h->ms_solve = t.stop();
+    return rc;
+}
+
+int rsrr_zgemm(int32_t path, int32_t opA, int32_t opB, int32_t M, int32_t N, int32_t K, const double* alpha_reim,
+               const void* A, int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB,
+               const double* beta_reim, void* C, int64_t ldc, int64_t sC, int32_t batch, void* stream) {
+    if (path < 0 || path > 2 || opA < 0 || opA > 2 || opB < 0 || opB > 2 || M < 0 || N < 0 || K < 0 || batch < 1 ||
+        !alpha_reim || !beta_reim || !A || !B || !C)
+        return set_error(RSRR_EINVAL, "rsrr_zgemm: bad argument");
+    const int64_t rowsA = opA == OP_N ? M : K, rowsB = opB == OP_N ? K : N;
+    if (lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB) || ldc < std::max<int64_t>(1, M))
+        return set_error(RSRR_EINVAL, "rsrr_zgemm: leading dimension too small");
+    Zgemm g;
+    g.opA = opA; g.opB = opB; g.M = M; g.N = N; g.K = K;
+    g.alpha = mk<double>(alpha_reim[0], alpha_reim[1]);
+    g.beta = mk<double>(beta_reim[0], beta_reim[1]);
+    g.A = static_cast<const c128*>(A); g.lda = lda; g.sA = sA;
+    g.B = static_cast<const c128*>(B); g.ldb = ldb; g.sB = sB;
+    g.C = static_cast<c128*>(C); g.ldc = ldc; g.sC = sC; g.batch = batch;
+    const int prev = zgemm_get_path();
+    zgemm_set_path(path);
+    const int rc = zgemm(g, reinterpret_cast<cudaStream_t>(stream));
+    zgemm_set_path(prev);
     return rc;
 }
 

@@ -133,6 +133,8 @@ int zgemm_shape(Zgemm g, cudaStream_t s) {
     else if (g.opA == OP_C && g.opB == OP_N) ZG(OP_C, OP_N)
     else if (g.opA == OP_C && g.opB == OP_C) ZG(OP_C, OP_C)
     else if (g.opA == OP_T && g.opB == OP_T) ZG(OP_T, OP_T)
+    else if (g.opA == OP_T && g.opB == OP_C) ZG(OP_T, OP_C)
+    else if (g.opA == OP_C && g.opB == OP_T) ZG(OP_C, OP_T)
     else return set_error(RSRR_EINVAL, "zgemm: unsupported op combination");
 #undef ZG
     RSRR_CUDA(cudaGetLastError());
@@ -187,6 +189,12 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
     return rc;
 }
 
+namespace {
+thread_local int g_zpath = 0;
+}
+void zgemm_set_path(int path) { g_zpath = path; }
+int zgemm_get_path() { return g_zpath; }
+
 static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s) {
     Zgemm g = g0;
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return RSRR_OK;
@@ -196,6 +204,7 @@ static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s) {
         RSRR_CUDA(cudaGetLastError());
         return RSRR_OK;
     }
+    if (g_zpath == 2 || (g_zpath == 0 && !g.fp64 && zgemm_tc_fits(g))) return zgemm_tc(g, s);
     if (g.M <= 32) return zgemm_shape<32, 128>(g, s);
     return zgemm_shape<64, 64>(g, s);
 }

@@ -22,8 +22,16 @@ struct Zgemm {
     int64_t ldc = 0, sC = 0;
     int batch = 1;
     int ksplit = 0;  // 0 = choose
+    bool fp64 = false;  // FP64 CUDA cores even where the tensor-core emulation would be chosen
 };
 int zgemm(const Zgemm& g, cudaStream_t s);
+// FP64-accurate ZGEMM on the tensor cores (exact BF16 digit products, see zgemm_tc.cu), and
+// the shapes for which zgemm() takes it.  zgemm_path: 0 = by shape, 1 = FP64 CUDA cores only,
+// 2 = tensor cores for every shape (per host thread; for tests and measurements).
+int zgemm_tc(const Zgemm& g, cudaStream_t s);
+bool zgemm_tc_fits(const Zgemm& g);
+void zgemm_set_path(int path);
+int zgemm_get_path();
 // Accounting of the ZGEMMs issued by this host thread between the two calls.
 void zgemm_profile_begin();
 void zgemm_profile_end(double* ms, double* flops);

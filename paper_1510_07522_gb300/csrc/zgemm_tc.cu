@@ -1,0 +1,492 @@
+// FP64-accurate complex GEMM on the tensor cores: C = alpha op(A) op(B) + beta C.
+//
+// This part runs FP64 at about 1.2 TFLOP/s and BF16 MMAs at about 1.8 PFLOP/s, so the large
+// ZGEMMs of the projection (the trailing updates of the Householder QR of S_hat, the basis,
+// S^H (A_i S)) are emulated with exact integer pieces (the splitting idea of Ozaki et al.):
+//
+//  1. Real form.  With a = op(A) (M x K) and b = op(B) (K x N) complex, K2 = K rounded up to 32:
+//       A' (2M x 2 K2) = [[Re a, -Im a], [Im a, Re a]],   B' (2 K2 x N) = [[Re b], [Im b]],
+//     so A' B' = [[Re ab], [Im ab]].  A tile holds 64 complex rows: their real parts in rows
+//     0..63 and their imaginary parts in rows 64..127.
+//  2. Exact digits.  Row i of a is scaled by 2^(55 - E_i), E_i the binary exponent of its largest
+//     |Re|, |Im| (so every scaled value is below 2^55 in magnitude), rounded to an integer X and
+//     written as X = sum_{s<8} d_s 128^(7-s) with d_1..d_7 balanced in [-64, 63] and |d_0| <= 64.
+//     Column j of b likewise with F_j.  Every digit is exact in BF16.
+//  3. Exact products.  A digit product is at most 2^12; the products of one diagonal q = s + t
+//     (at most 8 pairs) summed over 512 consecutive K' terms stay below 2^24, so the tensor cores
+//     accumulate them exactly in FP32: one TMEM accumulator per diagonal q = 0..7 (pairs with
+//     s + t >= 8 weigh below 2^-56 of the leading term and are not formed: 36 of 64 pairs).
+//  4. FP64 combination.  After each 512-term chunk the diagonal sums are added to an FP64
+//     accumulator with weights 2^(7 (14 - q)); at the end the tile is scaled by 2^(E_i + F_j - 110)
+//     and alpha, beta are applied.  The error is of the order of K' 2^-53 max_k |a_ik| max_k |b_kj|,
+//     the same size as an FP64 GEMM's normwise bound.
+//
+// Kernels: row and column maxima (atomicMax on the bit patterns of non-negative doubles), the
+// digit images of A' and B' in the MMA's shared-memory layout (K-major, 128-byte swizzle, one
+// 64-term slab per 128-byte row; 8 digit planes per slab), and the GEMM: one CTA per 128 x 32
+// output tile (and K range when split), a producer warp that bulk-copies each slab's 160 KB of
+// digit planes and issues the 144 MMAs of the 36 pairs, and four warps that drain the diagonal
+// accumulators (two TMEM buffers, so the MMAs of the next chunk overlap the drain) and write C.
+// Every wait is bounded; a timeout is reported through an error word and the call fails.
+#include <algorithm>
+#include <cmath>
+
+#include <cuda_bf16.h>
+
+#include "dense.cuh"
+#include "tc.cuh"
+
+namespace rsrr {
+namespace {
+using namespace tc;
+
+constexpr int OZ_D = 8;                      // digits per value, 7 bits each
+constexpr int OZ_ROWS = 128;                 // real rows per tile (64 complex rows)
+constexpr int OZ_CROWS = 64;
+constexpr int OZ_COLS = 32;                  // output columns per tile
+constexpr int OZ_KS = 64;                    // K' terms per slab (one swizzled 128-byte row)
+constexpr int OZ_CHUNK = 8;                  // slabs per exact FP32 accumulation (512 terms)
+constexpr uint32_t OZ_A_PLANE = OZ_ROWS * OZ_KS * 2;   // 16 KB
+constexpr uint32_t OZ_B_PLANE = OZ_COLS * OZ_KS * 2;   // 4 KB
+constexpr uint32_t OZ_A_BYTES = OZ_D * OZ_A_PLANE;     // 128 KB per (tile, slab)
+constexpr uint32_t OZ_B_BYTES = OZ_D * OZ_B_PLANE;     // 32 KB
+constexpr int OZ_EPI_WARPS = 4;
+constexpr int OZ_THREADS = (OZ_EPI_WARPS + 1) * 32;   // + one producer warp
+constexpr uint32_t OZ_TMEM_COLS = 512;                 // 2 buffers x 8 diagonals x 32 columns
+constexpr size_t OZ_SMEM = OZ_A_BYTES + OZ_B_BYTES + 1024;
+
+// ---- maxima ----------------------------------------------------------------------------------
+// out[b][u] = max over v < V of max(|Re|, |Im|) of X(u, v) = base[b*sb + u*su + v*sv], as the bit
+// pattern of a non-negative double (monotone as an unsigned integer).
+__global__ void oz_max_contig_u(const c128* X, int64_t sv, int64_t sb, int U, int V, int vch,
+                                unsigned long long* out) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.z;
+    if (u >= U) return;
+    const int v0 = blockIdx.y * vch, v1 = min(V, v0 + vch);
+    const c128* p = X + b * sb + u;
+    double m = 0.0;
+    for (int v = v0; v < v1; ++v) {
+        const c128 x = p[(int64_t)v * sv];
+        m = fmax(m, fmax(fabs(x.re), fabs(x.im)));
+    }
+    if (v1 > v0) atomicMax(out + (int64_t)b * U + u, (unsigned long long)__double_as_longlong(m));
+}
+__global__ void oz_max_contig_v(const c128* X, int64_t su, int64_t sb, int U, int V, int vch,
+                                unsigned long long* out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, b = blockIdx.z;
+    const int u = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (u >= U) return;
+    const int v0 = blockIdx.y * vch, v1 = min(V, v0 + vch);
+    const c128* p = X + b * sb + (int64_t)u * su;
+    double m = 0.0;
+    for (int v = v0 + lane; v < v1; v += 32) m = fmax(m, fmax(fabs(p[v].re), fabs(p[v].im)));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && v1 > v0) atomicMax(out + (int64_t)b * U + u, (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ __forceinline__ int oz_exp(unsigned long long bits) {
+    const double m = __longlong_as_double((long long)bits);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    return e;
+}
+
+// Digits of v * 2^(55 - E) (|v| < 2^E): d[0] most significant.
+__device__ __forceinline__ void oz_digits(double v, int E, float* d) {
+    long long X = llrint(ldexp(v, 55 - E));
+#pragma unroll
+    for (int s = OZ_D - 1; s >= 1; --s) {
+        int r = (int)(X & 127);
+        if (r >= 64) r -= 128;
+        d[s] = (float)r;
+        X = (X - r) >> 7;
+    }
+    d[0] = (float)X;
+}
+
+__device__ __forceinline__ uint4 oz_pack8(const float* v, float sign) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(sign * v[2 * e], sign * v[2 * e + 1]);
+    return *reinterpret_cast<uint4*>(h);
+}
+
+// Operand element access: op 0 = as stored (row u, column v at u + v*ld), 1 = transpose,
+// 2 = conjugate transpose, 3 = conjugate (no transpose).
+__device__ __forceinline__ c128 oz_at(const c128* X, int64_t ld, int op, int u, int v) {
+    c128 x = (op == 0 || op == 3) ? X[u + (int64_t)v * ld] : X[v + (int64_t)u * ld];
+    if (op >= 2) x.im = -x.im;
+    return x;
+}
+
+// ---- digit images -----------------------------------------------------------------------------
+// A': one thread per (complex row i, 8 consecutive k).  Image of batch b, row tile rt, slab sl
+// at byte (b * MT * nslab + rt * nslab + sl) * OZ_A_BYTES, plane s at + s * OZ_A_PLANE.
+__global__ void oz_slice_a(const c128* A, int64_t lda, int64_t sA, int op, int M, int K, int K2, int MT, int nslab,
+                           const unsigned long long* rmax, uint8_t* img) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.z, kgroups = K2 / 8;
+    const int64_t rows = (int64_t)MT * OZ_CROWS;
+    if (t >= rows * kgroups) return;
+    const int i = (int)(t % rows), k0 = (int)(t / rows) * 8;  // consecutive threads: consecutive rows
+    const c128* Ab = A + b * sA;
+    const int E = i < M ? oz_exp(rmax[(int64_t)b * M + i]) : 0;
+    c128 x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        x[e] = (i < M && k < K) ? oz_at(Ab, lda, op, i, k) : czero<double>();
+    }
+    const int rt = i / OZ_CROWS, rl = i % OZ_CROWS;
+    uint8_t* base = img + ((size_t)b * MT * nslab + (size_t)rt * nslab) * OZ_A_BYTES;
+    // k' = k0 (first half) and K2 + k0 (second half); re row: (Re, -Im), im row: (Im, Re)
+    uint8_t* lo = base + (size_t)(k0 / OZ_KS) * OZ_A_BYTES;
+    uint8_t* hi = base + (size_t)((K2 + k0) / OZ_KS) * OZ_A_BYTES;
+    const uint32_t re_lo = sw128_index16(rl, k0 % OZ_KS) * 2, im_lo = sw128_index16(rl + OZ_CROWS, k0 % OZ_KS) * 2;
+    const uint32_t re_hi = sw128_index16(rl, (K2 + k0) % OZ_KS) * 2;
+    const uint32_t im_hi = sw128_index16(rl + OZ_CROWS, (K2 + k0) % OZ_KS) * 2;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {  // 0: Re digits, 1: Im digits
+        float d[8][OZ_D];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) oz_digits(part == 0 ? x[e].re : x[e].im, E, d[e]);
+#pragma unroll
+        for (int sidx = 0; sidx < OZ_D; ++sidx) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = d[e][sidx];
+            const size_t po = (size_t)sidx * OZ_A_PLANE;
+            if (part == 0) {
+                *reinterpret_cast<uint4*>(lo + po + re_lo) = oz_pack8(v, 1.f);
+                *reinterpret_cast<uint4*>(hi + po + im_hi) = oz_pack8(v, 1.f);
+            } else {
+                *reinterpret_cast<uint4*>(hi + po + re_hi) = oz_pack8(v, -1.f);
+                *reinterpret_cast<uint4*>(lo + po + im_lo) = oz_pack8(v, 1.f);
+            }
+        }
+    }
+}
+
+// B': one thread per (column j, 8 consecutive k); rows of the K-major operand are columns j.
+__global__ void oz_slice_b(const c128* B, int64_t ldb, int64_t sB, int op, int N, int K, int K2, int NTt, int nslab,
+                           const unsigned long long* cmax, uint8_t* img) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.z, kgroups = K2 / 8;
+    const int64_t cols = (int64_t)NTt * OZ_COLS;
+    if (t >= cols * kgroups) return;
+    const int j = (int)(t % cols), k0 = (int)(t / cols) * 8;
+    const c128* Bb = B + b * sB;
+    const int F = j < N ? oz_exp(cmax[(int64_t)b * N + j]) : 0;
+    c128 x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        x[e] = (j < N && k < K) ? oz_at(Bb, ldb, op, k, j) : czero<double>();
+    }
+    const int ct = j / OZ_COLS, cl = j % OZ_COLS;
+    uint8_t* base = img + ((size_t)b * NTt * nslab + (size_t)ct * nslab) * OZ_B_BYTES;
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {  // Re digits at k' = k0, Im digits at k' = K2 + k0
+        const int kp = part == 0 ? k0 : K2 + k0;
+        uint8_t* slab = base + (size_t)(kp / OZ_KS) * OZ_B_BYTES;
+        const uint32_t at = sw128_index16(cl, kp % OZ_KS) * 2;
+        float d[8][OZ_D];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) oz_digits(part == 0 ? x[e].re : x[e].im, F, d[e]);
+#pragma unroll
+        for (int sidx = 0; sidx < OZ_D; ++sidx) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = d[e][sidx];
+            *reinterpret_cast<uint4*>(slab + (size_t)sidx * OZ_B_PLANE + at) = oz_pack8(v, 1.f);
+        }
+    }
+}
+
+__global__ void oz_scale_c(c128* C, int M, int N, int64_t ldc, int64_t sC, c128 beta) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * N) return;
+    c128* c = C + blockIdx.y * sC + idx % M + (idx / M) * ldc;
+    *c = (beta.re == 0.0 && beta.im == 0.0) ? czero<double>() : beta * (*c);
+}
+
+// ---- the GEMM -------------------------------------------------------------------------------
+struct OzArgs {
+    const uint8_t* imgA;
+    const uint8_t* imgB;
+    const unsigned long long* rmax;  // [batch][M]
+    const unsigned long long* cmax;  // [batch][N]
+    c128* C;
+    int64_t cs_i, cs_j, sC;          // C(i, j) of batch b at C + b*sC + i*cs_i + j*cs_j
+    int M, N, MT, NTt, nslab, nchunk, cper, ksplit;
+    c128 alpha, beta;                // beta applies when ksplit == 1 (else C was scaled before)
+    int* err;
+};
+
+struct OzShared {
+    // 0: slab loaded; 1: slab's MMAs done; 2 + b: chunk's MMAs into buffer b done; 4 + b: buffer b drained
+    uint64_t bar[6];
+    uint32_t tmem;
+    int fail;
+};
+
+__device__ __forceinline__ void oz_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OZ_EPI_WARPS * 32) : "memory"); }
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
+    extern __shared__ uint8_t oz_dyn[];
+    __shared__ OzShared sh;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_dyn) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + OZ_A_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rt = blockIdx.x, ct = blockIdx.y, b = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
+    const int c0 = ks * a.cper, c1 = min(a.nchunk, c0 + a.cper);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 6; ++i) mbar_init(&sh.bar[i], (i >= 4) ? OZ_EPI_WARPS : 1);
+        sh.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&sh.tmem)), "r"(OZ_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh.tmem;
+
+    if (warp == OZ_EPI_WARPS) {
+        // ---- producer: copies and MMAs (one thread) ----
+        if (lane == 0) {
+            // kind::f16: F32 accumulate, BF16 A and B, K-major both, N = 32, M = 128
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((OZ_COLS >> 3) << 17) | ((OZ_ROWS >> 4) << 24);
+            const uint64_t adesc = sw128_desc(smem_u32(sA)), bdesc = sw128_desc(smem_u32(sB));
+            const uint8_t* gA = a.imgA + ((size_t)b * a.MT * a.nslab + (size_t)rt * a.nslab) * OZ_A_BYTES;
+            const uint8_t* gB = a.imgB + ((size_t)b * a.NTt * a.nslab + (size_t)ct * a.nslab) * OZ_B_BYTES;
+            uint32_t n_load = 0, n_mma = 0, use[2] = {0, 0};
+            bool ok = true;
+            for (int c = c0; c < c1 && ok; ++c) {
+                const int buf = (c - c0) & 1;
+                if (use[buf] > 0 && !mbar_wait(&sh.bar[4 + buf], (use[buf] - 1) & 1)) { ok = false; break; }
+                const int s0 = c * OZ_CHUNK, s1 = min(a.nslab, s0 + OZ_CHUNK);
+                for (int sl = s0; sl < s1; ++sl) {
+                    if (n_mma > 0 && !mbar_wait(&sh.bar[1], (n_mma - 1) & 1)) { ok = false; break; }
+                    mbar_expect_tx(&sh.bar[0], OZ_A_BYTES + OZ_B_BYTES);
+                    bulk_g2s(sA, gA + (size_t)sl * OZ_A_BYTES, OZ_A_BYTES, &sh.bar[0]);
+                    bulk_g2s(sB, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, &sh.bar[0]);
+                    if (!mbar_wait(&sh.bar[0], n_load & 1)) { ok = false; break; }
+                    ++n_load;
+                    tc_fence_after();
+                    const uint32_t dbuf = tmem + (uint32_t)buf * (OZ_D * OZ_COLS);
+#pragma unroll 1
+                    for (int q = 0; q < OZ_D; ++q) {
+                        const uint32_t dq = dbuf + (uint32_t)q * OZ_COLS;
+                        for (int s = 0; s <= q; ++s) {
+                            const int t = q - s;
+#pragma unroll
+                            for (int kk = 0; kk < OZ_KS / 16; ++kk) {
+                                const uint32_t ao = (uint32_t)s * OZ_A_PLANE + kk * 32, bo = (uint32_t)t * OZ_B_PLANE + kk * 32;
+                                const uint32_t acc = (sl == s0 && s == 0 && kk == 0) ? 0u : 1u;
+                                tc_mma(dq, adesc + (ao >> 4), bdesc + (bo >> 4), idesc, acc);
+                            }
+                        }
+                    }
+                    tc_commit(&sh.bar[1]);
+                    ++n_mma;
+                }
+                if (!ok) break;
+                tc_commit(&sh.bar[2 + buf]);
+                ++use[buf];
+            }
+            if (!ok) {  // the epilogue warps see the flag after their own bounded wait and stop
+                atomicExch(a.err, 1);
+                *(volatile int*)&sh.fail = 1;
+            }
+            // let every issued MMA finish before the CTA frees tensor memory
+            if (n_mma > 0) mbar_wait(&sh.bar[1], (n_mma - 1) & 1);
+        }
+    } else {
+        // ---- epilogue warps: drain the diagonal sums of each chunk into FP64 ----
+        double acc[OZ_COLS];
+#pragma unroll
+        for (int j = 0; j < OZ_COLS; ++j) acc[j] = 0.0;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        uint32_t use[2] = {0, 0};
+        for (int c = c0; c < c1; ++c) {
+            const int buf = (c - c0) & 1;
+            bool got = false;
+            for (int tries = 0; tries < 4 && !got; ++tries) {
+                got = mbar_wait(&sh.bar[2 + buf], use[buf] & 1);
+                if (!got && *(volatile int*)&sh.fail) break;
+            }
+            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+            if (!got) { if (lane == 0) atomicExch(a.err, 1); break; }
+            ++use[buf];
+            tc_fence_after();
+            const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS);
+#pragma unroll 1
+            for (int q = 0; q < OZ_D; ++q) {
+                float v[32];
+                tc_ld16(dbuf + (uint32_t)q * OZ_COLS, v);
+                tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16, v + 16);
+                tc_wait_ld();
+                const double w = ldexp(1.0, 7 * (14 - q));
+#pragma unroll
+                for (int j = 0; j < OZ_COLS; ++j) acc[j] = fma((double)v[j], w, acc[j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.bar[4 + buf]);
+        }
+        // scale, exchange re/im halves through shared memory (the operand buffers are idle now),
+        // combine with alpha, beta and store
+        oz_epi_sync();
+        double* x = reinterpret_cast<double*>(sA);  // [OZ_ROWS][OZ_COLS + 1]
+        const int r = warp * 32 + lane, il = r % OZ_CROWS, i = rt * OZ_CROWS + il;
+        const int E = i < a.M ? oz_exp(a.rmax[(int64_t)b * a.M + i]) : 0;
+#pragma unroll
+        for (int j = 0; j < OZ_COLS; ++j) {
+            const int jj = ct * OZ_COLS + j;
+            const int F = jj < a.N ? oz_exp(a.cmax[(int64_t)b * a.N + jj]) : 0;
+            x[r * (OZ_COLS + 1) + j] = ldexp(acc[j], E + F - 110);
+        }
+        oz_epi_sync();
+        if (!*(volatile int*)&sh.fail) {
+            c128* Cb = a.C + b * a.sC;
+            for (int e = threadIdx.x; e < OZ_CROWS * OZ_COLS; e += OZ_EPI_WARPS * 32) {
+                const int il2 = e % OZ_CROWS, j = e / OZ_CROWS;
+                const int i2 = rt * OZ_CROWS + il2, j2 = ct * OZ_COLS + j;
+                if (i2 >= a.M || j2 >= a.N) continue;
+                const c128 p = mk<double>(x[il2 * (OZ_COLS + 1) + j], x[(il2 + OZ_CROWS) * (OZ_COLS + 1) + j]);
+                const c128 v = a.alpha * p;
+                c128* cp = Cb + (int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j;
+                if (a.ksplit > 1) {
+                    atomicAdd(&cp->re, v.re);
+                    atomicAdd(&cp->im, v.im);
+                } else if (a.beta.re == 0.0 && a.beta.im == 0.0) {
+                    *cp = v;
+                } else {
+                    *cp = v + a.beta * (*cp);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+    }
+}
+}  // namespace
+
+// Element strides of op(X) (row u, column v) for the maxima: op 0/3 -> (1, ld), op 1/2 -> (ld, 1).
+static void oz_strides(int op, int64_t ld, int64_t* su, int64_t* sv) {
+    if (op == 0 || op == 3) { *su = 1; *sv = ld; } else { *su = ld; *sv = 1; }
+}
+
+static int oz_max(const c128* X, int64_t ld, int64_t sb, int op, int U, int V, int batch, unsigned long long* out,
+                  cudaStream_t s) {
+    int64_t su, sv;
+    oz_strides(op, ld, &su, &sv);
+    const int vch = 2048;
+    const unsigned gy = (unsigned)ceil_div(V, vch);
+    if (su == 1) {
+        dim3 g((unsigned)ceil_div(U, 128), gy, batch);
+        { oz_max_contig_u<<<g, 128, 0, s>>>(X, sv, sb, U, V, vch, out); note_launch(); }
+    } else {
+        dim3 g((unsigned)ceil_div(U, 8), gy, batch);
+        { oz_max_contig_v<<<g, 256, 0, s>>>(X, su, sb, U, V, vch, out); note_launch(); }
+    }
+    return RSRR_OK;
+}
+
+// Worth it when the FP64 GEMM would take a while and both output sides fill tiles reasonably.
+bool zgemm_tc_fits(const Zgemm& g) {
+    const double work = 8.0 * g.M * (double)g.N * g.K * g.batch;
+    return work >= 4e8 && std::min(g.M, g.N) >= 16 && g.K >= 16;
+}
+
+int zgemm_tc(const Zgemm& g0, cudaStream_t s) {
+    Zgemm g = g0;
+    // orientation: the 32-column tile side goes to the smaller output side; computing C^T =
+    // op(B)^T op(A)^T swaps the operands (transposes the ops) and the output strides
+    // operand codes: 0 as stored, 1 transpose, 2 conjugate transpose, 3 conjugate
+    int64_t cs_i = 1, cs_j = g.ldc;
+    auto tr = [](int op) { return op == 0 ? 1 : op == 1 ? 0 : op == 2 ? 3 : 2; };
+    auto code = [](int op) { return op == OP_N ? 0 : op == OP_T ? 1 : 2; };
+    int opA = code(g.opA), opB = code(g.opB);
+    const c128 *A = g.A, *B = g.B;
+    int64_t lda = g.lda, ldb = g.ldb, sA = g.sA, sB = g.sB;
+    int M = g.M, N = g.N;
+    if (g.N > g.M) {
+        const int nA = tr(opB), nB = tr(opA);
+        std::swap(A, B);
+        std::swap(lda, ldb);
+        std::swap(sA, sB);
+        std::swap(M, N);
+        opA = nA;
+        opB = nB;
+        std::swap(cs_i, cs_j);
+    }
+    const int K = g.K, batch = g.batch;
+    const int K2 = (int)ceil_div(K, 32) * 32, nslab = 2 * K2 / OZ_KS, nchunk = (int)ceil_div(nslab, OZ_CHUNK);
+    const int MT = (int)ceil_div(M, OZ_CROWS), NTt = (int)ceil_div(N, OZ_COLS);
+    const int64_t tiles = (int64_t)MT * NTt * batch;
+    int ksplit = 1;
+    if (tiles < 2 * 152) ksplit = (int)std::min<int64_t>(nchunk, ceil_div(2 * 152, tiles));
+    const int cper = (int)ceil_div(nchunk, ksplit);
+    ksplit = (int)ceil_div(nchunk, cper);
+
+    unsigned long long *rmax = nullptr, *cmax = nullptr;
+    uint8_t *imgA = nullptr, *imgB = nullptr;
+    int* err = nullptr;
+    int rc = RSRR_OK;
+    auto release = [&]() {
+        for (void* p : {(void*)rmax, (void*)cmax, (void*)imgA, (void*)imgB, (void*)err}) dfree(p, s);
+    };
+    const size_t bytesA = (size_t)batch * MT * nslab * OZ_A_BYTES, bytesB = (size_t)batch * NTt * nslab * OZ_B_BYTES;
+    if ((rc = dalloc_n(&rmax, (size_t)batch * M, s)) || (rc = dalloc_n(&cmax, (size_t)batch * N, s)) ||
+        (rc = dalloc_n(&imgA, bytesA, s)) || (rc = dalloc_n(&imgB, bytesB, s)) || (rc = dalloc_n(&err, 1, s))) {
+        release();
+        return rc;
+    }
+    cudaMemsetAsync(rmax, 0, (size_t)batch * M * 8, s);
+    cudaMemsetAsync(cmax, 0, (size_t)batch * N * 8, s);
+    cudaMemsetAsync(err, 0, 4, s);
+    oz_max(A, lda, sA, opA, M, K, batch, rmax, s);
+    // columns of op(B) are the rows of op(B)^T
+    oz_max(B, ldb, sB, tr(opB), N, K, batch, cmax, s);
+    {
+        const int64_t na = (int64_t)MT * OZ_CROWS * (K2 / 8), nb = (int64_t)NTt * OZ_COLS * (K2 / 8);
+        { oz_slice_a<<<dim3((unsigned)ceil_div(na, 128), 1, batch), 128, 0, s>>>(A, lda, sA, opA, M, K, K2, MT, nslab, rmax, imgA); note_launch(); }
+        { oz_slice_b<<<dim3((unsigned)ceil_div(nb, 128), 1, batch), 128, 0, s>>>(B, ldb, sB, opB, N, K, K2, NTt, nslab, cmax, imgB); note_launch(); }
+    }
+    if (ksplit > 1) {
+        // C = beta C first; the K ranges then add alpha op(A) op(B) atomically
+        dim3 gsc((unsigned)ceil_div((int64_t)g.M * g.N, 256), batch);
+        { oz_scale_c<<<gsc, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
+    }
+    static bool attr_set = false;  // same value every time: concurrent callers cannot lower it
+    if (!attr_set) {
+        cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+        attr_set = true;
+    }
+    OzArgs oa{imgA, imgB, rmax, cmax, g.C, cs_i, cs_j, g.sC, M, N, MT, NTt, nslab, nchunk, cper, ksplit,
+              g.alpha, g.beta, err};
+    dim3 grid((unsigned)MT, (unsigned)NTt, (unsigned)(batch * ksplit));
+    { oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(oa); note_launch(); }
+    rc = cudaGetLastError() == cudaSuccess ? RSRR_OK : set_error(RSRR_ECUDA, "tensor-core ZGEMM launch");
+    int herr = 0;
+    if (rc == RSRR_OK) {
+        cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = set_error(RSRR_ECUDA, "tensor-core ZGEMM");
+        else if (herr) rc = set_error(RSRR_ETIMEOUT, "tensor-core ZGEMM: a bounded wait gave up");
+    }
+    release();
+    return rc;
+}
+
+}  // namespace rsrr
