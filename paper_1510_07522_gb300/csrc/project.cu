@@ -8,9 +8,10 @@
 //      After every panel the remaining trailing block is measured (Frobenius norm, then a
 //      power-iteration estimate of its 2-norm with a safety factor of 3); once its 2-norm is
 //      below 10% of delta * sigma_1 (sigma_1 from a power-iteration lower bound of ||S_hat||_2,
-//      so the rule errs on the side of keeping rows) the remaining rows of R are
-//      dropped: by Weyl's inequality they move no singular value by more than that, so the
-//      truncation only differs from the full SVD for sigma within 10% of the threshold.
+//      so the rule errs on the side of keeping rows), or below the rounding noise of S_hat
+//      (at most 30% of delta * sigma_1), the remaining rows of R are dropped: by Weyl's
+//      inequality they move no singular value by more than that, so the truncation only
+//      differs from the full SVD for sigma that close to the threshold.
 //   2. A second QR, of R_keep^H (m x k'), keeps only its k' x k' triangle R2; one-sided Jacobi
 //      on R2 with the rotations accumulated gives R2^H = J Sigma W^H, and the left singular
 //      vectors of R_keep = R2^H Q2^H are the columns of J.
@@ -309,12 +310,6 @@ int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, dou
             Zgemm g1;
             g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = mt; g1.K = (int)(rows - kb);
             g1.A = w.V; g1.lda = rows; g1.B = A + kb + (int64_t)kk * lda; g1.ldb = lda; g1.C = w.W; g1.ldc = kPB;
-            // The QR's updates stay in FP64: the tensor-core emulation's error is relative to the
-            // largest entries of each row and column, which leaves a noise floor in the trailing
-            // block above 0.1 delta sigma_1 and delays the early stop (measured on the 200 x 200
-            // damped QEP: 896 rows kept instead of 640 with both updates emulated, 704 with only
-            // A -= V W2 emulated); FP64 keeps the stop where the singular values put it
-            g1.fp64 = true;
             RSRR_TRY(zgemm(g1, st));
             Zgemm g2;
             g2.opA = OP_C; g2.opB = OP_N; g2.M = bw; g2.N = mt; g2.K = bw;
@@ -326,7 +321,6 @@ int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, dou
             g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
             g3.A = w.V; g3.lda = rows; g3.B = w.W2; g3.ldb = kPB; g3.C = A + kb + (int64_t)kk * lda; g3.ldc = lda;
             g3.ksplit = 1;
-            g3.fp64 = true;
             RSRR_TRY(zgemm(g3, st));
         }
         int berr = 0;
@@ -537,7 +531,8 @@ int project_run(rsrr_nep h, double delta) {
     if (!std::isfinite(smax)) { cleanup(); return set_error(RSRR_ENONFINITE, "non-finite sample matrix"); }
 
     // ---- Householder QR with early termination -----------------------------------------------
-    // stop once the trailing block's 2-norm is below 0.1 delta sigma_1: dropping it moves no
+    // stop once the trailing block's 2-norm is below 0.1 delta sigma_1 (or the noise level
+    // below): dropping it moves no
     // singular value by more than a tenth of the truncation level (Weyl).  sigma_1 is taken
     // from a power-iteration estimate of ||S_hat||_2 (a lower bound, so the rule stays safe).
     HqrWork hw;
@@ -545,8 +540,17 @@ int project_run(rsrr_nep h, double delta) {
     double s1_est = 0.0;
     TRYC(block_norm2_est(A, n, 0, (int)n, 0, m, 30, hw.px, hw.py, hw.dnorm, st, &s1_est));
     const double sref = std::max(smax, s1_est);
+    // The stop level is raised to the rounding noise of S_hat itself when that is higher, up
+    // to 0.3 delta sigma_1: in FP64 the trailing block of the QR levels off near u ||S_hat||_F
+    // (measured: a plateau at 0.7-0.9e-15 sigma_1 on the damped QEP, just under 0.1 delta
+    // sigma_1, so the stop point swung by hundreds of rows with the rounding), and rows at that
+    // level resolve no singular value.  Dropping a block of norm <= 0.3 delta sigma_1 still moves
+    // no singular value by more than that (Weyl).
+    double fro2 = 0.0;
+    for (double c : cn) fro2 += c * c;
+    const double noise = std::min(8.0 * 1.1102230246251565e-16 * std::sqrt(fro2), 0.3 * delta * sref);
     int kk = 0, npan = 0;
-    TRYC(householder_qr(A, n, m, n, hw, 0.1 * delta * sref, &kk, &npan));
+    TRYC(householder_qr(A, n, m, n, hw, std::max(0.1 * delta * sref, noise), &kk, &npan));
     pc.mark();  // QR done
     // ---- SVD of R_keep (kk x m) ---------------------------------------------------------------
     // R_keep^H = Q2 R2 (a second QR, only R2 kept), so R_keep = R2^H Q2^H and the left singular
