@@ -455,18 +455,24 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     { hankel_kernel<<<(unsigned)ceil_div(DD, 256), 256, 0, st>>>(mom, k, K, 1, Hl); note_launch(); }
     { identity_batch_kernel<<<dim3((unsigned)ceil_div(DD, 256), 1), 256, 0, st>>>(Jm, D, 1); note_launch(); }
     int sweeps = 0;
-    double hmax = 0.0;
+    double hmax = 0.0, hfro2 = 0.0;
     {
         TRYC(dalloc_n(&sig, (size_t)D, st));
         column_norms(H, D, D, D, sig, st);
         std::vector<double> cn(D);
         CUDAC(cudaMemcpyAsync(cn.data(), sig, D * 8, cudaMemcpyDeviceToHost, st));
         CUDAC(cudaStreamSynchronize(st));
-        for (double x : cn) hmax = std::max(hmax, x);
+        for (double x : cn) {
+            hmax = std::max(hmax, x);
+            hfro2 += x * x;
+        }
         dfree(sig, st);
         sig = nullptr;
     }
-    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, 1e-16 * hmax, 1e-12, 0.0));
+    // Columns at the rounding-noise level of H (a few u ||H||_F: the moments carry errors of
+    // that size) resolve no singular value and never settle, so they are not rotated.
+    const double hfloor = std::max(1e-16 * hmax, 4.0 * 1.1102230246251565e-16 * std::sqrt(hfro2));
+    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, hfloor, 1e-12, 0.0));
     h->jacobi_sweeps_solve = sweeps;
     cudaEventRecord(ev[2], st);  // Hankel SVD done
     TRYC(dalloc_n(&sig, (size_t)D, st));
