@@ -313,6 +313,11 @@ typedef struct {
                                    rsrr_project_chebyshev                                   */
     int32_t proj_cols;          /* columns of the matrix the last projection factored: N*L
                                    (rsrr_project) or K'*L (rsrr_project_moments)                 */
+    double ms_zgemm_tc;         /* the part of ms_zgemm spent in the tensor-core emulation       */
+    double zgemm_tc_gflop;      /* and its algorithmic work (8 M N K per product), GFLOP        */
+    double ms_jacobi;           /* device time of the one-sided Jacobi sweeps (project + solve)  */
+    double jacobi_gflop;        /* their algorithmic work: per sweep and column pair of an mb-row
+                                   matrix, 40 mb real flops (+ 24 k for the accumulated rotations) */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

@@ -91,7 +91,9 @@ class rsrr_info(ctypes.Structure):
                 ("ms_solve_inverse", ctypes.c_double), ("ms_solve_svd", ctypes.c_double),
                 ("ms_solve_extract", ctypes.c_double), ("ms_zgemm", ctypes.c_double),
                 ("zgemm_gflop", ctypes.c_double), ("dense_lu", ctypes.c_int32),
-                ("red_terms", ctypes.c_int32), ("proj_cols", ctypes.c_int32)]
+                ("red_terms", ctypes.c_int32), ("proj_cols", ctypes.c_int32),
+                ("ms_zgemm_tc", ctypes.c_double), ("zgemm_tc_gflop", ctypes.c_double),
+                ("ms_jacobi", ctypes.c_double), ("jacobi_gflop", ctypes.c_double)]
 
 
 _lib = None

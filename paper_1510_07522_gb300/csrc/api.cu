@@ -435,6 +435,10 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->dense_lu = h->dense_used ? 1 : 0;
     o->proj_cols = h->proj_cols;
     o->red_terms = h->red_J;
+    o->ms_zgemm_tc = h->ms_zgemm_tc_project + h->ms_zgemm_tc_solve;
+    o->zgemm_tc_gflop = (h->zgemm_tc_flops_project + h->zgemm_tc_flops_solve) * 1e-9;
+    o->ms_jacobi = h->ms_jacobi_project + h->ms_jacobi_solve;
+    o->jacobi_gflop = (h->jacobi_flops_project + h->jacobi_flops_solve) * 1e-9;
     return RSRR_OK;
 }
 

@@ -146,21 +146,20 @@ int zgemm_shape(Zgemm g, cudaStream_t s) {
 namespace {
 struct ZgemmProfile {
     bool on = false;
+    double flops = 0.0, flops_tc = 0.0;
+    struct Ev { cudaEvent_t a, b; bool tc; };
+    std::vector<Ev> ev;
+};
+thread_local ZgemmProfile g_zprof;
+struct JacobiProfile {
+    bool on = false;
     double flops = 0.0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
 };
-thread_local ZgemmProfile g_zprof;
-}  // namespace
-
-void zgemm_profile_begin() {
-    g_zprof.on = true;
-    g_zprof.flops = 0.0;
-    g_zprof.ev.clear();
-}
-
-void zgemm_profile_end(double* ms, double* flops) {
+thread_local JacobiProfile g_jprof;
+double drain_events(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& ev) {
     double t = 0.0;
-    for (auto& e : g_zprof.ev) {
+    for (auto& e : ev) {
         float x = 0.f;
         cudaEventSynchronize(e.second);
         cudaEventElapsedTime(&x, e.first, e.second);
@@ -168,13 +167,55 @@ void zgemm_profile_end(double* ms, double* flops) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
+    ev.clear();
+    return t;
+}
+}  // namespace
+
+void zgemm_profile_begin() {
+    g_zprof.on = true;
+    g_zprof.flops = g_zprof.flops_tc = 0.0;
+    g_zprof.ev.clear();
+}
+
+void zgemm_profile_end(double* ms, double* flops, double* ms_tc, double* flops_tc) {
+    double t = 0.0, t_tc = 0.0;
+    for (auto& e : g_zprof.ev) {
+        float x = 0.f;
+        cudaEventSynchronize(e.b);
+        cudaEventElapsedTime(&x, e.a, e.b);
+        t += x;
+        if (e.tc) t_tc += x;
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
     g_zprof.ev.clear();
     g_zprof.on = false;
     *ms = t;
     *flops = g_zprof.flops;
+    if (ms_tc) *ms_tc = t_tc;
+    if (flops_tc) *flops_tc = g_zprof.flops_tc;
+}
+
+void jacobi_profile_begin() {
+    g_jprof.on = true;
+    g_jprof.flops = 0.0;
+    g_jprof.ev.clear();
+}
+
+void jacobi_profile_end(double* ms, double* flops) {
+    *ms = drain_events(g_jprof.ev);
+    *flops = g_jprof.flops;
+    g_jprof.on = false;
 }
 
 static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s);
+
+namespace {
+thread_local int g_zpath = 0;
+}
+void zgemm_set_path(int path) { g_zpath = path; }
+int zgemm_get_path() { return g_zpath; }
 
 int zgemm(const Zgemm& g0, cudaStream_t s) {
     if (!g_zprof.on || g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.batch <= 0) return zgemm_dispatch(g0, s);
@@ -184,16 +225,13 @@ int zgemm(const Zgemm& g0, cudaStream_t s) {
     cudaEventRecord(a, s);
     const int rc = zgemm_dispatch(g0, s);
     cudaEventRecord(b, s);
-    g_zprof.ev.emplace_back(a, b);
-    g_zprof.flops += 8.0 * g0.M * (double)g0.N * g0.K * g0.batch;
+    const bool tc = g_zpath == 2 || (g_zpath == 0 && !g0.fp64 && zgemm_tc_fits(g0));
+    g_zprof.ev.push_back({a, b, tc});
+    const double f = 8.0 * g0.M * (double)g0.N * g0.K * g0.batch;
+    g_zprof.flops += f;
+    if (tc) g_zprof.flops_tc += f;
     return rc;
 }
-
-namespace {
-thread_local int g_zpath = 0;
-}
-void zgemm_set_path(int path) { g_zpath = path; }
-int zgemm_get_path() { return g_zpath; }
 
 static int zgemm_dispatch(const Zgemm& g0, cudaStream_t s) {
     Zgemm g = g0;
@@ -414,8 +452,21 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         cudaMemsetAsync(dmax, 0, 8, s);
         cudaMemsetAsync(drot, 0, 4, s);
         void* args[] = {&ja};
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (g_jprof.on) {
+            cudaEventCreate(&ea);
+            cudaEventCreate(&eb);
+            cudaEventRecord(ea, s);
+        }
         cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_sweep_kernel, G, 256, args, 0, s);
         note_launch();
+        if (g_jprof.on) {
+            cudaEventRecord(eb, s);
+            g_jprof.ev.emplace_back(ea, eb);
+            // algorithmic work of a full sweep: per column pair, three inner products over mb rows
+            // (16 real flops a row) and the rotation of both columns (24 a row), of B and of J
+            g_jprof.flops += 0.5 * k * (k - 1.0) * (40.0 * mb + (J ? 24.0 * k : 0.0));
+        }
         if (e != cudaSuccess) { rc = set_error(RSRR_ECUDA, cudaGetErrorString(e)); break; }
         int hrot = 0, herr = 0;
         unsigned long long hmax = 0;

@@ -34,7 +34,10 @@ void zgemm_set_path(int path);
 int zgemm_get_path();
 // Accounting of the ZGEMMs issued by this host thread between the two calls.
 void zgemm_profile_begin();
-void zgemm_profile_end(double* ms, double* flops);
+void zgemm_profile_end(double* ms, double* flops, double* ms_tc = nullptr, double* flops_tc = nullptr);
+// Accounting of the one-sided Jacobi sweeps (device time of the sweep kernels, algorithmic flops).
+void jacobi_profile_begin();
+void jacobi_profile_end(double* ms, double* flops);
 
 // Sum of v over a CTA (blockDim a multiple of 32, <= 1024); every thread gets the result.
 // Four block-wide sums at once (two CTA barriers instead of eight); every thread gets them.

@@ -109,5 +109,7 @@ struct rsrr_nep_s {
     double ms_project_parts[4] = {0, 0, 0, 0};
     double ms_solve_parts[3] = {0, 0, 0};
     double ms_zgemm_project = 0, zgemm_flops_project = 0, ms_zgemm_solve = 0, zgemm_flops_solve = 0;
+    double ms_zgemm_tc_project = 0, zgemm_tc_flops_project = 0, ms_zgemm_tc_solve = 0, zgemm_tc_flops_solve = 0;
+    double ms_jacobi_project = 0, jacobi_flops_project = 0, ms_jacobi_solve = 0, jacobi_flops_solve = 0;
     int64_t device_bytes = 0;
 };

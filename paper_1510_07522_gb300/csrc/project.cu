@@ -446,6 +446,7 @@ int project_run(rsrr_nep h, double delta) {
     PhaseClock pc(st);
     pc.mark();
     zgemm_profile_begin();
+    jacobi_profile_begin();
     const int64_t n = h->n;
     const int N = h->N, L = h->L, J = h->J;
     const int Kp = h->moment_order;
@@ -469,6 +470,7 @@ int project_run(rsrr_nep h, double delta) {
     auto cleanup = [&]() {
         double zm, zf;
         zgemm_profile_end(&zm, &zf);
+        jacobi_profile_end(&zm, &zf);
         for (void* p : {(void*)A, (void*)V, (void*)W, (void*)W2, (void*)tau, (void*)Tall, (void*)alpha,
                         (void*)part2, (void*)part3, (void*)Yb, (void*)B, (void*)Jm, (void*)Ybuf, (void*)Z,
                         (void*)Z2, (void*)AY, (void*)Eg, (void*)Jn, (void*)part, (void*)dnorm, (void*)colnrm, (void*)bar,
@@ -656,7 +658,9 @@ int project_run(rsrr_nep h, double delta) {
             pc.mark();
             CUDAC(cudaStreamSynchronize(st));
             for (int i = 0; i < 4; ++i) h->ms_project_parts[i] = pc.ms(i);
-            zgemm_profile_end(&h->ms_zgemm_project, &h->zgemm_flops_project);
+            zgemm_profile_end(&h->ms_zgemm_project, &h->zgemm_flops_project, &h->ms_zgemm_tc_project,
+                              &h->zgemm_tc_flops_project);
+            jacobi_profile_end(&h->ms_jacobi_project, &h->jacobi_flops_project);
             cleanup();
             return RSRR_OK;
         }
@@ -676,7 +680,9 @@ int project_run(rsrr_nep h, double delta) {
     }
     CUDAC(cudaStreamSynchronize(st));
     for (int i = 0; i < 4; ++i) h->ms_project_parts[i] = pc.ms(i);
-    zgemm_profile_end(&h->ms_zgemm_project, &h->zgemm_flops_project);
+    zgemm_profile_end(&h->ms_zgemm_project, &h->zgemm_flops_project, &h->ms_zgemm_tc_project,
+                      &h->zgemm_tc_flops_project);
+    jacobi_profile_end(&h->ms_jacobi_project, &h->jacobi_flops_project);
     cleanup();
 #undef TRYC
 #undef CUDAC

@@ -325,7 +325,14 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     cudaEventRecord(ev[0], st);
     for (double& x : h->ms_solve_parts) x = 0.0;
     zgemm_profile_begin();
-    struct ZpGuard { rsrr_nep h; ~ZpGuard() { zgemm_profile_end(&h->ms_zgemm_solve, &h->zgemm_flops_solve); } } zpg{h};
+    jacobi_profile_begin();
+    struct ZpGuard {
+        rsrr_nep h;
+        ~ZpGuard() {
+            zgemm_profile_end(&h->ms_zgemm_solve, &h->zgemm_flops_solve, &h->ms_zgemm_tc_solve, &h->zgemm_tc_flops_solve);
+            jacobi_profile_end(&h->ms_jacobi_solve, &h->jacobi_flops_solve);
+        }
+    } zpg{h};
     // J, fns: the reduced NEP's terms (T's own, or Chebyshev polynomials); the final residual
     // uses T itself (h->J, h->fns, the CSR values)
     const int k = h->kS, J = h->red_J;
