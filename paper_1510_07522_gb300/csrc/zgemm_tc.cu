@@ -16,8 +16,9 @@
 //     (at most 8 pairs) summed over 512 consecutive K' terms stay below 2^24, so the tensor cores
 //     accumulate them exactly in FP32: one TMEM accumulator per diagonal q = 0..7 (pairs with
 //     s + t >= 8 weigh below 2^-56 of the leading term and are not formed: 36 of 64 pairs).
-//  4. FP64 combination.  After each 512-term chunk the diagonal sums are added to an FP64
-//     accumulator with weights 2^(7 (14 - q)); at the end the tile is scaled by 2^(E_i + F_j - 110)
+//  4. FP64 combination.  After each 512-term chunk the diagonal sums (exact integers) are combined
+//     four at a time in int64 and added to an FP64 accumulator with weights 2^(7 (14 - q)); at
+//     the end the tile is scaled by 2^(E_i + F_j - 110)
 //     and alpha, beta are applied.  The error is of the order of K' 2^-53 max_k |a_ik| max_k |b_kj|,
 //     the same size as an FP64 GEMM's normwise bound.
 //
@@ -25,7 +26,8 @@
 // digit images of A' and B' in the MMA's shared-memory layout (K-major, 128-byte swizzle, one
 // 64-term slab per 128-byte row; 8 digit planes per slab), and the GEMM: one CTA per 128 x 32
 // output tile (and K range when split), a producer warp that bulk-copies each slab's 160 KB of
-// digit planes and issues the 144 MMAs of the 36 pairs, and four warps that drain the diagonal
+// digit planes and issues its 32 MMAs (one per A plane and K step, N up to 256, covering the 36
+// digit pairs), and four warps that drain the diagonal
 // accumulators (two TMEM buffers, so the MMAs of the next chunk overlap the drain) and write C.
 // Every wait is bounded; a timeout is reported through an error word and the call fails.
 #include <algorithm>
@@ -53,7 +55,12 @@ constexpr uint32_t OZ_B_BYTES = OZ_D * OZ_B_PLANE;     // 32 KB
 constexpr int OZ_EPI_WARPS = 4;
 constexpr int OZ_THREADS = (OZ_EPI_WARPS + 1) * 32;   // + one producer warp
 constexpr uint32_t OZ_TMEM_COLS = 512;                 // 2 buffers x 8 diagonals x 32 columns
-constexpr size_t OZ_SMEM = OZ_A_BYTES + OZ_B_BYTES + 1024;
+// Each slab is consumed in two pieces: digit planes 0..3 of A' with all 8 planes of B' (the 26
+// pairs with s <= 3), then planes 4..7 of A' (the 10 pairs with s >= 4, which need B' planes 0..3
+// only).  Two A slots (one per half) and two B slots let the next piece's copy run under the
+// current piece's MMAs.
+constexpr uint32_t OZ_A_HALF = OZ_A_BYTES / 2;          // 64 KB
+constexpr size_t OZ_SMEM = 2 * OZ_A_HALF + 2 * OZ_B_BYTES + 1024;
 
 // ---- maxima ----------------------------------------------------------------------------------
 // out[b][u] = max over v < V of max(|Re|, |Im|) of X(u, v) = base[b*sb + u*su + v*sv], as the bit
@@ -224,8 +231,9 @@ struct OzArgs {
 };
 
 struct OzShared {
-    // 0: slab loaded; 1: slab's MMAs done; 2 + b: chunk's MMAs into buffer b done; 4 + b: buffer b drained
-    uint64_t bar[6];
+    // 0 + h: piece of half h loaded; 2 + h: its MMAs done; 4 + b: chunk's MMAs into TMEM buffer b
+    // done; 6 + b: buffer b drained
+    uint64_t bar[8];
     uint32_t tmem;
     int fail;
 };
@@ -236,14 +244,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
     extern __shared__ uint8_t oz_dyn[];
     __shared__ OzShared sh;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_dyn) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + OZ_A_BYTES;
+    uint8_t* sA = smem;                   // two A halves of 64 KB
+    uint8_t* sB = smem + 2 * OZ_A_HALF;   // two B slabs of 32 KB
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rt = blockIdx.x, ct = blockIdx.y, b = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
     const int c0 = ks * a.cper, c1 = min(a.nchunk, c0 + a.cper);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 6; ++i) mbar_init(&sh.bar[i], (i >= 4) ? OZ_EPI_WARPS : 1);
+        for (int i = 0; i < 8; ++i) mbar_init(&sh.bar[i], (i >= 6) ? OZ_EPI_WARPS : 1);
         sh.fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -260,52 +268,69 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
     if (warp == OZ_EPI_WARPS) {
         // ---- producer: copies and MMAs (one thread) ----
         if (lane == 0) {
-            // kind::f16: F32 accumulate, BF16 A and B, K-major both, N = 32, M = 128
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((OZ_COLS >> 3) << 17) | ((OZ_ROWS >> 4) << 24);
+            // kind::f16: F32 accumulate, BF16 A and B, K-major both, M = 128; N is set per MMA
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((OZ_ROWS >> 4) << 24);
             const uint64_t adesc = sw128_desc(smem_u32(sA)), bdesc = sw128_desc(smem_u32(sB));
             const uint8_t* gA = a.imgA + ((size_t)b * a.MT * a.nslab + (size_t)rt * a.nslab) * OZ_A_BYTES;
             const uint8_t* gB = a.imgB + ((size_t)b * a.NTt * a.nslab + (size_t)ct * a.nslab) * OZ_B_BYTES;
-            uint32_t n_load = 0, n_mma = 0, use[2] = {0, 0};
+            const int S0 = c0 * OZ_CHUNK, S1 = min(a.nslab, c1 * OZ_CHUNK);
+            const int P = 2 * max(0, S1 - S0);
+            auto load = [&](int p) {
+                const int sl = S0 + p / 2, half = p & 1;
+                uint64_t* full = &sh.bar[half];
+                mbar_expect_tx(full, OZ_A_HALF + (half == 0 ? OZ_B_BYTES : 0u));
+                bulk_g2s(sA + half * OZ_A_HALF, gA + (size_t)sl * OZ_A_BYTES + half * OZ_A_HALF, OZ_A_HALF, full);
+                if (half == 0)
+                    bulk_g2s(sB + ((sl - S0) & 1) * OZ_B_BYTES, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, full);
+            };
+            uint32_t use[2] = {0, 0};
             bool ok = true;
-            for (int c = c0; c < c1 && ok; ++c) {
-                const int buf = (c - c0) & 1;
-                if (use[buf] > 0 && !mbar_wait(&sh.bar[4 + buf], (use[buf] - 1) & 1)) { ok = false; break; }
-                const int s0 = c * OZ_CHUNK, s1 = min(a.nslab, s0 + OZ_CHUNK);
-                for (int sl = s0; sl < s1; ++sl) {
-                    if (n_mma > 0 && !mbar_wait(&sh.bar[1], (n_mma - 1) & 1)) { ok = false; break; }
-                    mbar_expect_tx(&sh.bar[0], OZ_A_BYTES + OZ_B_BYTES);
-                    bulk_g2s(sA, gA + (size_t)sl * OZ_A_BYTES, OZ_A_BYTES, &sh.bar[0]);
-                    bulk_g2s(sB, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, &sh.bar[0]);
-                    if (!mbar_wait(&sh.bar[0], n_load & 1)) { ok = false; break; }
-                    ++n_load;
-                    tc_fence_after();
-                    const uint32_t dbuf = tmem + (uint32_t)buf * (OZ_D * OZ_COLS);
+            if (P > 0) load(0);
+            if (P > 1) load(1);
+            for (int p = 0; p < P && ok; ++p) {
+                const int sl = S0 + p / 2, half = p & 1, c = sl / OZ_CHUNK, buf = (c - c0) & 1;
+                const bool chunk_first = half == 0 && sl == c * OZ_CHUNK;
+                const bool chunk_last = half == 1 && sl + 1 == min(a.nslab, (c + 1) * OZ_CHUNK);
+                if (chunk_first && use[buf] > 0 && !mbar_wait(&sh.bar[6 + buf], (use[buf] - 1) & 1)) { ok = false; break; }
+                if (!mbar_wait(&sh.bar[half], (uint32_t)(p / 2) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t dbuf = tmem + (uint32_t)buf * (OZ_D * OZ_COLS);
+                const uint32_t a_base = (uint32_t)half * OZ_A_HALF, b_base = (uint32_t)((sl - S0) & 1) * OZ_B_BYTES;
+                // One MMA per A plane s and K step: B planes 0..7-s are consecutive 32-row blocks of
+                // one K-major operand of N = 32 (8 - s) rows, and the product's column block t lands
+                // on TMEM columns 32 (s + t), the accumulator of diagonal q = s + t.
+                const int s_lo = half == 0 ? 0 : 4;
 #pragma unroll 1
-                    for (int q = 0; q < OZ_D; ++q) {
-                        const uint32_t dq = dbuf + (uint32_t)q * OZ_COLS;
-                        for (int s = 0; s <= q; ++s) {
-                            const int t = q - s;
+                for (int s = s_lo; s < s_lo + 4; ++s) {
+                    const uint32_t n_s = (uint32_t)OZ_COLS * (OZ_D - s);
+                    const uint32_t id = idesc | ((n_s >> 3) << 17);
+                    const uint32_t ds = dbuf + (uint32_t)s * OZ_COLS;
 #pragma unroll
-                            for (int kk = 0; kk < OZ_KS / 16; ++kk) {
-                                const uint32_t ao = (uint32_t)s * OZ_A_PLANE + kk * 32, bo = (uint32_t)t * OZ_B_PLANE + kk * 32;
-                                const uint32_t acc = (sl == s0 && s == 0 && kk == 0) ? 0u : 1u;
-                                tc_mma(dq, adesc + (ao >> 4), bdesc + (bo >> 4), idesc, acc);
-                            }
-                        }
+                    for (int kk = 0; kk < OZ_KS / 16; ++kk) {
+                        const uint32_t ao = a_base + (uint32_t)(s - s_lo) * OZ_A_PLANE + kk * 32;
+                        const uint32_t bo = b_base + kk * 32;
+                        const uint32_t acc = (chunk_first && s == 0 && kk == 0) ? 0u : 1u;
+                        tc_mma(ds, adesc + (ao >> 4), bdesc + (bo >> 4), id, acc);
                     }
-                    tc_commit(&sh.bar[1]);
-                    ++n_mma;
                 }
-                if (!ok) break;
-                tc_commit(&sh.bar[2 + buf]);
-                ++use[buf];
+                tc_commit(&sh.bar[2 + half]);
+                if (chunk_last) {
+                    tc_commit(&sh.bar[4 + buf]);
+                    ++use[buf];
+                }
+                // refill: piece p + 1 goes into the slot piece p - 1 used, once its MMAs are done
+                if (p >= 1 && p + 1 < P) {
+                    if (!mbar_wait(&sh.bar[2 + ((p - 1) & 1)], (uint32_t)((p - 1) / 2) & 1)) { ok = false; break; }
+                    load(p + 1);
+                }
             }
             if (!ok) {  // the epilogue warps see the flag after their own bounded wait and stop
                 atomicExch(a.err, 1);
                 *(volatile int*)&sh.fail = 1;
             }
-            // let every issued MMA finish before the CTA frees tensor memory
-            if (n_mma > 0) mbar_wait(&sh.bar[1], (n_mma - 1) & 1);
+            // let every issued MMA finish before the CTA frees tensor memory (the last commit
+            // tracks all of them); when a wait gave up, also every copy still in flight
+            if (P > 0) mbar_wait(&sh.bar[2 + ((P - 1) & 1)], (uint32_t)((P - 1) / 2) & 1);
         }
     } else {
         // ---- epilogue warps: drain the diagonal sums of each chunk into FP64 ----
@@ -318,7 +343,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             const int buf = (c - c0) & 1;
             bool got = false;
             for (int tries = 0; tries < 4 && !got; ++tries) {
-                got = mbar_wait(&sh.bar[2 + buf], use[buf] & 1);
+                got = mbar_wait(&sh.bar[4 + buf], use[buf] & 1);
                 if (!got && *(volatile int*)&sh.fail) break;
             }
             got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
@@ -326,19 +351,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             ++use[buf];
             tc_fence_after();
             const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS);
-#pragma unroll 1
-            for (int q = 0; q < OZ_D; ++q) {
-                float v[32];
-                tc_ld16(dbuf + (uint32_t)q * OZ_COLS, v);
-                tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16, v + 16);
-                tc_wait_ld();
-                const double w = ldexp(1.0, 7 * (14 - q));
+            // The diagonal sums are integers below 2^24: four consecutive ones combine exactly in
+            // an int64 (below 2^46), so each column takes two FP64 FMAs instead of eight.
 #pragma unroll
-                for (int j = 0; j < OZ_COLS; ++j) acc[j] = fma((double)v[j], w, acc[j]);
+            for (int h2 = 0; h2 < OZ_COLS / 16; ++h2) {
+                float v[OZ_D][16];
+#pragma unroll
+                for (int q = 0; q < OZ_D; ++q) tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16 * h2, v[q]);
+                tc_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    long long g[2];
+#pragma unroll
+                    for (int hq = 0; hq < 2; ++hq) {
+                        const int q0 = 4 * hq;
+                        g[hq] = ((long long)__float2int_rn(v[q0][j]) << 21) + ((long long)__float2int_rn(v[q0 + 1][j]) << 14) +
+                                ((long long)__float2int_rn(v[q0 + 2][j]) << 7) + (long long)__float2int_rn(v[q0 + 3][j]);
+                    }
+                    // weights: diagonal q carries 2^(7 (14 - q)); g[0] is in units of q = 3, g[1] of q = 7
+                    acc[16 * h2 + j] = fma((double)g[0], 0x1p77, fma((double)g[1], 0x1p49, acc[16 * h2 + j]));
+                }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.bar[4 + buf]);
+            if (lane == 0) mbar_arrive(&sh.bar[6 + buf]);
         }
         // scale, exchange re/im halves through shared memory (the operand buffers are idle now),
         // combine with alpha, beta and store
