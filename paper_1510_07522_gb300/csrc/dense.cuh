@@ -38,6 +38,9 @@ void zgemm_profile_end(double* ms, double* flops, double* ms_tc = nullptr, doubl
 // Accounting of the one-sided Jacobi sweeps (device time of the sweep kernels, algorithmic flops).
 void jacobi_profile_begin();
 void jacobi_profile_end(double* ms, double* flops);
+// One-sided Jacobi SVD of a square D x D matrix with a QR preconditioner (project.cu): on return H
+// holds U Sigma and Jr the right singular vectors, as jacobi_orthogonalize(H, ..., Jr) would give.
+int jacobi_svd_preconditioned(c128* H, int D, c128* Jr, cudaStream_t st, double floor, double conv, int* sweeps);
 
 // Sum of v over a CTA (blockDim a multiple of 32, <= 1024); every thread gets the result.
 // Four block-wide sums at once (two CTA barriers instead of eight); every thread gets them.

@@ -351,6 +351,31 @@ int householder_qr(c128* A, int64_t rows, int cols, int64_t lda, HqrWork& w, dou
 }
 
 // y = A x for the block rows [r0, r1) x cols [c0, c1) (one thread per row)
+// Y (n x ncols, leading dimension n) <- Q Y with Q = H_0 H_1 ... from the reflectors that
+// householder_qr left in A (npan panels, kmax columns): the panels in reverse, each as
+// Y -= V (T (V^H Y)) with two work blocks Z, Z2 of kPB x ncols.
+int apply_q(const c128* A, int64_t n, int npan, int kmax, HqrWork& hw, c128* Y, int ncols, c128* Z, c128* Z2,
+            cudaStream_t st) {
+    for (int p = npan - 1; p >= 0; --p) {
+        const int kb = p * kPB, bw = std::min(kPB, kmax - kb);
+        { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, hw.V, n); note_launch(); }
+        Zgemm g1;
+        g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = ncols; g1.K = (int)(n - kb);
+        g1.A = hw.V; g1.lda = n; g1.B = Y + kb; g1.ldb = n; g1.C = Z; g1.ldc = kPB;
+        RSRR_TRY(zgemm(g1, st));
+        Zgemm g2;
+        g2.opA = OP_N; g2.opB = OP_N; g2.M = bw; g2.N = ncols; g2.K = bw;
+        g2.A = hw.Tall + (int64_t)p * kPB * kPB; g2.lda = bw; g2.B = Z; g2.ldb = kPB; g2.C = Z2; g2.ldc = kPB;
+        RSRR_TRY(zgemm(g2, st));
+        Zgemm g3;
+        g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = ncols; g3.K = bw;
+        g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
+        g3.A = hw.V; g3.lda = n; g3.B = Z2; g3.ldb = kPB; g3.C = Y + kb; g3.ldc = n; g3.ksplit = 1;
+        RSRR_TRY(zgemm(g3, st));
+    }
+    return RSRR_OK;
+}
+
 __global__ void gemv_n_kernel(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, const c128* x, c128* y) {
     const int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r1) return;
@@ -634,23 +659,7 @@ int project_run(rsrr_nep h, double delta) {
                                 kS, cudaMemcpyDeviceToDevice, st));
         TRYC(dalloc_n(&Z, (size_t)kPB * kS, st));
         TRYC(dalloc_n(&Z2, (size_t)kPB * kS, st));
-        for (int p = npan - 1; p >= 0; --p) {
-            const int kb = p * kPB, bw = std::min(kPB, kmax - kb);
-            { extract_v_kernel<<<(unsigned)ceil_div((n - kb) * bw, 256), 256, 0, st>>>(A, n, (int)n, kb, bw, hw.V, n); note_launch(); }
-            Zgemm g1;
-            g1.opA = OP_C; g1.opB = OP_N; g1.M = bw; g1.N = kS; g1.K = (int)(n - kb);
-            g1.A = hw.V; g1.lda = n; g1.B = Ybuf + kb; g1.ldb = n; g1.C = Z; g1.ldc = kPB;
-            TRYC(zgemm(g1, st));
-            Zgemm g2;
-            g2.opA = OP_N; g2.opB = OP_N; g2.M = bw; g2.N = kS; g2.K = bw;
-            g2.A = hw.Tall + (int64_t)p * kPB * kPB; g2.lda = bw; g2.B = Z; g2.ldb = kPB; g2.C = Z2; g2.ldc = kPB;
-            TRYC(zgemm(g2, st));
-            Zgemm g3;
-            g3.opA = OP_N; g3.opB = OP_N; g3.M = (int)(n - kb); g3.N = kS; g3.K = bw;
-            g3.alpha = mk<double>(-1.0, 0.0); g3.beta = mk<double>(1.0, 0.0);
-            g3.A = hw.V; g3.lda = n; g3.B = Z2; g3.ldb = kPB; g3.C = Ybuf + kb; g3.ldc = n; g3.ksplit = 1;
-            TRYC(zgemm(g3, st));
-        }
+        TRYC(apply_q(A, n, npan, kmax, hw, Ybuf, kS, Z, Z2, st));
         pc.mark();  // basis done
         if (h->tz) {  // no A_i: rsrr_project_chebyshev forms the reduced NEP from T(x_k)
             h->d_Q = Ybuf;
@@ -804,6 +813,87 @@ int chebyshev_reduce(rsrr_nep h, int d, double lo, double hi) {
     h->red_fns = fns;
     h->red_J = m;
     return RSRR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// One-sided Jacobi SVD of a square D x D matrix H with a QR preconditioner (after Drmac and
+// Veselic): the columns of H are put in order of decreasing norm, H P = Q R by Householder QR, and
+// the one-sided Jacobi runs on X = R^H with its rotations accumulated, X J = W = U Sigma.  Then
+// H = (Q J) Sigma (P U)^H.  The graded triangular factor converges in fewer sweeps than H itself
+// (on the Hankel matrices of the reduced solve, 16 -> 12 sweeps in a replay of the same rotations).
+// On return H holds (Q J) Sigma and Jr the right singular vectors P U: the same contract as a plain
+// one-sided Jacobi of H with the rotations accumulated into Jr, which the callers' extraction uses.
+// Columns below `floor` are not rotated (their right vectors come out as zero).
+// ---------------------------------------------------------------------------------------------
+namespace {
+__global__ void permute_cols_kernel(const c128* src, int D, const int* perm, c128* dst) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)D * D) return;
+    const int64_t r = idx % D, c = idx / D;
+    dst[idx] = src[r + (int64_t)perm[c] * D];
+}
+// H[:, j] = Y[:, j] sigma_j;  Jr[perm[i], j] = W[i, j] / sigma_j  (zero where sigma_j is zero)
+__global__ void svd_finish_kernel(const c128* W, const c128* Y, const double* sig, const int* perm, int D, c128* H,
+                                  c128* Jr) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)D * D) return;
+    const int64_t i = idx % D, j = idx / D;
+    const double sj = sig[j], inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    H[idx] = cscale(Y[idx], sj);
+    Jr[perm[i] + j * (int64_t)D] = cscale(W[idx], inv);
+}
+}  // namespace
+
+int jacobi_svd_preconditioned(c128* H, int D, c128* Jr, cudaStream_t st, double floor, double conv, int* sweeps) {
+    if (sweeps) *sweeps = 0;
+    if (D < 2) return jacobi_orthogonalize(H, D, D, Jr, st, 40, sweeps, floor, conv, 0.0);
+    const int64_t DD = (int64_t)D * D;
+    c128 *A = nullptr, *X = nullptr, *Z = nullptr, *Z2 = nullptr;
+    double* sig = nullptr;
+    int* perm_d = nullptr;
+    int rc = RSRR_OK;
+    auto release = [&]() {
+        for (void* q : {(void*)A, (void*)X, (void*)Z, (void*)Z2, (void*)sig, (void*)perm_d}) dfree(q, st);
+    };
+#define TRYR(expr) do { rc = (expr); if (rc != RSRR_OK) { release(); return rc; } } while (0)
+    TRYR(dalloc_n(&A, (size_t)DD, st));
+    TRYR(dalloc_n(&X, (size_t)DD, st));
+    TRYR(dalloc_n(&Z, (size_t)kPB * D, st));
+    TRYR(dalloc_n(&Z2, (size_t)kPB * D, st));
+    TRYR(dalloc_n(&sig, (size_t)D, st));
+    TRYR(dalloc_n(&perm_d, (size_t)D, st));
+    // columns in order of decreasing norm
+    column_norms(H, D, D, D, sig, st);
+    std::vector<double> hn(D);
+    if (cudaMemcpyAsync(hn.data(), sig, (size_t)D * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { release(); return set_error(RSRR_ECUDA, "column norms"); }
+    std::vector<int> perm(D);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hn[a] > hn[b]; });
+    cudaMemcpyAsync(perm_d, perm.data(), (size_t)D * 4, cudaMemcpyHostToDevice, st);
+    { permute_cols_kernel<<<(unsigned)ceil_div(DD, 256), 256, 0, st>>>(H, D, perm_d, A); note_launch(); }
+    // H P = Q R
+    HqrWork hw;
+    TRYR(hw.alloc(D, D, D, st));
+    int kk = 0, npan = 0;
+    TRYR(householder_qr(A, D, D, D, hw, -1.0, &kk, &npan));
+    // X = R^H, then the Jacobi with the rotations accumulated into Jr (used as J here)
+    { rkeep_h_kernel<<<(unsigned)ceil_div(DD, 256), 256, 0, st>>>(A, D, D, D, X); note_launch(); }
+    { identity_kernel<<<(unsigned)ceil_div(DD, 256), 256, 0, st>>>(Jr, D); note_launch(); }
+    TRYR(jacobi_orthogonalize(X, D, D, Jr, st, 40, sweeps, floor, conv, 0.0));
+    // left singular vectors Q J (in place of J), sigma_j = |W_j|, right vectors P W Sigma^{-1}
+    TRYR(apply_q(A, D, npan, kk, hw, Jr, D, Z, Z2, st));
+    column_norms(X, D, D, D, sig, st);
+    // the reflectors are no longer needed: A takes Q J while Jr receives the right vectors
+    if (cudaMemcpyAsync(A, Jr, (size_t)DD * sizeof(c128), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        release();
+        return set_error(RSRR_ECUDA, "copy of Q J");
+    }
+    { svd_finish_kernel<<<(unsigned)ceil_div(DD, 256), 256, 0, st>>>(X, A, sig, perm_d, D, H, Jr); note_launch(); }
+    if (cudaStreamSynchronize(st) != cudaSuccess) { release(); return set_error(RSRR_ECUDA, "preconditioned Jacobi"); }
+#undef TRYR
+    release();
+    return rc;
 }
 
 }  // namespace rsrr

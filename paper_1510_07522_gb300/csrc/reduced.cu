@@ -479,7 +479,7 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     // Columns at the rounding-noise level of H (a few u ||H||_F: the moments carry errors of
     // that size) resolve no singular value and never settle, so they are not rotated.
     const double hfloor = std::max(1e-16 * hmax, 4.0 * 1.1102230246251565e-16 * std::sqrt(hfro2));
-    TRYC(jacobi_orthogonalize(H, D, D, Jm, st, 40, &sweeps, hfloor, 1e-12, 0.0));
+    TRYC(jacobi_svd_preconditioned(H, D, Jm, st, hfloor, 1e-12, &sweeps));
     h->jacobi_sweeps_solve = sweeps;
     cudaEventRecord(ev[2], st);  // Hankel SVD done
     TRYC(dalloc_n(&sig, (size_t)D, st));
