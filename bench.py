@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--rates", default="1,4,16", help="serve: Poisson arrival rates, requests/s")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per rate")
     ap.add_argument("--batch", type=int, default=0, help="config 3: members of the batch (0 = the config's own)")
+    ap.add_argument("--banded", action="store_true",
+                    help="config 3: iterative sampler - factor only each member's grid-Laplacian band (half-width "
+                         "s, natural ordering) and iterate with the full T (rsrr_set_band_preconditioner)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="points in the CPU baseline sample (0 = cores)")
@@ -417,7 +420,14 @@ def run_batch(args):
     # handles go through rsrr_project / rsrr_solve in a host thread of their own
     streams = [torch.cuda.Stream() for _ in range(SOLVE_STREAMS)]
     sps = [ctypes.c_void_p(st.cuda_stream) for st in streams]
-    hs = [rs.Nep(p.n, p.rowptr, p.colind, p.vals, fns_of(p), 0, sps[i % len(sps)]) for i, p in enumerate(probs)]
+    flags = rs.RSRR_NATURAL_ORDER if args.banded else 0
+
+    def make(i, p, rowptr, colind, vals):
+        h = rs.Nep(p.n, rowptr, colind, vals, fns_of(p), flags, sps[i % len(sps)])
+        if args.banded:
+            h.set_band_preconditioner(p.meta["nx"])  # the grid Laplacian: half-width s
+        return h
+    hs = [make(i, p, p.rowptr, p.colind, p.vals) for i, p in enumerate(probs)]
     contours = [(p.gamma, p.a, p.b) for p in probs]
     Ns, Ls = [p.N for p in probs], [p.L for p in probs]
 
@@ -474,10 +484,22 @@ def run_batch(args):
     med = lambda key: statistics.median(sum(i[key] for i in step_infos) for step_infos in infos)
     fac_ms = statistics.median(step_infos[0]["ms_factor"] for step_infos in infos)
     launches_f = infos[-1][0]["factor_launches"]
-    flops = sum(p.N * dense_lu_flops(p.n) for p in probs)
+    if args.banded:  # band LU of the band part, kl = ku = s: 8 n kl (kl + ku) real flops per point
+        flops = sum(p.N * 8.0 * p.n * p.meta["nx"] * 2 * p.meta["nx"] for p in probs)
+        fac_ms = med("ms_factor")
+        launches_f = sum(i["factor_launches"] for i in infos[-1])
+    else:
+        flops = sum(p.N * dense_lu_flops(p.n) for p in probs)
     achieved = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
     bf16, _, src = measured_peaks()
-    if precision == "c64":
+    if args.banded:
+        lu_peak = FFMA_PEAK_TFLOPS if precision == "c64" else FP64_PEAK_TFLOPS
+        roof = {"kernel": "band_factor_kernel<%s> (band part of T only: the incomplete factor of the iterative "
+                          "sampler)" % ("float" if precision == "c64" else "double"), "bound": "alu",
+                "achieved": achieved, "peak": lu_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived FFMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)" if precision == "c64"
+                else "nominal FP64 rate (measured 1.19)"}
+    elif precision == "c64":
         roof = {"kernel": "dense_factor_kernel<float> (persistent dense LU, one CTA per point; trailing update "
                           "on tcgen05 BF16 tensor cores)", "bound": "tensor", "achieved": achieved, "peak": bf16,
                 "unit": "TFLOP/s", "traffic": None, "peak_source": "BF16 dense, " + src,
@@ -488,7 +510,9 @@ def run_batch(args):
         roof = {"kernel": "dense_factor_kernel<double> (persistent dense LU, CUDA-core FP64)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "nominal FP64 rate (measured 1.19)"}
-    roof.update({"algorithmic": f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
+    roof.update({"algorithmic": (f"8 n s (2 s) real flops per point (band half-width s), {points} points in "
+                                  f"{launches_f} launches") if args.banded else
+                 f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
                  "ms_per_step": fac_ms})
     roof["frac"] = achieved / roof["peak"] if achieved else None
     if "split_ceiling" in roof and achieved:
@@ -506,8 +530,7 @@ def run_batch(args):
         t0 = time.perf_counter()
         d2h = 0
         for _ in range(args.steps):
-            gs = [rs.Nep(p.n, t[0], t[1], t[2], fns_of(p), 0, sps[i % len(sps)])
-                  for i, (p, t) in enumerate(zip(probs, host))]
+            gs = [make(i, p, t[0], t[1], t[2]) for i, (p, t) in enumerate(zip(probs, host))]
             rs.sample_batch(gs, contours, Ns, Ls, [t[3] for t in host], prec, args.tol, 20)
             _, out = finish(gs, vectors=True)
             d2h = sum(lam.nbytes + V.nbytes + res.nbytes for lam, V, res in out.values())
@@ -530,6 +553,8 @@ def run_batch(args):
                 "config": dict({k: v for k, v in W.items() if k != "data"}, batch=B, precision=precision,
                                n_range=[min(p.n for p in probs), max(p.n for p in probs)],
                                parallelism=f"replicas x{world}" if world > 1 else "1 GPU", tol=args.tol,
+                               sampler=("iterative: band part factored (half-width s), full-T FP64 residual "
+                                        "iteration") if args.banded else "dense LU",
                                l2="inputs larger than L2 (dense factors of GBs per step)"),
                 "phases_ms_median": phases, "eigs_inside": counts,
                 "max_eta": max(i["max_eta"] for step_infos in infos for i in step_infos),

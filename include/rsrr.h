@@ -167,6 +167,20 @@ int rsrr_create_nep_tz(int64_t n, const int64_t* rowptr, const int32_t* colind, 
 int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
                 const double* U_reim, int32_t precision, double tol, int32_t max_refine);
 
+/* ---- rsrr_set_band_preconditioner -----------------------------------------------------
+ * An iterative sampler for NEPs whose full band is too wide to factor but whose dominant part
+ * is banded (Section 7.3-7.4 solve such systems iteratively with an incomplete factorisation,
+ * GMRES with ILU).  With band >= 0, the following rsrr_sample / rsrr_sample_points /
+ * rsrr_sample_batch calls factor only the entries of T(z_j) with |i - j| <= band (in the
+ * handle's ordering: pass RSRR_NATURAL_ORDER at creation to keep the caller's) and reach the
+ * tolerance by the refinement iteration X += M^{-1} (U - T(z_j) X) with the FP64 residual of
+ * the full T(z_j) (the same loop as RSRR_C64_IR; in RSRR_FP64 the incomplete factor is FP64).
+ * The iteration converges when ||M^{-1} (T - M)|| < 1; otherwise the call fails with
+ * ENOTCONVERGED after max_refine sweeps (the halving rule stops it earlier).  band = -1 turns it
+ * off (the default: the full band, or the dense LU).  It overrides RSRR_DENSE_LU.
+ * Errors: EINVAL (NULL handle, band < -1 or >= n). */
+int rsrr_set_band_preconditioner(rsrr_nep h, int32_t band);
+
 /* ---- rsrr_sample_points ---------------------------------------------------------------
  * rsrr_sample at sampling points the caller chooses.  The sampling scheme needs only the
  * solutions T(z_j)^{-1} U at some points z_j (Eq. eq-hatS): nothing ties them to a quadrature

@@ -102,7 +102,7 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
            "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz",
-           "rsrr_zgemm"]
+           "rsrr_zgemm", "rsrr_set_band_preconditioner"]
 
 
 def lib():
@@ -138,6 +138,7 @@ def lib():
         "rsrr_create_nep_tz": ([I64, P, P, RSRR_TZ_CB, P, U32, P, P], ctypes.c_int),
         "rsrr_zgemm": ([I32, I32, I32, I32, I32, I32, P, P, I64, I64, P, I64, I64, P, P, I64, I64, I32, P],
                        ctypes.c_int),
+        "rsrr_set_band_preconditioner": ([P, I32], ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -372,6 +373,10 @@ class Nep:
         """The SSRR moment scheme: rsrr_project on K' quadrature moments of the samples."""
         self.kS = rsrr_project_moments(self.h, Kp, delta)
         return self.kS
+
+    def set_band_preconditioner(self, band):
+        """rsrr_set_band_preconditioner: factor only |i - j| <= band and iterate (-1 = off)."""
+        _check(lib().rsrr_set_band_preconditioner(self.h, int(band)))
 
     def project_chebyshev(self, d, x_lo, x_hi, delta=1e-14):
         """rsrr_project, then the reduced NEP as its degree-d Chebyshev interpolant on [x_lo, x_hi]."""

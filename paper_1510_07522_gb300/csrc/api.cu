@@ -369,6 +369,13 @@ int rsrr_solve(rsrr_nep h, int32_t N_S, int32_t K, double tol_gap, int32_t cap, 
     return rc;
 }
 
+int rsrr_set_band_preconditioner(rsrr_nep h, int32_t band) {
+    if (!h) return set_error(RSRR_EINVAL, "NULL handle");
+    if (band < -1 || band >= h->n) return set_error(RSRR_EINVAL, "band must be -1 (off) or in 0..n-1");
+    h->precond_band = band;
+    return RSRR_OK;
+}
+
 int rsrr_zgemm(int32_t path, int32_t opA, int32_t opB, int32_t M, int32_t N, int32_t K, const double* alpha_reim,
                const void* A, int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB,
                const double* beta_reim, void* C, int64_t ldc, int64_t sC, int32_t batch, void* stream) {

@@ -63,6 +63,7 @@ struct rsrr_nep_s {
     rsrr::c128* d_vals = nullptr;  // [J][nnz]
     int32_t* d_perm = nullptr;     // [n] perm[new] = old
     bool force_dense = false;      // RSRR_DENSE_LU: factor every point with the dense LU
+    int32_t precond_band = -1;     // >= 0: factor only |i - j| <= precond_band of T(z_j) and iterate
     bool dense_used = false;       // the last rsrr_sample factored densely
     std::vector<double> normA;     // ||A_i||_F
     rsrr_tz_cb tz = nullptr;       // T known by its values (rsrr_create_nep_tz): the library calls

@@ -25,7 +25,7 @@ namespace {
 template <typename R>
 __global__ void assemble_kernel(const c128* __restrict__ vals, int J, int64_t nnz,
                                 const int32_t* __restrict__ rowidx, const int32_t* __restrict__ colind,
-                                const c128* __restrict__ F, int j0, int kv, int ldab,
+                                const c128* __restrict__ F, int j0, int kl, int ku, int ldab,
                                 c128* __restrict__ tvals, cplx<R>* __restrict__ ab, int64_t ab_stride) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int pt = blockIdx.y;
@@ -34,9 +34,10 @@ __global__ void assemble_kernel(const c128* __restrict__ vals, int J, int64_t nn
     c128 v = czero<double>();
     for (int i = 0; i < J; ++i) cfma(v, f[i], vals[(int64_t)i * nnz + k]);
     tvals[(int64_t)pt * nnz + k] = v;
-    if (ab) {
+    if (ab) {  // entries outside the factored band (an incomplete factorisation) are left out
         const int r = rowidx[k], c = colind[k];
-        ab[pt * ab_stride + (int64_t)(kv + r - c) + (int64_t)c * ldab] = ccast<R>(v);
+        if (r - c <= kl && c - r <= ku)
+            ab[pt * ab_stride + (int64_t)(kl + ku + r - c) + (int64_t)c * ldab] = ccast<R>(v);
     }
 }
 
@@ -234,7 +235,12 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
     const int64_t n = h->n, nnz = h->nnz;
     const int N = h->N, L = h->L, J = h->J;
     BandDims d;
-    RSRR_TRY(pick_dims(n, h->ord.kl, h->ord.ku, sizeof(R) == 4, &d));
+    int64_t kl = h->ord.kl, ku = h->ord.ku;
+    if (h->precond_band >= 0) {  // factor the band part only; the refinement iterates with the full T
+        kl = std::min<int64_t>(kl, h->precond_band);
+        ku = std::min<int64_t>(ku, h->precond_band);
+    }
+    RSRR_TRY(pick_dims(n, kl, ku, sizeof(R) == 4, &d));
     const int64_t nl = n * L;
     // per-point footprint
     const size_t es = sizeof(cplx<R>);
@@ -294,7 +300,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         CUDAC(cudaMemsetAsync(ab, 0, ab_b * np, st));
         {
             dim3 g((unsigned)ceil_div(nnz, 256), np);
-            { assemble_kernel<R><<<g, 256, 0, st>>>(h->d_vals, J, nnz, h->d_rowidx, h->d_colind, dF, j0, d.kv,
+            { assemble_kernel<R><<<g, 256, 0, st>>>(h->d_vals, J, nnz, h->d_rowidx, h->d_colind, dF, j0, d.kl, d.ku,
                                                   d.ldab, tvals, ab, (int64_t)(ab_b / es)); note_launch(); }
             CUDAC(cudaGetLastError());
             CUDAC(cudaMemsetAsync(colsum, 0, (size_t)n * np * 8, st));
@@ -564,6 +570,7 @@ int sample_prepare(rsrr_nep h, const double* U_reim, std::vector<c128>* Fout) {
 }
 
 bool use_dense(const rsrr_nep h) {
+    if (h->precond_band >= 0) return false;
     const int64_t n = h->n, kl = h->ord.kl, ku = h->ord.ku;
     return h->force_dense || kl > 768 || ku > 768 || (n >= 128 && 5 * (kl + ku) > 2 * n);
 }
