@@ -439,10 +439,12 @@ static int oz_max(const c128* X, int64_t ld, int64_t sb, int op, int U, int V, i
     return RSRR_OK;
 }
 
-// Worth it when the FP64 GEMM would take a while and both output sides fill tiles reasonably.
+// Worth it when the FP64 GEMM would take a while.  A thin output side (the moments' 2K columns,
+// the traces' J columns) wastes most of a 32-column tile, but the FP64 kernel wastes more of
+// its 64 x 64 tile on such shapes (measured 0.05-0.07 TFLOP/s on the moments and traces).
 bool zgemm_tc_fits(const Zgemm& g) {
     const double work = 8.0 * g.M * (double)g.N * g.K * g.batch;
-    return work >= 4e8 && std::min(g.M, g.N) >= 16 && g.K >= 16;
+    return work >= 4e8 && g.K >= 16;
 }
 
 int zgemm_tc(const Zgemm& g0, cudaStream_t s) {
