@@ -301,8 +301,9 @@ def run_ours(args):
                 "achieved": jac_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": (jac_tf / FP64_PEAK_TFLOPS) if jac_tf else None, "traffic": None,
                 "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s); an FMA probe measured 1.19",
-                "algorithmic": "per sweep and column pair of an mb-row matrix: 40 mb real flops, + 24 k for the "
-                               "accumulated rotations (k columns)", "ms_per_step": jac_ms}
+                "algorithmic": "per sweep: 4 mb k for the column norms, 8 mb per pair whose inner product is "
+                               "formed, 32 mb + 24 k per rotated pair (rotation of B and of the k-row J, new "
+                               "norms); pairs and rotations counted by the kernel", "ms_per_step": jac_ms}
     phases["zgemm_ms"] = zg_ms
     phases["zgemm_tc_ms"] = tc_ms
     phases["jacobi_ms"] = jac_ms

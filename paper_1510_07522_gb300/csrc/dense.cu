@@ -300,10 +300,16 @@ void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, dou
 
 // ---------------------------------------------------------------------------------------------
 // One-sided Jacobi.  A sweep is one cooperative kernel: round-robin rounds separated by grid
-// barriers, one warp per column pair.  A pair is rotated when its inner product is above
-// tol relative to the column norms and both columns are above an absolute floor: columns
-// below the floor are rounding noise, and rotating them against anything changes no
-// column above the floor by more than the floor itself.
+// barriers, one CTA per column pair.  A pair is rotated when its inner product is above tol
+// relative to the column norms and both columns are above an absolute floor: columns below the
+// floor are rounding noise, and rotating them against anything changes no column above the floor
+// by more than the floor itself.
+//
+// The squared column norms live in a small array: computed once at the start of the sweep and
+// recomputed from the rotated entries by the CTA that rotates a pair, so they are always the sums
+// a fresh pass over the stored columns would give.  A pair then costs one complex inner product
+// (4 FP64 fused multiply-adds a row) when it is not rotated, nothing when a column is below the
+// floor, and the columns it rotates are held in registers between the two passes.
 // ---------------------------------------------------------------------------------------------
 namespace {
 __device__ __forceinline__ int rr_pos(int k, int r, int n) {  // player at seat k in round r
@@ -315,40 +321,90 @@ struct JacobiArgs {
     int mb, kk, npad;
     c128* J;
     double tol, floor2, abs_g;
+    double* nrm2;  // squared column norms of B (kk entries)
     unsigned long long* max_off;
-    int* rotations;
+    int* rotations;  // [0] pairs rotated, [1] pairs whose inner product was formed
     GridBar gb;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
+// Two block-wide sums; every thread gets both, summed in the same order (two CTA barriers).
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double red2_[2][33];
+    for (int off = 16; off; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { red2_[0][w] = a; red2_[1][w] = b; }
+    __syncthreads();
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < nw; ++i) {
+        s0 += red2_[0][i];
+        s1 += red2_[1][i];
+    }
+    a = s0;
+    b = s1;
 }
 
-__global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
+constexpr int kJacThreads = 256;
+constexpr int kJacCache = 3;  // rows per thread kept in registers (columns up to 768 rows)
+
+__device__ __forceinline__ void jac_norm_acc(double& acc, c128 x) { acc = fma(x.re, x.re, fma(x.im, x.im, acc)); }
+// conj(x) y accumulated into (gr, gi)
+__device__ __forceinline__ void jac_dot_acc(double& gr, double& gi, c128 x, c128 y) {
+    gr = fma(x.re, y.re, fma(x.im, y.im, gr));
+    gi = fma(x.re, y.im, fma(-x.im, y.re, gi));
+}
+// (x, y) <- (c x - sp y, s x + cp y): the rotation with the phase folded into the two complex
+// coefficients (12 FP64 operations a row)
+__device__ __forceinline__ void jac_rotate(c128& x, c128& y, double c, double s, c128 sp, c128 cp) {
+    const c128 nx = mk<double>(fma(-sp.re, y.re, fma(sp.im, y.im, c * x.re)),
+                               fma(-sp.re, y.im, fma(-sp.im, y.re, c * x.im)));
+    const c128 ny = mk<double>(fma(cp.re, y.re, fma(-cp.im, y.im, s * x.re)),
+                               fma(cp.re, y.im, fma(cp.im, y.re, s * x.im)));
+    x = nx;
+    y = ny;
+}
+
+__global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs a) {
     // one CTA per column pair (CTAs loop over the pairs of a round), so every round spreads
     // its FP64 work over all SMs
     const int tid = threadIdx.x;
-    __shared__ double sh[4];
+    for (int c = blockIdx.x; c < a.kk; c += gridDim.x) {
+        const c128* bc = a.B + (int64_t)c * a.mb;
+        double s = 0.0, unused = 0.0;
+        for (int r = tid; r < a.mb; r += kJacThreads) jac_norm_acc(s, bc[r]);
+        block_sum2(s, unused);
+        if (tid == 0) a.nrm2[c] = s;
+    }
+    if (!grid_sync(a.gb)) return;
     for (int round = 0; round < a.npad - 1; ++round) {
         for (int i = blockIdx.x; i < a.npad / 2; i += gridDim.x) {
             int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
             if (p > q) { const int t = p; p = q; q = t; }
             if (q >= a.kk) continue;  // uniform across the CTA
+            const double al = __ldcg(a.nrm2 + p), be = __ldcg(a.nrm2 + q);
+            if (fmin(al, be) <= a.floor2) continue;  // uniform
             c128* bp = a.B + (int64_t)p * a.mb;
             c128* bq = a.B + (int64_t)q * a.mb;
-            double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-#pragma unroll 2
-            for (int r = tid; r < a.mb; r += 256) {
-                const c128 x = bp[r], y = bq[r];
-                al += cnorm2(x);
-                be += cnorm2(y);
-                gr += x.re * y.re + x.im * y.im;  // conj(x) y
-                gi += x.re * y.im - x.im * y.re;
+            c128 xc[kJacCache], yc[kJacCache];
+            double gr = 0.0, gi = 0.0;
+#pragma unroll
+            for (int u = 0; u < kJacCache; ++u) {
+                const int r = tid + kJacThreads * u;
+                xc[u] = yc[u] = czero<double>();
+                if (r < a.mb) {
+                    xc[u] = bp[r];
+                    yc[u] = bq[r];
+                    jac_dot_acc(gr, gi, xc[u], yc[u]);
+                }
             }
-            block_sum4(al, be, gr, gi);
+            for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads) jac_dot_acc(gr, gi, bp[r], bq[r]);
+            block_sum2(gr, gi);
+            if (tid == 0) atomicAdd(a.rotations + 1, 1);
             const double g = sqrt(gr * gr + gi * gi);
-            if (fmin(al, be) <= a.floor2 || g <= a.abs_g) continue;  // uniform
+            if (g <= a.abs_g) continue;  // uniform
             const double off = g / sqrt(al * be);
             if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
             if (off <= a.tol) continue;  // uniform
@@ -356,35 +412,48 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(JacobiArgs a) {
             const double zeta = (be - al) / (2.0 * g);
             const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-            // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q), the phase folded
-            // into the two complex coefficients (12 FP64 operations per row)
+            // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q)
             const c128 sp = cscale(ph, s), cp = cscale(ph, c);
-#pragma unroll 2
-            for (int r = tid; r < a.mb; r += 256) {
-                const c128 x = bp[r], y = bq[r];
-                bp[r] = mk<double>(fma(-sp.re, y.re, fma(sp.im, y.im, c * x.re)),
-                                   fma(-sp.re, y.im, fma(-sp.im, y.re, c * x.im)));
-                bq[r] = mk<double>(fma(cp.re, y.re, fma(-cp.im, y.im, s * x.re)),
-                                   fma(cp.re, y.im, fma(cp.im, y.re, s * x.im)));
+            double an = 0.0, bn = 0.0;
+#pragma unroll
+            for (int u = 0; u < kJacCache; ++u) {
+                const int r = tid + kJacThreads * u;
+                if (r < a.mb) {
+                    jac_rotate(xc[u], yc[u], c, s, sp, cp);
+                    bp[r] = xc[u];
+                    bq[r] = yc[u];
+                    jac_norm_acc(an, xc[u]);
+                    jac_norm_acc(bn, yc[u]);
+                }
+            }
+            for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads) {
+                c128 x = bp[r], y = bq[r];
+                jac_rotate(x, y, c, s, sp, cp);
+                bp[r] = x;
+                bq[r] = y;
+                jac_norm_acc(an, x);
+                jac_norm_acc(bn, y);
             }
             if (a.J) {
                 c128* jp = a.J + (int64_t)p * a.kk;
                 c128* jq = a.J + (int64_t)q * a.kk;
 #pragma unroll 2
-                for (int r = tid; r < a.kk; r += 256) {
-                    const c128 x = jp[r], y = jq[r];
-                    jp[r] = mk<double>(fma(-sp.re, y.re, fma(sp.im, y.im, c * x.re)),
-                                       fma(-sp.re, y.im, fma(-sp.im, y.re, c * x.im)));
-                    jq[r] = mk<double>(fma(cp.re, y.re, fma(-cp.im, y.im, s * x.re)),
-                                       fma(cp.re, y.im, fma(cp.im, y.re, s * x.im)));
+                for (int r = tid; r < a.kk; r += kJacThreads) {
+                    c128 x = jp[r], y = jq[r];
+                    jac_rotate(x, y, c, s, sp, cp);
+                    jp[r] = x;
+                    jq[r] = y;
                 }
             }
-            if (tid == 0) atomicAdd(a.rotations, 1);
-            __syncthreads();
+            block_sum2(an, bn);
+            if (tid == 0) {
+                a.nrm2[p] = an;
+                a.nrm2[q] = bn;
+                atomicAdd(a.rotations, 1);
+            }
         }
         if (!grid_sync(a.gb)) return;
     }
-    (void)sh;
 }
 }  // namespace
 
@@ -407,18 +476,20 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     int dev = 0, nsm = 0, occ = 0;
     RSRR_CUDA(cudaGetDevice(&dev));
     RSRR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, 256, 0));
+    RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, kJacThreads, 0));
     if (occ < 1) return set_error(RSRR_ECUDA, "jacobi kernel cannot be resident");
     const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 4), npad / 2);
     unsigned long long* dmax = nullptr;
     int* drot = nullptr;
     unsigned* bar = nullptr;
+    double* dn2 = nullptr;
+    RSRR_TRY(dalloc_n(&dn2, (size_t)k, s));
     RSRR_TRY(dalloc_n(&dmax, 1, s));
-    RSRR_TRY(dalloc_n(&drot, 1, s));
+    RSRR_TRY(dalloc_n(&drot, 2, s));
     RSRR_TRY(dalloc_n(&bar, kGridBarWords, s));
     cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s);
     JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
-                  dmax, drot, grid_bar_at(bar)};
+                  dn2, dmax, drot, grid_bar_at(bar)};
     // Before each sweep the columns (and J's with them) are put in order of decreasing norm: the
     // round-robin pairs then meet in an order that converges in fewer sweeps, and the caller,
     // which sorts the final column norms itself, sees no difference.
@@ -450,7 +521,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
             }
         }
         cudaMemsetAsync(dmax, 0, 8, s);
-        cudaMemsetAsync(drot, 0, 4, s);
+        cudaMemsetAsync(drot, 0, 8, s);
         void* args[] = {&ja};
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (g_jprof.on) {
@@ -458,29 +529,32 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
             cudaEventCreate(&eb);
             cudaEventRecord(ea, s);
         }
-        cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_sweep_kernel, G, 256, args, 0, s);
+        cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_sweep_kernel, G, kJacThreads, args, 0, s);
         note_launch();
         if (g_jprof.on) {
             cudaEventRecord(eb, s);
             g_jprof.ev.emplace_back(ea, eb);
-            // algorithmic work of a full sweep: per column pair, three inner products over mb rows
-            // (16 real flops a row) and the rotation of both columns (24 a row), of B and of J
-            g_jprof.flops += 0.5 * k * (k - 1.0) * (40.0 * mb + (J ? 24.0 * k : 0.0));
         }
         if (e != cudaSuccess) { rc = set_error(RSRR_ECUDA, cudaGetErrorString(e)); break; }
-        int hrot = 0, herr = 0;
+        int hrot[2] = {0, 0}, herr = 0;
         unsigned long long hmax = 0;
-        cudaMemcpyAsync(&hrot, drot, 4, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hrot, drot, 8, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&herr, bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
         if (herr) { rc = set_error(RSRR_ETIMEOUT, "grid barrier gave up in the Jacobi sweep"); break; }
+        // the sweep's work: the column norms (4 real flops a row), one complex inner product for
+        // every pair formed (8 a row), and for every rotated pair the rotation of both columns of
+        // B and J (24 a row each) and the two new norms (8 a row)
+        if (g_jprof.on)
+            g_jprof.flops += 4.0 * mb * k + 8.0 * mb * hrot[1] + hrot[0] * (32.0 * mb + (J ? 24.0 * k : 0.0));
         double off;
         std::memcpy(&off, &hmax, 8);
         // converged: no rotation left, or every pair above the floor orthogonal to `conv` (the
         // remaining effect on the singular values is of second order in that number)
-        if (hrot == 0 || off <= conv) { ++sweep; break; }
+        if (hrot[0] == 0 || off <= conv) { ++sweep; break; }
     }
+    dfree(dn2, s);
     dfree(dmax, s);
     dfree(drot, s);
     dfree(bar, s);
