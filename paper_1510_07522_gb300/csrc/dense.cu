@@ -299,8 +299,8 @@ void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, dou
 }
 
 // ---------------------------------------------------------------------------------------------
-// One-sided Jacobi.  A sweep is one cooperative kernel: round-robin rounds separated by grid
-// barriers, one CTA per column pair.  A pair is rotated when its inner product is above tol
+// One-sided Jacobi.  A sweep is one cooperative kernel over the round-robin rounds, one CTA per
+// column pair, each pair ordered after the two pairs of the previous round that held its columns.  A pair is rotated when its inner product is above tol
 // relative to the column norms and both columns are above an absolute floor: columns below the
 // floor are rounding noise, and rotating them against anything changes no column above the floor
 // by more than the floor itself.
@@ -322,6 +322,7 @@ struct JacobiArgs {
     c128* J;
     double tol, floor2, abs_g;
     double* nrm2;  // squared column norms of B (kk entries)
+    int* ver;      // rounds each column has finished in this sweep (kk entries, zero at launch)
     unsigned long long* max_off;
     int* rotations;  // [0] pairs rotated, [1] pairs whose inner product was formed
     GridBar gb;
@@ -348,6 +349,11 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 }
 
 constexpr int kJacThreads = 256;
+// Columns are read past L1: between rounds they are rewritten by CTAs on other SMs.
+__device__ __forceinline__ c128 ldcg_c(const c128* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk<double>(v.x, v.y);
+}
 constexpr int kJacCache = 3;  // rows per thread kept in registers (columns up to 768 rows)
 
 __device__ __forceinline__ void jac_norm_acc(double& acc, c128 x) { acc = fma(x.re, x.re, fma(x.im, x.im, acc)); }
@@ -367,14 +373,107 @@ __device__ __forceinline__ void jac_rotate(c128& x, c128& y, double c, double s,
     y = ny;
 }
 
-__global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs a) {
-    // one CTA per column pair (CTAs loop over the pairs of a round), so every round spreads
-    // its FP64 work over all SMs
+// One column pair (p, q) of a round, p < q < kk; every thread of the CTA takes the same branches.
+__device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
     const int tid = threadIdx.x;
+    const double al = __ldcg(a.nrm2 + p), be = __ldcg(a.nrm2 + q);
+    if (fmin(al, be) <= a.floor2) return;
+    c128* bp = a.B + (int64_t)p * a.mb;
+    c128* bq = a.B + (int64_t)q * a.mb;
+    c128 xc[kJacCache], yc[kJacCache];
+    double gr = 0.0, gi = 0.0;
+#pragma unroll
+    for (int u = 0; u < kJacCache; ++u) {
+        const int r = tid + kJacThreads * u;
+        xc[u] = yc[u] = czero<double>();
+        if (r < a.mb) {
+            xc[u] = ldcg_c(bp + r);
+            yc[u] = ldcg_c(bq + r);
+            jac_dot_acc(gr, gi, xc[u], yc[u]);
+        }
+    }
+    for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads)
+        jac_dot_acc(gr, gi, ldcg_c(bp + r), ldcg_c(bq + r));
+    block_sum2(gr, gi);
+    if (tid == 0) atomicAdd(a.rotations + 1, 1);
+    const double g = sqrt(gr * gr + gi * gi);
+    if (g <= a.abs_g) return;
+    const double off = g / sqrt(al * be);
+    if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
+    if (off <= a.tol) return;
+    const c128 ph = mk<double>(gr / g, -gi / g);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
+    const double zeta = (be - al) / (2.0 * g);
+    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+    // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q)
+    const c128 sp = cscale(ph, s), cp = cscale(ph, c);
+    double an = 0.0, bn = 0.0;
+#pragma unroll
+    for (int u = 0; u < kJacCache; ++u) {
+        const int r = tid + kJacThreads * u;
+        if (r < a.mb) {
+            jac_rotate(xc[u], yc[u], c, s, sp, cp);
+            bp[r] = xc[u];
+            bq[r] = yc[u];
+            jac_norm_acc(an, xc[u]);
+            jac_norm_acc(bn, yc[u]);
+        }
+    }
+    for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads) {
+        c128 x = ldcg_c(bp + r), y = ldcg_c(bq + r);
+        jac_rotate(x, y, c, s, sp, cp);
+        bp[r] = x;
+        bq[r] = y;
+        jac_norm_acc(an, x);
+        jac_norm_acc(bn, y);
+    }
+    if (a.J) {
+        c128* jp = a.J + (int64_t)p * a.kk;
+        c128* jq = a.J + (int64_t)q * a.kk;
+        for (int r = tid; r < a.kk; r += kJacThreads) {
+            c128 x = ldcg_c(jp + r), y = ldcg_c(jq + r);
+            jac_rotate(x, y, c, s, sp, cp);
+            jp[r] = x;
+            jq[r] = y;
+        }
+    }
+    block_sum2(an, bn);
+    if (tid == 0) {
+        a.nrm2[p] = an;
+        a.nrm2[q] = bn;
+        atomicAdd(a.rotations, 1);
+    }
+}
+
+// Thread 0 waits until column c has finished `target` rounds.  Bounded: after the spin limit, or
+// once another CTA has reported a timeout, it records the failure and returns false.
+__device__ __forceinline__ bool jac_wait(const int* ver, int c, int target, int* err) {
+    const volatile int* v = ver + c;
+    long long spins = 0;
+    unsigned backoff = 16;
+    while (*v < target) {
+        if (++spins > (1LL << 24) || *(volatile int*)err != 0) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(backoff);
+        if (backoff < 256) backoff <<= 1;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs a) {
+    // One CTA per column pair (CTAs loop over the pairs of a round), so every round spreads its
+    // FP64 work over all SMs.  The rounds are not separated by grid barriers: a pair of round r
+    // starts as soon as both of its columns have come out of round r - 1 (a per-column count of
+    // finished rounds), so a slow pair holds up only the pairs that need its columns.  The pairs,
+    // their order and every value are those of the barrier-separated sweep.
+    const int tid = threadIdx.x;
+    __shared__ int s_ok;
     for (int c = blockIdx.x; c < a.kk; c += gridDim.x) {
         const c128* bc = a.B + (int64_t)c * a.mb;
         double s = 0.0, unused = 0.0;
-        for (int r = tid; r < a.mb; r += kJacThreads) jac_norm_acc(s, bc[r]);
+        for (int r = tid; r < a.mb; r += kJacThreads) jac_norm_acc(s, ldcg_c(bc + r));
         block_sum2(s, unused);
         if (tid == 0) a.nrm2[c] = s;
     }
@@ -383,76 +482,22 @@ __global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs
         for (int i = blockIdx.x; i < a.npad / 2; i += gridDim.x) {
             int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
             if (p > q) { const int t = p; p = q; q = t; }
-            if (q >= a.kk) continue;  // uniform across the CTA
-            const double al = __ldcg(a.nrm2 + p), be = __ldcg(a.nrm2 + q);
-            if (fmin(al, be) <= a.floor2) continue;  // uniform
-            c128* bp = a.B + (int64_t)p * a.mb;
-            c128* bq = a.B + (int64_t)q * a.mb;
-            c128 xc[kJacCache], yc[kJacCache];
-            double gr = 0.0, gi = 0.0;
-#pragma unroll
-            for (int u = 0; u < kJacCache; ++u) {
-                const int r = tid + kJacThreads * u;
-                xc[u] = yc[u] = czero<double>();
-                if (r < a.mb) {
-                    xc[u] = bp[r];
-                    yc[u] = bq[r];
-                    jac_dot_acc(gr, gi, xc[u], yc[u]);
-                }
-            }
-            for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads) jac_dot_acc(gr, gi, bp[r], bq[r]);
-            block_sum2(gr, gi);
-            if (tid == 0) atomicAdd(a.rotations + 1, 1);
-            const double g = sqrt(gr * gr + gi * gi);
-            if (g <= a.abs_g) continue;  // uniform
-            const double off = g / sqrt(al * be);
-            if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
-            if (off <= a.tol) continue;  // uniform
-            const c128 ph = mk<double>(gr / g, -gi / g);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
-            const double zeta = (be - al) / (2.0 * g);
-            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-            // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q)
-            const c128 sp = cscale(ph, s), cp = cscale(ph, c);
-            double an = 0.0, bn = 0.0;
-#pragma unroll
-            for (int u = 0; u < kJacCache; ++u) {
-                const int r = tid + kJacThreads * u;
-                if (r < a.mb) {
-                    jac_rotate(xc[u], yc[u], c, s, sp, cp);
-                    bp[r] = xc[u];
-                    bq[r] = yc[u];
-                    jac_norm_acc(an, xc[u]);
-                    jac_norm_acc(bn, yc[u]);
-                }
-            }
-            for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads) {
-                c128 x = bp[r], y = bq[r];
-                jac_rotate(x, y, c, s, sp, cp);
-                bp[r] = x;
-                bq[r] = y;
-                jac_norm_acc(an, x);
-                jac_norm_acc(bn, y);
-            }
-            if (a.J) {
-                c128* jp = a.J + (int64_t)p * a.kk;
-                c128* jq = a.J + (int64_t)q * a.kk;
-#pragma unroll 2
-                for (int r = tid; r < a.kk; r += kJacThreads) {
-                    c128 x = jp[r], y = jq[r];
-                    jac_rotate(x, y, c, s, sp, cp);
-                    jp[r] = x;
-                    jq[r] = y;
-                }
-            }
-            block_sum2(an, bn);
+            const bool real_pair = q < a.kk;  // q == kk is the padding column of an odd count
             if (tid == 0) {
-                a.nrm2[p] = an;
-                a.nrm2[q] = bn;
-                atomicAdd(a.rotations, 1);
+                const bool ok = jac_wait(a.ver, p, round, a.gb.err) && (!real_pair || jac_wait(a.ver, q, round, a.gb.err));
+                __threadfence();
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            if (real_pair) jac_pair(a, p, q);
+            __syncthreads();  // every store of the pair issued
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(a.ver + p, round + 1);
+                if (real_pair) atomicExch(a.ver + q, round + 1);
             }
         }
-        if (!grid_sync(a.gb)) return;
     }
 }
 }  // namespace
@@ -483,13 +528,15 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     int* drot = nullptr;
     unsigned* bar = nullptr;
     double* dn2 = nullptr;
+    int* dver = nullptr;
     RSRR_TRY(dalloc_n(&dn2, (size_t)k, s));
+    RSRR_TRY(dalloc_n(&dver, (size_t)k, s));
     RSRR_TRY(dalloc_n(&dmax, 1, s));
     RSRR_TRY(dalloc_n(&drot, 2, s));
     RSRR_TRY(dalloc_n(&bar, kGridBarWords, s));
     cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s);
     JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
-                  dn2, dmax, drot, grid_bar_at(bar)};
+                  dn2, dver, dmax, drot, grid_bar_at(bar)};
     // Before each sweep the columns (and J's with them) are put in order of decreasing norm: the
     // round-robin pairs then meet in an order that converges in fewer sweeps, and the caller,
     // which sorts the final column norms itself, sees no difference.
@@ -522,6 +569,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         }
         cudaMemsetAsync(dmax, 0, 8, s);
         cudaMemsetAsync(drot, 0, 8, s);
+        cudaMemsetAsync(dver, 0, (size_t)k * sizeof(int), s);
         void* args[] = {&ja};
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (g_jprof.on) {
@@ -542,7 +590,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         cudaMemcpyAsync(&herr, bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
-        if (herr) { rc = set_error(RSRR_ETIMEOUT, "grid barrier gave up in the Jacobi sweep"); break; }
+        if (herr) { rc = set_error(RSRR_ETIMEOUT, "a wait in the Jacobi sweep gave up"); break; }
         // the sweep's work: the column norms (4 real flops a row), one complex inner product for
         // every pair formed (8 a row), and for every rotated pair the rotation of both columns of
         // B and J (24 a row each) and the two new norms (8 a row)
@@ -555,6 +603,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         if (hrot[0] == 0 || off <= conv) { ++sweep; break; }
     }
     dfree(dn2, s);
+    dfree(dver, s);
     dfree(dmax, s);
     dfree(drot, s);
     dfree(bar, s);
