@@ -328,24 +328,26 @@ struct JacobiArgs {
     GridBar gb;
 };
 
-// Two block-wide sums; every thread gets both, summed in the same order (two CTA barriers).
+// Two block-wide sums; every thread gets both, summed in the same order (two CTA barriers).  The
+// per-warp partials are combined by a shuffle tree in every warp (log2 of the warp count FP64
+// additions a thread), not by a loop over them: FP64 issue slots are the scarce resource here.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-    __shared__ double red2_[2][33];
+    __shared__ double red2_[2][32];
     for (int off = 16; off; off >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, off);
         b += __shfl_down_sync(0xffffffffu, b, off);
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) { red2_[0][w] = a; red2_[1][w] = b; }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red2_[0][w] = a; red2_[1][w] = b; }
     __syncthreads();
-    double s0 = 0.0, s1 = 0.0;
-    for (int i = 0; i < nw; ++i) {
-        s0 += red2_[0][i];
-        s1 += red2_[1][i];
+    double s0 = lane < nw ? red2_[0][lane] : 0.0, s1 = lane < nw ? red2_[1][lane] : 0.0;
+    for (int off = nw >> 1; off; off >>= 1) {  // nw is a power of two
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
     }
-    a = s0;
-    b = s1;
+    a = __shfl_sync(0xffffffffu, s0, 0);
+    b = __shfl_sync(0xffffffffu, s1, 0);
 }
 
 constexpr int kJacThreads = 256;
@@ -395,18 +397,38 @@ __device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
     for (int r = tid + kJacThreads * kJacCache; r < a.mb; r += kJacThreads)
         jac_dot_acc(gr, gi, ldcg_c(bp + r), ldcg_c(bq + r));
     block_sum2(gr, gi);
-    if (tid == 0) atomicAdd(a.rotations + 1, 1);
-    const double g = sqrt(gr * gr + gi * gi);
-    if (g <= a.abs_g) return;
-    const double off = g / sqrt(al * be);
-    if (tid == 0) atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
-    if (off <= a.tol) return;
-    const c128 ph = mk<double>(gr / g, -gi / g);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
-    const double zeta = (be - al) / (2.0 * g);
-    const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+    // the decision and the rotation are computed once, by thread 0, and shared
+    __shared__ double s_par[6];
+    __shared__ int s_act;
+    if (tid == 0) {
+        atomicAdd(a.rotations + 1, 1);
+        int act = 0;
+        const double g = sqrt(gr * gr + gi * gi);
+        if (g > a.abs_g) {
+            const double off = g / sqrt(al * be);
+            atomicMax(a.max_off, (unsigned long long)__double_as_longlong(off));
+            if (off > a.tol) {
+                const double ig = 1.0 / g;
+                const c128 ph = mk<double>(gr * ig, -gi * ig);  // e^{-i phi}, phi = arg(conj(b_p) b_q)
+                const double zeta = (be - al) * (0.5 * ig);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                s_par[0] = c;
+                s_par[1] = sn;
+                s_par[2] = ph.re * sn;
+                s_par[3] = ph.im * sn;
+                s_par[4] = ph.re * c;
+                s_par[5] = ph.im * c;
+                act = 1;
+            }
+        }
+        s_act = act;
+    }
+    __syncthreads();
+    if (!s_act) return;
     // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q)
-    const c128 sp = cscale(ph, s), cp = cscale(ph, c);
+    const double c = s_par[0], s = s_par[1];
+    const c128 sp = mk<double>(s_par[2], s_par[3]), cp = mk<double>(s_par[4], s_par[5]);
     double an = 0.0, bn = 0.0;
 #pragma unroll
     for (int u = 0; u < kJacCache; ++u) {
