@@ -79,3 +79,34 @@ def test_product_path_never_loads_the_oracle():
         if f.endswith(".py"):
             src = open(os.path.join(ROOT, "oracle", f)).read()
             assert not re.search(r"^\s*(import|from)\s+paper_1510_07522_gb300", src, flags=re.M), f
+
+
+def test_argument_checks_of_the_later_entry_points(rs):
+    """Entry points beyond the core four reject a NULL handle, and rsrr_zgemm rejects a bad path,
+    operation or leading dimension, before any device work."""
+    L = rs.lib()
+    k = ctypes.c_int32()
+    assert L.rsrr_project_moments(None, 4, 1e-14, ctypes.byref(k)) == -1
+    assert L.rsrr_project_chebyshev(None, 8, -1.0, 1.0, 1e-14, ctypes.byref(k)) == -1
+    assert L.rsrr_set_band_preconditioner(None, 3) == -1
+    assert L.rsrr_solve(None, 500, 2, 1e10, 10, None, None, None, None) == -1
+    assert L.rsrr_sample_points(None, None, 4, None, 1, None, 0, 1e-10, 1) == -1
+    info = ctypes.create_string_buffer(4096)
+    assert L.rsrr_get_info(None, info) == -1
+    buf = np.zeros(64)
+    one = np.array([1.0, 0.0])
+    zero = np.array([0.0, 0.0])
+    p = buf.ctypes.data
+
+    def zg(path, opA, opB, M, N, K, lda, ldb, ldc, batch=1):
+        return L.rsrr_zgemm(path, opA, opB, M, N, K, one.ctypes.data, p, lda, 0, p, ldb, 0, zero.ctypes.data,
+                            p, ldc, 0, batch, None)
+
+    assert zg(3, 0, 0, 2, 2, 2, 2, 2, 2) == -1 and b"bad argument" in L.rsrr_last_error()
+    assert zg(0, 3, 0, 2, 2, 2, 2, 2, 2) == -1
+    assert zg(0, 0, 0, -1, 2, 2, 2, 2, 2) == -1
+    assert zg(0, 0, 0, 2, 2, 2, 2, 2, 2, batch=0) == -1
+    # op(A) = A is M x K: lda must be at least M; op(A) = A^H is K x M stored: lda at least K
+    assert zg(0, 0, 0, 4, 2, 3, 3, 3, 4) == -1 and b"leading dimension" in L.rsrr_last_error()
+    assert zg(0, 2, 0, 4, 2, 3, 2, 3, 4) == -1 and b"leading dimension" in L.rsrr_last_error()
+    assert zg(0, 0, 0, 4, 2, 3, 4, 3, 3) == -1 and b"leading dimension" in L.rsrr_last_error()
