@@ -300,10 +300,10 @@ void block_norm2(const c128* A, int64_t lda, int r0, int r1, int c0, int c1, dou
 
 // ---------------------------------------------------------------------------------------------
 // One-sided Jacobi.  A sweep is one cooperative kernel over the round-robin rounds, one CTA per
-// column pair, each pair ordered after the two pairs of the previous round that held its columns.  A pair is rotated when its inner product is above tol
-// relative to the column norms and both columns are above an absolute floor: columns below the
-// floor are rounding noise, and rotating them against anything changes no column above the floor
-// by more than the floor itself.
+// column pair, each pair ordered after the two pairs of the previous round that held its columns.
+// A pair is rotated when its inner product is above tol relative to the column norms and both
+// columns are above an absolute floor: columns below the floor are rounding noise, and rotating
+// them against anything changes no column above the floor by more than the floor itself.
 //
 // The squared column norms live in a small array: computed once at the start of the sweep and
 // recomputed from the rotated entries by the CTA that rotates a pair, so they are always the sums
@@ -325,7 +325,7 @@ struct JacobiArgs {
     int* ver;      // rounds each column has finished in this sweep (kk entries, zero at launch)
     unsigned long long* max_off;
     int* rotations;  // [0] pairs rotated, [1] pairs whose inner product was formed
-    GridBar gb;
+    GridBar gb;      // the barrier after the norms; its error word also records a wait that gave up
 };
 
 // Two block-wide sums; every thread gets both, summed in the same order (two CTA barriers).  The
