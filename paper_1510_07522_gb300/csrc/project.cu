@@ -510,7 +510,6 @@ int project_run(rsrr_nep h, double delta) {
     CUDAC(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CUDAC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hqr_panel_kernel, 256, 0));
     if (occ < 1) { cleanup(); return set_error(RSRR_ECUDA, "panel kernel cannot be resident"); }
-    const int G = nsm;
 
     TRYC(dalloc_n(&A, (size_t)n * m, st));
     if (Kp > 0) {
