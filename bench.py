@@ -11,8 +11,8 @@ e2e   = the same metric through the public calls from pinned host buffers: rsrr_
         rsrr_sample with the host U, project, solve with host outputs, destroy.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-For N > 1 the ranks run independent replicas (the sampling points of one NEP do not need a
-collective; see the design notes): value = all ranks' points / max rank time.
+For N > 1 the ranks run independent replicas (the sampling points of one NEP are independent
+solves, so no collective is needed): value = all ranks' points / max rank time.
 """
 import argparse
 import json
@@ -83,6 +83,7 @@ def parse():
                     help="config 3: iterative sampler - factor only each member's grid-Laplacian band (half-width "
                          "s, natural ordering) and iterate with the full T (rsrr_set_band_preconditioner)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 arm of the same workload")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="points in the CPU baseline sample (0 = cores)")
     return ap.parse_args()
@@ -148,6 +149,16 @@ def fns_of(p):
     return [(f.kind, f.params()) for f in p.fns]
 
 
+def line_config(W, args, prob, precision, world):
+    """The `config` of the JSON line, the same for this arm and the oracle (reference) arm."""
+    return dict({k: v for k, v in W.items() if k != "data"},
+                parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                tol=args.tol, precision=precision, refine="to working accuracy",
+                n=prob.n, N=prob.N, L=prob.L,
+                l2="inputs larger than L2" if prob.n * prob.N * prob.L * 16 >= 2 * 129e6 else
+                   "L2 flushed between steps (256 MB write outside the timed events)")
+
+
 def cpu_oracle_rate(prob, npts, steps=1):
     """The oracle (plain C band LU + NumPy) on the host cores: sampling points per second."""
     import oracle
@@ -184,10 +195,14 @@ def run_reference(args):
     v = npts * args.steps / el
     sample = (f"sampling phase only (band LU + L-column solves) of {npts} of the {prob.N} points per step, "
               "threads over points")
+    precision = args.precision or W["precision"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(W, parallelism="cpu threads"),
+            "data": W["data"], "config": line_config(W, args, prob, precision, 1),
+            "timed_part": (f"the oracle's sampling phase (Algorithm 2 Steps 1-2: FP64 band LU + L-column solves) "
+                           f"of {npts} of the {prob.N} points per step, on {cores} host threads; its Steps 3-5 "
+                           f"are not timed, so this rate is an upper bound on the oracle's full-pass rate"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -324,13 +339,50 @@ def run_ours(args):
             g.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, U, prec, args.tol, 20)
             g.project(W["delta"])
             lam, V, res = g.solve(W["N_S"], W["K"], 1e3, 4096, True)
-            d2h = lam.nbytes + (V.nbytes if V is not None else 0) + res.nbytes
+            eta = g.eta()   # the acceptance measure of every sample column (eta <= tol)
+            d2h = lam.nbytes + (V.nbytes if V is not None else 0) + res.nbytes + eta.nbytes
             g.close()
         barrier()
         el = time.perf_counter() - t0
         e2e_value, _ = job_value(prob.N, args.steps, 1e3 * el, device="cuda")
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    h.close()
+    # ---- the same workload in plain FP64 (complex128 LU and solves), the form the mixed
+    # precision path is measured against, at the same acceptance eta <= tol ---------------------
+    vs_fp64 = None
+    if precision == "c64" and not args.no_fp64:
+        prec64 = rs.RSRR_FP64 | rs.RSRR_REFINE_FULL
+        g = rs.Nep(prob.n, prob.rowptr, prob.colind, prob.vals, fns_of(prob), 0, sp)
+
+        def step64():
+            g.sample(prob.gamma, prob.a, prob.b, prob.N, prob.L, prob.U, prec64, args.tol, 20)
+            g.project(W["delta"])
+            g.solve(W["N_S"], W["K"], 1e3, 4096, True)
+            return g.info()
+        step64()
+        k64 = max(1, min(args.steps, 2))
+        barrier()
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
+        inf64 = []
+        for e0, e1 in ev64:
+            if flush is not None:
+                flush.random_(0, 255)
+            e0.record(stream)
+            inf64.append(step64())
+            e1.record(stream)
+        barrier()
+        g.close()
+        ms64 = sum(e0.elapsed_time(e1) for e0, e1 in ev64)
+        v64, _ = job_value(prob.N, k64, ms64, device="cuda")
+        s64 = statistics.median(i["ms_sample"] for i in inf64)
+        vs_fp64 = {"value": v64, "unit": UNIT, "steps": k64, "warmup": 1, "ms_per_step": ms64 / k64,
+                   "max_eta": max(i["max_eta"] for i in inf64), "k_S": inf64[-1]["k_S"],
+                   "sample_ms": s64, "factor": value / v64 if v64 else None,
+                   "sampling_factor": s64 / phases["sample_ms"] if phases["sample_ms"] else None,
+                   "note": "the same full pass with complex128 band LU and solves (RSRR_FP64), events on "
+                           "the same stream; factor = mixed-precision value / this value at the same tol"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -340,24 +392,19 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"sampling phase only (band LU + L-column solves) of {npts} of the {prob.N} points, "
                          f"FP64 C band LU threaded over points, {times[0]:.1f} s"}
-    h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "c64+f64" if precision == "c64" else "c128",
                 "data": W["data"],
-                "config": dict({k: v for k, v in W.items() if k != "data"},
-                               parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
-                               tol=args.tol, precision=precision, refine="to working accuracy",
-                               n=prob.n, N=prob.N, L=prob.L,
-                               l2="inputs larger than L2" if flush is None else
-                                  "L2 flushed between steps (256 MB write outside the timed events)"),
+                "config": line_config(W, args, prob, precision, world),
                 "phases_ms_median": phases, "k_S": infos[-1]["k_S"], "refine_sweeps": infos[-1]["refine_sweeps"],
                 "rows_kept": infos[-1]["rows_kept"],
                 "jacobi_sweeps": [infos[-1]["jacobi_sweeps_project"], infos[-1]["jacobi_sweeps_solve"]],
                 "max_eta": max(i["max_eta"] for i in infos), "n_eigs_inside": int(lam.size),
-                "roofline": roof, "rooflines": {"band_lu": roof_lu, "zgemm_tc": roof_tc, "jacobi": roof_jac}, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "rooflines": {"band_lu": roof_lu, "zgemm_tc": roof_tc, "jacobi": roof_jac},
+                "vs_fp64": vs_fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -374,6 +374,22 @@ int rsrr_get_hankel_sigma(rsrr_nep h, double* out);
 int rsrr_band_solve_noalloc(int64_t n, int32_t kl, int32_t ku, double* ab_reim, int32_t L, double* b_reim,
                             void* stream);
 
+/* ---- rsrr_selftest_bounded_wait (diagnostics) ---------------------------------------------
+ * The paper has no counterpart.  Every device-side wait of this library (the grid barrier of its
+ * cooperative kernels, the mbarrier waits of its tensor-core pipelines) gives up after a bounded
+ * number of polls, records the failure and lets the kernel return, and the call that launched it
+ * reports RSRR_ETIMEOUT.  This call runs one such wait with a short poll limit (well under a
+ * second) on a condition the host arranged, so that a test can check that chain without faulting
+ * or hanging the device:
+ *   kind 0  a grid barrier (2 CTAs, cooperative launch) whose arrival count starts where no CTA
+ *           can complete it: returns RSRR_ETIMEOUT
+ *   kind 1  an mbarrier wait on a phase that nothing arrives at: returns RSRR_ETIMEOUT
+ *   kind 2  the same grid barrier from a zero count: returns RSRR_OK
+ *   kind 3  the same mbarrier wait after its one expected arrival: returns RSRR_OK
+ *   stream  cudaStream_t for the work (NULL = default); returns after it completes.
+ * The device context stays usable after every kind.  Errors: EINVAL (kind), ENOMEM, ECUDA. */
+int rsrr_selftest_bounded_wait(int32_t kind, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 int64_t rsrr_kernel_launches(void);
 

@@ -6,8 +6,7 @@ baseline use this module.  Steps follow the paper's order and notation; the
 library primitives used as steps are numpy's SVD/eig/solve and scipy's sparse
 products.  Parity pins live in tests/test_oracle_*.py.
 
-Readings of the paper where it is silent or garbled (each also listed in the
-design notes):
+Readings of the paper where it is silent or garbled:
   * theta_j = 2 pi (j + 1/2) / N_S for j = 0..N_S-1 (Eq. eq-Ap-num prints j = 0..N_S).
   * V_0 / W_0 are the first nbar columns of V / W (Section 4.3 prints rows).
   * the singular-value gap rule runs over the whole SVD of H (length K k_S).

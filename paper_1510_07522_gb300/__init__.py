@@ -102,7 +102,7 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
            "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz",
-           "rsrr_zgemm", "rsrr_set_band_preconditioner"]
+           "rsrr_zgemm", "rsrr_set_band_preconditioner", "rsrr_selftest_bounded_wait"]
 
 
 def lib():
@@ -139,6 +139,7 @@ def lib():
         "rsrr_zgemm": ([I32, I32, I32, I32, I32, I32, P, P, I64, I64, P, I64, I64, P, P, I64, I64, I32, P],
                        ctypes.c_int),
         "rsrr_set_band_preconditioner": ([P, I32], ctypes.c_int),
+        "rsrr_selftest_bounded_wait": ([I32, P], ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -322,6 +323,12 @@ def rsrr_band_solve_noalloc(n, kl, ku, ab_ptr, L, b_ptr, stream=None):
     _check(lib().rsrr_band_solve_noalloc(int(n), int(kl), int(ku), ctypes.c_void_p(ab_ptr), int(L),
                                          ctypes.c_void_p(b_ptr),
                                          stream if stream is not None else current_stream()))
+
+
+def rsrr_selftest_bounded_wait(kind, stream=None):
+    """Run one bounded device wait made to run out (kind 0: grid barrier, 1: mbarrier) or to
+    complete (2, 3); raises RsrrError('ETIMEOUT') when the wait gave up."""
+    _check(lib().rsrr_selftest_bounded_wait(int(kind), ctypes.c_void_p(stream) if stream else None))
 
 
 def rsrr_destroy(h):

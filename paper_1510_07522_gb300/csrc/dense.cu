@@ -551,47 +551,67 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     unsigned* bar = nullptr;
     double* dn2 = nullptr;
     int* dver = nullptr;
-    RSRR_TRY(dalloc_n(&dn2, (size_t)k, s));
-    RSRR_TRY(dalloc_n(&dver, (size_t)k, s));
-    RSRR_TRY(dalloc_n(&dmax, 1, s));
-    RSRR_TRY(dalloc_n(&drot, 2, s));
-    RSRR_TRY(dalloc_n(&bar, kGridBarWords, s));
-    cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s);
-    JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
-                  dn2, dver, dmax, drot, grid_bar_at(bar)};
-    // Before each sweep the columns (and J's with them) are put in order of decreasing norm: the
-    // round-robin pairs then meet in an order that converges in fewer sweeps, and the caller,
-    // which sorts the final column norms itself, sees no difference.
     double* dnrm = nullptr;
     int* dperm = nullptr;
     c128* tmp = nullptr;
-    RSRR_TRY(dalloc_n(&dnrm, (size_t)k, s));
-    RSRR_TRY(dalloc_n(&dperm, (size_t)k, s));
-    RSRR_TRY(dalloc_n(&tmp, (size_t)mb * k + (J ? (size_t)k * k : 0), s));
+    auto cleanup = [&]() {
+        dfree(dn2, s);
+        dfree(dver, s);
+        dfree(dmax, s);
+        dfree(drot, s);
+        dfree(bar, s);
+        dfree(dnrm, s);
+        dfree(dperm, s);
+        dfree(tmp, s);
+    };
+    int rc = RSRR_OK;
+#define JTRY(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); return rc; } } while (0)
+    JTRY(dalloc_n(&dn2, (size_t)k, s));
+    JTRY(dalloc_n(&dver, (size_t)k, s));
+    JTRY(dalloc_n(&dmax, 1, s));
+    JTRY(dalloc_n(&drot, 2, s));
+    JTRY(dalloc_n(&bar, kGridBarWords, s));
+    // Before each sweep the columns (and J's with them) are put in order of decreasing norm: the
+    // round-robin pairs then meet in an order that converges in fewer sweeps, and the caller,
+    // which sorts the final column norms itself, sees no difference.
+    JTRY(dalloc_n(&dnrm, (size_t)k, s));
+    JTRY(dalloc_n(&dperm, (size_t)k, s));
+    JTRY(dalloc_n(&tmp, (size_t)mb * k + (J ? (size_t)k * k : 0), s));
+    if (cudaMemsetAsync(bar, 0, kGridBarWords * sizeof(unsigned), s) != cudaSuccess)
+        JTRY(set_error(RSRR_ECUDA, "jacobi: clearing the grid barrier"));
+#undef JTRY
+    JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
+                  dn2, dver, dmax, drot, grid_bar_at(bar)};
     std::vector<double> hn(k);
     std::vector<int> order(k);
-    int sweep = 0, rc = RSRR_OK;
+    int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         column_norms(B, mb, k, mb, dnrm, s);
-        cudaMemcpyAsync(hn.data(), dnrm, (size_t)k * 8, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi norms"); break; }
+        if (cudaMemcpyAsync(hn.data(), dnrm, (size_t)k * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi norms"); break; }
         for (int i = 0; i < k; ++i) order[i] = i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hn[a] > hn[b]; });
         bool sorted = true;
         for (int i = 0; i < k && sorted; ++i) sorted = order[i] == i;
         if (!sorted) {
-            cudaMemcpyAsync(dperm, order.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s);
+            if (cudaMemcpyAsync(dperm, order.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                rc = set_error(RSRR_ECUDA, "jacobi: column order upload");
+                break;
+            }
             { gather_cols_kernel<<<(unsigned)ceil_div((int64_t)mb * k, 256), 256, 0, s>>>(B, mb, k, dperm, tmp); note_launch(); }
-            cudaMemcpyAsync(B, tmp, (size_t)mb * k * sizeof(c128), cudaMemcpyDeviceToDevice, s);
-            if (J) {
+            cudaError_t ce = cudaMemcpyAsync(B, tmp, (size_t)mb * k * sizeof(c128), cudaMemcpyDeviceToDevice, s);
+            if (J && ce == cudaSuccess) {
                 c128* tj = tmp + (size_t)mb * k;
                 { gather_cols_kernel<<<(unsigned)ceil_div((int64_t)k * k, 256), 256, 0, s>>>(J, k, k, dperm, tj); note_launch(); }
-                cudaMemcpyAsync(J, tj, (size_t)k * k * sizeof(c128), cudaMemcpyDeviceToDevice, s);
+                ce = cudaMemcpyAsync(J, tj, (size_t)k * k * sizeof(c128), cudaMemcpyDeviceToDevice, s);
             }
+            if (ce != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi: column reorder"); break; }
         }
-        cudaMemsetAsync(dmax, 0, 8, s);
-        cudaMemsetAsync(drot, 0, 8, s);
-        cudaMemsetAsync(dver, 0, (size_t)k * sizeof(int), s);
+        if (cudaMemsetAsync(dmax, 0, 8, s) != cudaSuccess || cudaMemsetAsync(drot, 0, 8, s) != cudaSuccess ||
+            cudaMemsetAsync(dver, 0, (size_t)k * sizeof(int), s) != cudaSuccess) {
+            rc = set_error(RSRR_ECUDA, "jacobi: clearing the sweep counters");
+            break;
+        }
         void* args[] = {&ja};
         cudaEvent_t ea = nullptr, eb = nullptr;
         if (g_jprof.on) {
@@ -608,10 +628,10 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         if (e != cudaSuccess) { rc = set_error(RSRR_ECUDA, cudaGetErrorString(e)); break; }
         int hrot[2] = {0, 0}, herr = 0;
         unsigned long long hmax = 0;
-        cudaMemcpyAsync(hrot, drot, 8, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&herr, bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
+        if (cudaMemcpyAsync(hrot, drot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&herr, bar + kGridBarErrWord, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&hmax, dmax, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi sync"); break; }
         if (herr) { rc = set_error(RSRR_ETIMEOUT, "a wait in the Jacobi sweep gave up"); break; }
         // the sweep's work: the column norms (4 real flops a row), one complex inner product for
         // every pair formed (8 a row), and for every rotated pair the rotation of both columns of
@@ -624,14 +644,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         // remaining effect on the singular values is of second order in that number)
         if (hrot[0] == 0 || off <= conv) { ++sweep; break; }
     }
-    dfree(dn2, s);
-    dfree(dver, s);
-    dfree(dmax, s);
-    dfree(drot, s);
-    dfree(bar, s);
-    dfree(dnrm, s);
-    dfree(dperm, s);
-    dfree(tmp, s);
+    cleanup();
     if (sweeps_out) *sweeps_out = sweep;
     return rc;
 }

@@ -86,11 +86,14 @@ struct GridBar {
     unsigned* count;
     unsigned* gen;
     int* err;
+    long long spin_limit;  // polls before a wait gives up (2^24 with backoff: about a second)
 };
 // The three words sit on separate 128-byte lines: the arrival atomics on `count` must not
 // queue behind hundreds of CTAs polling `gen` in the same L2 line.
 constexpr int kGridBarWords = 96;  // allocation size in unsigned words
-inline GridBar grid_bar_at(unsigned* base) { return GridBar{base, base + 32, reinterpret_cast<int*>(base + 64)}; }
+inline GridBar grid_bar_at(unsigned* base, long long spin_limit = 1LL << 24) {
+    return GridBar{base, base + 32, reinterpret_cast<int*>(base + 64), spin_limit};
+}
 constexpr int kGridBarErrWord = 64;
 __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
     __shared__ int s_ok;
@@ -109,7 +112,7 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
             long long spins = 0;
             unsigned backoff = 8;
             while (*vgen == g) {
-                if (++spins > (1LL << 24)) {  // bounded: give up, report, return
+                if (++spins > gb.spin_limit) {  // bounded: give up, report, return
                     atomicExch(gb.err, 1);
                     ok = 0;
                     break;

@@ -9,8 +9,10 @@ their streams, and a request's factors and samples stay on the device from sampl
 Admission: a waiting request is admitted as soon as a slot is free and its estimated device
 footprint fits in what is left of the HBM budget; requests are taken in arrival order, but a
 request that does not fit yet may be passed by later, smaller ones (at most `max_bypass`
-times, so none starves).  A request refused by the device for lack of memory goes back to the
-head of the queue.
+times, so none starves).  A request refused by the device for lack of memory (ENOMEM) goes
+back to the head of the queue, but only while other requests are in flight, whose completion can
+free memory: it is not taken again before one of them completes, and after `max_retries`
+refusals, or a refusal while it ran alone, it is finished with the error.
 """
 from __future__ import annotations
 
@@ -25,18 +27,34 @@ import numpy as np
 from . import RSRR_C64_IR, RSRR_REFINE_FULL, Nep, RsrrError
 
 
-def select_admissible(pending: List["Request"], free: int, max_bypass: int) -> Optional[int]:
+def select_admissible(pending: List["Request"], free: int, max_bypass: int, completions: int = 0) -> Optional[int]:
     """Index of the oldest pending request whose footprint fits in `free` bytes, or None.
     Every older request it passes counts one bypass; a request that has been passed
-    `max_bypass` times blocks everything behind it until it fits."""
+    `max_bypass` times blocks everything behind it until it fits.  A request sent back after
+    ENOMEM waits for `completions` (the server's count of finished requests) to pass the value
+    it recorded; until then it is skipped and neither counts bypasses nor blocks."""
     for i, r in enumerate(pending):
+        if r.held_until >= completions:
+            continue
         if r.footprint <= free:
             for older in pending[:i]:
-                older.bypassed += 1
+                if older.held_until < completions:
+                    older.bypassed += 1
             return i
         if r.bypassed >= max_bypass:
             return None
     return None
+
+
+def after_enomem(req: "Request", others_inflight: int, completions: int, max_retries: int) -> bool:
+    """Decide what happens to a request the device refused for lack of memory.  Returns True to
+    requeue it (held until one more request completes), False to finish it with the error: when
+    nothing else was in flight (no completion can free memory for it) or after max_retries."""
+    req.retries += 1
+    if others_inflight == 0 or req.retries > max_retries:
+        return False
+    req.held_until = completions
+    return True
 
 
 def band_of(n: int, rowptr: np.ndarray, colind: np.ndarray):
@@ -87,6 +105,8 @@ class Request:
     k_S: int = -1
     error: Optional[str] = None
     bypassed: int = 0
+    retries: int = 0             # ENOMEM refusals so far
+    held_until: int = -1         # not admitted until more than this many requests have completed
 
     @property
     def latency(self) -> float:
@@ -94,12 +114,15 @@ class Request:
 
 
 class Server:
-    def __init__(self, budget_bytes: float = 150e9, slots: int = 4, max_bypass: int = 8, device: int = 0):
+    def __init__(self, budget_bytes: float = 150e9, slots: int = 4, max_bypass: int = 8, device: int = 0,
+                 max_retries: int = 3):
         import torch
         self.torch = torch
         self.budget = int(budget_bytes)
         self.in_use = 0
         self.max_bypass = max_bypass
+        self.max_retries = max_retries
+        self.completions = 0
         self.device = device
         self.pending: List[Request] = []
         self.done: List[Request] = []
@@ -132,7 +155,7 @@ class Server:
             self.cv.notify_all()
 
     def _take(self) -> Optional[Request]:
-        i = select_admissible(self.pending, self.budget - self.in_use, self.max_bypass)
+        i = select_admissible(self.pending, self.budget - self.in_use, self.max_bypass, self.completions)
         return None if i is None else self.pending.pop(i)
 
     def _worker(self, slot: int) -> None:
@@ -154,7 +177,7 @@ class Server:
                 self.inflight += 1
                 self.peak_inflight = max(self.peak_inflight, self.inflight)
                 req.t_admit = self.now()
-            retry = False
+            enomem = None
             try:
                 with torch.cuda.stream(stream):
                     h = Nep(req.n, req.rowptr, req.colind, req.vals, req.fns, 0, sp)
@@ -167,17 +190,20 @@ class Server:
                         h.close()
             except RsrrError as e:
                 if e.name == "ENOMEM":
-                    retry = True
+                    enomem = str(e)
                 else:
                     req.error = str(e)
             with self.cv:
                 self.in_use -= req.footprint
                 self.inflight -= 1
-                if retry:
+                if enomem is not None and after_enomem(req, self.inflight, self.completions, self.max_retries):
                     self.pending.insert(0, req)
                 else:
+                    if enomem is not None:
+                        req.error = enomem
                     req.t_done = self.now()
                     self.done.append(req)
+                    self.completions += 1
                 self.cv.notify_all()
 
     def wait(self, count: int, timeout: float = 3600.0) -> List[Request]:

@@ -110,3 +110,8 @@ def test_argument_checks_of_the_later_entry_points(rs):
     assert zg(0, 0, 0, 4, 2, 3, 3, 3, 4) == -1 and b"leading dimension" in L.rsrr_last_error()
     assert zg(0, 2, 0, 4, 2, 3, 2, 3, 4) == -1 and b"leading dimension" in L.rsrr_last_error()
     assert zg(0, 0, 0, 4, 2, 3, 4, 3, 3) == -1 and b"leading dimension" in L.rsrr_last_error()
+
+
+def test_selftest_rejects_unknown_kind(rs):
+    assert rs.lib().rsrr_selftest_bounded_wait(7, None) == -1
+    assert b"kind" in rs.lib().rsrr_last_error()

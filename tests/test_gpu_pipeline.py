@@ -2,7 +2,8 @@
 Algorithm 2 Step 5) with the oracle, closed forms and the paper's printed counts.
 
 Bars: eigenvalues to relative 1e-9 (matched by minimum-cost assignment), the same count, and
-scaled residuals ||T(l) v|| / sum_i |f_i(l)| ||A_i||_F <= 1e-10 (FP64 floor, see design notes)."""
+scaled residuals ||T(l) v|| / sum_i |f_i(l)| ||A_i||_F <= 1e-10 (the raw residual's FP64 floor
+u ||T(l)|| exceeds 1e-10 on the grid problems, whose K is scaled by 1/h^2)."""
 import json
 import os
 

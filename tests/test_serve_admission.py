@@ -1,12 +1,13 @@
 """Admission logic of the RSRR server (host only): arrival order, bypass by smaller requests
-within the budget, and the bypass limit that prevents starvation."""
+within the budget, the bypass limit that prevents starvation, and what happens to a request the
+device refused for lack of memory (held until another request completes, bounded retries)."""
 from types import SimpleNamespace
 
-from paper_1510_07522_gb300.serve import footprint_bytes, select_admissible
+from paper_1510_07522_gb300.serve import after_enomem, footprint_bytes, select_admissible
 
 
-def req(fp, bypassed=0):
-    return SimpleNamespace(footprint=fp, bypassed=bypassed)
+def req(fp, bypassed=0, held_until=-1):
+    return SimpleNamespace(footprint=fp, bypassed=bypassed, held_until=held_until, retries=0)
 
 
 def test_oldest_fitting_request_first():
@@ -36,3 +37,23 @@ def test_footprint_grows_with_band_and_points():
     c = footprint_bytes(40000, 100, 100, 64, 32, 200000, 3)
     assert a > b and a > c
     assert 15e9 < a < 40e9  # 64 points of a band-200 problem: ~17.5 GB of factors plus S_hat
+
+
+def test_enomem_alone_finishes_with_error():
+    r = req(10)
+    assert after_enomem(r, others_inflight=0, completions=5, max_retries=3) is False
+
+
+def test_enomem_requeued_only_after_a_completion():
+    r = req(10)
+    assert after_enomem(r, others_inflight=2, completions=5, max_retries=3) is True
+    q = [r, req(20)]
+    assert select_admissible(q, 100, 4, completions=5) == 1     # held: skipped, not a bypass
+    assert r.bypassed == 0
+    assert select_admissible(q, 100, 4, completions=6) == 0     # one more request completed
+
+
+def test_enomem_retries_are_bounded():
+    r = req(10)
+    outcomes = [after_enomem(r, others_inflight=1, completions=k, max_retries=3) for k in range(5)]
+    assert outcomes == [True, True, True, False, False]

@@ -2,7 +2,9 @@
 with all scratch in the library's fixed device array.  Some callers cannot allocate device
 memory (their process gives all of it to its own allocator, or the call sits in a loop that
 must not allocate); this entry point serves them.  Its result must equal what rsrr_sample
-computes for the same point, on two calls in a row (the scratch array is reused)."""
+computes for the same point, on two calls in a row (the scratch array is reused), and what the
+oracle's own band LU and solves compute (Algorithm 2 Step 2): the same X, and the same U factor,
+since both pivot by |re| + |im| with ties to the lowest row."""
 import math
 
 import numpy as np
@@ -40,6 +42,11 @@ def test_noalloc_matches_rsrr_sample_twice(rs):
     ref = h.samples()
     h.close()
     ab, kl, ku = band_of_point(prob, z0)
+    import oracle
+    ab_o, ipiv_o, info_o = oracle.band_lu(ab, kl, ku)
+    assert info_o == 0
+    X_o = oracle.band_solve(ab_o, ipiv_o, kl, ku, prob.U)
+    kv = kl + ku
     dev = torch.device("cuda")
     for _ in range(2):
         d_ab = torch.from_numpy(np.ascontiguousarray(ab.T).view(np.float64).copy()).to(dev)
@@ -48,6 +55,11 @@ def test_noalloc_matches_rsrr_sample_twice(rs):
         torch.cuda.synchronize()
         X = d_b.cpu().numpy().view(np.complex128).reshape(prob.L, prob.n).T
         assert rel_err_cols(X, ref).max() < 1e-8
+        assert rel_err_cols(X, X_o).max() < 1e-8
+        # U of P A = L U: band rows 0..kv (rows <= the diagonal), element by element
+        U_dev = d_ab.cpu().numpy().view(np.complex128).reshape(prob.n, -1).T[:kv + 1]
+        U_orc = ab_o[:kv + 1]
+        assert np.abs(U_dev - U_orc).max() <= 1e-12 * np.abs(U_orc).max()
 
 
 def test_noalloc_rejects_oversized_band(rs):
