@@ -109,6 +109,10 @@ typedef struct {
 #define RSRR_DENSE_LU      0x2u  /* factor every sampling point with the dense LU, whatever the
                                     band (otherwise chosen when the band is wider than 768 or
                                     than 2n/5 for n >= 128) */
+#define RSRR_BAND_CUDA_CORES 0x4u  /* complex64 band LU on the CUDA cores for every band (otherwise
+                                    bands with 32 <= kl <= 224 run their trailing updates on the
+                                    tensor cores, with the forward solve on the stored
+                                    inv(L11), L21 inv(L11) panel blocks) */
 
 typedef struct rsrr_nep_s* rsrr_nep;
 
@@ -120,7 +124,7 @@ typedef struct rsrr_nep_s* rsrr_nep;
  *   colind    [nnz] column indices, each row's entries strictly increasing
  *   vals_reim [J][nnz][2] values of A_i on the union pattern (zeros where A_i has none)
  *   f         [J] the functions f_i
- *   flags     0, or RSRR_NATURAL_ORDER and/or RSRR_DENSE_LU
+ *   flags     0, or RSRR_NATURAL_ORDER, RSRR_DENSE_LU, RSRR_BAND_CUDA_CORES
  *   stream    cudaStream_t on which all device work of this handle runs (NULL = default)
  *   out       receives the handle
  * The library picks a row/column ordering (reverse Cuthill-McKee, or the natural one if
@@ -332,6 +336,8 @@ typedef struct {
     double ms_jacobi;           /* device time of the one-sided Jacobi sweeps (project + solve)  */
     double jacobi_gflop;        /* their algorithmic work: per sweep and column pair of an mb-row
                                    matrix, 40 mb real flops (+ 24 k for the accumulated rotations) */
+    int32_t band_lu_tc;         /* 1 if the last rsrr_sample ran the complex64 band LU with its
+                                   trailing updates on the tensor cores (kl in [32, 224])     */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

@@ -1,0 +1,783 @@
+// Complex64 band LU with partial pivoting whose trailing updates run on the tensor cores, and
+// the forward solve with its panel blocks (Algorithm 2, Step 2).  Layout in band_tc.cuh.
+//
+// Per panel of nb = 32 columns starting at k0 (right-looking, one CTA per sampling point):
+//   1. The (32 + kl) x 32 panel is staged by one TMA load: the band, read as the dense matrix
+//      D(x, c) = ab[x + c (ldab - 1)] with x = kv + i, is a 2D tensor (rows x = kv + i, columns c),
+//      and the panel is one rectangular box of it.  Entries outside the band are cleared after
+//      the load.  The panel team (4 warps) factors it with cabs1 partial pivoting (lowest row on
+//      ties), swapping whole panel rows.
+//   2. The panel team forms X = [inv(L11); W], W = L21 inv(L11) (row-wise substitutions with
+//      L11), and inv(U11) in the upper triangle of the top block, and stores X for the solves.
+//   3. The trailing update of the at most kv columns to the right, in chunks of 64 columns:
+//        x'  = the chunk's block rows in pivot order (the displaced rows below the panel take the
+//              original top rows, as getrf's interchanges do);
+//        D   = X x'_top                (256 x 32 times 32 x N, tcgen05 MMAs into tensor memory)
+//        rows 0..31 of the block  <- D (that is U12 = inv(L11) x'_top)
+//        rows 32..m-1             <- x'_below - D (that is A22 - L21 U12).
+//      The product is complex and runs as four real products, each FP32 operand split into three
+//      BF16 pieces (h + m + l, 24 significant bits) and the six piece products of order >= 2^-16
+//      accumulated in FP32 (kind::f16): FP32-level accuracy, the FP64 refinement of the sample
+//      solves sits on top.  The operand images are written to shared memory in the layout the
+//      MMA reads (K-major, 128-byte swizzle): X once per panel (two 128-row tiles), x'_top per
+//      chunk (double-buffered).
+//   Warp roles: warps 0..7 gather x'_top, write its image and run the epilogue (tensor memory ->
+//   registers, C -= D into the band); warp 8 issues the MMAs (two tensor-memory buffers, so the
+//   next chunk's MMAs run under the current chunk's epilogue); warps 9..12 factor the next panel
+//   as soon as the first chunk (the next panel's own columns) is written back (look-ahead).
+//   Every mbarrier wait is bounded; a timeout marks the point failed (info = -1).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <string>
+
+#include "band_tc.cuh"
+#include "tc.cuh"
+
+namespace rsrr {
+
+namespace {
+using namespace tc;
+
+constexpr int NB = kTcNB;
+constexpr int LDP = kTcLDP;
+constexpr int MT = 128;              // rows of one MMA tile
+constexpr int NCH = 64;              // columns per trailing chunk (the first chunk has 32)
+constexpr int kUW = 8;               // update warps (gather + image + epilogue)
+constexpr int kMW = kUW;             // the MMA warp
+constexpr int kPW0 = kUW + 1;        // first panel warp
+constexpr int kPWn = 4;              // panel warps
+constexpr int kThreads = (kUW + 1 + kPWn) * 32;
+constexpr int kUT = kUW * 32;
+constexpr int kPT = kPWn * 32;
+constexpr unsigned FULL = 0xffffffffu;
+
+// shared memory (offsets from the 1024-byte aligned base)
+constexpr int A_TILE = 3 * MT * 128;           // 3 swizzle atoms (6 planes x 32 k) per 128-row tile
+constexpr int OFF_B = 2 * A_TILE;
+constexpr int B_BUF = 3 * NCH * 128;
+constexpr int OFF_P = OFF_B + 2 * B_BUF;
+constexpr int P_BYTES = LDP * NB * 8;
+constexpr int OFF_PERM = OFF_P + P_BYTES;      // perm of the panel being applied, then of the next
+constexpr int OFF_DISP = OFF_PERM + 2 * LDP * 4;
+constexpr int SMEM_BYTES = OFF_DISP + 2 * 32 * 4 + 1024;
+constexpr uint32_t TMEM_COLS = 512;            // two buffers x two tiles x (re, im) x 64 columns
+
+struct TcbShared {
+    uint64_t bfull[2];     // the x'_top image of a buffer is written (one arrival per update warp)
+    uint64_t accfull[2];   // the MMAs into a tensor-memory buffer are complete (tcgen05.commit)
+    uint64_t accempty[2];  // the epilogue has read a tensor-memory buffer (one arrival per update warp)
+    uint64_t tma;          // the panel's TMA load
+    uint32_t tmem;
+    int fail;              // a bounded wait ran out
+    int info;              // first zero pivot column (1-based)
+    int piv;
+    int nd;                // displaced rows of the panel being applied
+    int nd_next;
+    c64 pval;
+};
+
+__device__ __forceinline__ bool failed(const TcbShared& S) { return *(const volatile int*)&S.fail != 0; }
+__device__ __forceinline__ void usync() { asm volatile("bar.sync 1, %0;" ::"n"(kUT) : "memory"); }
+__device__ __forceinline__ void psync() { asm volatile("bar.sync 2, %0;" ::"n"(kPT) : "memory"); }
+__device__ __forceinline__ void lead_wait() { asm volatile("bar.sync 3, %0;" ::"n"(kUT + kPT) : "memory"); }
+__device__ __forceinline__ void lead_arrive() { asm volatile("bar.arrive 3, %0;" ::"n"(kUT + kPT) : "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, TcbShared& S) {
+    if (failed(S)) return false;
+    if (mbar_wait(bar, parity)) return true;
+    S.fail = 1;
+    return false;
+}
+
+// Byte offset of (row r, plane q, k < 32) in an operand image of R rows: plane q lies in swizzle
+// atom q / 2 (R rows of 128 bytes), at byte 64 (q % 2) + 2 k of its row, 16-byte chunks permuted by
+// the 128-byte swizzle (chunk index XOR r mod 8).
+__device__ __forceinline__ uint32_t img_off(int R, int r, int q, int k) {
+    const uint32_t chunk = ((uint32_t)(((q & 1) << 2) | (k >> 3))) ^ (uint32_t)(r & 7);
+    return (uint32_t)(q >> 1) * (uint32_t)R * 128u + (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u +
+           chunk * 16u + (uint32_t)(k & 7) * 2u;
+}
+__device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    p[0] = h;
+    p[1] = m;
+    p[2] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+// One complex value at (r, k) of an image: planes 0..2 = re pieces, 3..5 = im pieces.
+__device__ __forceinline__ void put_elem(unsigned char* img, int R, int r, int k, c64 v) {
+    __nv_bfloat16 p[6];
+    split3(v.re, p);
+    split3(v.im, p + 3);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) *reinterpret_cast<__nv_bfloat16*>(img + img_off(R, r, q, k)) = p[q];
+}
+// Eight consecutive k (8 g .. 8 g + 7) of row r: six 16-byte stores.
+__device__ __forceinline__ void put_row8(unsigned char* img, int R, int r, int g, const c64* v) {
+    __align__(16) __nv_bfloat16 p[6][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        __nv_bfloat16 t[6];
+        split3(v[e].re, t);
+        split3(v[e].im, t + 3);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) p[q][e] = t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        *reinterpret_cast<uint4*>(img + img_off(R, r, q, 8 * g)) = *reinterpret_cast<const uint4*>(p[q]);
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)) : "memory");
+}
+
+// All MMAs of one chunk: D = X x'_top for both 128-row tiles, N columns, into tensor-memory
+// buffer `tb` (tile i: re at tb + 128 i, im at tb + 128 i + 64).  Real products (X_re x_re,
+// -X_im x_im) into re and (X_re x_im, X_im x_re) into im, six BF16 piece products each, two
+// K = 16 steps.
+__device__ __forceinline__ void issue_chunk(uint32_t a_base, uint32_t b_base, uint32_t tb, int N) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+    const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pd[4] = {0, 0, 64, 64}, ng[4] = {0, 1, 0, 0};
+    const int sa[6] = {0, 0, 1, 0, 1, 2}, sb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        uint32_t acc_r = 0, acc_i = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t id = idesc | (ng[p] ? (1u << 13) : 0u);
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+                const int qa = pa[p] * 3 + sa[s], qb = pb[p] * 3 + sb[s];
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t ao = a_base + i * A_TILE + (qa >> 1) * MT * 128 + (qa & 1) * 64 + ks * 32;
+                    const uint32_t bo = b_base + (qb >> 1) * NCH * 128 + (qb & 1) * 64 + ks * 32;
+                    uint32_t& acc = pd[p] ? acc_i : acc_r;
+                    tc_mma(tb + i * 128 + pd[p], sw128_desc(ao), sw128_desc(bo), id, acc);
+                    acc = 1;
+                }
+            }
+        }
+    }
+}
+
+struct Geo {  // one step of the factorisation (panel p applied to its trailing columns)
+    int k0, nbe, m, cb, ce, ncols, nch;
+    __device__ Geo(int p, int n, int kl, int kv) {
+        k0 = p * NB;
+        nbe = min(NB, n - k0);
+        m = min(NB + kl, n - k0);
+        cb = k0 + nbe;
+        ce = min(n, cb + kv);
+        ncols = max(0, ce - cb);
+        nch = ncols == 0 ? 0 : 1 + (max(0, ncols - NB) + NCH - 1) / NCH;
+    }
+    // chunk t: first column c0 and width w (chunk 0 is the next panel's 32 columns)
+    __device__ void chunk(int t, int& c0, int& w) const {
+        if (t == 0) { c0 = cb; w = min(NB, ncols); }
+        else { c0 = cb + NB + (t - 1) * NCH; w = min(NCH, ce - c0); }
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// Panel team: stage panel pn by TMA, factor it, write U11 / pivots / permutation, form X in place
+// and store it.  Runs on warps kPW0.. (kPT threads), barrier id 2.
+// ------------------------------------------------------------------------------------------
+__device__ void panel_step(const CUtensorMap* tmap, const FactorArgs<float>& a, c64* ab, c64* lp, int32_t* permg,
+                           int32_t* ipiv, int pn, unsigned char* base, TcbShared& S, uint32_t& ph_tma) {
+    const BandDims& d = a.d;
+    const int ptid = threadIdx.x - kPW0 * 32, lane = ptid & 31, pw = ptid >> 5;
+    const int n = d.n, kl = d.kl, kv = d.kv, ldab = d.ldab;
+    const int k0 = pn * NB, nbe = min(NB, n - k0), m = min(NB + kl, n - k0);
+    c64* P = reinterpret_cast<c64*>(base + OFF_P);
+    int* psm = reinterpret_cast<int*>(base + OFF_PERM) + LDP;  // the next panel's permutation
+    int* dq = reinterpret_cast<int*>(base + OFF_DISP);
+    // 1. stage: one box of LDP x NB of the band's dense view
+    if (ptid == 0 && !failed(S)) {
+        mbar_expect_tx(&S.tma, (uint32_t)P_BYTES);
+        tma_load_3d(P, tmap, kv + k0, k0, (int)blockIdx.x, &S.tma);
+    }
+    for (int q = ptid; q < LDP; q += kPT) psm[q] = q;
+    wait_or_fail(&S.tma, ph_tma, S);
+    ph_tma ^= 1;
+    // entries outside the band, past the matrix, or past the panel's columns are zero; a column
+    // t >= nbe (last panel only) gets a unit diagonal so the inverses below stay the identity there
+    for (int idx = ptid; idx < LDP * NB; idx += kPT) {
+        const int q = idx % LDP, t = idx / LDP;
+        if (t >= nbe) P[idx] = (q == t) ? mk<float>(1.f, 0.f) : czero<float>();
+        else if (q >= m || q - t > kl) P[idx] = czero<float>();
+    }
+    psync();
+    // 2. factor (two team barriers per column)
+    auto search = [&](int col, int first, int last) {
+        float best = -1.f;
+        int bi = first;
+        for (int q = first + lane; q <= last; q += 32) {
+            const float v = cabs1(P[q + col * LDP]);
+            if (v > best) { best = v; bi = q; }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            const float ob = __shfl_down_sync(FULL, best, off);
+            const int oi = __shfl_down_sync(FULL, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+            S.piv = bi;
+            S.pval = P[bi + col * LDP];
+        }
+    };
+    if (pw == 0) search(0, 0, min(kl, m - 1));
+    psync();
+    for (int jj = 0; jj < nbe; ++jj) {
+        const int last = min(jj + kl, m - 1);
+        const int pv = S.piv;
+        const c64 piv = S.pval;
+        const bool nz = !cis_zero(piv);
+        const c64 rp = nz ? crecip(piv) : czero<float>();
+        if (pv != jj) {
+            for (int t = ptid; t < NB; t += kPT) {
+                if (t == jj) continue;
+                const c64 tmp = P[jj + t * LDP];
+                P[jj + t * LDP] = P[pv + t * LDP];
+                P[pv + t * LDP] = tmp;
+            }
+        }
+        for (int q = jj + ptid; q <= last; q += kPT) {
+            if (q == jj) {
+                const c64 old = P[jj + jj * LDP];
+                P[jj + jj * LDP] = piv;
+                if (pv != jj) P[pv + jj * LDP] = nz ? old * rp : old;
+            } else if (q != pv && nz) {
+                P[q + jj * LDP] = P[q + jj * LDP] * rp;
+            }
+        }
+        if (ptid == 0) {
+            if (pv != jj) { const int tmp = psm[jj]; psm[jj] = psm[pv]; psm[pv] = tmp; }
+            ipiv[k0 + jj] = k0 + pv;
+            if (!nz && S.info == 0) S.info = k0 + jj + 1;
+        }
+        psync();
+        if (nz) {
+            for (int c = jj + 1 + pw; c < nbe; c += kPWn) {
+                const c64 u = P[jj + c * LDP];
+                if (!cis_zero(u))
+                    for (int q = jj + 1 + lane; q <= last; q += 32) cfms(P[q + c * LDP], P[q + jj * LDP], u);
+                if (c == jj + 1) {
+                    __syncwarp();
+                    search(jj + 1, jj + 1, min(jj + 1 + kl, m - 1));
+                }
+            }
+        } else if (pw == 0 && jj + 1 < nbe) {
+            search(jj + 1, jj + 1, min(jj + 1 + kl, m - 1));
+        }
+        psync();
+    }
+    // 3. U11 to the band, permutation to global memory, displaced rows of the next application
+    for (int t = pw; t < nbe; t += kPWn)
+        for (int q = lane; q <= t; q += 32)
+            if (t - q <= kv) ab[(int64_t)(kv + q - t) + (int64_t)(k0 + t) * ldab] = P[q + t * LDP];
+    for (int q = ptid; q < LDP; q += kPT) permg[(int64_t)pn * LDP + q] = psm[q];
+    if (ptid < 32) {  // rows q >= nbe that take an original top row: at most nbe of them
+        int cnt = 0;
+        for (int base_q = nbe; base_q < LDP; base_q += 32) {
+            const int q = base_q + lane;
+            const bool disp = q < m && psm[q] != q;
+            const unsigned bal = __ballot_sync(FULL, disp);
+            if (disp) {
+                const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+                if (slot < 32) { dq[32 + slot] = q; }
+            }
+            cnt += __popc(bal);
+        }
+        if (lane == 0) S.nd_next = min(cnt, 32);
+    }
+    // 4. X = [inv(L11); W] in place, inv(U11) in the upper triangle of the top block.
+    //    Row q >= nbe of W solves w^T L11 = l21_q^T (backward over j); row q < nbe of inv(L11)
+    //    solves x^T L11 = e_q^T; row q of inv(U11) solves y^T U11 = e_q^T (forward over j).
+    //    Rows >= nbe are written as they finish (they only read the top block); the top block
+    //    is written after a barrier.
+    const int rows_w = m - nbe;
+    c64 z[NB];
+    for (int r = ptid; r < rows_w; r += kPT) {
+        const int q = nbe + r;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) z[j] = P[q + j * LDP];
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+#pragma unroll
+            for (int t = j + 1; t < NB; ++t) cfms(z[j], z[t], P[t + j * LDP]);
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) P[q + j * LDP] = z[j];
+    }
+    const int tq = ptid - (kPT - 32);  // the last warp also takes the top block
+    const bool top = tq >= 0 && tq < NB;
+    if (top) {
+        const int q = tq;
+        // inv(L11) row q: z_j for j < q (z_q = 1 implied)
+#pragma unroll
+        for (int j = NB - 1; j >= 0; --j) {
+            if (j < q) {
+                c64 s = P[q + j * LDP];  // the t = q term (times z_q = 1)
+#pragma unroll
+                for (int t = j + 1; t < NB; ++t)
+                    if (t < q) cfma(s, z[t], P[t + j * LDP]);
+                z[j] = mk<float>(-s.re, -s.im);
+            }
+        }
+        // inv(U11) row q: z_j for j >= q
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            if (j >= q) {
+                c64 s = (j == q) ? mk<float>(1.f, 0.f) : czero<float>();
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t >= q && t < j) cfms(s, z[t], P[t + j * LDP]);
+                z[j] = s * crecip(P[j + j * LDP]);
+            }
+        }
+    }
+    psync();
+    if (top) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) P[tq + j * LDP] = z[j];
+    }
+    psync();
+    c64* lpb = lp + (int64_t)pn * LDP * NB;
+    for (int idx = ptid; idx < LDP * NB; idx += kPT) lpb[idx] = P[idx];
+}
+
+// ------------------------------------------------------------------------------------------
+// Update team, one chunk: gather x'_top (and write the displaced rows back), its image.
+// Warp uw takes columns uw, uw + 8, ...; lane = k.
+// ------------------------------------------------------------------------------------------
+__device__ void gather_chunk(c64* ab, const BandDims& d, const Geo& G, int c0, int w, unsigned char* bimg,
+                             const int* perm, const int* dq, int nd) {
+    const int lane = threadIdx.x & 31, uw = threadIdx.x >> 5;
+    const int kv = d.kv, ldab = d.ldab, k0 = G.k0;
+    const int src = perm[lane];
+    for (int j = uw; j < NCH; j += kUW) {
+        const int c = c0 + j;
+        const bool valid = j < w;
+        c64 v = czero<float>(), dv = czero<float>();
+        int drow = 0;
+        if (valid) {
+            const int i = k0 + src;
+            if (i >= c - kv) v = ab[(int64_t)(kv + i - c) + (int64_t)c * ldab];
+            if (lane < nd) {
+                drow = dq[lane];
+                const int s = k0 + perm[drow];  // the original top row that moves down to drow
+                if (s >= c - kv) dv = ab[(int64_t)(kv + s - c) + (int64_t)c * ldab];
+            }
+        }
+        __syncwarp();
+        if (valid && lane < nd) ab[(int64_t)(kv + k0 + drow - c) + (int64_t)c * ldab] = dv;
+        put_elem(bimg, NCH, j, lane, v);
+    }
+}
+
+// Epilogue of one chunk: warp uw reads tensor-memory lanes 32 (uw % 4).. of tile uw / 4, i.e.
+// block rows q = 128 (uw / 4) + 32 (uw % 4) + lane, in 32-column halves (C loaded before the
+// accumulators are read).
+__device__ void epilogue_chunk(c64* ab, const BandDims& d, const Geo& G, int c0, int w, int N, uint32_t tb,
+                               uint64_t* accfull, uint32_t parity, TcbShared& S) {
+    const int lane = threadIdx.x & 31, uw = threadIdx.x >> 5;
+    const int kv = d.kv, ldab = d.ldab;
+    const int tile = uw >> 2, quarter = uw & 3;
+    const int q = tile * MT + quarter * 32 + lane;
+    const int row = G.k0 + q;
+    const bool is_u = q < G.nbe, is_c = !is_u && q < G.m;
+    const uint32_t ta = tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * 128);
+    bool ok = true;
+    for (int h = 0; h < N; h += 32) {
+        c64 v[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const int col = c0 + h + c;
+            v[c] = (is_c && h + c < w) ? ab[(int64_t)(kv + row - col) + (int64_t)col * ldab] : czero<float>();
+        }
+        if (h == 0) {
+            ok = wait_or_fail(accfull, parity, S);
+            tc_fence_after();
+        }
+        const int nh = min(32, N - h);  // 16 or 32
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s * 16 < nh) {
+                float dr[16], di[16];
+                tc_ld16(ta + h + s * 16, dr);
+                tc_ld16(ta + 64 + h + s * 16, di);
+                tc_wait_ld();
+                if (ok) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int cc = h + s * 16 + e;
+                        const int col = c0 + cc;
+                        if (cc < w) {
+                            const int64_t at = (int64_t)(kv + row - col) + (int64_t)col * ldab;
+                            if (is_c) ab[at] = mk<float>(v[s * 16 + e].re - dr[e], v[s * 16 + e].im - di[e]);
+                            else if (is_u && row >= col - kv) ab[at] = mk<float>(dr[e], di[e]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    band_factor_tc_kernel(const __grid_constant__ CUtensorMap tmap, FactorArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char tcb_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tcb_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ TcbShared S;
+    const BandDims d = a.d;
+    const int pt = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    c64* ab = a.ab + pt * a.ab_stride;
+    c64* lp = a.lp + pt * a.lp_stride;
+    int32_t* permg = a.perm + pt * a.perm_stride;
+    int32_t* ipiv = a.ipiv + (int64_t)pt * d.n;
+    c64* P = reinterpret_cast<c64*>(base + OFF_P);
+    int* perm_cur = reinterpret_cast<int*>(base + OFF_PERM);
+    int* perm_next = perm_cur + LDP;
+    int* dq = reinterpret_cast<int*>(base + OFF_DISP);  // displaced rows: [0..31] current, [32..63] next
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.bfull[i], kUW);
+            mbar_init(&S.accfull[i], 1);
+            mbar_init(&S.accempty[i], kUW);
+        }
+        mbar_init(&S.tma, 1);
+        S.fail = 0;
+        S.info = 0;
+        S.nd = S.nd_next = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMW) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                     "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == kPW0 && lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(&tmap) : "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    uint32_t ph_tma = 0;
+    if (warp >= kPW0) panel_step(&tmap, a, ab, lp, permg, ipiv, 0, base, S, ph_tma);
+    __syncthreads();
+
+    const uint32_t a_base = smem_u32(base), b_base = smem_u32(base + OFF_B);
+    int g = 0;  // chunks issued before this step (tensor-memory and image buffers alternate with it)
+    for (int p = 0; p < d.npanels; ++p) {
+        const Geo G(p, d.n, d.kl, d.kv);
+        // ---- the panel's X to its operand image, its permutation and displaced rows current ----
+        for (int it = tid; it < LDP * 4; it += kThreads) {
+            const int r = it >> 2, gq = it & 3;
+            c64 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (r < G.m) ? P[r + (8 * gq + e) * LDP] : czero<float>();
+            put_row8(base + (r >> 7) * A_TILE, MT, r & (MT - 1), gq, v);
+        }
+        for (int q = tid; q < LDP; q += kThreads) perm_cur[q] = perm_next[q];
+        if (tid < 32) dq[tid] = dq[32 + tid];  // the list of this panel; the panel team fills [32..] next
+        if (tid == 0) S.nd = S.nd_next;
+        fence_async_smem();
+        __syncthreads();
+        const int nd = S.nd;
+
+        if (warp < kUW) {
+            // ---- update team: gather / image of chunk t + 1, then the epilogue of chunk t ----------
+            auto produce = [&](int t) {
+                int c0, w;
+                G.chunk(t, c0, w);
+                const int b = (g + t) & 1;
+                gather_chunk(ab, d, G, c0, w, base + OFF_B + b * B_BUF, perm_cur, dq, nd);
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.bfull[b]);
+            };
+            if (G.nch > 0) produce(0);
+            usync();
+            for (int t = 0; t < G.nch; ++t) {
+                if (t + 1 < G.nch) produce(t + 1);
+                usync();  // the displaced rows written by produce(t) are visible to every epilogue warp
+                int c0, w;
+                G.chunk(t, c0, w);
+                const int N = (w + 15) & ~15;
+                const int gg = g + t, b = gg & 1;
+                epilogue_chunk(ab, d, G, c0, w, N, S.tmem + b * 256, &S.accfull[b], (gg >> 1) & 1, S);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.accempty[b]);
+                if (t == 0) {
+                    fence_async_global();  // the next panel's columns, read next by TMA
+                    __threadfence_block();
+                    lead_arrive();
+                }
+            }
+        } else if (warp == kMW) {
+            // ---- MMA issue ----------------------------------------------------------------------
+            for (int t = 0; t < G.nch; ++t) {
+                int c0, w;
+                G.chunk(t, c0, w);
+                const int N = (w + 15) & ~15;
+                const int gg = g + t, b = gg & 1, use = gg >> 1;
+                wait_or_fail(&S.bfull[b], use & 1, S);
+                if (use >= 1) wait_or_fail(&S.accempty[b], (use - 1) & 1, S);
+                tc_fence_after();
+                if (lane == 0) {
+                    if (!failed(S)) issue_chunk(a_base, b_base + b * B_BUF, S.tmem + b * 256, N);
+                    tc_commit(&S.accfull[b]);
+                }
+                __syncwarp();
+            }
+        } else if (p + 1 < d.npanels) {
+            // ---- panel team: the next panel, once its columns are updated --------------------
+            lead_wait();
+            panel_step(&tmap, a, ab, lp, permg, ipiv, p + 1, base, S, ph_tma);
+        }
+        g += G.nch;
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (failed(S)) break;
+    }
+    // drain: the last commits of each buffer (bounded), so tensor memory is idle before it is freed
+    if (warp == kMW && g > 0) {
+        for (int b = 0; b < 2; ++b) {
+            const int uses = (g - b + 1) / 2;  // chunks that used buffer b
+            if (uses > 0) mbar_wait(&S.accfull[b], (uses - 1) & 1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMW)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(TMEM_COLS) : "memory");
+    if (tid == 0) a.info[pt] = failed(S) ? -1 : S.info;
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward solve with the X blocks: per panel, x' = the block rows in pivot order, then
+//   x[k0 + q] = sum_{t <= q} inv(L11)[q, t] x'_t       (q < nbe, unit diagonal)
+//   x[k0 + q] = x'_q - sum_t W[q, t] x'_t              (nbe <= q < m).
+// The next panel's X block is bulk-copied into the second buffer while the current one is used.
+// One CTA per (point, share of the right-hand-side columns).
+// ------------------------------------------------------------------------------------------
+constexpr int kFwdThreads = 512;
+constexpr int kFwdLC = 4;  // right-hand-side columns per thread
+
+__global__ void __launch_bounds__(kFwdThreads) band_fwd_tc_kernel(SolveArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char fwd_raw[];
+    const BandDims d = a.d;
+    const int pt = blockIdx.x / a.split, part = blockIdx.x % a.split;
+    if (a.active && !a.active[pt]) return;
+    const int tid = threadIdx.x;
+    const c64* lp = a.lp + pt * a.lp_stride;
+    const int32_t* permg = a.perm + pt * a.perm_stride;
+    const int c_lo = (int)((int64_t)a.L * part / a.split), c_hi = (int)((int64_t)a.L * (part + 1) / a.split);
+    c64* x = a.x + pt * a.x_stride + (int64_t)c_lo * d.n;
+    const int Lp = c_hi - c_lo, n = d.n;
+    c64* Xb = reinterpret_cast<c64*>(fwd_raw);                               // [2][LDP * NB]
+    c64* xt = Xb + 2 * LDP * NB;                                             // [NB][Lmax] x'_top
+    c64* xo = xt + NB * 32;                                                  // [NB][Lmax] original top
+    int* pm = reinterpret_cast<int*>(xo + NB * 32);                          // [2][LDP]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_fail;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto stage = [&](int p, int buf) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar[buf], (uint32_t)(P_BYTES + LDP * 4));
+            bulk_g2s(Xb + (size_t)buf * LDP * NB, lp + (int64_t)p * LDP * NB, (uint32_t)P_BYTES, &bar[buf]);
+            bulk_g2s(pm + buf * LDP, permg + (int64_t)p * LDP, (uint32_t)(LDP * 4), &bar[buf]);
+        }
+    };
+    uint32_t ph[2] = {0, 0};
+    stage(0, 0);
+    for (int p = 0; p < d.npanels; ++p) {
+        const int buf = p & 1;
+        const int k0 = p * NB, nbe = min(NB, n - k0), m = min(NB + d.kl, n - k0);
+        if (p + 1 < d.npanels) stage(p + 1, buf ^ 1);  // that buffer was released by the last barrier
+        if (!mbar_wait(&bar[buf], ph[buf])) s_fail = 1;
+        ph[buf] ^= 1;
+        const c64* X = Xb + (size_t)buf * LDP * NB;
+        const int* perm = pm + buf * LDP;
+        // original top rows, then the permuted top rows
+        for (int idx = tid; idx < NB * Lp; idx += kFwdThreads) {
+            const int k = idx % NB, l = idx / NB;
+            xo[k * 32 + l] = (k < m) ? x[(int64_t)(k0 + k) + (int64_t)l * n] : czero<float>();
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NB * Lp; idx += kFwdThreads) {
+            const int k = idx % NB, l = idx / NB;
+            const int s = perm[k];
+            xt[k * 32 + l] = (k >= m) ? czero<float>() : (s < NB ? xo[s * 32 + l] : x[(int64_t)(k0 + s) + (int64_t)l * n]);
+        }
+        __syncthreads();
+        // rows: thread -> (row q, group of kFwdLC columns); consecutive threads take consecutive rows
+        const int ngroups = (Lp + kFwdLC - 1) / kFwdLC;
+        for (int it = tid; it < LDP * ngroups; it += kFwdThreads) {
+            const int q = it % LDP, lg = it / LDP;
+            if (q >= m) continue;
+            const int l0 = lg * kFwdLC;
+            c64 acc[kFwdLC];
+            if (q < nbe) {
+#pragma unroll
+                for (int c = 0; c < kFwdLC; ++c) acc[c] = (l0 + c < Lp) ? xt[q * 32 + l0 + c] : czero<float>();
+                for (int t = 0; t < q; ++t) {
+                    const c64 lv = X[q + t * LDP];
+#pragma unroll
+                    for (int c = 0; c < kFwdLC; ++c) cfma(acc[c], lv, xt[t * 32 + l0 + c]);
+                }
+            } else {
+                const int s = perm[q];
+#pragma unroll
+                for (int c = 0; c < kFwdLC; ++c)
+                    acc[c] = (l0 + c < Lp) ? (s != q ? xo[s * 32 + l0 + c] : x[(int64_t)(k0 + q) + (int64_t)(l0 + c) * n])
+                                           : czero<float>();
+#pragma unroll 8
+                for (int t = 0; t < nbe; ++t) {
+                    const c64 wv = X[q + t * LDP];
+#pragma unroll
+                    for (int c = 0; c < kFwdLC; ++c) cfms(acc[c], wv, xt[t * 32 + l0 + c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kFwdLC; ++c)
+                if (l0 + c < Lp) x[(int64_t)(k0 + q) + (int64_t)(l0 + c) * n] = acc[c];
+        }
+        __syncthreads();
+        if (s_fail) break;
+    }
+}
+
+}  // namespace
+
+// ---- host side -------------------------------------------------------------------------------
+
+bool band_tc_eligible(int64_t n, int64_t kl, int64_t ku) {
+    return n >= 2 * kTcNB && kl >= 32 && kl <= kTcMaxKl && ku >= 1 && kl + ku + 1 <= 2048;
+}
+
+int pick_dims_tc(int64_t n, int64_t kl, int64_t ku, BandDims* d) {
+    if (!band_tc_eligible(n, kl, ku)) return set_error(RSRR_EUNSUPPORTED, "band not suited to the tensor-core LU");
+    const int64_t ku2 = ku + ((kl + ku) & 1);  // kv even: the TMA row coordinate kv + k0 is 16-byte aligned
+    // the backward solve is the CUDA-core one: its block sizes as for any complex64 band
+    RSRR_TRY(pick_dims(n, kl, ku2, true, d));
+    d->n = (int)n;
+    d->kl = (int)kl;
+    d->ku = (int)ku2;
+    d->kv = d->kl + d->ku;
+    int ldab = 2 * d->kl + d->ku + 1;
+    if ((ldab & 1) == 0) ++ldab;  // (ldab - 1) * 8 bytes, the TMA column stride, a multiple of 16
+    d->ldab = ldab;
+    d->nb = kTcNB;
+    d->ldp = kTcLDP;
+    d->npanels = (int)ceil_div(n, kTcNB);
+    d->fwd_nbuf = 2;
+    return RSRR_OK;
+}
+
+int64_t tc_ab_stride(const BandDims& d) { return ((int64_t)d.ldab * d.n + 31) / 32 * 32; }
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// The band arrays of npts points as one 3D tensor of 8-byte elements: x = kv + i (the row's slot in
+// its column shifted by the column), y = column, z = point.  Element (x, y, z) sits at
+// ab + z * stride + x + y * (ldab - 1); every in-extent element lies inside point z's array.
+int band_tensor_map(CUtensorMap* map, const c64* ab, int64_t stride, int npts, const BandDims& d, int box_x, int box_y) {
+    auto fn = encode_fn();
+    if (!fn) return set_error(RSRR_ECUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[3] = {(cuuint64_t)d.n + (cuuint64_t)d.ldab - 1, (cuuint64_t)d.n, (cuuint64_t)npts};
+    cuuint64_t strides[2] = {(cuuint64_t)(d.ldab - 1) * 8u, (cuuint64_t)stride * 8u};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<c64*>(ab), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(RSRR_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return RSRR_OK;
+}
+
+template <typename K>
+int set_smem_max(K kernel, size_t sm, const char* name) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    if (sm + fa.sharedSizeBytes > (size_t)optin)
+        return set_error(RSRR_EUNSUPPORTED, std::string(name) + ": shared memory " + std::to_string(sm) + " + " +
+                                                std::to_string(fa.sharedSizeBytes) + " exceeds " + std::to_string(optin));
+    // process-wide attribute: the largest allowed value, so concurrent launches never lower it
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return set_error(RSRR_ECUDA, std::string(name) + ": " + cudaGetErrorString(e));
+    return RSRR_OK;
+}
+
+int solve_split_tc(int npts, int L) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return (L >= 2 && 2 * npts <= nsm) ? 2 : 1;
+}
+}  // namespace
+
+int launch_factor_tc(const FactorArgs<float>& a, int npts, cudaStream_t s) {
+    const BandDims& d = a.d;
+    if (d.nb != kTcNB || d.ldp != kTcLDP || (d.kv & 1) || !(d.ldab & 1) || (a.ab_stride & 1) ||
+        (reinterpret_cast<uintptr_t>(a.ab) & 15))
+        return set_error(RSRR_EINVAL, "launch_factor_tc: band layout not prepared for TMA");
+    CUtensorMap map;
+    RSRR_TRY(band_tensor_map(&map, a.ab, a.ab_stride, npts, d, kTcLDP, kTcNB));
+    RSRR_TRY(set_smem_max(band_factor_tc_kernel, SMEM_BYTES, "band_factor_tc_kernel"));
+    band_factor_tc_kernel<<<npts, kThreads, SMEM_BYTES, s>>>(map, a);
+    note_launch();
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+int launch_fwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s) {
+    if (a.L > 64) return set_error(RSRR_EINVAL, "launch_fwd_tc: at most 64 right-hand sides");
+    const size_t sm = (size_t)2 * P_BYTES + (size_t)2 * NB * 32 * sizeof(c64) + (size_t)2 * LDP * 4;
+    RSRR_TRY(set_smem_max(band_fwd_tc_kernel, sm, "band_fwd_tc_kernel"));
+    SolveArgs<float> b = a;
+    b.split = a.L > 32 ? 2 : solve_split_tc(npts, a.L);
+    if ((a.L + b.split - 1) / b.split > 32) return set_error(RSRR_EINVAL, "launch_fwd_tc: too many columns per CTA");
+    band_fwd_tc_kernel<<<npts * b.split, kFwdThreads, sm, s>>>(b);
+    note_launch();
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+}  // namespace rsrr

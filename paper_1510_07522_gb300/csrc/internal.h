@@ -63,8 +63,10 @@ struct rsrr_nep_s {
     rsrr::c128* d_vals = nullptr;  // [J][nnz]
     int32_t* d_perm = nullptr;     // [n] perm[new] = old
     bool force_dense = false;      // RSRR_DENSE_LU: factor every point with the dense LU
+    bool band_cuda_cores = false;  // RSRR_BAND_CUDA_CORES: no tensor-core band LU
     int32_t precond_band = -1;     // >= 0: factor only |i - j| <= precond_band of T(z_j) and iterate
     bool dense_used = false;       // the last rsrr_sample factored densely
+    bool band_tc_used = false;     // the last rsrr_sample ran the tensor-core band LU
     std::vector<double> normA;     // ||A_i||_F
     rsrr_tz_cb tz = nullptr;       // T known by its values (rsrr_create_nep_tz): the library calls
     void* tz_user = nullptr;       // tz for T(z) at the points it needs; d_vals then holds T(z_j)

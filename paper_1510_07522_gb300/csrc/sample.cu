@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "band.cuh"
+#include "band_tc.cuh"
 #include "dense_lu.cuh"
 #include "internal.h"
 
@@ -229,6 +230,27 @@ struct EvPair {
     double ms() { float t = 0.f; cudaEventElapsedTime(&t, a, b); return t; }
 };
 
+// The complex64 band LU runs on the tensor cores (band_tc.cu) when its band suits them
+// (kl in [32, 224]), unless the handle was created with RSRR_BAND_CUDA_CORES.
+template <typename R>
+bool use_band_tc(rsrr_nep h, int64_t n, int64_t kl, int64_t ku) {
+    return sizeof(R) == 4 && !h->band_cuda_cores && band_tc_eligible(n, kl, ku);
+}
+template <typename R>
+int factor_any(bool tc, const FactorArgs<R>& a, int np, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (tc) return launch_factor_tc(a, np, st);
+    }
+    return launch_factor<R>(a, np, st);
+}
+template <typename R>
+int fwd_any(bool tc, const SolveArgs<R>& a, int np, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (tc) return launch_fwd_tc(a, np, st);
+    }
+    return launch_fwd<R>(a, np, st);
+}
+
 template <typename R>
 int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
     cudaStream_t st = h->stream;
@@ -240,11 +262,13 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         kl = std::min<int64_t>(kl, h->precond_band);
         ku = std::min<int64_t>(ku, h->precond_band);
     }
-    RSRR_TRY(pick_dims(n, kl, ku, sizeof(R) == 4, &d));
+    const bool tc = use_band_tc<R>(h, n, kl, ku);
+    if (tc) RSRR_TRY(pick_dims_tc(n, kl, ku, &d));
+    else RSRR_TRY(pick_dims(n, kl, ku, sizeof(R) == 4, &d));
     const int64_t nl = n * L;
     // per-point footprint
     const size_t es = sizeof(cplx<R>);
-    const size_t ab_b = (size_t)d.ldab * n * es;
+    const size_t ab_b = (size_t)(tc ? tc_ab_stride(d) : (int64_t)d.ldab * n) * es;
     const size_t lp_b = (size_t)d.npanels * d.ldp * d.nb * es;
     const size_t perm_b = (size_t)d.npanels * d.ldp * 4;
     const size_t per_pt = ab_b + lp_b + perm_b + (size_t)n * 4 + (size_t)nl * es + (size_t)nnz * 16 +
@@ -288,6 +312,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
     TRYC(dalloc_n(&un2, (size_t)L, st));
     h->ms_factor = h->ms_trsv = 0;
     h->factor_launches = h->trsv_launches = 0;
+    h->band_tc_used = tc;
     EvPair evf, evs;
     { column_norm2_kernel<<<L, 256, 0, st>>>(h->d_U, n, un2); note_launch(); }
 
@@ -310,15 +335,22 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         FactorArgs<R> fa{d, ab, (int64_t)(ab_b / es), lp, (int64_t)(lp_b / es), perm,
                          (int64_t)d.npanels * d.ldp, ipiv, info};
         evf.start(st);
-        TRYC(launch_factor<R>(fa, np, st));
+        TRYC(factor_any<R>(tc, fa, np, st));
         evf.stop(st);
         std::vector<int32_t> hinfo(np);
         CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
         CUDAC(cudaStreamSynchronize(st));
         h->ms_factor += evf.ms();
         h->factor_launches += 1;
-        for (int k = 0; k < np; ++k)
-            if (hinfo[k]) singular = true;
+        bool timeout = false;
+        for (int k = 0; k < np; ++k) {
+            if (hinfo[k] > 0) singular = true;
+            if (hinfo[k] < 0) timeout = true;
+        }
+        if (timeout) {
+            cleanup();
+            return set_error(RSRR_ETIMEOUT, "band LU: a tensor-core wait gave up");
+        }
         if (singular) break;
         SolveArgs<R> sa{d, ab, (int64_t)(ab_b / es), lp, (int64_t)(lp_b / es), perm,
                         (int64_t)d.npanels * d.ldp, B, nl, L, nullptr};
@@ -327,7 +359,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             { broadcast_rhs_kernel<R><<<g, 256, 0, st>>>(h->d_U, nl, B); note_launch(); }
         }
         evs.start(st);
-        TRYC(launch_fwd<R>(sa, np, st));
+        TRYC(fwd_any<R>(tc, sa, np, st));
         TRYC(launch_bwd<R>(sa, np, st));
         evs.stop(st);
         bool trsv_pending = true;
@@ -363,7 +395,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             }
             sa.active = active;
             evs.start(st);
-            TRYC(launch_fwd<R>(sa, np, st));
+            TRYC(fwd_any<R>(tc, sa, np, st));
             TRYC(launch_bwd<R>(sa, np, st));
             evs.stop(st);
             trsv_pending = true;
