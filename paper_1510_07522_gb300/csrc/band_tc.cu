@@ -44,11 +44,10 @@ constexpr int NB = kTcNB;
 constexpr int LDP = kTcLDP;
 constexpr int MT = 128;              // rows of one MMA tile
 constexpr int NCH = 64;              // columns per trailing chunk (the first chunk has 32)
-constexpr int kUW = 8;               // update warps (gather + image + epilogue)
-constexpr int kMW = kUW;             // the MMA warp
-constexpr int kPW0 = kUW + 1;        // first panel warp
-constexpr int kPWn = 4;              // panel warps
-constexpr int kThreads = (kUW + 1 + kPWn) * 32;
+constexpr int kUW = 8;               // update warps (gather + image + MMA issue + epilogue)
+constexpr int kPW0 = kUW;            // first panel warp
+constexpr int kPWn = 8;              // panel warps: one panel row per thread
+constexpr int kThreads = (kUW + kPWn) * 32;
 constexpr int kUT = kUW * 32;
 constexpr int kPT = kPWn * 32;
 constexpr unsigned FULL = 0xffffffffu;
@@ -65,17 +64,17 @@ constexpr int SMEM_BYTES = OFF_DISP + 2 * 32 * 4 + 1024;
 constexpr uint32_t TMEM_COLS = 512;            // two buffers x two tiles x (re, im) x 64 columns
 
 struct TcbShared {
-    uint64_t bfull[2];     // the x'_top image of a buffer is written (one arrival per update warp)
-    uint64_t accfull[2];   // the MMAs into a tensor-memory buffer are complete (tcgen05.commit)
-    uint64_t accempty[2];  // the epilogue has read a tensor-memory buffer (one arrival per update warp)
+    uint64_t accfull[2];   // the MMAs into a tensor-memory buffer are complete (one tcgen05.commit per tile)
     uint64_t tma;          // the panel's TMA load
     uint32_t tmem;
     int fail;              // a bounded wait ran out
     int info;              // first zero pivot column (1-based)
-    int piv;
     int nd;                // displaced rows of the panel being applied
     int nd_next;
-    c64 pval;
+    float pbest[1][kPWn];  // per panel warp: best cabs1 of the pivot search and its position
+    int ppos[1][kPWn];
+    c64 urow[NB];          // the pivot row of the current column
+    c64 dinv[NB];          // 1 / U11(j, j)
 };
 
 __device__ __forceinline__ bool failed(const TcbShared& S) { return *(const volatile int*)&S.fail != 0; }
@@ -86,9 +85,22 @@ __device__ __forceinline__ void lead_arrive() { asm volatile("bar.arrive 3, %0;"
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
+// Bounded wait that sleeps between polls (from the second one), so that waiting warps leave the
+// issue slots to the warps that share their scheduler; gives up after ~2^18 polls (~0.1 s).
+__device__ __forceinline__ bool wait_backoff(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < (1u << 18); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(it < 8 ? 32 : 256);
+    }
+    return false;
+}
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, TcbShared& S) {
     if (failed(S)) return false;
-    if (mbar_wait(bar, parity)) return true;
+    if (wait_backoff(bar, parity)) return true;
     S.fail = 1;
     return false;
 }
@@ -101,36 +113,48 @@ __device__ __forceinline__ uint32_t img_off(int R, int r, int q, int k) {
     return (uint32_t)(q >> 1) * (uint32_t)R * 128u + (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u +
            chunk * 16u + (uint32_t)(k & 7) * 2u;
 }
-__device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    p[0] = h;
-    p[1] = m;
-    p[2] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+// x = h + m + l with h, m, l in BF16 (24 significant bits together), as raw 16-bit patterns.
+__device__ __forceinline__ void split3(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
+    const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(bh);
+    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 bl = __float2bfloat16_rn(r1 - __bfloat162float(bm));
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
 }
 // One complex value at (r, k) of an image: planes 0..2 = re pieces, 3..5 = im pieces.
 __device__ __forceinline__ void put_elem(unsigned char* img, int R, int r, int k, c64 v) {
-    __nv_bfloat16 p[6];
-    split3(v.re, p);
-    split3(v.im, p + 3);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) *reinterpret_cast<__nv_bfloat16*>(img + img_off(R, r, q, k)) = p[q];
+    uint32_t p0, p1, p2, p3, p4, p5;
+    split3(v.re, p0, p1, p2);
+    split3(v.im, p3, p4, p5);
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 0, k)) = (unsigned short)p0;
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 1, k)) = (unsigned short)p1;
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 2, k)) = (unsigned short)p2;
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 3, k)) = (unsigned short)p3;
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 4, k)) = (unsigned short)p4;
+    *reinterpret_cast<unsigned short*>(img + img_off(R, r, 5, k)) = (unsigned short)p5;
 }
-// Eight consecutive k (8 g .. 8 g + 7) of row r: six 16-byte stores.
+// Eight consecutive k (8 g .. 8 g + 7) of row r: six 16-byte stores, packed in registers.
 __device__ __forceinline__ void put_row8(unsigned char* img, int R, int r, int g, const c64* v) {
-    __align__(16) __nv_bfloat16 p[6][8];
+    uint32_t w[6][4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        __nv_bfloat16 t[6];
-        split3(v[e].re, t);
-        split3(v[e].im, t + 3);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) p[q][e] = t[q];
+    for (int e = 0; e < 8; e += 2) {
+        uint32_t a0, a1, a2, a3, a4, a5, b0, b1, b2, b3, b4, b5;
+        split3(v[e].re, a0, a1, a2);
+        split3(v[e].im, a3, a4, a5);
+        split3(v[e + 1].re, b0, b1, b2);
+        split3(v[e + 1].im, b3, b4, b5);
+        w[0][e >> 1] = a0 | (b0 << 16);
+        w[1][e >> 1] = a1 | (b1 << 16);
+        w[2][e >> 1] = a2 | (b2 << 16);
+        w[3][e >> 1] = a3 | (b3 << 16);
+        w[4][e >> 1] = a4 | (b4 << 16);
+        w[5][e >> 1] = a5 | (b5 << 16);
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q)
-        *reinterpret_cast<uint4*>(img + img_off(R, r, q, 8 * g)) = *reinterpret_cast<const uint4*>(p[q]);
+        *reinterpret_cast<uint4*>(img + img_off(R, r, q, 8 * g)) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
@@ -139,31 +163,31 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)) : "memory");
 }
 
-// All MMAs of one chunk: D = X x'_top for both 128-row tiles, N columns, into tensor-memory
+// The MMAs of one chunk for one 128-row tile i: D_i = X_i x'_top, N columns, into tensor-memory
 // buffer `tb` (tile i: re at tb + 128 i, im at tb + 128 i + 64).  Real products (X_re x_re,
 // -X_im x_im) into re and (X_re x_im, X_im x_re) into im, six BF16 piece products each, two
 // K = 16 steps.
-__device__ __forceinline__ void issue_chunk(uint32_t a_base, uint32_t b_base, uint32_t tb, int N) {
+__device__ __forceinline__ void issue_tile(uint32_t a_base, uint32_t b_base, uint32_t tb, int N, int i) {
+    // descriptors differ only in the start-address field (address >> 4, below 2^14 for the whole
+    // shared window), so each is the base descriptor plus a constant
+    const uint64_t ad0 = sw128_desc(a_base + i * A_TILE), bd0 = sw128_desc(b_base);
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
     const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pd[4] = {0, 0, 64, 64}, ng[4] = {0, 1, 0, 0};
     const int sa[6] = {0, 0, 1, 0, 1, 2}, sb[6] = {0, 1, 0, 2, 1, 0};
+    uint32_t acc_r = 0, acc_i = 0;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        uint32_t acc_r = 0, acc_i = 0;
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t id = idesc | (ng[p] ? (1u << 13) : 0u);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const uint32_t id = idesc | (ng[p] ? (1u << 13) : 0u);
+        for (int s = 0; s < 6; ++s) {
+            const int qa = pa[p] * 3 + sa[s], qb = pb[p] * 3 + sb[s];
 #pragma unroll
-            for (int s = 0; s < 6; ++s) {
-                const int qa = pa[p] * 3 + sa[s], qb = pb[p] * 3 + sb[s];
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t ao = a_base + i * A_TILE + (qa >> 1) * MT * 128 + (qa & 1) * 64 + ks * 32;
-                    const uint32_t bo = b_base + (qb >> 1) * NCH * 128 + (qb & 1) * 64 + ks * 32;
-                    uint32_t& acc = pd[p] ? acc_i : acc_r;
-                    tc_mma(tb + i * 128 + pd[p], sw128_desc(ao), sw128_desc(bo), id, acc);
-                    acc = 1;
-                }
+            for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t ao = (qa >> 1) * MT * 128 + (qa & 1) * 64 + ks * 32;
+                const uint32_t bo = (qb >> 1) * NCH * 128 + (qb & 1) * 64 + ks * 32;
+                uint32_t& acc = pd[p] ? acc_i : acc_r;
+                tc_mma(tb + i * 128 + pd[p], ad0 + (ao >> 4), bd0 + (bo >> 4), id, acc);
+                acc = 1;
             }
         }
     }
@@ -188,8 +212,16 @@ struct Geo {  // one step of the factorisation (panel p applied to its trailing 
 };
 
 // ------------------------------------------------------------------------------------------
-// Panel team: stage panel pn by TMA, factor it, write U11 / pivots / permutation, form X in place
-// and store it.  Runs on warps kPW0.. (kPT threads), barrier id 2.
+// Panel team (kPT = 256 threads, barrier id 2): stage panel pn by TMA, factor it with one panel
+// row per thread held in registers, write U11 / pivots / permutation, form X and store it.
+//
+// Rows are not moved during the factorisation: each thread keeps the logical position `pos` of
+// its row, and an interchange of positions jj and pv only swaps two labels.  Per column jj:
+//   the candidates (positions >= jj) reduce (cabs1, then lowest position) within each warp, the
+//   warp results through shared memory (first barrier); the pivot row's thread publishes its row;
+//   after the second barrier every row below scales its multiplier and applies the rank-1
+//   update in registers.  Rows further than kl below the diagonal are structurally zero in the
+//   column, so taking them as candidates changes neither the pivot nor the tie rule.
 // ------------------------------------------------------------------------------------------
 __device__ void panel_step(const CUtensorMap* tmap, const FactorArgs<float>& a, c64* ab, c64* lp, int32_t* permg,
                            int32_t* ipiv, int pn, unsigned char* base, TcbShared& S, uint32_t& ph_tma) {
@@ -205,151 +237,147 @@ __device__ void panel_step(const CUtensorMap* tmap, const FactorArgs<float>& a, 
         mbar_expect_tx(&S.tma, (uint32_t)P_BYTES);
         tma_load_3d(P, tmap, kv + k0, k0, (int)blockIdx.x, &S.tma);
     }
-    for (int q = ptid; q < LDP; q += kPT) psm[q] = q;
     wait_or_fail(&S.tma, ph_tma, S);
     ph_tma ^= 1;
-    // entries outside the band, past the matrix, or past the panel's columns are zero; a column
-    // t >= nbe (last panel only) gets a unit diagonal so the inverses below stay the identity there
-    for (int idx = ptid; idx < LDP * NB; idx += kPT) {
-        const int q = idx % LDP, t = idx / LDP;
-        if (t >= nbe) P[idx] = (q == t) ? mk<float>(1.f, 0.f) : czero<float>();
-        else if (q >= m || q - t > kl) P[idx] = czero<float>();
-    }
-    psync();
-    // 2. factor (two team barriers per column)
-    auto search = [&](int col, int first, int last) {
-        float best = -1.f;
-        int bi = first;
-        for (int q = first + lane; q <= last; q += 32) {
-            const float v = cabs1(P[q + col * LDP]);
-            if (v > best) { best = v; bi = q; }
-        }
+    // My row (block row q = ptid) in registers.  Entries outside the band, past the matrix or past
+    // the panel's columns are zero; a column t >= nbe (last panel only) gets a unit diagonal so
+    // that the inverses below are the identity there.
+    const int q = ptid;
+    c64 r[NB];
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            const float ob = __shfl_down_sync(FULL, best, off);
-            const int oi = __shfl_down_sync(FULL, bi, off);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) {
-            S.piv = bi;
-            S.pval = P[bi + col * LDP];
-        }
-    };
-    if (pw == 0) search(0, 0, min(kl, m - 1));
-    psync();
-    for (int jj = 0; jj < nbe; ++jj) {
-        const int last = min(jj + kl, m - 1);
-        const int pv = S.piv;
-        const c64 piv = S.pval;
-        const bool nz = !cis_zero(piv);
-        const c64 rp = nz ? crecip(piv) : czero<float>();
-        if (pv != jj) {
-            for (int t = ptid; t < NB; t += kPT) {
-                if (t == jj) continue;
-                const c64 tmp = P[jj + t * LDP];
-                P[jj + t * LDP] = P[pv + t * LDP];
-                P[pv + t * LDP] = tmp;
+    for (int t = 0; t < NB; ++t) {
+        const c64 v = P[q + t * LDP];
+        r[t] = (t >= nbe) ? ((q == t) ? mk<float>(1.f, 0.f) : czero<float>())
+                          : ((q < m && q - t <= kl) ? v : czero<float>());
+    }
+    int pos = q;
+    psync();  // every row read before the buffer is rewritten below
+    // 2. factor (the column loop is unrolled: the row stays in registers, indexed statically)
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj) {
+        if (jj < nbe) {
+            float v = (pos >= jj) ? cabs1(r[jj]) : -1.f;
+            int pp = pos;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const float ov = __shfl_down_sync(FULL, v, off);
+                const int op = __shfl_down_sync(FULL, pp, off);
+                if (ov > v || (ov == v && op < pp)) { v = ov; pp = op; }
             }
-        }
-        for (int q = jj + ptid; q <= last; q += kPT) {
-            if (q == jj) {
-                const c64 old = P[jj + jj * LDP];
-                P[jj + jj * LDP] = piv;
-                if (pv != jj) P[pv + jj * LDP] = nz ? old * rp : old;
-            } else if (q != pv && nz) {
-                P[q + jj * LDP] = P[q + jj * LDP] * rp;
+            if (lane == 0) {
+                S.pbest[0][pw] = v;
+                S.ppos[0][pw] = pp;
             }
-        }
-        if (ptid == 0) {
-            if (pv != jj) { const int tmp = psm[jj]; psm[jj] = psm[pv]; psm[pv] = tmp; }
-            ipiv[k0 + jj] = k0 + pv;
-            if (!nz && S.info == 0) S.info = k0 + jj + 1;
-        }
-        psync();
-        if (nz) {
-            for (int c = jj + 1 + pw; c < nbe; c += kPWn) {
-                const c64 u = P[jj + c * LDP];
-                if (!cis_zero(u))
-                    for (int q = jj + 1 + lane; q <= last; q += 32) cfms(P[q + c * LDP], P[q + jj * LDP], u);
-                if (c == jj + 1) {
-                    __syncwarp();
-                    search(jj + 1, jj + 1, min(jj + 1 + kl, m - 1));
+            psync();
+            float bv = S.pbest[0][0];
+            int bp = S.ppos[0][0];
+#pragma unroll
+            for (int w2 = 1; w2 < kPWn; ++w2) {
+                const float ov = S.pbest[0][w2];
+                const int op = S.ppos[0][w2];
+                if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
+            }
+            if (pos == bp) {  // the pivot row: publish it
+#pragma unroll
+                for (int t = jj; t < NB; ++t) S.urow[t] = r[t];
+                ipiv[k0 + jj] = k0 + bp;
+                if (cis_zero(r[jj]) && S.info == 0) S.info = k0 + jj + 1;
+            }
+            if (pos == jj) pos = bp;
+            else if (pos == bp) pos = jj;
+            psync();
+            const c64 piv = S.urow[jj];
+            if (pos > jj && !cis_zero(piv)) {
+                const c64 l = r[jj] * crecip(piv);
+                r[jj] = l;
+                if (!cis_zero(l)) {
+#pragma unroll
+                    for (int c = jj + 1; c < NB; ++c) cfms(r[c], l, S.urow[c]);
                 }
             }
-        } else if (pw == 0 && jj + 1 < nbe) {
-            search(jj + 1, jj + 1, min(jj + 1 + kl, m - 1));
         }
-        psync();
     }
-    // 3. U11 to the band, permutation to global memory, displaced rows of the next application
-    for (int t = pw; t < nbe; t += kPWn)
-        for (int q = lane; q <= t; q += 32)
-            if (t - q <= kv) ab[(int64_t)(kv + q - t) + (int64_t)(k0 + t) * ldab] = P[q + t * LDP];
-    for (int q = ptid; q < LDP; q += kPT) permg[(int64_t)pn * LDP + q] = psm[q];
-    if (ptid < 32) {  // rows q >= nbe that take an original top row: at most nbe of them
+    // 3. the factored panel in pivot order, the permutation, U11 to the band
+#pragma unroll
+    for (int t = 0; t < NB; ++t) P[pos + t * LDP] = r[t];
+    psm[pos] = q;
+    permg[(int64_t)pn * LDP + pos] = q;
+    if (pos < nbe) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+            if (t >= pos && t < nbe) ab[(int64_t)(kv + pos - t) + (int64_t)(k0 + t) * ldab] = r[t];
+        S.dinv[pos] = crecip(P[pos + pos * LDP]);  // (a runtime index into r would put r in local memory)
+    } else if (pos < NB) {
+        S.dinv[pos] = mk<float>(1.f, 0.f);
+    }
+    psync();
+    // displaced rows of the next application (positions >= nbe whose row started in the top
+    // block): at most nbe of them
+    if (pw == 0) {
         int cnt = 0;
-        for (int base_q = nbe; base_q < LDP; base_q += 32) {
-            const int q = base_q + lane;
-            const bool disp = q < m && psm[q] != q;
+        for (int base_q = nbe; base_q < m; base_q += 32) {
+            const int qq = base_q + lane;
+            const bool disp = qq < m && psm[qq] != qq;
             const unsigned bal = __ballot_sync(FULL, disp);
             if (disp) {
                 const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
-                if (slot < 32) { dq[32 + slot] = q; }
+                if (slot < 32) dq[32 + slot] = qq;
             }
             cnt += __popc(bal);
         }
         if (lane == 0) S.nd_next = min(cnt, 32);
     }
-    // 4. X = [inv(L11); W] in place, inv(U11) in the upper triangle of the top block.
-    //    Row q >= nbe of W solves w^T L11 = l21_q^T (backward over j); row q < nbe of inv(L11)
-    //    solves x^T L11 = e_q^T; row q of inv(U11) solves y^T U11 = e_q^T (forward over j).
-    //    Rows >= nbe are written as they finish (they only read the top block); the top block
-    //    is written after a barrier.
-    const int rows_w = m - nbe;
-    c64 z[NB];
-    for (int r = ptid; r < rows_w; r += kPT) {
-        const int q = nbe + r;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) z[j] = P[q + j * LDP];
-#pragma unroll
-        for (int j = NB - 1; j >= 0; --j) {
-#pragma unroll
-            for (int t = j + 1; t < NB; ++t) cfms(z[j], z[t], P[t + j * LDP]);
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j) P[q + j * LDP] = z[j];
-    }
-    const int tq = ptid - (kPT - 32);  // the last warp also takes the top block
-    const bool top = tq >= 0 && tq < NB;
-    if (top) {
-        const int q = tq;
-        // inv(L11) row q: z_j for j < q (z_q = 1 implied)
-#pragma unroll
-        for (int j = NB - 1; j >= 0; --j) {
-            if (j < q) {
-                c64 s = P[q + j * LDP];  // the t = q term (times z_q = 1)
-#pragma unroll
-                for (int t = j + 1; t < NB; ++t)
-                    if (t < q) cfma(s, z[t], P[t + j * LDP]);
-                z[j] = mk<float>(-s.re, -s.im);
+    // 4. inv(L11) (warp 1) and inv(U11) (warp 2) in place in the top block: inv(L11) strictly below
+    //    the diagonal, inv(U11) on and above it.  Both are column sweeps with lane = row:
+    //      inv(L11), column j from 31 down: x_i = -(L_ij + sum_{j<t<i} inv(L)_it L_tj), i > j
+    //      (the columns right of j are final, column j itself is still L's);
+    //      inv(U11), column j from 0 up: x_i = -(sum_{i<=t<j} inv(U)_it U_tj) / U_jj, i < j, and
+    //      x_j = 1 / U_jj (the columns left of j are final, column j itself is still U's).
+    //    Each lane computes its entry before the warp writes the column.
+    if (pw == 1) {
+        const int i = lane;
+        for (int j = NB - 2; j >= 0; --j) {
+            c64 x = czero<float>();
+            if (i > j) {
+                x = P[i + j * LDP];
+                for (int t = j + 1; t < i; ++t) cfma(x, P[i + t * LDP], P[t + j * LDP]);
+                x = mk<float>(-x.re, -x.im);
             }
+            __syncwarp();
+            if (i > j) P[i + j * LDP] = x;
+            __syncwarp();
         }
-        // inv(U11) row q: z_j for j >= q
-#pragma unroll
+    } else if (pw == 2) {
+        const int i = lane;
         for (int j = 0; j < NB; ++j) {
-            if (j >= q) {
-                c64 s = (j == q) ? mk<float>(1.f, 0.f) : czero<float>();
-#pragma unroll
-                for (int t = 0; t < NB; ++t)
-                    if (t >= q && t < j) cfms(s, z[t], P[t + j * LDP]);
-                z[j] = s * crecip(P[j + j * LDP]);
+            c64 x = czero<float>();
+            if (i < j) {
+                for (int t = i; t < j; ++t) cfma(x, P[i + t * LDP], P[t + j * LDP]);
+                x = mk<float>(-x.re, -x.im) * S.dinv[j];
             }
+            __syncwarp();
+            if (i < j) P[i + j * LDP] = x;
+            else if (i == j) P[i + j * LDP] = S.dinv[j];
+            __syncwarp();
         }
     }
     psync();
-    if (top) {
+    // 5. W = L21 inv(L11): the row at position pos >= nbe, eight columns at a time (a short loop:
+    //    straight-line code this size would not stay in the instruction cache)
+    if (pos >= nbe && pos < m) {
+        for (int jb = 0; jb < NB; jb += 8) {
+            c64 acc[8];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) P[tq + j * LDP] = z[j];
+            for (int e = 0; e < 8; ++e) acc[e] = P[pos + (jb + e) * LDP];  // unit diagonal of inv(L11)
+            for (int t = jb + 1; t < NB; ++t) {
+                const c64 lt = P[pos + t * LDP];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (t > jb + e) cfma(acc[e], lt, P[t + (jb + e) * LDP]);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) P[pos + (jb + e) * LDP] = acc[e];
+        }
     }
     psync();
     c64* lpb = lp + (int64_t)pn * LDP * NB;
@@ -362,32 +390,32 @@ __device__ void panel_step(const CUtensorMap* tmap, const FactorArgs<float>& a, 
 // ------------------------------------------------------------------------------------------
 __device__ void gather_chunk(c64* ab, const BandDims& d, const Geo& G, int c0, int w, unsigned char* bimg,
                              const int* perm, const int* dq, int nd) {
+    constexpr int CPW = NCH / kUW;  // columns per warp
     const int lane = threadIdx.x & 31, uw = threadIdx.x >> 5;
     const int kv = d.kv, ldab = d.ldab, k0 = G.k0;
-    const int src = perm[lane];
-    for (int j = uw; j < NCH; j += kUW) {
-        const int c = c0 + j;
+    const int i = k0 + perm[lane];
+    const int drow = lane < nd ? dq[lane] : 0;
+    const int s = k0 + (lane < nd ? perm[drow] : 0);  // the original top row that moves down to drow
+    c64 v[CPW], dv[CPW];
+#pragma unroll
+    for (int e = 0; e < CPW; ++e) {  // every load in flight before any store
+        const int j = uw + e * kUW, c = c0 + j;
         const bool valid = j < w;
-        c64 v = czero<float>(), dv = czero<float>();
-        int drow = 0;
-        if (valid) {
-            const int i = k0 + src;
-            if (i >= c - kv) v = ab[(int64_t)(kv + i - c) + (int64_t)c * ldab];
-            if (lane < nd) {
-                drow = dq[lane];
-                const int s = k0 + perm[drow];  // the original top row that moves down to drow
-                if (s >= c - kv) dv = ab[(int64_t)(kv + s - c) + (int64_t)c * ldab];
-            }
-        }
-        __syncwarp();
-        if (valid && lane < nd) ab[(int64_t)(kv + k0 + drow - c) + (int64_t)c * ldab] = dv;
-        put_elem(bimg, NCH, j, lane, v);
+        v[e] = (valid && i >= c - kv) ? ab[(int64_t)(kv + i - c) + (int64_t)c * ldab] : czero<float>();
+        dv[e] = (valid && lane < nd && s >= c - kv) ? ab[(int64_t)(kv + s - c) + (int64_t)c * ldab] : czero<float>();
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < CPW; ++e) {
+        const int j = uw + e * kUW, c = c0 + j;
+        if (j < w && lane < nd) ab[(int64_t)(kv + k0 + drow - c) + (int64_t)c * ldab] = dv[e];
+        put_elem(bimg, NCH, j, lane, v[e]);
     }
 }
 
 // Epilogue of one chunk: warp uw reads tensor-memory lanes 32 (uw % 4).. of tile uw / 4, i.e.
-// block rows q = 128 (uw / 4) + 32 (uw % 4) + lane, in 32-column halves (C loaded before the
-// accumulators are read).
+// block rows q = 128 (uw / 4) + 32 (uw % 4) + lane, 16 columns at a time (the C values are loaded
+// before the accumulators are read).
 __device__ void epilogue_chunk(c64* ab, const BandDims& d, const Geo& G, int c0, int w, int N, uint32_t tb,
                                uint64_t* accfull, uint32_t parity, TcbShared& S) {
     const int lane = threadIdx.x & 31, uw = threadIdx.x >> 5;
@@ -398,10 +426,10 @@ __device__ void epilogue_chunk(c64* ab, const BandDims& d, const Geo& G, int c0,
     const bool is_u = q < G.nbe, is_c = !is_u && q < G.m;
     const uint32_t ta = tb + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * 128);
     bool ok = true;
-    for (int h = 0; h < N; h += 32) {
-        c64 v[32];
+    for (int h = 0; h < N; h += 16) {
+        c64 v[16];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
+        for (int c = 0; c < 16; ++c) {
             const int col = c0 + h + c;
             v[c] = (is_c && h + c < w) ? ab[(int64_t)(kv + row - col) + (int64_t)col * ldab] : czero<float>();
         }
@@ -409,25 +437,19 @@ __device__ void epilogue_chunk(c64* ab, const BandDims& d, const Geo& G, int c0,
             ok = wait_or_fail(accfull, parity, S);
             tc_fence_after();
         }
-        const int nh = min(32, N - h);  // 16 or 32
+        float dr[16], di[16];
+        tc_ld16(ta + h, dr);
+        tc_ld16(ta + 64 + h, di);
+        tc_wait_ld();
+        if (ok) {
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            if (s * 16 < nh) {
-                float dr[16], di[16];
-                tc_ld16(ta + h + s * 16, dr);
-                tc_ld16(ta + 64 + h + s * 16, di);
-                tc_wait_ld();
-                if (ok) {
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int cc = h + s * 16 + e;
-                        const int col = c0 + cc;
-                        if (cc < w) {
-                            const int64_t at = (int64_t)(kv + row - col) + (int64_t)col * ldab;
-                            if (is_c) ab[at] = mk<float>(v[s * 16 + e].re - dr[e], v[s * 16 + e].im - di[e]);
-                            else if (is_u && row >= col - kv) ab[at] = mk<float>(dr[e], di[e]);
-                        }
-                    }
+            for (int e = 0; e < 16; ++e) {
+                const int cc = h + e;
+                const int col = c0 + cc;
+                if (cc < w) {
+                    const int64_t at = (int64_t)(kv + row - col) + (int64_t)col * ldab;
+                    if (is_c) ab[at] = mk<float>(v[e].re - dr[e], v[e].im - di[e]);
+                    else if (is_u && row >= col - kv) ab[at] = mk<float>(dr[e], di[e]);
                 }
             }
         }
@@ -452,18 +474,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     int* dq = reinterpret_cast<int*>(base + OFF_DISP);  // displaced rows: [0..31] current, [32..63] next
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&S.bfull[i], kUW);
-            mbar_init(&S.accfull[i], 1);
-            mbar_init(&S.accempty[i], kUW);
-        }
+        for (int i = 0; i < 2; ++i) mbar_init(&S.accfull[i], 2);
         mbar_init(&S.tma, 1);
         S.fail = 0;
         S.info = 0;
         S.nd = S.nd_next = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMW) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
                      "r"(TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -483,10 +501,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Geo G(p, d.n, d.kl, d.kv);
         // ---- the panel's X to its operand image, its permutation and displaced rows current ----
         for (int it = tid; it < LDP * 4; it += kThreads) {
-            const int r = it >> 2, gq = it & 3;
+            const int r = it & (LDP - 1), gq = it >> 8;
             c64 v[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = (r < G.m) ? P[r + (8 * gq + e) * LDP] : czero<float>();
+            for (int e = 0; e < 8; ++e) {
+                const int t = 8 * gq + e;
+                // rows of the top block hold inv(U11) on and above the diagonal (for the solves):
+                // the operand takes inv(L11) there, unit diagonal and zeros above it
+                c64 val = (r < G.m) ? P[r + t * LDP] : czero<float>();
+                if (r < G.nbe && t >= r) val = (t == r) ? mk<float>(1.f, 0.f) : czero<float>();
+                v[e] = val;
+            }
             put_row8(base + (r >> 7) * A_TILE, MT, r & (MT - 1), gq, v);
         }
         for (int q = tid; q < LDP; q += kThreads) perm_cur[q] = perm_next[q];
@@ -497,50 +522,47 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nd = S.nd;
 
         if (warp < kUW) {
-            // ---- update team: gather / image of chunk t + 1, then the epilogue of chunk t ----------
+            // ---- update team: image of chunk t + 1 and its MMAs, then the epilogue of chunk t -----
+            // Warps 0 and 4 issue the MMAs of tile 0 and tile 1 right after the team barrier that
+            // follows the image writes; the epilogues of the buffer's previous chunk were complete
+            // (tensor-memory loads waited for) before that barrier.
             auto produce = [&](int t) {
                 int c0, w;
                 G.chunk(t, c0, w);
-                const int b = (g + t) & 1;
-                gather_chunk(ab, d, G, c0, w, base + OFF_B + b * B_BUF, perm_cur, dq, nd);
+                gather_chunk(ab, d, G, c0, w, base + OFF_B + ((g + t) & 1) * B_BUF, perm_cur, dq, nd);
                 fence_async_smem();
+            };
+            auto issue = [&](int t) {
+                int c0, w;
+                G.chunk(t, c0, w);
+                const int N = (w + 15) & ~15;
+                const int b = (g + t) & 1;
+                tc_fence_after();
+                if ((warp & 3) == 0 && lane == 0) {
+                    if (!failed(S)) issue_tile(a_base, b_base + b * B_BUF, S.tmem + b * 256, N, warp >> 2);
+                    tc_commit(&S.accfull[b]);
+                }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&S.bfull[b]);
             };
             if (G.nch > 0) produce(0);
+            tc_fence_before();
             usync();
+            if (G.nch > 0) issue(0);
             for (int t = 0; t < G.nch; ++t) {
                 if (t + 1 < G.nch) produce(t + 1);
-                usync();  // the displaced rows written by produce(t) are visible to every epilogue warp
+                tc_fence_before();
+                usync();  // image t + 1 written; displaced rows of chunk t visible to every epilogue warp
+                if (t + 1 < G.nch) issue(t + 1);
                 int c0, w;
                 G.chunk(t, c0, w);
                 const int N = (w + 15) & ~15;
                 const int gg = g + t, b = gg & 1;
                 epilogue_chunk(ab, d, G, c0, w, N, S.tmem + b * 256, &S.accfull[b], (gg >> 1) & 1, S);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.accempty[b]);
                 if (t == 0) {
                     fence_async_global();  // the next panel's columns, read next by TMA
                     __threadfence_block();
                     lead_arrive();
                 }
-            }
-        } else if (warp == kMW) {
-            // ---- MMA issue ----------------------------------------------------------------------
-            for (int t = 0; t < G.nch; ++t) {
-                int c0, w;
-                G.chunk(t, c0, w);
-                const int N = (w + 15) & ~15;
-                const int gg = g + t, b = gg & 1, use = gg >> 1;
-                wait_or_fail(&S.bfull[b], use & 1, S);
-                if (use >= 1) wait_or_fail(&S.accempty[b], (use - 1) & 1, S);
-                tc_fence_after();
-                if (lane == 0) {
-                    if (!failed(S)) issue_chunk(a_base, b_base + b * B_BUF, S.tmem + b * 256, N);
-                    tc_commit(&S.accfull[b]);
-                }
-                __syncwarp();
             }
         } else if (p + 1 < d.npanels) {
             // ---- panel team: the next panel, once its columns are updated --------------------
@@ -554,16 +576,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (failed(S)) break;
     }
     // drain: the last commits of each buffer (bounded), so tensor memory is idle before it is freed
-    if (warp == kMW && g > 0) {
+    if (warp == 0 && g > 0) {
         for (int b = 0; b < 2; ++b) {
             const int uses = (g - b + 1) / 2;  // chunks that used buffer b
-            if (uses > 0) mbar_wait(&S.accfull[b], (uses - 1) & 1);
+            if (uses > 0) wait_backoff(&S.accfull[b], (uses - 1) & 1);
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMW)
+    if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(TMEM_COLS) : "memory");
     if (tid == 0) a.info[pt] = failed(S) ? -1 : S.info;
 }
