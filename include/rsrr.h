@@ -164,7 +164,8 @@ int rsrr_create_nep_tz(int64_t n, const int64_t* rowptr, const int32_t* colind, 
  *   precision  RSRR_FP64 or RSRR_C64_IR, optionally | RSRR_REFINE_FULL
  *   tol        backward-error target per column,
  *              eta = ||u - T x||_2 / (||T||_1 ||x||_2 + ||u||_2) <= tol  (e.g. 1e-10)
- *   max_refine refinement sweeps allowed in RSRR_C64_IR (ignored for RSRR_FP64)
+ *   max_refine refinement sweeps allowed in RSRR_C64_IR (ignored for RSRR_FP64), 0..100; after
+ *              rsrr_set_band_preconditioner the budget of Krylov iterations, 0..100000
  * Errors: EINVAL, ESINGULAR (a zero pivot: some z_j is an eigenvalue),
  *         ENOTCONVERGED (eta > tol after max_refine sweeps, or > tol in FP64),
  *         ENONFINITE, ENOMEM, ECUDA. */
@@ -173,15 +174,17 @@ int rsrr_sample(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L,
 
 /* ---- rsrr_set_band_preconditioner -----------------------------------------------------
  * An iterative sampler for NEPs whose full band is too wide to factor but whose dominant part
- * is banded (Section 7.3-7.4 solve such systems iteratively with an incomplete factorisation,
- * GMRES with ILU).  With band >= 0, the following rsrr_sample / rsrr_sample_points /
+ * is banded (Section 7.3 solves such systems iteratively: GMRES preconditioned by an incomplete
+ * factorisation).  With band >= 0, the following rsrr_sample / rsrr_sample_points /
  * rsrr_sample_batch calls factor only the entries of T(z_j) with |i - j| <= band (in the
- * handle's ordering: pass RSRR_NATURAL_ORDER at creation to keep the caller's) and reach the
- * tolerance by the refinement iteration X += M^{-1} (U - T(z_j) X) with the FP64 residual of
- * the full T(z_j) (the same loop as RSRR_C64_IR; in RSRR_FP64 the incomplete factor is FP64).
- * The iteration converges when ||M^{-1} (T - M)|| < 1; otherwise the call fails with
- * ENOTCONVERGED after max_refine sweeps (the halving rule stops it earlier).  band = -1 turns it
- * off (the default: the full band, or the dense LU).  It overrides RSRR_DENSE_LU.
+ * handle's ordering: pass RSRR_NATURAL_ORDER at creation to keep the caller's) and solve
+ * T(z_j) X = U by restarted flexible GMRES in FP64 (restart length up to 30, fewer when device
+ * memory is short), right-preconditioned by that factor (complex64 in RSRR_C64_IR, complex128 in
+ * RSRR_FP64), starting from X = M^{-1} U.  Every (point, column) system iterates until its
+ * residual estimate gives eta <= tol / 2 (eta ~ 2e-16 with RSRR_REFINE_FULL); max_refine is the
+ * budget of preconditioned products over all restarts, after which a column with eta > tol fails
+ * the call with ENOTCONVERGED.  band = -1 turns it off (the default: the full band, or the dense
+ * LU).  It overrides RSRR_DENSE_LU.
  * Errors: EINVAL (NULL handle, band < -1 or >= n). */
 int rsrr_set_band_preconditioner(rsrr_nep h, int32_t band);
 

@@ -224,7 +224,9 @@ int check_sample_args(rsrr_nep h, const rsrr_contour* C, int32_t N, int32_t L, i
     const int mode = precision & 0xff;
     if ((mode != RSRR_FP64 && mode != RSRR_C64_IR) || (precision & ~(0xff | RSRR_REFINE_FULL)))
         return set_error(RSRR_EINVAL, "unknown precision or flag");
-    if (!(tol > 0) || max_refine < 0 || max_refine > 100) return set_error(RSRR_EINVAL, "bad tol or max_refine");
+    // max_refine: refinement sweeps (direct factor), or Krylov iterations (iterative sampler)
+    if (!(tol > 0) || max_refine < 0 || max_refine > (h->precond_band >= 0 ? 100000 : 100))
+        return set_error(RSRR_EINVAL, "bad tol or max_refine");
     if ((int64_t)N * L * h->n > (int64_t)1 << 34) return set_error(RSRR_ENOMEM, "S_hat too large");
     return RSRR_OK;
 }

@@ -17,6 +17,7 @@
 #include "band_tc.cuh"
 #include "dense_lu.cuh"
 #include "internal.h"
+#include "krylov.cuh"
 
 namespace rsrr {
 
@@ -367,6 +368,59 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         {
             dim3 g((unsigned)ceil_div(nl, 256), np);
             { accumulate_kernel<R><<<g, 256, 0, st>>>(X, B, nl, 0, nullptr); note_launch(); }
+        }
+        if (h->precond_band >= 0) {
+            // Iterative sampler: flexible GMRES from X = M^{-1} U, preconditioned by the factor of
+            // the band part of T(z_j) (krylov.cu); max_refine counts preconditioned products.
+            size_t fb = 0, tbytes = 0;
+            CUDAC(cudaMemGetInfo(&fb, &tbytes));
+            KrylovArgs<R> ka;
+            ka.st = st;
+            ka.n = n;
+            ka.nnz = nnz;
+            ka.np = np;
+            ka.L = L;
+            ka.rowptr = h->d_rowptr;
+            ka.colind = h->d_colind;
+            ka.tvals = tvals;
+            ka.U = h->d_U;
+            ka.X = X;
+            ka.normT = normT;
+            ka.un2 = un2;
+            ka.tau = h->refine_full ? 2e-16 : 0.5 * h->tol;
+            ka.m = krylov_restart(n, (int64_t)np * L, fb);
+            ka.max_iter = max_refine;
+            ka.B = B;
+            ka.precond = [&](const int32_t* act) {
+                SolveArgs<R> s2 = sa;
+                s2.active = act;
+                int r = fwd_any<R>(tc, s2, np, st);
+                if (r == RSRR_OK) r = launch_bwd<R>(s2, np, st);
+                h->trsv_launches += 2;
+                return r;
+            };
+            int kit = 0;
+            TRYC(krylov_solve<R>(ka, &kit));
+            max_sweeps = std::max(max_sweeps, kit);
+            // backward errors of the result; every column must meet tol
+            CUDAC(cudaMemsetAsync(rn2, 0, (size_t)L * np * 8, st));
+            CUDAC(cudaMemsetAsync(xn2, 0, (size_t)L * np * 8, st));
+            CUDAC(cudaMemsetAsync(counters, 0, 16, st));
+            dim3 g((unsigned)ceil_div(n, 128), np);
+            { residual_kernel<R><<<g, 128, 0, st>>>(h->d_rowptr, h->d_colind, tvals, nnz, n, L, h->d_U, X, B, rn2, xn2,
+                                                  nullptr); note_launch(); }
+            { eta_kernel<<<np, 32, 0, st>>>(rn2, xn2, un2, normT, np, L, h->tol, h->tol, eta, active, prev_max,
+                                          counters, 1); note_launch(); }
+            int32_t hc[4];
+            std::vector<double> he((size_t)np * L);
+            CUDAC(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, st));
+            CUDAC(cudaMemcpyAsync(he.data(), eta, he.size() * 8, cudaMemcpyDeviceToHost, st));
+            CUDAC(cudaStreamSynchronize(st));
+            if (trsv_pending) { h->ms_trsv += evs.ms(); trsv_pending = false; }
+            if (hc[1]) { nonfinite = true; break; }
+            for (double e : he) if (!(e <= h->tol)) notconv = true;
+            if (notconv) break;
+            continue;
         }
         int sweeps = 0;
         for (;;) {
