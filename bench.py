@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--banded", action="store_true",
                     help="config 3: iterative sampler - factor only each member's grid-Laplacian band (half-width "
                          "s, natural ordering) and iterate with the full T (rsrr_set_band_preconditioner)")
+    ap.add_argument("--dense", action="store_true",
+                    help="config 3: the dense LU for every member (no autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 arm of the same workload")
     ap.add_argument("--no-cpu", action="store_true")
@@ -474,7 +476,10 @@ def run_batch(args):
     # handles go through rsrr_project / rsrr_solve in a host thread of their own
     streams = [torch.cuda.Stream() for _ in range(SOLVE_STREAMS)]
     sps = [ctypes.c_void_p(st.cuda_stream) for st in streams]
-    flags = rs.RSRR_NATURAL_ORDER if args.banded else 0
+    # default: the library's autotuner picks each member's sampler (timed on one point, cached
+    # per size bucket); --banded forces the iterative sampler on the grid band, --dense the dense LU
+    autotune = not (args.banded or args.dense)
+    flags = rs.RSRR_NATURAL_ORDER if args.banded else (rs.RSRR_NATURAL_ORDER | rs.RSRR_AUTOTUNE if autotune else 0)
 
     def make(i, p, rowptr, colind, vals):
         h = rs.Nep(p.n, rowptr, colind, vals, fns_of(p), flags, sps[i % len(sps)])
@@ -538,7 +543,12 @@ def run_batch(args):
     med = lambda key: statistics.median(sum(i[key] for i in step_infos) for step_infos in infos)
     fac_ms = statistics.median(step_infos[0]["ms_factor"] for step_infos in infos)
     launches_f = infos[-1][0]["factor_launches"]
-    if args.banded:  # band LU of the band part, kl = ku = s: 8 n kl (kl + ku) real flops per point
+    strategies = [i["tune_strategy"] for i in infos[-1]]
+    iterative = [i["iterative_band"] >= 0 for i in infos[-1]]
+    if any(iterative) and not all(iterative):
+        pass  # mixed: the roofline below follows the majority
+    banded_now = args.banded or (autotune and sum(iterative) * 2 > len(iterative))
+    if banded_now:  # band LU of the band part, kl = ku = s: 8 n kl (kl + ku) real flops per point
         flops = sum(p.N * 8.0 * p.n * p.meta["nx"] * 2 * p.meta["nx"] for p in probs)
         fac_ms = med("ms_factor")
         launches_f = sum(i["factor_launches"] for i in infos[-1])
@@ -546,7 +556,7 @@ def run_batch(args):
         flops = sum(p.N * dense_lu_flops(p.n) for p in probs)
     achieved = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
     bf16, _, src = measured_peaks()
-    if args.banded:
+    if banded_now:
         lu_peak = FFMA_PEAK_TFLOPS if precision == "c64" else FP64_PEAK_TFLOPS
         roof = {"kernel": "band_factor_kernel<%s> (band part of T only: the incomplete factor of the iterative "
                           "sampler)" % ("float" if precision == "c64" else "double"), "bound": "alu",
@@ -565,7 +575,7 @@ def run_batch(args):
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
                 "peak_source": "nominal FP64 rate"}
     roof.update({"algorithmic": (f"8 n s (2 s) real flops per point (band half-width s), {points} points in "
-                                  f"{launches_f} launches") if args.banded else
+                                  f"{launches_f} launches") if banded_now else
                  f"(8/3) n^3 real flops per point, {points} points in {launches_f} launches",
                  "ms_per_step": fac_ms})
     roof["frac"] = achieved / roof["peak"] if achieved else None
@@ -607,10 +617,12 @@ def run_batch(args):
                 "config": dict({k: v for k, v in W.items() if k != "data"}, batch=B, precision=precision,
                                n_range=[min(p.n for p in probs), max(p.n for p in probs)],
                                parallelism=f"replicas x{world}" if world > 1 else "1 GPU", tol=args.tol,
-                               sampler=("iterative: band part factored (half-width s), full-T FP64 residual "
-                                        "iteration") if args.banded else "dense LU",
+                               sampler=("iterative: band part factored (half-width s), FGMRES on the full T")
+                               if args.banded else ("autotuned per member (RSRR_AUTOTUNE)" if autotune else "dense LU"),
                                l2="inputs larger than L2 (dense factors of GBs per step)"),
                 "phases_ms_median": phases, "eigs_inside": counts,
+                "tune_strategies": {name: strategies.count(code) for code, name in
+                                    ((0, "band_tc"), (1, "band_cuda_cores"), (2, "dense"), (3, "iterative"), (-1, "untuned"))},
                 "max_eta": max(i["max_eta"] for step_infos in infos for i in step_infos),
                 "refine_sweeps": max(i["refine_sweeps"] for i in infos[-1]),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}

@@ -109,6 +109,14 @@ typedef struct {
 #define RSRR_DENSE_LU      0x2u  /* factor every sampling point with the dense LU, whatever the
                                     band (otherwise chosen when the band is wider than 768 or
                                     than 2n/5 for n >= 128) */
+#define RSRR_AUTOTUNE      0x8u  /* before the first sampling, time the sampler strategies on one
+                                    sampling point and keep the fastest that meets the tolerance:
+                                    band LU on the tensor cores, band LU on the CUDA cores, the
+                                    dense LU, or the iterative sampler (GMRES preconditioned by the
+                                    factor of the band part holding all but 1e-12 of the weight of
+                                    T(z_0)); decisions are cached process-wide per size bucket
+                                    (rsrr_info.tune_*).  Overrides the flags and the band
+                                    preconditioner set before that sampling. */
 #define RSRR_BAND_CUDA_CORES 0x4u  /* complex64 band LU on the CUDA cores for every band (otherwise
                                     bands with 32 <= kl <= 224 run their trailing updates on the
                                     tensor cores, with the forward solve on the stored
@@ -124,7 +132,7 @@ typedef struct rsrr_nep_s* rsrr_nep;
  *   colind    [nnz] column indices, each row's entries strictly increasing
  *   vals_reim [J][nnz][2] values of A_i on the union pattern (zeros where A_i has none)
  *   f         [J] the functions f_i
- *   flags     0, or RSRR_NATURAL_ORDER, RSRR_DENSE_LU, RSRR_BAND_CUDA_CORES
+ *   flags     0, or RSRR_NATURAL_ORDER, RSRR_DENSE_LU, RSRR_BAND_CUDA_CORES, RSRR_AUTOTUNE
  *   stream    cudaStream_t on which all device work of this handle runs (NULL = default)
  *   out       receives the handle
  * The library picks a row/column ordering (reverse Cuthill-McKee, or the natural one if
@@ -341,6 +349,11 @@ typedef struct {
                                    matrix, 40 mb real flops (+ 24 k for the accumulated rotations) */
     int32_t band_lu_tc;         /* 1 if the last rsrr_sample ran the complex64 band LU with its
                                    trailing updates on the tensor cores (kl in [32, 224])     */
+    int32_t tune_strategy;      /* RSRR_AUTOTUNE's choice: 0 band LU (tensor cores), 1 band LU
+                                   (CUDA cores), 2 dense LU, 3 iterative sampler; -1 untuned */
+    int32_t tune_band;          /* the iterative sampler's band half-width it chose, else -1   */
+    int32_t tune_cached;        /* 1 if the choice came from the cache of a similar NEP        */
+    int32_t iterative_band;     /* the band preconditioner in force (-1: direct solves)       */
 } rsrr_info;
 
 int rsrr_get_info(rsrr_nep h, rsrr_info* out);

@@ -25,6 +25,7 @@ RSRR_REFINE_FULL = 0x100
 RSRR_NATURAL_ORDER = 0x1
 RSRR_DENSE_LU = 0x2
 RSRR_BAND_CUDA_CORES = 0x4
+RSRR_AUTOTUNE = 0x8
 
 F_CONST, F_Z, F_Z2, F_ISQRT_SHIFT, F_EXP_DELAY, F_RATIONAL, F_CALLBACK, F_CHEBYSHEV = range(8)
 
@@ -95,7 +96,9 @@ class rsrr_info(ctypes.Structure):
                 ("red_terms", ctypes.c_int32), ("proj_cols", ctypes.c_int32),
                 ("ms_zgemm_tc", ctypes.c_double), ("zgemm_tc_gflop", ctypes.c_double),
                 ("ms_jacobi", ctypes.c_double), ("jacobi_gflop", ctypes.c_double),
-                ("band_lu_tc", ctypes.c_int32)]
+                ("band_lu_tc", ctypes.c_int32), ("tune_strategy", ctypes.c_int32),
+                ("tune_band", ctypes.c_int32), ("tune_cached", ctypes.c_int32),
+                ("iterative_band", ctypes.c_int32)]
 
 
 _lib = None

@@ -91,7 +91,7 @@ int create_impl(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* coli
     if (n < 1 || n > (int64_t)INT32_MAX - 1) return set_error(RSRR_EINVAL, "n out of range");
     if (tz ? J != 0 : (J < 1 || J > 16)) return set_error(RSRR_EINVAL, "J must be in 1..16");
     if (!rowptr || !colind || (!tz && (!vals_reim || !f))) return set_error(RSRR_EINVAL, "NULL input array");
-    if (flags & ~(RSRR_NATURAL_ORDER | RSRR_DENSE_LU | RSRR_BAND_CUDA_CORES))
+    if (flags & ~(RSRR_NATURAL_ORDER | RSRR_DENSE_LU | RSRR_BAND_CUDA_CORES | RSRR_AUTOTUNE))
         return set_error(RSRR_EINVAL, "unknown flag bits");
     if (rowptr[0] != 0) return set_error(RSRR_EINVAL, "rowptr[0] must be 0");
     for (int64_t r = 0; r < n; ++r) {
@@ -124,6 +124,7 @@ int create_impl(int64_t n, int32_t J, const int64_t* rowptr, const int32_t* coli
     choose_ordering(n, rowptr, colind, (flags & RSRR_NATURAL_ORDER) != 0, &h->ord);
     h->force_dense = (flags & RSRR_DENSE_LU) != 0;
     h->band_cuda_cores = (flags & RSRR_BAND_CUDA_CORES) != 0;
+    h->autotune = (flags & RSRR_AUTOTUNE) != 0;
     // permuted CSR (rows in new order, columns renumbered and sorted) and values
     std::vector<int64_t> prow(n + 1, 0);
     std::vector<int32_t> pcol(nnz), prowidx(nnz);
@@ -445,6 +446,10 @@ int rsrr_get_info(rsrr_nep h, rsrr_info* o) {
     o->zgemm_gflop = (h->zgemm_flops_project + h->zgemm_flops_solve) * 1e-9;
     o->dense_lu = h->dense_used ? 1 : 0;
     o->band_lu_tc = (h->band_tc_used && !h->dense_used) ? 1 : 0;
+    o->tune_strategy = h->tuned ? h->tune_strategy : -1;
+    o->tune_band = h->tuned ? h->tune_band : -1;
+    o->tune_cached = h->tune_cached ? 1 : 0;
+    o->iterative_band = h->precond_band;
     o->proj_cols = h->proj_cols;
     o->red_terms = h->red_J;
     o->ms_zgemm_tc = h->ms_zgemm_tc_project + h->ms_zgemm_tc_solve;

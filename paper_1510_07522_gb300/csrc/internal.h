@@ -64,6 +64,9 @@ struct rsrr_nep_s {
     int32_t* d_perm = nullptr;     // [n] perm[new] = old
     bool force_dense = false;      // RSRR_DENSE_LU: factor every point with the dense LU
     bool band_cuda_cores = false;  // RSRR_BAND_CUDA_CORES: no tensor-core band LU
+    bool autotune = false;         // RSRR_AUTOTUNE: the sampler strategy is timed and chosen
+    bool tuned = false, tune_cached = false;
+    int tune_strategy = -1, tune_band = -1;
     int32_t precond_band = -1;     // >= 0: factor only |i - j| <= precond_band of T(z_j) and iterate
     bool dense_used = false;       // the last rsrr_sample factored densely
     bool band_tc_used = false;     // the last rsrr_sample ran the tensor-core band LU

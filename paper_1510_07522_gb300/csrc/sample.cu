@@ -11,6 +11,9 @@
 // factors fit in free device memory.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "band.cuh"
@@ -680,9 +683,175 @@ int dense_run(const std::vector<rsrr_nep>& hs, const std::vector<std::vector<c12
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------
+// Sampler autotuner (handles created with RSRR_AUTOTUNE).  Before a handle's first sampling, the
+// candidate strategies for its T(z_j) solves are timed on one sampling point (z_0) with the call's
+// own precision, tolerance and budget, and the fastest that meets the tolerance is kept:
+//   band LU on the tensor cores (when the band suits them), band LU on the CUDA cores, the dense
+//   LU, and the iterative sampler (flexible GMRES preconditioned by the factor of a band part,
+//   the half-width p holding all but 1e-12 of the Frobenius weight of T(z_0)).
+// A dense point is timed only for n <= 2048; above that its time is extrapolated with n^3 from
+// the last dense measurement.  Decisions are cached process-wide per size bucket (n, kl, ku in
+// steps of 25 %, J, precision, ordering), so a batch of similar NEPs tunes once.
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int nb, klb, kub, J, prec, natural;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nb, klb, kub, J, prec, natural) < std::tie(o.nb, o.klb, o.kub, o.J, o.prec, o.natural);
+    }
+};
+std::mutex g_tune_mx;
+std::map<TuneKey, std::pair<int, int>> g_tune;   // -> (strategy, band)
+double g_dense_ms_per_n3 = 0.0;                  // last dense trial: ms / n^3
+
+int size_bucket(int64_t x) { return x <= 0 ? -1 : (int)std::floor(std::log((double)x) / std::log(1.25)); }
+
+// weight of T(z_0) per |row - col| offset (device atomics), then the smallest half-width holding
+// all but `frac` of it
+__global__ void offset_weight_kernel(const c128* __restrict__ vals, int J, int64_t nnz, const int32_t* __restrict__ rowidx,
+                                     const int32_t* __restrict__ colind, const c128* __restrict__ F,
+                                     double* __restrict__ w) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    c128 v = czero<double>();
+    for (int i = 0; i < J; ++i) cfma(v, F[i], vals[(int64_t)i * nnz + k]);
+    atomicAdd(&w[abs(rowidx[k] - colind[k])], cnorm2(v));
+}
+
+int dominant_band(rsrr_nep h, const c128* F0, double frac, int64_t* band) {
+    cudaStream_t st = h->stream;
+    const int64_t n = h->n;
+    double* w = nullptr;
+    c128* dF = nullptr;
+    RSRR_TRY(dalloc_n(&w, (size_t)n, st));
+    int rc = dalloc_n(&dF, (size_t)h->J, st);
+    std::vector<double> hw((size_t)n);
+    if (rc == RSRR_OK && (cudaMemsetAsync(w, 0, (size_t)n * 8, st) != cudaSuccess ||
+                          cudaMemcpyAsync(dF, F0, (size_t)h->J * sizeof(c128), cudaMemcpyHostToDevice, st) != cudaSuccess))
+        rc = set_error(RSRR_ECUDA, "autotune: copies");
+    if (rc == RSRR_OK) {
+        offset_weight_kernel<<<(unsigned)ceil_div(h->nnz, 256), 256, 0, st>>>(h->d_vals, h->J, h->nnz, h->d_rowidx,
+                                                                             h->d_colind, dF, w);
+        note_launch();
+        if (cudaMemcpyAsync(hw.data(), w, (size_t)n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_error(RSRR_ECUDA, "autotune: offset weights");
+    }
+    dfree(w, st);
+    dfree(dF, st);
+    RSRR_TRY(rc);
+    double total = 0.0;
+    for (double x : hw) total += x;
+    double acc = 0.0;
+    int64_t p = 0;
+    for (; p < n; ++p) {
+        acc += hw[p];
+        if (total - acc <= frac * total) break;
+    }
+    *band = p;
+    return RSRR_OK;
+}
+
+enum { TUNE_BAND_TC = 0, TUNE_BAND_CC = 1, TUNE_DENSE = 2, TUNE_ITER = 3 };
+
+void apply_strategy(rsrr_nep h, int strategy, int band) {
+    h->precond_band = strategy == TUNE_ITER ? band : -1;
+    h->band_cuda_cores = strategy == TUNE_BAND_CC;
+    h->force_dense = strategy == TUNE_DENSE;
+}
+
+// Time of one sampling point (z_0) with a strategy, in ms; +inf if it fails or does not converge.
+double trial_ms(rsrr_nep h, const std::vector<c128>& F0, int strategy, int band, int max_refine) {
+    const int N0 = h->N, pb = h->precond_band;
+    const bool cc = h->band_cuda_cores, fd = h->force_dense;
+    apply_strategy(h, strategy, band);
+    h->N = 1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h->stream);
+    int rc;
+    if (strategy == TUNE_DENSE) {
+        std::vector<rsrr_nep> hs{h};
+        std::vector<std::vector<c128>> Fs{F0};
+        rc = h->precision == RSRR_FP64 ? dense_run<double>(hs, Fs, max_refine) : dense_run<float>(hs, Fs, max_refine);
+    } else {
+        rc = h->precision == RSRR_FP64 ? sample_impl<double>(h, F0, max_refine) : sample_impl<float>(h, F0, max_refine);
+    }
+    cudaEventRecord(b, h->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->N = N0;
+    h->precond_band = pb;
+    h->band_cuda_cores = cc;
+    h->force_dense = fd;
+    return rc == RSRR_OK ? (double)ms : INFINITY;
+}
+
+int autotune(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
+    if (!h->autotune || h->tuned || h->tz) return RSRR_OK;
+    const int64_t n = h->n, kl = h->ord.kl, ku = h->ord.ku;
+    const TuneKey key{size_bucket(n), size_bucket(kl), size_bucket(ku), h->J, h->precision | (h->refine_full ? 0x100 : 0),
+                      h->ord.natural ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mx);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            int64_t band = it->second.second;
+            if (it->second.first == TUNE_ITER) RSRR_TRY(dominant_band(h, F.data(), 1e-12, &band));
+            apply_strategy(h, it->second.first, (int)band);
+            h->tuned = true;
+            h->tune_cached = true;
+            h->tune_strategy = it->second.first;
+            h->tune_band = (int)band;
+            return RSRR_OK;
+        }
+    }
+    const std::vector<c128> F0(F.begin(), F.begin() + h->J);
+    double best = INFINITY;
+    int best_s = -1, best_band = -1;
+    auto consider = [&](int s, int band, double ms) {
+        if (ms < best) { best = ms; best_s = s; best_band = band; }
+    };
+    const bool band_ok = kl <= 2048 && ku <= 2048;
+    if (band_ok) {
+        if (h->precision != RSRR_FP64 && band_tc_eligible(n, kl, ku))
+            consider(TUNE_BAND_TC, -1, trial_ms(h, F0, TUNE_BAND_TC, -1, max_refine));
+        consider(TUNE_BAND_CC, -1, trial_ms(h, F0, TUNE_BAND_CC, -1, max_refine));
+    }
+    if (n <= 2048) {
+        const double ms = trial_ms(h, F0, TUNE_DENSE, -1, max_refine);
+        if (std::isfinite(ms)) g_dense_ms_per_n3 = ms / ((double)n * n * n);
+        consider(TUNE_DENSE, -1, ms);
+    } else if (g_dense_ms_per_n3 > 0.0) {
+        consider(TUNE_DENSE, -1, g_dense_ms_per_n3 * (double)n * n * n);
+    } else if (!band_ok) {
+        consider(TUNE_DENSE, -1, 1e30);  // the only direct option left
+    }
+    int64_t p = 0;
+    RSRR_TRY(dominant_band(h, F0.data(), 1e-12, &p));
+    if (p < std::min(kl, ku) && p < n - 1)
+        consider(TUNE_ITER, (int)p, trial_ms(h, F0, TUNE_ITER, (int)p, max_refine));
+    if (best_s < 0) best_s = band_ok ? TUNE_BAND_CC : TUNE_DENSE;
+    apply_strategy(h, best_s, best_band);
+    h->tuned = true;
+    h->tune_cached = false;
+    h->tune_strategy = best_s;
+    h->tune_band = best_band;
+    std::lock_guard<std::mutex> lk(g_tune_mx);
+    g_tune[key] = {best_s, best_band};
+    return RSRR_OK;
+}
+}  // namespace
+
 int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
     std::vector<std::vector<c128>> F(1);
     RSRR_TRY(sample_prepare(h, U_reim, &F[0]));
+    RSRR_TRY(autotune(h, F[0], max_refine));
     h->dense_used = use_dense(h);
     if (h->dense_used) {
         std::vector<rsrr_nep> hs{h};
@@ -697,6 +866,7 @@ int sample_run(rsrr_nep h, const double* U_reim, int max_refine) {
 int sample_batch_run(const std::vector<rsrr_nep>& hs, const std::vector<const double*>& U, int max_refine) {
     std::vector<std::vector<c128>> F(hs.size());
     for (size_t i = 0; i < hs.size(); ++i) RSRR_TRY(sample_prepare(hs[i], U[i], &F[i]));
+    for (size_t i = 0; i < hs.size(); ++i) RSRR_TRY(autotune(hs[i], F[i], max_refine));
     std::vector<rsrr_nep> dh;
     std::vector<std::vector<c128>> dFs;
     for (size_t i = 0; i < hs.size(); ++i) {
