@@ -78,6 +78,8 @@ def parse():
                                                        "every member on an s x s grid)")
     ap.add_argument("--rates", default="1,4,16", help="serve: Poisson arrival rates, requests/s")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per rate")
+    ap.add_argument("--fp64-requests", type=int, default=0,
+                    help="serve: requests of the plain-FP64 one-at-a-time comparison (0 = min(requests, 40))")
     ap.add_argument("--batch", type=int, default=0, help="config 3: members of the batch (0 = the config's own)")
     ap.add_argument("--banded", action="store_true",
                     help="config 3: iterative sampler - factor only each member's grid-Laplacian band (half-width "
@@ -327,6 +329,22 @@ def run_ours(args):
                 "algorithmic": "per sweep: 4 mb k for the column norms, 8 mb per pair whose inner product is "
                                "formed, 32 mb + 24 k per rotated pair (rotation of B and of the k-row J, new "
                                "norms); pairs and rotations counted by the kernel", "ms_per_step": jac_ms}
+    # the SVD stages against a fixed count that does not grow with the sweeps: a bidiagonalising
+    # SVD with both vector sets, ~4 (4 m n^2 + 8 n^3) real flops for a complex m x n (m >= n):
+    # the projection's SVD of R^H (N L x rows kept) and the Hankel SVD (K k_S square)
+    def gk(m, nn):
+        m, nn = max(m, nn), min(m, nn)
+        return 4.0 * (4.0 * m * nn * nn + 8.0 * nn ** 3)
+    svd_ms = phases["project_svd_ms"] + phases["solve_svd_ms"]
+    svd_work = gk(prob.N * prob.L, infos[-1]["rows_kept"]) + gk(W["K"] * infos[-1]["k_S"], W["K"] * infos[-1]["k_S"])
+    svd_tf = svd_work / (svd_ms / 1e3) / 1e12 if svd_ms > 0 else None
+    roof_svd = {"kernel": "SVD stages (QR preconditioner, one-sided Jacobi sweeps, vectors), project + solve",
+                "bound": "alu", "achieved": svd_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (svd_tf / FP64_PEAK_TFLOPS) if svd_tf else None, "traffic": None,
+                "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                "algorithmic": "fixed count of a bidiagonalising SVD with vectors, 4 (4 m n^2 + 8 n^3) real flops "
+                               "per complex m x n: R^H (N L x rows kept) and H (K k_S square)",
+                "ms_per_step": svd_ms}
     phases["zgemm_ms"] = zg_ms
     phases["zgemm_tc_ms"] = tc_ms
     phases["jacobi_ms"] = jac_ms
@@ -411,7 +429,8 @@ def run_ours(args):
                 "rows_kept": infos[-1]["rows_kept"],
                 "jacobi_sweeps": [infos[-1]["jacobi_sweeps_project"], infos[-1]["jacobi_sweeps_solve"]],
                 "max_eta": max(i["max_eta"] for i in infos), "n_eigs_inside": int(lam.size),
-                "roofline": roof, "rooflines": {"band_lu": roof_lu, "zgemm_tc": roof_tc, "jacobi": roof_jac},
+                "roofline": roof, "rooflines": {"band_lu": roof_lu, "zgemm_tc": roof_tc, "jacobi": roof_jac,
+                                                "svd_stage": roof_svd},
                 "vs_fp64": vs_fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -690,13 +709,16 @@ def run_serve(args):
                   errors=sorted({r.error for r in done if r.error}),
                   by_type={t: sum(1 for r in done if r.tag == t) for t in SERVE_TYPES})
         per_rate.append(st)
-    # the plain FP64 per-request path: the last rate's requests, one at a time, no overlap
-    reqs = serve_requests(serve, args.requests, len(rates) - 1, plain)
+    # the plain FP64 per-request path: the first requests of the last rate's stream, one at a time,
+    # no overlap (bounded: FP64 requests of the larger configs take seconds each)
+    n64 = args.fp64_requests or min(args.requests, 40)
+    reqs = serve_requests(serve, args.requests, len(rates) - 1, plain)[:n64]
     srv = serve.Server(budget_bytes=150e9, slots=1)
     done = serve.replay(srv, reqs, serve.poisson_arrivals(rates[-1], len(reqs), seed=1))
     srv.close()
     fp64 = serve.latency_stats(done)
-    fp64.update(rate=rates[-1], errors=sorted({r.error for r in done if r.error}))
+    fp64.update(rate=rates[-1], requests=len(reqs), errors=sorted({r.error for r in done if r.error}),
+                by_type={t: sum(1 for r in done if r.tag == t) for t in SERVE_TYPES})
     clk = clocks.stop()
     launches = rs.lib().rsrr_kernel_launches() - l0
     top = per_rate[-1]

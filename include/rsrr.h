@@ -310,6 +310,18 @@ int rsrr_zgemm(int32_t path, int32_t opA, int32_t opB, int32_t M, int32_t N, int
                const void* A, int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB,
                const double* beta_reim, void* C, int64_t ldc, int64_t sC, int32_t batch, void* stream);
 
+/* ---- rsrr_zinv_batch (diagnostics) -----------------------------------------------------
+ * The reduced solve's matrix inverse on caller device memory: A (batch x [k][k], column-major,
+ * complex128 as [2] doubles, consecutive matrices) is replaced by its inverse, computed by
+ * blocked Gauss-Jordan elimination with partial pivoting (Algorithm 1 needs T_S(z_j)^{-1} in
+ * full for the moments of Eq. eq-Ap-num).  Its rank-b updates run on rsrr_zgemm's `path` (as
+ * there).  info (device, batch int32) is zeroed here and set to 1 for a matrix that met an
+ * exactly zero pivot column (its result is then meaningless).  Runs on `stream` (NULL = the
+ * default stream) and returns after the work finished.
+ * Errors: EINVAL (bad sizes or path), EUNSUPPORTED (k above the panel limit, about 1600),
+ *         ENOMEM, ETIMEOUT, ECUDA. */
+int rsrr_zinv_batch(int32_t path, int32_t k, int32_t batch, void* A, int32_t* info, void* stream);
+
 /* ---- introspection (tests, diagnostics) ------------------------------------------------ */
 typedef struct {
     int64_t n, nnz;
@@ -411,6 +423,11 @@ int rsrr_band_solve_noalloc(int64_t n, int32_t kl, int32_t ku, double* ab_reim, 
  *   stream  cudaStream_t for the work (NULL = default); returns after it completes.
  * The device context stays usable after every kind.  Errors: EINVAL (kind), ENOMEM, ECUDA. */
 int rsrr_selftest_bounded_wait(int32_t kind, void* stream);
+
+/* Diagnostics: the largest number of bytes the library's device allocations (the current
+ * device's default stream-ordered memory pool) have held at once since the last reset; reset != 0
+ * starts a new measurement after reading.  Negative RSRR_E* code on failure. */
+int64_t rsrr_device_peak_bytes(int32_t reset);
 
 /* Number of CUDA kernels this library has launched in the process so far (all handles). */
 int64_t rsrr_kernel_launches(void);

@@ -107,7 +107,8 @@ EXPORTS = ["rsrr_create_nep", "rsrr_sample", "rsrr_project", "rsrr_solve", "rsrr
            "rsrr_get_projected", "rsrr_get_hankel_sigma", "rsrr_destroy", "rsrr_last_error",
            "rsrr_version", "rsrr_kernel_launches", "rsrr_band_solve_noalloc", "rsrr_sample_batch",
            "rsrr_project_moments", "rsrr_sample_points", "rsrr_project_chebyshev", "rsrr_create_nep_tz",
-           "rsrr_zgemm", "rsrr_set_band_preconditioner", "rsrr_selftest_bounded_wait"]
+           "rsrr_zgemm", "rsrr_set_band_preconditioner", "rsrr_selftest_bounded_wait",
+           "rsrr_device_peak_bytes", "rsrr_zinv_batch"]
 
 
 def lib():
@@ -145,6 +146,8 @@ def lib():
                        ctypes.c_int),
         "rsrr_set_band_preconditioner": ([P, I32], ctypes.c_int),
         "rsrr_selftest_bounded_wait": ([I32, P], ctypes.c_int),
+        "rsrr_device_peak_bytes": ([I32], ctypes.c_int64),
+        "rsrr_zinv_batch": ([I32, I32, I32, P, P, P], ctypes.c_int),
         "rsrr_sample_points": ([P, P, I32, P, I32, P, I32, D, I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -283,6 +286,14 @@ def zgemm(path, A, B, C, opA=0, opB=0, alpha=1.0, beta=0.0, M=None, N=None, K=No
                             ctypes.c_void_p(B.data_ptr()), int(ldb), int(strides[1]), be,
                             ctypes.c_void_p(C.data_ptr()), int(ldc), int(strides[2]), int(batch),
                             stream if stream is not None else current_stream()))
+
+
+def zinv_batch(path, A, info, k, batch, stream=None):
+    """rsrr_zinv_batch: A (device, batch consecutive k x k complex128 column-major matrices) is
+    replaced by its inverse; info (device int32 [batch]) flags matrices with a zero pivot."""
+    _check(lib().rsrr_zinv_batch(int(path), int(k), int(batch), ctypes.c_void_p(A.data_ptr()),
+                                 ctypes.c_void_p(info.data_ptr()),
+                                 stream if stream is not None else current_stream()))
 
 
 def rsrr_project_chebyshev(h, d, x_lo, x_hi, delta=1e-14):

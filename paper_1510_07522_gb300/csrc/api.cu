@@ -79,6 +79,22 @@ const char* rsrr_last_error(void) { return rsrr::last_error(); }
 const char* rsrr_version(void) { return "rsrr-gb300 0.1 (sm_103a)"; }
 int64_t rsrr_kernel_launches(void) { return rsrr::launches_total(); }
 
+int64_t rsrr_device_peak_bytes(int32_t reset) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return rsrr::set_error(RSRR_ECUDA, "cudaGetDevice failed");
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess)
+        return rsrr::set_error(RSRR_ECUDA, "no default memory pool");
+    uint64_t high = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess)
+        return rsrr::set_error(RSRR_ECUDA, "cudaMemPoolGetAttribute failed");
+    if (reset) {
+        uint64_t zero = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    }
+    return (int64_t)high;
+}
+
 }  // extern "C"
 
 namespace {
@@ -401,6 +417,20 @@ int rsrr_zgemm(int32_t path, int32_t opA, int32_t opB, int32_t M, int32_t N, int
     zgemm_set_path(path);
     const int rc = zgemm(g, reinterpret_cast<cudaStream_t>(stream));
     zgemm_set_path(prev);
+    return rc;
+}
+
+int rsrr_zinv_batch(int32_t path, int32_t k, int32_t batch, void* A, int32_t* info, void* stream) {
+    if (path < 0 || path > 2 || k < 1 || batch < 1 || !A || !info)
+        return set_error(RSRR_EINVAL, "rsrr_zinv_batch: bad argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(info, 0, (size_t)batch * 4, st) != cudaSuccess)
+        return set_error(RSRR_ECUDA, "rsrr_zinv_batch: memset");
+    const int prev = zgemm_get_path();
+    zgemm_set_path(path);
+    int rc = zinv_batch(static_cast<c128*>(A), k, batch, info, st);
+    zgemm_set_path(prev);
+    if (rc == RSRR_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = set_error(RSRR_ECUDA, "rsrr_zinv_batch");
     return rc;
 }
 

@@ -595,7 +595,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 //   x[k0 + q] = sum_{t <= q} inv(L11)[q, t] x'_t       (q < nbe, unit diagonal)
 //   x[k0 + q] = x'_q - sum_t W[q, t] x'_t              (nbe <= q < m).
 // The next panel's X block is bulk-copied into the second buffer while the current one is used.
-// One CTA per (point, share of the right-hand-side columns).
+// One CTA per (point, share of the right-hand-side columns).  A bounded wait that gives up marks
+// the point's solution non-finite (the caller's residual check then reports it).
 // ------------------------------------------------------------------------------------------
 constexpr int kFwdThreads = 512;
 constexpr int kFwdLC = 4;  // right-hand-side columns per thread
@@ -686,7 +687,140 @@ __global__ void __launch_bounds__(kFwdThreads) band_fwd_tc_kernel(SolveArgs<floa
                 if (l0 + c < Lp) x[(int64_t)(k0 + q) + (int64_t)(l0 + c) * n] = acc[c];
         }
         __syncthreads();
-        if (s_fail) break;
+        // every thread reads the flag between two barriers, so all of them leave together
+        const int stop = s_fail;
+        __syncthreads();
+        if (stop) break;
+    }
+    if (s_fail) {
+        // let the copies in flight land (bounded), then mark this share of the solution non-finite
+        if (tid == 0) {
+            mbar_wait(&bar[0], ph[0], 1u << 16);
+            mbar_wait(&bar[1], ph[1], 1u << 16);
+        }
+        const float nan = __int_as_float(0x7fc00000);
+        for (int64_t idx = tid; idx < (int64_t)Lp * n; idx += kFwdThreads) x[idx] = mk<float>(nan, nan);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward solve with U in the band and inv(U11) from the stored blocks: per panel, from the
+// last one up,
+//   r = x_blk - U12 x_right        (U12: the block's rows of U right of its diagonal block, at most
+//                                   kv columns; x_right: the rows already solved)
+//   x_blk = inv(U11) r
+// U12 is a rectangle of the band's dense view (rows x = kv + k0 .. + 31, columns c), so it
+// arrives by TMA in chunks of 32 x 64 into a ring of nbuf shared-memory buffers; thread 0 keeps
+// the ring nbuf - 1 chunks ahead of the consumers, across panel boundaries.  Entries of a chunk
+// right of a row's band (c > row + kv) are never used.  The solved rows a panel needs (the kv
+// rows below it) stay in a circular window of shared memory (row c at c mod wrows).
+// Thread (lane q, warp l): block row q, right-hand side l; the window entries are broadcast.
+// One CTA per (point, share of the right-hand sides).  A bounded wait that gives up marks the
+// point's solution non-finite (the caller's residual check then reports it).
+// ------------------------------------------------------------------------------------------
+constexpr int kBwdThreads = 512;
+constexpr int kBwdCh = 64;                                  // U12 columns per chunk
+constexpr uint32_t kBwdChBytes = kBwdCh * NB * 8;           // 16 KB
+constexpr int kBwdMaxBuf = 4;
+
+__global__ void __launch_bounds__(kBwdThreads)
+    band_bwd_tc_kernel(const __grid_constant__ CUtensorMap umap, SolveArgs<float> a, int wrows, int nbuf) {
+    extern __shared__ __align__(16) unsigned char bwd_raw[];
+    __shared__ __align__(8) uint64_t fb[kBwdMaxBuf];
+    __shared__ int s_fail;
+    const BandDims d = a.d;
+    const int pt = blockIdx.x / a.split, part = blockIdx.x % a.split;
+    if (a.active && !a.active[pt]) return;
+    const int tid = threadIdx.x, q = tid & 31, l = tid >> 5;
+    const c64* lp = a.lp + pt * a.lp_stride;
+    const int c_lo = (int)((int64_t)a.L * part / a.split), c_hi = (int)((int64_t)a.L * (part + 1) / a.split);
+    c64* x = a.x + pt * a.x_stride + (int64_t)c_lo * d.n;
+    const int Lp = c_hi - c_lo, n = d.n, kv = d.kv;
+    // [nbuf][kBwdCh][32] U12 chunks (TMA box layout), 1024-byte aligned (the size includes the slack)
+    c64* ub = reinterpret_cast<c64*>(bwd_raw + ((1024u - (smem_u32(bwd_raw) & 1023u)) & 1023u));
+    c64* win = ub + (size_t)nbuf * kBwdCh * 32;     // [wrows][32]
+    c64* ui = win + (size_t)wrows * 32;             // [32][33] inv(U11)
+    c64* rb = ui + 32 * 33;                         // [32][33] r
+    const bool act = l < Lp;
+    auto chunks_of = [&](int p) {
+        const int k0 = p * NB, cb = k0 + min(NB, n - k0), c_end = min(n, k0 + NB + kv);
+        return cb < c_end ? (c_end - cb + kBwdCh - 1) / kBwdCh : 0;
+    };
+    // producer state (thread 0): the next chunk to load
+    int pp = d.npanels - 1, pc = 0;
+    auto issue_next = [&](int slot) {
+        while (pp >= 0 && pc >= chunks_of(pp)) { --pp; pc = 0; }
+        if (pp < 0) return;
+        const int k0 = pp * NB, cb = k0 + min(NB, n - k0);
+        mbar_expect_tx(&fb[slot], kBwdChBytes);
+        tma_load_3d(ub + (size_t)slot * kBwdCh * 32, &umap, kv + k0, cb + pc * kBwdCh, pt, &fb[slot]);
+        ++pc;
+    };
+    if (tid == 0) {
+        for (int i = 0; i < nbuf; ++i) mbar_init(&fb[i], 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&umap) : "memory");
+    }
+    // the last chunk of a panel can reach columns whose window slots were never written
+    for (int idx = tid; idx < wrows * 32; idx += kBwdThreads) win[idx] = czero<float>();
+    __syncthreads();
+    if (tid == 0)
+        for (int i = 0; i < nbuf; ++i) issue_next(i);
+    int g = 0;  // chunks consumed
+    for (int p = d.npanels - 1; p >= 0; --p) {
+        const int k0 = p * NB, nbe = min(NB, n - k0), cb = k0 + nbe, row = k0 + q;
+        for (int idx = tid; idx < NB * NB; idx += kBwdThreads) {
+            const int qq = idx % NB, j = idx / NB;
+            ui[qq * 33 + j] = (qq <= j && j < nbe) ? lp[(int64_t)p * LDP * NB + qq + (int64_t)j * LDP] : czero<float>();
+        }
+        const int nch = chunks_of(p);
+        c64 acc0 = czero<float>(), acc1 = czero<float>();
+        if (act && q < nbe) acc0 = x[row + (int64_t)l * n];
+        // this row's band ends at column row + kv (and the matrix at n - 1)
+        const int c_stop = min(n, row + kv + 1);
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+            const int slot = g % nbuf;
+            if (!mbar_wait(&fb[slot], (uint32_t)((g / nbuf) & 1))) s_fail = 1;
+            const c64* u = ub + (size_t)slot * kBwdCh * 32;
+            const int c0 = cb + ch * kBwdCh;
+            if (act && q < nbe && !s_fail) {
+                const int jl = min(kBwdCh, c_stop - c0);
+                int slot_w = c0 % wrows, j = 0;
+                for (; j + 1 < jl; j += 2) {
+                    int s1 = slot_w + 1;
+                    if (s1 >= wrows) s1 -= wrows;
+                    cfms(acc0, u[j * 32 + q], win[slot_w * 32 + l]);
+                    cfms(acc1, u[(j + 1) * 32 + q], win[s1 * 32 + l]);
+                    slot_w = s1 + 1;
+                    if (slot_w >= wrows) slot_w -= wrows;
+                }
+                if (j < jl) cfms(acc0, u[j * 32 + q], win[slot_w * 32 + l]);
+            }
+            __syncthreads();  // the slot is free again
+            if (tid == 0 && !s_fail) issue_next(slot);
+        }
+        if (act && q < nbe) rb[q * 33 + l] = acc0 + acc1;
+        __syncthreads();
+        if (act && q < nbe) {
+            c64 sacc = czero<float>();
+            for (int j = q; j < nbe; ++j) cfma(sacc, ui[q * 33 + j], rb[j * 33 + l]);
+            x[row + (int64_t)l * n] = sacc;
+            win[(row % wrows) * 32 + l] = sacc;
+        }
+        __syncthreads();
+        // every thread reads the flag between two barriers, so all of them leave together
+        const int stop = s_fail;
+        __syncthreads();
+        if (stop) break;
+    }
+    if (s_fail) {
+        // let the loads in flight land (bounded) before the block's shared memory is released,
+        // then mark this share of the solution non-finite
+        if (tid == 0)
+            for (int i = 0; i < nbuf; ++i) mbar_wait(&fb[(g + i) % nbuf], (uint32_t)(((g + i) / nbuf) & 1), 1u << 16);
+        const float nan = __int_as_float(0x7fc00000);
+        for (int64_t idx = tid; idx < (int64_t)Lp * n; idx += kBwdThreads) x[idx] = mk<float>(nan, nan);
     }
 }
 
@@ -784,6 +918,42 @@ int launch_factor_tc(const FactorArgs<float>& a, int npts, cudaStream_t s) {
     RSRR_TRY(band_tensor_map(&map, a.ab, a.ab_stride, npts, d, kTcLDP, kTcNB));
     RSRR_TRY(set_smem_max(band_factor_tc_kernel, SMEM_BYTES, "band_factor_tc_kernel"));
     band_factor_tc_kernel<<<npts, kThreads, SMEM_BYTES, s>>>(map, a);
+    note_launch();
+    RSRR_CUDA(cudaGetLastError());
+    return RSRR_OK;
+}
+
+namespace {
+int bwd_window_rows(const BandDims& d) { return (d.kv + 2 * NB + 31) / 32 * 32; }  // >= kv + 64 solved rows
+size_t bwd_smem(const BandDims& d, int nbuf) {
+    return (size_t)nbuf * kBwdChBytes + (size_t)bwd_window_rows(d) * 32 * sizeof(c64) +
+           (size_t)2 * 32 * 33 * sizeof(c64) + 1024;
+}
+constexpr size_t kBwdSmemMax = 224 * 1024;
+int bwd_nbuf(const BandDims& d) {
+    for (int nb : {kBwdMaxBuf, 2})
+        if (bwd_smem(d, nb) <= kBwdSmemMax) return nb;
+    return 0;
+}
+}  // namespace
+
+bool band_bwd_tc_fits(const BandDims& d) { return bwd_nbuf(d) > 0; }
+
+int launch_bwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s) {
+    if (a.L > 64) return set_error(RSRR_EINVAL, "launch_bwd_tc: at most 64 right-hand sides");
+    const int nbuf = bwd_nbuf(a.d);
+    if (!nbuf) return set_error(RSRR_EINVAL, "launch_bwd_tc: band too wide for the solved-row window");
+    if ((a.d.kv & 1) || (a.ab_stride & 1) || (reinterpret_cast<uintptr_t>(a.ab) & 15))
+        return set_error(RSRR_EINVAL, "launch_bwd_tc: band layout not prepared for TMA");
+    const int wrows = bwd_window_rows(a.d);
+    const size_t sm = bwd_smem(a.d, nbuf);
+    CUtensorMap map;
+    RSRR_TRY(band_tensor_map(&map, a.ab, a.ab_stride, npts, a.d, NB, kBwdCh));
+    RSRR_TRY(set_smem_max(band_bwd_tc_kernel, sm, "band_bwd_tc_kernel"));
+    SolveArgs<float> b = a;
+    b.split = a.L > 16 ? 2 : solve_split_tc(npts, a.L);
+    if ((a.L + b.split - 1) / b.split > 16) b.split = (a.L + 15) / 16;
+    band_bwd_tc_kernel<<<npts * b.split, kBwdThreads, sm, s>>>(map, b, wrows, nbuf);
     note_launch();
     RSRR_CUDA(cudaGetLastError());
     return RSRR_OK;

@@ -30,6 +30,12 @@ int pick_dims_tc(int64_t n, int64_t kl, int64_t ku, BandDims* d);
 int64_t tc_ab_stride(const BandDims& d);
 
 int launch_factor_tc(const FactorArgs<float>& a, int npts, cudaStream_t s);
+// Solves take at most 64 right-hand sides per launch (EINVAL beyond).
 int launch_fwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
+// Backward solve with U in the band and the stored inv(U11) blocks; its shared-memory window of
+// kv + 64 solved rows fits for kv up to about 770 (band_bwd_tc_fits), beyond that the CUDA-core
+// backward solve (band.cuh) takes the same storage.
+bool band_bwd_tc_fits(const BandDims& d);
+int launch_bwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
 
 }  // namespace rsrr

@@ -25,6 +25,13 @@ struct Zgemm {
     bool fp64 = false;  // FP64 CUDA cores even where the tensor-core emulation would be chosen
 };
 int zgemm(const Zgemm& g, cudaStream_t s);
+// In-place inverses of `batch` dense k x k complex128 matrices (column-major, stride k^2) by
+// blocked Gauss-Jordan elimination with partial pivoting (zinv.cu); info[t] (zeroed by the
+// caller) is set to 1 where matrix t met an exactly zero pivot column.  zinv_block(k) is the block
+// width, 0 when a k-row panel does not fit shared memory (EUNSUPPORTED).
+int zinv_block(int k);
+size_t zinv_bytes_per_matrix(int k);
+int zinv_batch(c128* X, int k, int batch, int32_t* info, cudaStream_t st);
 // FP64-accurate ZGEMM on the tensor cores (exact BF16 digit products, see zgemm_tc.cu), and
 // the shapes for which zgemm() takes it.  zgemm_path: 0 = by shape, 1 = FP64 CUDA cores only,
 // 2 = tensor cores for every shape (per host thread; for tests and measurements).

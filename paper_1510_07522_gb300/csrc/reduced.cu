@@ -3,8 +3,10 @@
 //
 //   moments   A_alpha = 1/(i N_S) sum_j w_j^alpha phi'(theta_j) T_S(z_j)^{-1},
 //             w_j = (z_j - gamma)/rho, rho = max(a, b)                       (Eq. eq-Ap-num)
-//             T_S(z_j)^{-1}: dense LU of each T_S(z_j) with the band kernels (kl = ku = k_S-1)
-//             and a solve against I; the weighted sums are one ZGEMM.
+//             T_S(z_j)^{-1}: blocked Gauss-Jordan elimination with partial pivoting, batched
+//             over the points, its rank-bb updates on the ZGEMM (zinv.cu); for k_S too large
+//             for its panels, a dense LU on the band kernels (kl = ku = k_S-1) solved against I.
+//             The weighted sums are one ZGEMM.
 //   winding   1/(i N_S) sum_j phi'_j tr(T_S(z_j)^{-1} T_S'(z_j))            (Eq. eq-ncs)
 //   Hankel    H, H^< from A_0..A_{2K-1}                                      (Eq. eq-HH)
 //   SVD of H  one-sided Jacobi with accumulated rotations                  (Eq. eq-svdH)
@@ -36,6 +38,18 @@ __global__ void assemble_reduced_kernel(const c128* P, int J, int k, const c128*
     c128 v = czero<double>();
     for (int i = 0; i < J; ++i) cfma(v, f[i], P[(int64_t)i * k * k + idx]);
     ab[pt * ab_stride + (int64_t)(kv + r - c) + (int64_t)c * ldab] = v;
+}
+
+// T_S(z_j) = sum_i F[j][i] P_i, dense column-major (k x k per point).
+__global__ void assemble_reduced_dense_kernel(const c128* P, int J, int k, const c128* F, int j0, c128* X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pt = blockIdx.y;
+    const int64_t kk = (int64_t)k * k;
+    if (idx >= kk) return;
+    const c128* f = F + (int64_t)(j0 + pt) * J;
+    c128 v = czero<double>();
+    for (int i = 0; i < J; ++i) cfma(v, f[i], P[(int64_t)i * kk + idx]);
+    X[pt * kk + idx] = v;
 }
 
 __global__ void identity_batch_kernel(c128* X, int k, int npts) {
@@ -367,14 +381,28 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
         }
     }
     const int64_t kk = (int64_t)k * k;
-    BandDims d;
-    RSRR_TRY(pick_dims(k, k - 1, k - 1, false, &d));
-    const size_t ab_e = (size_t)d.ldab * k, lp_e = (size_t)d.npanels * d.ldp * d.nb,
-                 perm_e = (size_t)d.npanels * d.ldp;
-    const size_t per_pt = (ab_e + lp_e + kk) * sizeof(c128) + perm_e * 4 + (size_t)k * 4 + 64;
+    // The inverses: blocked Gauss-Jordan (zinv.cu) while a k-row panel fits shared memory, else
+    // the band LU and solve kernels on dense band storage (kl = ku = k - 1) against I.
+    const bool gje = zinv_block(k) > 0;
+    BandDims d{};
+    size_t ab_e = 0, lp_e = 0, perm_e = 0, per_pt = 0;
+    if (gje) {
+        per_pt = zinv_bytes_per_matrix(k) + 64;
+    } else {
+        RSRR_TRY(pick_dims(k, k - 1, k - 1, false, &d));
+        ab_e = (size_t)d.ldab * k;
+        lp_e = (size_t)d.npanels * d.ldp * d.nb;
+        perm_e = (size_t)d.npanels * d.ldp;
+        per_pt = (ab_e + lp_e + kk) * sizeof(c128) + perm_e * 4 + (size_t)k * 4 + 64;
+    }
     size_t free_b = 0, total_b = 0;
     RSRR_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(N_S, (int64_t)(0.6 * free_b) / (int64_t)per_pt));
+    // Points factored at once: as many as fit 60 % of the free memory and a fixed 24 GiB (so that
+    // a caller can bound the request's footprint: at most max(per_pt, 24 GiB) here), spread
+    // evenly over the chunks.
+    const int64_t fit = std::min<int64_t>((int64_t)(0.6 * free_b), (int64_t)24 << 30) / (int64_t)per_pt;
+    const int64_t nchunk = ceil_div((int64_t)N_S, std::max<int64_t>(1, fit));
+    const int chunk = (int)ceil_div((int64_t)N_S, nchunk);
 
     c128 *dFt = nullptr, *dWt = nullptr, *ab = nullptr, *lp = nullptr, *X = nullptr, *mom = nullptr,
          *Pt = nullptr, *trc = nullptr, *H = nullptr, *Hl = nullptr, *Jm = nullptr, *V0 = nullptr, *W0 = nullptr,
@@ -399,11 +427,13 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     CUDAC(cudaMemcpyAsync(dFt, F.data(), F.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
     TRYC(dalloc_n(&dWt, Wt.size(), st));
     CUDAC(cudaMemcpyAsync(dWt, Wt.data(), Wt.size() * sizeof(c128), cudaMemcpyHostToDevice, st));
-    TRYC(dalloc(reinterpret_cast<void**>(&ab), ab_e * sizeof(c128) * chunk, st));
-    TRYC(dalloc(reinterpret_cast<void**>(&lp), lp_e * sizeof(c128) * chunk, st));
+    if (!gje) {
+        TRYC(dalloc(reinterpret_cast<void**>(&ab), ab_e * sizeof(c128) * chunk, st));
+        TRYC(dalloc(reinterpret_cast<void**>(&lp), lp_e * sizeof(c128) * chunk, st));
+        TRYC(dalloc_n(&perm, perm_e * chunk, st));
+        TRYC(dalloc_n(&ipiv, (size_t)k * chunk, st));
+    }
     TRYC(dalloc_n(&X, (size_t)kk * chunk, st));
-    TRYC(dalloc_n(&perm, perm_e * chunk, st));
-    TRYC(dalloc_n(&ipiv, (size_t)k * chunk, st));
     TRYC(dalloc_n(&info, (size_t)chunk, st));
     TRYC(alloc_zero(&mom, (size_t)2 * K * kk, st));
     TRYC(dalloc_n(&Pt, (size_t)J * kk, st));
@@ -415,17 +445,24 @@ int solve_run(rsrr_nep h, int N_S, int K, double tol_gap, int cap, double* lambd
     // ---- moments and traces, chunk by chunk ------------------------------------------------------
     for (int j0 = 0; j0 < N_S; j0 += chunk) {
         const int np = std::min(chunk, N_S - j0);
-        CUDAC(cudaMemsetAsync(ab, 0, ab_e * sizeof(c128) * np, st));
         dim3 ga((unsigned)ceil_div(kk, 256), np);
-        { assemble_reduced_kernel<<<ga, 256, 0, st>>>(h->d_P, J, k, dFt, j0, d.kv, d.ldab, ab, (int64_t)ab_e); note_launch(); }
-        FactorArgs<double> fa{d, ab, (int64_t)ab_e, lp, (int64_t)lp_e, perm, (int64_t)perm_e, ipiv, info};
-        TRYC(launch_factor<double>(fa, np, st));
         std::vector<int32_t> hinfo(np);
-        CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
-        { identity_batch_kernel<<<ga, 256, 0, st>>>(X, k, np); note_launch(); }
-        SolveArgs<double> sa{d, ab, (int64_t)ab_e, lp, (int64_t)lp_e, perm, (int64_t)perm_e, X, kk, k, nullptr};
-        TRYC(launch_fwd<double>(sa, np, st));
-        TRYC(launch_bwd<double>(sa, np, st));
+        if (gje) {
+            { assemble_reduced_dense_kernel<<<ga, 256, 0, st>>>(h->d_P, J, k, dFt, j0, X); note_launch(); }
+            CUDAC(cudaMemsetAsync(info, 0, (size_t)np * 4, st));
+            TRYC(zinv_batch(X, k, np, info, st));
+            CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
+        } else {
+            CUDAC(cudaMemsetAsync(ab, 0, ab_e * sizeof(c128) * np, st));
+            { assemble_reduced_kernel<<<ga, 256, 0, st>>>(h->d_P, J, k, dFt, j0, d.kv, d.ldab, ab, (int64_t)ab_e); note_launch(); }
+            FactorArgs<double> fa{d, ab, (int64_t)ab_e, lp, (int64_t)lp_e, perm, (int64_t)perm_e, ipiv, info};
+            TRYC(launch_factor<double>(fa, np, st));
+            CUDAC(cudaMemcpyAsync(hinfo.data(), info, np * 4, cudaMemcpyDeviceToHost, st));
+            { identity_batch_kernel<<<ga, 256, 0, st>>>(X, k, np); note_launch(); }
+            SolveArgs<double> sa{d, ab, (int64_t)ab_e, lp, (int64_t)lp_e, perm, (int64_t)perm_e, X, kk, k, nullptr};
+            TRYC(launch_fwd<double>(sa, np, st));
+            TRYC(launch_bwd<double>(sa, np, st));
+        }
         CUDAC(cudaStreamSynchronize(st));
         for (int t = 0; t < np; ++t)
             if (hinfo[t]) { cleanup(); return set_error(RSRR_ESINGULAR, "T_S(z) is singular at a quadrature point"); }

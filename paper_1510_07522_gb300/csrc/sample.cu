@@ -247,12 +247,32 @@ int factor_any(bool tc, const FactorArgs<R>& a, int np, cudaStream_t st) {
     }
     return launch_factor<R>(a, np, st);
 }
+// The tensor-core factor's solves take at most 64 right-hand sides per launch: more run as
+// column blocks (each a separate set of systems with the same factors).
+template <typename R, typename F>
+int by_column_blocks(const SolveArgs<R>& a, F&& launch) {
+    for (int c0 = 0; c0 < a.L; c0 += 64) {
+        SolveArgs<R> b = a;
+        b.x = a.x + (int64_t)c0 * a.d.n;
+        b.L = std::min(64, a.L - c0);
+        RSRR_TRY(launch(b));
+    }
+    return RSRR_OK;
+}
 template <typename R>
 int fwd_any(bool tc, const SolveArgs<R>& a, int np, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (tc) return launch_fwd_tc(a, np, st);
+        if (tc) return by_column_blocks(a, [&](const SolveArgs<R>& b) { return launch_fwd_tc(b, np, st); });
     }
     return launch_fwd<R>(a, np, st);
+}
+template <typename R>
+int bwd_any(bool tc, const SolveArgs<R>& a, int np, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (tc && band_bwd_tc_fits(a.d))
+            return by_column_blocks(a, [&](const SolveArgs<R>& b) { return launch_bwd_tc(b, np, st); });
+    }
+    return launch_bwd<R>(a, np, st);
 }
 
 template <typename R>
@@ -364,7 +384,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
         }
         evs.start(st);
         TRYC(fwd_any<R>(tc, sa, np, st));
-        TRYC(launch_bwd<R>(sa, np, st));
+        TRYC(bwd_any<R>(tc, sa, np, st));
         evs.stop(st);
         bool trsv_pending = true;
         h->trsv_launches += 2;
@@ -398,7 +418,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
                 SolveArgs<R> s2 = sa;
                 s2.active = act;
                 int r = fwd_any<R>(tc, s2, np, st);
-                if (r == RSRR_OK) r = launch_bwd<R>(s2, np, st);
+                if (r == RSRR_OK) r = bwd_any<R>(tc, s2, np, st);
                 h->trsv_launches += 2;
                 return r;
             };
@@ -453,7 +473,7 @@ int sample_impl(rsrr_nep h, const std::vector<c128>& F, int max_refine) {
             sa.active = active;
             evs.start(st);
             TRYC(fwd_any<R>(tc, sa, np, st));
-            TRYC(launch_bwd<R>(sa, np, st));
+            TRYC(bwd_any<R>(tc, sa, np, st));
             evs.stop(st);
             trsv_pending = true;
             h->trsv_launches += 2;

@@ -63,16 +63,25 @@ def band_of(n: int, rowptr: np.ndarray, colind: np.ndarray):
     return int(max(0, -d.min())), int(max(0, d.max()))
 
 
-def footprint_bytes(n: int, kl: int, ku: int, N: int, L: int, nnz: int, J: int, c64: bool = True) -> int:
-    """Device memory a request needs at its peak (sampling factors or projection work)."""
+def footprint_bytes(n: int, kl: int, ku: int, N: int, L: int, nnz: int, J: int, c64: bool = True,
+                    N_S: int = 500, K: int = 2) -> int:
+    """An upper bound of the device memory a request holds at its peak: the sum of the sampling
+    factors, the projection work and the reduced solve's inverses (each phase frees its work
+    before the next, so the sum over-states the peak).  The reduced solve factors at most N_S
+    points of T_S(z) at once, and no more than 24 GiB of them (k_S <= min(n, N L) rows, dense
+    kept in band storage with kl = ku = k_S - 1: about 5 k_S^2 complex128 values per point)."""
     es = 8 if c64 else 16
     ldab = 2 * kl + ku + 1
     ldp = (32 + kl + 31) // 32 * 32
     per_point = ldab * n * es + n * ldp * es + n * L * es + nnz * 16 + n * 16
     sample = N * per_point
     s_hat = n * N * L * 16
-    project = 2 * s_hat + J * n * min(n, N * L) * 16 // 4
-    return int(sample + s_hat + project + J * nnz * 16 + (64 << 20))
+    k = min(n, N * L)
+    project = 4 * s_hat + J * n * k * 16
+    per_sample = 16 * (5 * k * k + 64 * k) + k * (k + 64) + 4 * k + 64
+    reduced = min(N_S * per_sample, max(per_sample, 24 << 30)) + 16 * k * k * (J + 2 * K + 4 * K * K + 8) \
+        + N_S * J * 16
+    return int(sample + s_hat + project + reduced + J * nnz * 16 + (64 << 20))
 
 
 @dataclass
@@ -141,7 +150,7 @@ class Server:
     def submit(self, req: Request) -> None:
         kl, ku = band_of(req.n, req.rowptr, req.colind)
         req.footprint = footprint_bytes(req.n, kl, ku, req.N, req.L, int(req.colind.size), int(req.vals.shape[0]),
-                                        (req.precision & 0xff) == RSRR_C64_IR)
+                                        (req.precision & 0xff) == RSRR_C64_IR, req.N_S, req.K)
         if req.footprint > self.budget:
             req.error = "request larger than the whole memory budget"
             req.t_done = self.now()

@@ -70,3 +70,34 @@ def test_request_larger_than_budget_is_refused(rs):
     done = srv.wait(1, timeout=30)
     srv.close()
     assert done[0].error and "budget" in done[0].error
+
+
+def test_admission_footprint_bounds_measured_peak(rs):
+    """The server admits a request when its estimated footprint fits the budget.  For each request
+    type of the serving stream at its serving size (configs 0, 1, 2 and a time-delay member), the
+    estimate must bound the device memory the request really holds at its peak (the library's
+    pool high-water mark, measured with the request running alone)."""
+    from paper_1510_07522_gb300 import serve
+    import bench
+    reqs = bench.serve_requests(serve, 4, 0, lambda t: (rs.RSRR_FP64 if t == "0" else rs.RSRR_C64_IR) | rs.RSRR_REFINE_FULL)
+    by_type = {}
+    for t in bench.SERVE_TYPES:   # one of each type, whatever the seeded draw gave
+        p = bench.workload(t) if t != "3" else w.config3_member(7, s=40)
+        prec = (rs.RSRR_FP64 if t == "0" else rs.RSRR_C64_IR) | rs.RSRR_REFINE_FULL
+        by_type[t] = serve.Request(rid=int(t), n=p.n, rowptr=p.rowptr, colind=p.colind, vals=p.vals, fns=fns_of(p),
+                                   gamma=p.gamma, a=p.a, b=p.b, N=p.N, L=p.L, U=p.U, precision=prec)
+    assert len(reqs) == 4
+    peaks = {}
+    for t, r in by_type.items():
+        kl, ku = serve.band_of(r.n, r.rowptr, r.colind)
+        fp = serve.footprint_bytes(r.n, kl, ku, r.N, r.L, int(r.colind.size), int(r.vals.shape[0]),
+                                   (r.precision & 0xff) == rs.RSRR_C64_IR)
+        rs.lib().rsrr_device_peak_bytes(1)
+        h = rs.Nep(r.n, r.rowptr, r.colind, r.vals, r.fns)
+        h.sample(r.gamma, r.a, r.b, r.N, r.L, r.U, r.precision, r.tol, 20)
+        h.project(r.delta)
+        h.solve(r.N_S, r.K, 1e3, 4096, False)
+        h.close()
+        peaks[t] = (rs.lib().rsrr_device_peak_bytes(0), fp)
+    for t, (peak, fp) in peaks.items():
+        assert 0 < peak <= fp, (t, peaks)

@@ -36,7 +36,12 @@ def test_footprint_grows_with_band_and_points():
     b = footprint_bytes(40000, 200, 200, 32, 32, 200000, 3)
     c = footprint_bytes(40000, 100, 100, 64, 32, 200000, 3)
     assert a > b and a > c
-    assert 15e9 < a < 40e9  # 64 points of a band-200 problem: ~17.5 GB of factors plus S_hat
+    # 64 points of a band-200 problem: ~17.5 GB of factors, S_hat and the projection work, and
+    # the reduced solve's inverses (k_S <= N L = 2048: capped at 24 GiB)
+    assert 15e9 < a < 80e9
+    d = footprint_bytes(40000, 200, 200, 64, 32, 200000, 3, N_S=50)
+    # 500 points of k_S = 2048 hit the cap (25.8 GB), 50 points take 50 x 0.34 GB
+    assert 7e9 < a - d < 10e9
 
 
 def test_enomem_alone_finishes_with_error():
