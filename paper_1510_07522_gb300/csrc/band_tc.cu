@@ -713,15 +713,20 @@ __global__ void __launch_bounds__(kFwdThreads) band_fwd_tc_kernel(SolveArgs<floa
 // arrives by TMA in chunks of 32 x 64 into a ring of nbuf shared-memory buffers; thread 0 keeps
 // the ring nbuf - 1 chunks ahead of the consumers, across panel boundaries.  Entries of a chunk
 // right of a row's band (c > row + kv) are never used.  The solved rows a panel needs (the kv
-// rows below it) stay in a circular window of shared memory (row c at c mod wrows).
-// Thread (lane q, warp l): block row q, right-hand side l; the window entries are broadcast.
-// One CTA per (point, share of the right-hand sides).  A bounded wait that gives up marks the
-// point's solution non-finite (the caller's residual check then reports it).
+// rows below it) stay in a circular window of shared memory (row c at c mod wrows, 16 columns).
+// U12 x_right is tiled over the threads: lane q = block row, warp w = (column group w % 4 of four
+// right-hand sides, quarter w / 4 of each chunk's 64 columns); the four quarters' partial sums are
+// added at the end of the panel.  Per step a thread loads one U entry and four window entries
+// (broadcast) for four complex multiply-adds.
+// One CTA per (point, share of at most 16 right-hand sides).  A bounded wait that gives up marks
+// the point's solution non-finite (the caller's residual check then reports it).
 // ------------------------------------------------------------------------------------------
 constexpr int kBwdThreads = 512;
 constexpr int kBwdCh = 64;                                  // U12 columns per chunk
 constexpr uint32_t kBwdChBytes = kBwdCh * NB * 8;           // 16 KB
-constexpr int kBwdMaxBuf = 4;
+constexpr int kBwdMaxBuf = 8;
+constexpr int kBwdCols = 16;                                // right-hand sides per CTA
+constexpr int kBwdPartLd = 18;                              // row stride of the partial sums (16-byte rows)
 
 __global__ void __launch_bounds__(kBwdThreads)
     band_bwd_tc_kernel(const __grid_constant__ CUtensorMap umap, SolveArgs<float> a, int wrows, int nbuf) {
@@ -731,17 +736,17 @@ __global__ void __launch_bounds__(kBwdThreads)
     const BandDims d = a.d;
     const int pt = blockIdx.x / a.split, part = blockIdx.x % a.split;
     if (a.active && !a.active[pt]) return;
-    const int tid = threadIdx.x, q = tid & 31, l = tid >> 5;
+    const int tid = threadIdx.x, q = tid & 31, w = tid >> 5, cg = w & 3, ks = w >> 2;
     const c64* lp = a.lp + pt * a.lp_stride;
     const int c_lo = (int)((int64_t)a.L * part / a.split), c_hi = (int)((int64_t)a.L * (part + 1) / a.split);
     c64* x = a.x + pt * a.x_stride + (int64_t)c_lo * d.n;
     const int Lp = c_hi - c_lo, n = d.n, kv = d.kv;
     // [nbuf][kBwdCh][32] U12 chunks (TMA box layout), 1024-byte aligned (the size includes the slack)
     c64* ub = reinterpret_cast<c64*>(bwd_raw + ((1024u - (smem_u32(bwd_raw) & 1023u)) & 1023u));
-    c64* win = ub + (size_t)nbuf * kBwdCh * 32;     // [wrows][32]
-    c64* ui = win + (size_t)wrows * 32;             // [32][33] inv(U11)
-    c64* rb = ui + 32 * 33;                         // [32][33] r
-    const bool act = l < Lp;
+    c64* win = ub + (size_t)nbuf * kBwdCh * 32;         // [wrows][16]
+    c64* ui = win + (size_t)wrows * kBwdCols;           // [32][33] inv(U11)
+    c64* pr = ui + 32 * 33;                             // [4][32][kBwdPartLd] partial sums, then r
+    const bool grp = 4 * cg < Lp;                       // this thread's column group holds a right-hand side
     auto chunks_of = [&](int p) {
         const int k0 = p * NB, cb = k0 + min(NB, n - k0), c_end = min(n, k0 + NB + kv);
         return cb < c_end ? (c_end - cb + kBwdCh - 1) / kBwdCh : 0;
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(kBwdThreads)
         asm volatile("prefetch.tensormap [%0];" ::"l"(&umap) : "memory");
     }
     // the last chunk of a panel can reach columns whose window slots were never written
-    for (int idx = tid; idx < wrows * 32; idx += kBwdThreads) win[idx] = czero<float>();
+    for (int idx = tid; idx < wrows * kBwdCols; idx += kBwdThreads) win[idx] = czero<float>();
     __syncthreads();
     if (tid == 0)
         for (int i = 0; i < nbuf; ++i) issue_next(i);
@@ -775,8 +780,7 @@ __global__ void __launch_bounds__(kBwdThreads)
             ui[qq * 33 + j] = (qq <= j && j < nbe) ? lp[(int64_t)p * LDP * NB + qq + (int64_t)j * LDP] : czero<float>();
         }
         const int nch = chunks_of(p);
-        c64 acc0 = czero<float>(), acc1 = czero<float>();
-        if (act && q < nbe) acc0 = x[row + (int64_t)l * n];
+        c64 acc[4] = {czero<float>(), czero<float>(), czero<float>(), czero<float>()};
         // this row's band ends at column row + kv (and the matrix at n - 1)
         const int c_stop = min(n, row + kv + 1);
         for (int ch = 0; ch < nch; ++ch, ++g) {
@@ -784,29 +788,41 @@ __global__ void __launch_bounds__(kBwdThreads)
             if (!mbar_wait(&fb[slot], (uint32_t)((g / nbuf) & 1))) s_fail = 1;
             const c64* u = ub + (size_t)slot * kBwdCh * 32;
             const int c0 = cb + ch * kBwdCh;
-            if (act && q < nbe && !s_fail) {
-                const int jl = min(kBwdCh, c_stop - c0);
-                int slot_w = c0 % wrows, j = 0;
-                for (; j + 1 < jl; j += 2) {
-                    int s1 = slot_w + 1;
-                    if (s1 >= wrows) s1 -= wrows;
-                    cfms(acc0, u[j * 32 + q], win[slot_w * 32 + l]);
-                    cfms(acc1, u[(j + 1) * 32 + q], win[s1 * 32 + l]);
-                    slot_w = s1 + 1;
-                    if (slot_w >= wrows) slot_w -= wrows;
+            if (grp && q < nbe && !s_fail) {
+                const int j0 = ks * (kBwdCh / 4), j1 = min(j0 + kBwdCh / 4, c_stop - c0);
+                int sw = (c0 + j0) % wrows;
+                for (int j = j0; j < j1; ++j) {
+                    const c64 uv = u[j * 32 + q];
+                    const float4* wp = reinterpret_cast<const float4*>(win + (size_t)sw * kBwdCols + 4 * cg);
+                    const float4 w01 = wp[0], w23 = wp[1];
+                    cfms(acc[0], uv, mk<float>(w01.x, w01.y));
+                    cfms(acc[1], uv, mk<float>(w01.z, w01.w));
+                    cfms(acc[2], uv, mk<float>(w23.x, w23.y));
+                    cfms(acc[3], uv, mk<float>(w23.z, w23.w));
+                    if (++sw == wrows) sw = 0;
                 }
-                if (j < jl) cfms(acc0, u[j * 32 + q], win[slot_w * 32 + l]);
             }
             __syncthreads();  // the slot is free again
             if (tid == 0 && !s_fail) issue_next(slot);
         }
-        if (act && q < nbe) rb[q * 33 + l] = acc0 + acc1;
+        {
+            float4* pp4 = reinterpret_cast<float4*>(pr + ((size_t)ks * 32 + q) * kBwdPartLd + 4 * cg);
+            pp4[0] = make_float4(acc[0].re, acc[0].im, acc[1].re, acc[1].im);
+            pp4[1] = make_float4(acc[2].re, acc[2].im, acc[3].re, acc[3].im);
+        }
         __syncthreads();
-        if (act && q < nbe) {
+        // r = x_blk - sum of the quarters (thread: row q, right-hand side w)
+        if (w < Lp && q < nbe) {
+            c64 r = x[row + (int64_t)w * n];
+            for (int s2 = 0; s2 < 4; ++s2) r = r + pr[((size_t)s2 * 32 + q) * kBwdPartLd + w];
+            pr[(size_t)q * kBwdPartLd + w] = r;
+        }
+        __syncthreads();
+        if (w < Lp && q < nbe) {
             c64 sacc = czero<float>();
-            for (int j = q; j < nbe; ++j) cfma(sacc, ui[q * 33 + j], rb[j * 33 + l]);
-            x[row + (int64_t)l * n] = sacc;
-            win[(row % wrows) * 32 + l] = sacc;
+            for (int j = q; j < nbe; ++j) cfma(sacc, ui[q * 33 + j], pr[(size_t)j * kBwdPartLd + w]);
+            x[row + (int64_t)w * n] = sacc;
+            win[(size_t)(row % wrows) * kBwdCols + w] = sacc;
         }
         __syncthreads();
         // every thread reads the flag between two barriers, so all of them leave together
@@ -926,12 +942,12 @@ int launch_factor_tc(const FactorArgs<float>& a, int npts, cudaStream_t s) {
 namespace {
 int bwd_window_rows(const BandDims& d) { return (d.kv + 2 * NB + 31) / 32 * 32; }  // >= kv + 64 solved rows
 size_t bwd_smem(const BandDims& d, int nbuf) {
-    return (size_t)nbuf * kBwdChBytes + (size_t)bwd_window_rows(d) * 32 * sizeof(c64) +
-           (size_t)2 * 32 * 33 * sizeof(c64) + 1024;
+    return (size_t)nbuf * kBwdChBytes + (size_t)bwd_window_rows(d) * kBwdCols * sizeof(c64) +
+           (size_t)32 * 33 * sizeof(c64) + (size_t)4 * 32 * kBwdPartLd * sizeof(c64) + 1024;
 }
 constexpr size_t kBwdSmemMax = 224 * 1024;
 int bwd_nbuf(const BandDims& d) {
-    for (int nb : {kBwdMaxBuf, 2})
+    for (int nb : {kBwdMaxBuf, 4, 2})
         if (bwd_smem(d, nb) <= kBwdSmemMax) return nb;
     return 0;
 }
@@ -951,8 +967,8 @@ int launch_bwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s) {
     RSRR_TRY(band_tensor_map(&map, a.ab, a.ab_stride, npts, a.d, NB, kBwdCh));
     RSRR_TRY(set_smem_max(band_bwd_tc_kernel, sm, "band_bwd_tc_kernel"));
     SolveArgs<float> b = a;
-    b.split = a.L > 16 ? 2 : solve_split_tc(npts, a.L);
-    if ((a.L + b.split - 1) / b.split > 16) b.split = (a.L + 15) / 16;
+    b.split = a.L > kBwdCols ? 2 : solve_split_tc(npts, a.L);
+    if ((a.L + b.split - 1) / b.split > kBwdCols) b.split = (a.L + kBwdCols - 1) / kBwdCols;
     band_bwd_tc_kernel<<<npts * b.split, kBwdThreads, sm, s>>>(map, b, wrows, nbuf);
     note_launch();
     RSRR_CUDA(cudaGetLastError());
