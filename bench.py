@@ -307,8 +307,16 @@ def run_ours(args):
                        ("float", "complex64") if precision == "c64" else ("double", "complex128")), "bound": "alu",
                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (no FP32 figure in the "
                                    "measured peaks)") if precision == "c64" else "nominal FP64 rate"}
+    lu_traffic = None
+    if infos[-1]["band_lu_tc"]:
+        # DRAM bytes of one launch: an ncu capture of this kernel on the 100 x 100 grid (64 points,
+        # kl = ku = 100) read 1.57 GB and wrote 2.74 GB, 0.979 of the compulsory bytes (band read
+        # and written, stored panel blocks); scaled to this launch by the same per-point formula
+        ldab = 2 * kl + ku + 1
+        per_point = 2.0 * ldab * n * 8 + -(-n // 32) * 256 * 32 * 8
+        lu_traffic = 0.979 * per_point * prob.N / max(1, infos[-1]["factor_launches"])
     roof_lu.update({"achieved": achieved, "peak": lu_peak, "unit": "TFLOP/s",
-                    "frac": (achieved / lu_peak) if achieved else None, "traffic": None,
+                    "frac": (achieved / lu_peak) if achieved else None, "traffic": lu_traffic,
                     "algorithmic": f"8 n kl (kl+ku) real flops per point x {prob.N} points per launch",
                     "ms_per_step": phases["factor_ms"], "ms_per_launch": fac_ms_launch})
     zg_ms = statistics.median(i["ms_zgemm"] for i in infos)

@@ -24,11 +24,13 @@
 //
 // Kernels: row and column maxima (atomicMax on the bit patterns of non-negative doubles), the
 // digit images of A' and B' in the MMA's shared-memory layout (K-major, 128-byte swizzle, one
-// 64-term slab per 128-byte row; 8 digit planes per slab), and the GEMM: one CTA per 128 x 32
-// output tile (and K range when split), a producer warp that bulk-copies each slab's 160 KB of
-// digit planes and issues its 32 MMAs (one per A plane and K step, N up to 256, covering the 36
-// digit pairs), and four warps that drain the diagonal
-// accumulators (two TMEM buffers, so the MMAs of the next chunk overlap the drain) and write C.
+// 64-term slab per 128-byte row; 8 digit planes per slab), and the GEMM over 128 x 32 output
+// tiles (and K ranges when split): a producer warp that bulk-copies each slab's 160 KB of digit
+// planes and issues its 32 MMAs (one per A plane and K step, N up to 256, covering the 36 digit
+// pairs), and four warps that drain the diagonal accumulators (two TMEM buffers, so the MMAs of
+// the next chunk overlap the drain) and write C.  The CTAs are persistent (one per SM, each
+// walking its share of the tiles): the next tile's copies and MMAs run under the current tile's
+// drain, scaling and stores.
 // Every wait is bounded; a timeout is reported through an error word and the call fails.
 #include <algorithm>
 #include <cmath>
@@ -60,7 +62,9 @@ constexpr uint32_t OZ_TMEM_COLS = 512;                 // 2 buffers x 8 diagonal
 // only).  Two A slots (one per half) and two B slots let the next piece's copy run under the
 // current piece's MMAs.
 constexpr uint32_t OZ_A_HALF = OZ_A_BYTES / 2;          // 64 KB
-constexpr size_t OZ_SMEM = 2 * OZ_A_HALF + 2 * OZ_B_BYTES + 1024;
+constexpr int OZ_XCOLS = 16;                            // output columns per exchange round
+constexpr size_t OZ_XBYTES = (size_t)OZ_ROWS * (OZ_XCOLS + 1) * 8;
+constexpr size_t OZ_SMEM = 2 * OZ_A_HALF + 2 * OZ_B_BYTES + OZ_XBYTES + 1024;
 
 // ---- maxima ----------------------------------------------------------------------------------
 // out[b][u] = max over v < V of max(|Re|, |Im|) of X(u, v) = base[b*sb + u*su + v*sv], as the bit
@@ -91,16 +95,45 @@ __global__ void oz_max_contig_v(const c128* X, int64_t su, int64_t sb, int U, in
     if (lane == 0 && v1 > v0) atomicMax(out + (int64_t)b * U + u, (unsigned long long)__double_as_longlong(m));
 }
 
+// The FP64 pipe of this part issues two operations per clock per SM, the integer pipe 64: the
+// exponent reads, the fixed-point digits and the conversions of the exact integer sums below are
+// integer operations on the bit patterns, with the FP64 library call only on the rare subnormal
+// or out-of-range path.
+
+// E with m = f 2^E, f in [0.5, 1) (frexp's exponent) of the non-negative double with bits `bits`.
 __device__ __forceinline__ int oz_exp(unsigned long long bits) {
+    const int ev = (int)((bits >> 52) & 0x7ff);
+    if (ev != 0) return ev - 1022;
     const double m = __longlong_as_double((long long)bits);
     int e = 0;
     if (m > 0.0) frexp(m, &e);
     return e;
 }
 
+// llrint(v 2^(55 - E)) for |v| < 2^E (round to nearest, ties to even), from the bits of v.
+__device__ __forceinline__ long long oz_fixed(double v, int E) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int ev = (int)((bits >> 52) & 0x7ff);
+    if (ev == 0) return llrint(ldexp(v, 55 - E));  // zero or subnormal
+    const unsigned long long m = (bits & ((1ull << 52) - 1)) | (1ull << 52);  // |v| = m 2^(ev - 1075)
+    const int sh = ev - 1075 + 55 - E;  // <= 2 since |v| < 2^E
+    unsigned long long q;
+    if (sh >= 0) {
+        q = m << sh;
+    } else if (sh <= -54) {
+        q = 0;  // below one half
+    } else {
+        const int r = -sh;
+        q = m >> r;
+        const unsigned long long rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+    }
+    return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
 // Digits of v * 2^(55 - E) (|v| < 2^E): d[0] most significant.
 __device__ __forceinline__ void oz_digits(double v, int E, float* d) {
-    long long X = llrint(ldexp(v, 55 - E));
+    long long X = oz_fixed(v, E);
 #pragma unroll
     for (int s = OZ_D - 1; s >= 1; --s) {
         int r = (int)(X & 127);
@@ -109,6 +142,41 @@ __device__ __forceinline__ void oz_digits(double v, int E, float* d) {
         X = (X - r) >> 7;
     }
     d[0] = (float)X;
+}
+
+// The double nearest to t (ties to even), |t| < 2^126.
+__device__ __forceinline__ double oz_i128_to_double(__int128 t) {
+    if (t == 0) return 0.0;
+    const bool neg = t < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned long long m;
+    if (msb <= 52) {
+        m = lo << (52 - msb);
+    } else {
+        const int r = msb - 52;
+        m = (unsigned long long)(u >> r);
+        const unsigned __int128 rem = u & (((unsigned __int128)1 << r) - 1), half = (unsigned __int128)1 << (r - 1);
+        if (rem > half || (rem == half && (m & 1))) {
+            ++m;
+            if (m == (1ull << 53)) {
+                m >>= 1;
+                ++msb;
+            }
+        }
+    }
+    const unsigned long long out = ((unsigned long long)(msb + 1023) << 52) | (m & ((1ull << 52) - 1)) |
+                                   (neg ? (1ull << 63) : 0ull);
+    return __longlong_as_double((long long)out);
+}
+
+// x 2^s, exact: the exponent field moves by s (ldexp where the result would leave the normal range).
+__device__ __forceinline__ double oz_scale2(double x, int s) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ev = (int)((bits >> 52) & 0x7ff);
+    if (ev == 0 || ev + s <= 0 || ev + s >= 2047) return ldexp(x, s);
+    return __longlong_as_double((long long)(bits + ((unsigned long long)(long long)s << 52)));
 }
 
 __device__ __forceinline__ uint4 oz_pack8(const float* v, float sign) {
@@ -226,6 +294,7 @@ struct OzArgs {
     c128* C;
     int64_t cs_i, cs_j, sC;          // C(i, j) of batch b at C + b*sC + i*cs_i + j*cs_j
     int M, N, MT, NTt, nslab, nchunk, cper, ksplit;
+    int ntiles;                      // MT * NTt * batch * ksplit; CTA c takes tiles c, c + grid, ...
     c128 alpha, beta;                // beta applies when ksplit == 1 (else C was scaled before)
     int* err;
 };
@@ -240,15 +309,42 @@ struct OzShared {
 
 __device__ __forceinline__ void oz_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OZ_EPI_WARPS * 32) : "memory"); }
 
+// Tile t of the launch: row tile rt (fastest), column tile ct, then batch b and K range ks.
+struct OzTile {
+    int rt, ct, b, ks, S0, S1;
+};
+__device__ __forceinline__ OzTile oz_tile(const OzArgs& a, int t) {
+    OzTile o;
+    o.rt = t % a.MT;
+    const int r = t / a.MT;
+    o.ct = r % a.NTt;
+    const int z = r / a.NTt;
+    o.b = z / a.ksplit;
+    o.ks = z % a.ksplit;
+    const int c0 = o.ks * a.cper, c1 = min(a.nchunk, c0 + a.cper);
+    o.S0 = c0 * OZ_CHUNK;
+    o.S1 = min(a.nslab, c1 * OZ_CHUNK);
+    return o;
+}
+
+// Persistent: each CTA walks its tiles in order.  The producer's pieces (half slabs) and the
+// epilogue's chunks are numbered across the CTA's tiles, so the copies and MMAs of the next tile
+// run while the epilogue warps drain and store the current one (two TMEM buffers, two A slots,
+// two B slots).  All tiles of a CTA have the same number of pieces: the launch uses K splits
+// only with one tile per CTA.
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
     extern __shared__ uint8_t oz_dyn[];
     __shared__ OzShared sh;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_dyn) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;                   // two A halves of 64 KB
     uint8_t* sB = smem + 2 * OZ_A_HALF;   // two B slabs of 32 KB
+    double* xs = reinterpret_cast<double*>(sB + 2 * OZ_B_BYTES);  // [OZ_ROWS][OZ_XCOLS + 1] exchange
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rt = blockIdx.x, ct = blockIdx.y, b = blockIdx.z / a.ksplit, ks = blockIdx.z % a.ksplit;
-    const int c0 = ks * a.cper, c1 = min(a.nchunk, c0 + a.cper);
+    const int G = gridDim.x;
+    const int ntl = blockIdx.x < a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this CTA
+    const OzTile t0 = oz_tile(a, blockIdx.x);
+    const int P = 2 * max(0, t0.S1 - t0.S0);      // pieces per tile
+    const int nch = (t0.S1 - t0.S0 + OZ_CHUNK - 1) / OZ_CHUNK;  // chunks per tile
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 8; ++i) mbar_init(&sh.bar[i], (i >= 6) ? OZ_EPI_WARPS : 1);
@@ -271,31 +367,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             // kind::f16: F32 accumulate, BF16 A and B, K-major both, M = 128; N is set per MMA
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((OZ_ROWS >> 4) << 24);
             const uint64_t adesc = sw128_desc(smem_u32(sA)), bdesc = sw128_desc(smem_u32(sB));
-            const uint8_t* gA = a.imgA + ((size_t)b * a.MT * a.nslab + (size_t)rt * a.nslab) * OZ_A_BYTES;
-            const uint8_t* gB = a.imgB + ((size_t)b * a.NTt * a.nslab + (size_t)ct * a.nslab) * OZ_B_BYTES;
-            const int S0 = c0 * OZ_CHUNK, S1 = min(a.nslab, c1 * OZ_CHUNK);
-            const int P = 2 * max(0, S1 - S0);
-            auto load = [&](int p) {
-                const int sl = S0 + p / 2, half = p & 1;
+            const int total = ntl * P;
+            auto load = [&](int gp) {
+                const OzTile tt = oz_tile(a, (int)blockIdx.x + (gp / P) * G);
+                const int w = gp % P, sl = tt.S0 + w / 2, half = w & 1;
+                const uint8_t* gA = a.imgA + ((size_t)tt.b * a.MT * a.nslab + (size_t)tt.rt * a.nslab) * OZ_A_BYTES;
+                const uint8_t* gB = a.imgB + ((size_t)tt.b * a.NTt * a.nslab + (size_t)tt.ct * a.nslab) * OZ_B_BYTES;
                 uint64_t* full = &sh.bar[half];
                 mbar_expect_tx(full, OZ_A_HALF + (half == 0 ? OZ_B_BYTES : 0u));
                 bulk_g2s(sA + half * OZ_A_HALF, gA + (size_t)sl * OZ_A_BYTES + half * OZ_A_HALF, OZ_A_HALF, full);
                 if (half == 0)
-                    bulk_g2s(sB + ((sl - S0) & 1) * OZ_B_BYTES, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, full);
+                    bulk_g2s(sB + ((gp / 2) & 1) * OZ_B_BYTES, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, full);
             };
             uint32_t use[2] = {0, 0};
             bool ok = true;
-            if (P > 0) load(0);
-            if (P > 1) load(1);
-            for (int p = 0; p < P && ok; ++p) {
-                const int sl = S0 + p / 2, half = p & 1, c = sl / OZ_CHUNK, buf = (c - c0) & 1;
-                const bool chunk_first = half == 0 && sl == c * OZ_CHUNK;
-                const bool chunk_last = half == 1 && sl + 1 == min(a.nslab, (c + 1) * OZ_CHUNK);
+            if (total > 0) load(0);
+            if (total > 1) load(1);
+            for (int gp = 0; gp < total && ok; ++gp) {
+                const int lt = gp / P, w = gp % P, ls = w / 2, half = w & 1;  // ls: slab within the tile
+                const int cl = ls / OZ_CHUNK, buf = (lt * nch + cl) & 1;
+                const bool chunk_first = half == 0 && ls % OZ_CHUNK == 0;
+                const bool chunk_last = half == 1 && (ls + 1 == P / 2 || (ls + 1) % OZ_CHUNK == 0);
                 if (chunk_first && use[buf] > 0 && !mbar_wait(&sh.bar[6 + buf], (use[buf] - 1) & 1)) { ok = false; break; }
-                if (!mbar_wait(&sh.bar[half], (uint32_t)(p / 2) & 1)) { ok = false; break; }
+                if (!mbar_wait(&sh.bar[half], (uint32_t)(gp / 2) & 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dbuf = tmem + (uint32_t)buf * (OZ_D * OZ_COLS);
-                const uint32_t a_base = (uint32_t)half * OZ_A_HALF, b_base = (uint32_t)((sl - S0) & 1) * OZ_B_BYTES;
+                const uint32_t a_base = (uint32_t)half * OZ_A_HALF, b_base = (uint32_t)((gp / 2) & 1) * OZ_B_BYTES;
                 // One MMA per A plane s and K step: B planes 0..7-s are consecutive 32-row blocks of
                 // one K-major operand of N = 32 (8 - s) rows, and the product's column block t lands
                 // on TMEM columns 32 (s + t), the accumulator of diagonal q = s + t.
@@ -318,10 +415,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
                     tc_commit(&sh.bar[4 + buf]);
                     ++use[buf];
                 }
-                // refill: piece p + 1 goes into the slot piece p - 1 used, once its MMAs are done
-                if (p >= 1 && p + 1 < P) {
-                    if (!mbar_wait(&sh.bar[2 + ((p - 1) & 1)], (uint32_t)((p - 1) / 2) & 1)) { ok = false; break; }
-                    load(p + 1);
+                // refill: piece gp + 1 goes into the slot piece gp - 1 used, once its MMAs are done
+                if (gp >= 1 && gp + 1 < total) {
+                    if (!mbar_wait(&sh.bar[2 + ((gp - 1) & 1)], (uint32_t)((gp - 1) / 2) & 1)) { ok = false; break; }
+                    load(gp + 1);
                 }
             }
             if (!ok) {  // the epilogue warps see the flag after their own bounded wait and stop
@@ -330,82 +427,107 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             }
             // let every issued MMA finish before the CTA frees tensor memory (the last commit
             // tracks all of them); when a wait gave up, also every copy still in flight
-            if (P > 0) mbar_wait(&sh.bar[2 + ((P - 1) & 1)], (uint32_t)((P - 1) / 2) & 1);
+            if (total > 0) mbar_wait(&sh.bar[2 + ((total - 1) & 1)], (uint32_t)((total - 1) / 2) & 1);
         }
     } else {
-        // ---- epilogue warps: drain the diagonal sums of each chunk into FP64 ----
-        double acc[OZ_COLS];
-#pragma unroll
-        for (int j = 0; j < OZ_COLS; ++j) acc[j] = 0.0;
+        // ---- epilogue warps: drain the diagonal sums of each chunk, then scale and store ----
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int r = warp * 32 + lane, il = r % OZ_CROWS;
+        // a real alpha of +-1 (the trailing updates' -1) is a sign on the scaled sums
+        const bool alpha_pm1 = a.alpha.im == 0.0 && fabs(a.alpha.re) == 1.0;
+        const unsigned long long sgn = (alpha_pm1 && a.alpha.re < 0.0) ? (1ull << 63) : 0ull;
+        const bool beta0 = a.beta.re == 0.0 && a.beta.im == 0.0, beta1 = a.beta.re == 1.0 && a.beta.im == 0.0;
         uint32_t use[2] = {0, 0};
-        for (int c = c0; c < c1; ++c) {
-            const int buf = (c - c0) & 1;
-            bool got = false;
-            for (int tries = 0; tries < 4 && !got; ++tries) {
-                got = mbar_wait(&sh.bar[4 + buf], use[buf] & 1);
-                if (!got && *(volatile int*)&sh.fail) break;
-            }
-            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
-            if (!got) { if (lane == 0) atomicExch(a.err, 1); break; }
-            ++use[buf];
-            tc_fence_after();
-            const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS);
-            // The diagonal sums are integers below 2^24: four consecutive ones combine exactly in
-            // an int64 (below 2^46), so each column takes two FP64 FMAs instead of eight.
+        bool stop = false;
+        for (int lt = 0; lt < ntl && !stop; ++lt) {
+            const OzTile tt = oz_tile(a, (int)blockIdx.x + lt * G);
+            double acc[OZ_COLS];
 #pragma unroll
-            for (int h2 = 0; h2 < OZ_COLS / 16; ++h2) {
-                float v[OZ_D][16];
-#pragma unroll
-                for (int q = 0; q < OZ_D; ++q) tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16 * h2, v[q]);
-                tc_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    long long g[2];
-#pragma unroll
-                    for (int hq = 0; hq < 2; ++hq) {
-                        const int q0 = 4 * hq;
-                        g[hq] = ((long long)__float2int_rn(v[q0][j]) << 21) + ((long long)__float2int_rn(v[q0 + 1][j]) << 14) +
-                                ((long long)__float2int_rn(v[q0 + 2][j]) << 7) + (long long)__float2int_rn(v[q0 + 3][j]);
+            for (int j = 0; j < OZ_COLS; ++j) acc[j] = 0.0;
+            for (int c = 0; c < nch; ++c) {
+                const int buf = (lt * nch + c) & 1;
+                bool got = false;
+                for (int tries = 0; tries < 4 && !got; ++tries) {
+                    got = mbar_wait(&sh.bar[4 + buf], use[buf] & 1);
+                    if (!got && *(volatile int*)&sh.fail) break;
+                }
+                got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                if (!got) {
+                    if (lane == 0) {
+                        atomicExch(a.err, 1);
+                        *(volatile int*)&sh.fail = 1;
                     }
-                    // weights: diagonal q carries 2^(7 (14 - q)); g[0] is in units of q = 3, g[1] of q = 7
-                    acc[16 * h2 + j] = fma((double)g[0], 0x1p77, fma((double)g[1], 0x1p49, acc[16 * h2 + j]));
+                    stop = true;
+                    break;
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.bar[6 + buf]);
-        }
-        // scale, exchange re/im halves through shared memory (the operand buffers are idle now),
-        // combine with alpha, beta and store
-        oz_epi_sync();
-        double* x = reinterpret_cast<double*>(sA);  // [OZ_ROWS][OZ_COLS + 1]
-        const int r = warp * 32 + lane, il = r % OZ_CROWS, i = rt * OZ_CROWS + il;
-        const int E = i < a.M ? oz_exp(a.rmax[(int64_t)b * a.M + i]) : 0;
+                ++use[buf];
+                tc_fence_after();
+                const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS);
+                // The diagonal sums are integers below 2^24: four consecutive ones combine exactly
+                // in an int64 (below 2^46), the two groups in an int128.
 #pragma unroll
-        for (int j = 0; j < OZ_COLS; ++j) {
-            const int jj = ct * OZ_COLS + j;
-            const int F = jj < a.N ? oz_exp(a.cmax[(int64_t)b * a.N + jj]) : 0;
-            x[r * (OZ_COLS + 1) + j] = ldexp(acc[j], E + F - 110);
-        }
-        oz_epi_sync();
-        if (!*(volatile int*)&sh.fail) {
-            c128* Cb = a.C + b * a.sC;
-            for (int e = threadIdx.x; e < OZ_CROWS * OZ_COLS; e += OZ_EPI_WARPS * 32) {
-                const int il2 = e % OZ_CROWS, j = e / OZ_CROWS;
-                const int i2 = rt * OZ_CROWS + il2, j2 = ct * OZ_COLS + j;
-                if (i2 >= a.M || j2 >= a.N) continue;
-                const c128 p = mk<double>(x[il2 * (OZ_COLS + 1) + j], x[(il2 + OZ_CROWS) * (OZ_COLS + 1) + j]);
-                const c128 v = a.alpha * p;
-                c128* cp = Cb + (int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j;
-                if (a.ksplit > 1) {
-                    atomicAdd(&cp->re, v.re);
-                    atomicAdd(&cp->im, v.im);
-                } else if (a.beta.re == 0.0 && a.beta.im == 0.0) {
-                    *cp = v;
-                } else {
-                    *cp = v + a.beta * (*cp);
+                for (int h2 = 0; h2 < OZ_COLS / 16; ++h2) {
+                    float v[OZ_D][16];
+#pragma unroll
+                    for (int q = 0; q < OZ_D; ++q) tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16 * h2, v[q]);
+                    tc_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        long long g[2];
+#pragma unroll
+                        for (int hq = 0; hq < 2; ++hq) {
+                            const int q0 = 4 * hq;
+                            g[hq] = ((long long)__float2int_rn(v[q0][j]) << 21) + ((long long)__float2int_rn(v[q0 + 1][j]) << 14) +
+                                    ((long long)__float2int_rn(v[q0 + 2][j]) << 7) + (long long)__float2int_rn(v[q0 + 3][j]);
+                        }
+                        // weights: diagonal q carries 2^(7 (14 - q)); g[0] is in units of q = 3, g[1] of
+                        // q = 7, so the chunk's exact sum is 2^49 (g[0] 2^28 + g[1]); acc is in units of 2^49
+                        const __int128 t = ((__int128)g[0] << 28) + (__int128)g[1];
+                        acc[16 * h2 + j] += oz_i128_to_double(t);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.bar[6 + buf]);
+            }
+            // every epilogue warp takes the same decision (the flag is read between two barriers)
+            oz_epi_sync();
+            const bool failed_now = *(volatile int*)&sh.fail != 0 || stop;
+            oz_epi_sync();
+            if (failed_now) { stop = true; break; }
+            // scale, exchange re/im halves through shared memory, combine with alpha, beta, store
+            const int i = tt.rt * OZ_CROWS + il;
+            const int E = i < a.M ? oz_exp(a.rmax[(int64_t)tt.b * a.M + i]) : 0;
+            c128* Cb = a.C + tt.b * a.sC;
+#pragma unroll
+            for (int xg = 0; xg < OZ_COLS / OZ_XCOLS; ++xg) {
+#pragma unroll
+                for (int jx = 0; jx < OZ_XCOLS; ++jx) {
+                    const int j = xg * OZ_XCOLS + jx, jj = tt.ct * OZ_COLS + j;
+                    const int F = jj < a.N ? oz_exp(a.cmax[(int64_t)tt.b * a.N + jj]) : 0;
+                    const double y = oz_scale2(acc[j], E + F - 61);
+                    xs[r * (OZ_XCOLS + 1) + jx] = __longlong_as_double(__double_as_longlong(y) ^ (long long)sgn);
+                }
+                oz_epi_sync();
+                for (int e = threadIdx.x; e < OZ_CROWS * OZ_XCOLS; e += OZ_EPI_WARPS * 32) {
+                    const int il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
+                    const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + xg * OZ_XCOLS + jx;
+                    if (i2 >= a.M || j2 >= a.N) continue;
+                    const c128 p = mk<double>(xs[il2 * (OZ_XCOLS + 1) + jx], xs[(il2 + OZ_CROWS) * (OZ_XCOLS + 1) + jx]);
+                    const c128 v = alpha_pm1 ? p : a.alpha * p;
+                    c128* cp = Cb + (int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j;
+                    if (a.ksplit > 1) {
+                        atomicAdd(&cp->re, v.re);
+                        atomicAdd(&cp->im, v.im);
+                    } else if (beta0) {
+                        *cp = v;
+                    } else if (beta1) {
+                        *cp = v + *cp;
+                    } else {
+                        *cp = v + a.beta * (*cp);
+                    }
+                }
+                oz_epi_sync();  // the exchange buffer is reused by the next column group
             }
         }
     }
@@ -512,10 +634,16 @@ int zgemm_tc(const Zgemm& g0, cudaStream_t s) {
         cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
         attr_set = true;
     }
+    // one CTA per SM walking the tiles (the next tile's copies and MMAs under the current tile's
+    // epilogue); with K split, one CTA per tile (the ranges differ in length)
+    const int ntiles = MT * NTt * batch * ksplit;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int G = ksplit == 1 ? std::min(ntiles, std::max(1, nsm)) : ntiles;
     OzArgs oa{imgA, imgB, rmax, cmax, g.C, cs_i, cs_j, g.sC, M, N, MT, NTt, nslab, nchunk, cper, ksplit,
-              g.alpha, g.beta, err};
-    dim3 grid((unsigned)MT, (unsigned)NTt, (unsigned)(batch * ksplit));
-    { oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, s>>>(oa); note_launch(); }
+              ntiles, g.alpha, g.beta, err};
+    { oz_gemm_kernel<<<G, OZ_THREADS, OZ_SMEM, s>>>(oa); note_launch(); }
     rc = cudaGetLastError() == cudaSuccess ? RSRR_OK : set_error(RSRR_ECUDA, "tensor-core ZGEMM launch");
     int herr = 0;
     if (rc == RSRR_OK) {

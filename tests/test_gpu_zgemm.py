@@ -96,3 +96,33 @@ def test_zgemm_argument_checks(rs):
         with pytest.raises(rs.RsrrError) as e:
             rs.zgemm(kw.get("path", 2), x, x, x, kw.get("oa", 0), 0, 1.0, 0.0, M=4, N=4, K=4, lds=kw.get("lds", (4, 4, 4)))
         assert e.value.name == "EINVAL"
+
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("alpha,beta", [(-1.0, 1.0), (1.0, 0.0), (-1.0, 0.0), (2.5, 1.0), (1j, 1.0)])
+def test_zgemm_update_forms_and_extreme_scales(rs, path, alpha, beta):
+    """The forms the trailing updates use (alpha = -1, beta = 1 and the like), with rows and
+    columns scaled from 1e-310 (subnormal inputs) to 1e300, so that results run from the
+    subnormal range to 1e305: the digit and scale steps' slow paths and the fast ones agree."""
+    import torch
+    rng = np.random.default_rng([int(abs(alpha) * 10), int(abs(beta))])
+    M, N, K = 70, 40, 96
+    a = rand(rng, M, K)
+    b = rand(rng, K, N)
+    rs_ = np.ones(M)
+    rs_[:4] = [1e300, 1e-300, 1e-310, 1e-200]
+    cs_ = np.ones(N)
+    cs_[:3] = [1e-5, 1e5, 1e-100]
+    a = a * rs_[:, None]
+    b = b * cs_[None, :]
+    C0 = rand(rng, M, N) * rs_[:, None] * cs_[None, :]
+    dA, lda = dev(a)
+    dB, ldb = dev(b)
+    dC, ldc = dev(C0)
+    rs.zgemm(path, dA, dB, dC, 0, 0, alpha, beta, M=M, N=N, K=K, lds=(lda, ldb, ldc))
+    torch.cuda.synchronize()
+    C = dC.cpu().numpy().T
+    ref = alpha * (a @ b) + beta * C0
+    bound = 4 * (K + 2) * 2.0 ** -52 * abs(alpha) * np.outer(inf(a, 1), inf(b, 0)) + 2.0 ** -52 * np.abs(beta * C0)
+    assert np.all(np.isfinite(C))
+    assert np.all(np.abs(C - ref) <= bound + K * 1e-320)
