@@ -309,16 +309,16 @@ struct OzShared {
 
 __device__ __forceinline__ void oz_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OZ_EPI_WARPS * 32) : "memory"); }
 
-// Tile t of the launch: row tile rt (fastest), column tile ct, then batch b and K range ks.
+// Tile t of the launch: column tile ct (fastest), row tile rt, then batch b and K range ks.
 struct OzTile {
     int rt, ct, b, ks, S0, S1;
 };
 __device__ __forceinline__ OzTile oz_tile(const OzArgs& a, int t) {
     OzTile o;
-    o.rt = t % a.MT;
-    const int r = t / a.MT;
-    o.ct = r % a.NTt;
-    const int z = r / a.NTt;
+    o.ct = t % a.NTt;
+    const int r = t / a.NTt;
+    o.rt = r % a.MT;
+    const int z = r / a.MT;
     o.b = z / a.ksplit;
     o.ks = z % a.ksplit;
     const int c0 = o.ks * a.cper, c1 = min(a.nchunk, c0 + a.cper);
@@ -327,11 +327,12 @@ __device__ __forceinline__ OzTile oz_tile(const OzArgs& a, int t) {
     return o;
 }
 
-// Persistent: each CTA walks its tiles in order.  The producer's pieces (half slabs) and the
-// epilogue's chunks are numbered across the CTA's tiles, so the copies and MMAs of the next tile
-// run while the epilogue warps drain and store the current one (two TMEM buffers, two A slots,
-// two B slots).  All tiles of a CTA have the same number of pieces: the launch uses K splits
-// only with one tile per CTA.
+// Persistent: each CTA walks a contiguous range of tiles.  The producer's pieces (half slabs) and
+// the epilogue's chunks are numbered across the CTA's tiles, so the copies and MMAs of the next
+// tile run while the epilogue warps drain and store the current one (two TMEM buffers, two A
+// slots, two B slots).  With a single slab (K' <= 64) consecutive tiles of the same row tile keep
+// A' in shared memory and load only their 32 KB of B'.  All tiles of a CTA have the same number
+// of pieces: the launch uses K splits only with one tile per CTA.
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
     extern __shared__ uint8_t oz_dyn[];
     __shared__ OzShared sh;
@@ -341,8 +342,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
     double* xs = reinterpret_cast<double*>(sB + 2 * OZ_B_BYTES);  // [OZ_ROWS][OZ_XCOLS + 1] exchange
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
-    const int ntl = blockIdx.x < a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this CTA
-    const OzTile t0 = oz_tile(a, blockIdx.x);
+    const int tbeg = (int)((int64_t)a.ntiles * blockIdx.x / G), tend = (int)((int64_t)a.ntiles * (blockIdx.x + 1) / G);
+    const int ntl = tend - tbeg;  // tiles of this CTA
+    const OzTile t0 = oz_tile(a, tbeg);
     const int P = 2 * max(0, t0.S1 - t0.S0);      // pieces per tile
     const int nch = (t0.S1 - t0.S0 + OZ_CHUNK - 1) / OZ_CHUNK;  // chunks per tile
 
@@ -369,13 +371,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             const uint64_t adesc = sw128_desc(smem_u32(sA)), bdesc = sw128_desc(smem_u32(sB));
             const int total = ntl * P;
             auto load = [&](int gp) {
-                const OzTile tt = oz_tile(a, (int)blockIdx.x + (gp / P) * G);
+                const int lt = gp / P;
+                const OzTile tt = oz_tile(a, tbeg + lt);
                 const int w = gp % P, sl = tt.S0 + w / 2, half = w & 1;
+                bool needA = true;
+                if (P == 2 && lt > 0) {  // one slab: A' stays while the row tile and batch do
+                    const OzTile tp = oz_tile(a, tbeg + lt - 1);
+                    needA = tp.rt != tt.rt || tp.b != tt.b;
+                }
                 const uint8_t* gA = a.imgA + ((size_t)tt.b * a.MT * a.nslab + (size_t)tt.rt * a.nslab) * OZ_A_BYTES;
                 const uint8_t* gB = a.imgB + ((size_t)tt.b * a.NTt * a.nslab + (size_t)tt.ct * a.nslab) * OZ_B_BYTES;
                 uint64_t* full = &sh.bar[half];
-                mbar_expect_tx(full, OZ_A_HALF + (half == 0 ? OZ_B_BYTES : 0u));
-                bulk_g2s(sA + half * OZ_A_HALF, gA + (size_t)sl * OZ_A_BYTES + half * OZ_A_HALF, OZ_A_HALF, full);
+                const uint32_t bytes = (needA ? OZ_A_HALF : 0u) + (half == 0 ? OZ_B_BYTES : 0u);
+                if (bytes == 0) {
+                    mbar_arrive(full);  // nothing to copy: complete the phase
+                    return;
+                }
+                mbar_expect_tx(full, bytes);
+                if (needA) bulk_g2s(sA + half * OZ_A_HALF, gA + (size_t)sl * OZ_A_BYTES + half * OZ_A_HALF, OZ_A_HALF, full);
                 if (half == 0)
                     bulk_g2s(sB + ((gp / 2) & 1) * OZ_B_BYTES, gB + (size_t)sl * OZ_B_BYTES, OZ_B_BYTES, full);
             };
@@ -440,7 +453,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
         uint32_t use[2] = {0, 0};
         bool stop = false;
         for (int lt = 0; lt < ntl && !stop; ++lt) {
-            const OzTile tt = oz_tile(a, (int)blockIdx.x + lt * G);
+            const OzTile tt = oz_tile(a, tbeg + lt);
             double acc[OZ_COLS];
 #pragma unroll
             for (int j = 0; j < OZ_COLS; ++j) acc[j] = 0.0;
@@ -498,19 +511,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             // scale, exchange re/im halves through shared memory, combine with alpha, beta, store
             const int i = tt.rt * OZ_CROWS + il;
             const int E = i < a.M ? oz_exp(a.rmax[(int64_t)tt.b * a.M + i]) : 0;
+            // column exponents: lane j reads column j's, the others take it by shuffle
+            const int jl = tt.ct * OZ_COLS + lane;
+            const int Fl = jl < a.N ? oz_exp(a.cmax[(int64_t)tt.b * a.N + jl]) : 0;
             c128* Cb = a.C + tt.b * a.sC;
 #pragma unroll
             for (int xg = 0; xg < OZ_COLS / OZ_XCOLS; ++xg) {
 #pragma unroll
                 for (int jx = 0; jx < OZ_XCOLS; ++jx) {
-                    const int j = xg * OZ_XCOLS + jx, jj = tt.ct * OZ_COLS + j;
-                    const int F = jj < a.N ? oz_exp(a.cmax[(int64_t)tt.b * a.N + jj]) : 0;
+                    const int j = xg * OZ_XCOLS + jx;
+                    const int F = __shfl_sync(0xffffffffu, Fl, j);
                     const double y = oz_scale2(acc[j], E + F - 61);
                     xs[r * (OZ_XCOLS + 1) + jx] = __longlong_as_double(__double_as_longlong(y) ^ (long long)sgn);
                 }
+                // this thread's C entries of the group, all loads in flight before any use
+                constexpr int kPer = OZ_CROWS * OZ_XCOLS / (OZ_EPI_WARPS * 32);
+                c128 cold[kPer];
+                const bool need_c = a.ksplit == 1 && !beta0;
+#pragma unroll
+                for (int it = 0; it < kPer; ++it) {
+                    const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
+                    const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + xg * OZ_XCOLS + jx;
+                    cold[it] = (need_c && i2 < a.M && j2 < a.N) ? Cb[(int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j]
+                                                               : czero<double>();
+                }
                 oz_epi_sync();
-                for (int e = threadIdx.x; e < OZ_CROWS * OZ_XCOLS; e += OZ_EPI_WARPS * 32) {
-                    const int il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
+#pragma unroll
+                for (int it = 0; it < kPer; ++it) {
+                    const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
                     const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + xg * OZ_XCOLS + jx;
                     if (i2 >= a.M || j2 >= a.N) continue;
                     const c128 p = mk<double>(xs[il2 * (OZ_XCOLS + 1) + jx], xs[(il2 + OZ_CROWS) * (OZ_XCOLS + 1) + jx]);
@@ -522,9 +550,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
                     } else if (beta0) {
                         *cp = v;
                     } else if (beta1) {
-                        *cp = v + *cp;
+                        *cp = v + cold[it];
                     } else {
-                        *cp = v + a.beta * (*cp);
+                        *cp = v + a.beta * cold[it];
                     }
                 }
                 oz_epi_sync();  // the exchange buffer is reused by the next column group
@@ -634,8 +662,8 @@ int zgemm_tc(const Zgemm& g0, cudaStream_t s) {
         cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
         attr_set = true;
     }
-    // one CTA per SM walking the tiles (the next tile's copies and MMAs under the current tile's
-    // epilogue); with K split, one CTA per tile (the ranges differ in length)
+    // one CTA per SM walking a contiguous range of tiles (the next tile's copies and MMAs under
+    // the current tile's epilogue); with K split, one CTA per tile (the ranges differ in length)
     const int ntiles = MT * NTt * batch * ksplit;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
