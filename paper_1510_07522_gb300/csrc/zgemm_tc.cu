@@ -54,7 +54,7 @@ constexpr uint32_t OZ_A_PLANE = OZ_ROWS * OZ_KS * 2;   // 16 KB
 constexpr uint32_t OZ_B_PLANE = OZ_COLS * OZ_KS * 2;   // 4 KB
 constexpr uint32_t OZ_A_BYTES = OZ_D * OZ_A_PLANE;     // 128 KB per (tile, slab)
 constexpr uint32_t OZ_B_BYTES = OZ_D * OZ_B_PLANE;     // 32 KB
-constexpr int OZ_EPI_WARPS = 4;
+constexpr int OZ_EPI_WARPS = 8;                        // two per TMEM lane group: 16 columns each
 constexpr int OZ_THREADS = (OZ_EPI_WARPS + 1) * 32;   // + one producer warp
 constexpr uint32_t OZ_TMEM_COLS = 512;                 // 2 buffers x 8 diagonals x 32 columns
 // Each slab is consumed in two pieces: digit planes 0..3 of A' with all 8 planes of B' (the 26
@@ -62,7 +62,7 @@ constexpr uint32_t OZ_TMEM_COLS = 512;                 // 2 buffers x 8 diagonal
 // only).  Two A slots (one per half) and two B slots let the next piece's copy run under the
 // current piece's MMAs.
 constexpr uint32_t OZ_A_HALF = OZ_A_BYTES / 2;          // 64 KB
-constexpr int OZ_XCOLS = 16;                            // output columns per exchange round
+constexpr int OZ_XCOLS = OZ_COLS;                       // output columns per exchange round
 constexpr size_t OZ_XBYTES = (size_t)OZ_ROWS * (OZ_XCOLS + 1) * 8;
 constexpr size_t OZ_SMEM = 2 * OZ_A_HALF + 2 * OZ_B_BYTES + OZ_XBYTES + 1024;
 
@@ -444,8 +444,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
         }
     } else {
         // ---- epilogue warps: drain the diagonal sums of each chunk, then scale and store ----
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        const int r = warp * 32 + lane, il = r % OZ_CROWS;
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (the rows it may access) and the 16 columns
+        // 16 (w / 4) .. + 15 of every diagonal
+        const int lg = warp & 3, hc = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
+        const int r = lg * 32 + lane, il = r % OZ_CROWS;
         // a real alpha of +-1 (the trailing updates' -1) is a sign on the scaled sums
         const bool alpha_pm1 = a.alpha.im == 0.0 && fabs(a.alpha.re) == 1.0;
         const unsigned long long sgn = (alpha_pm1 && a.alpha.re < 0.0) ? (1ull << 63) : 0ull;
@@ -454,9 +457,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
         bool stop = false;
         for (int lt = 0; lt < ntl && !stop; ++lt) {
             const OzTile tt = oz_tile(a, tbeg + lt);
-            double acc[OZ_COLS];
+            double acc[16];
 #pragma unroll
-            for (int j = 0; j < OZ_COLS; ++j) acc[j] = 0.0;
+            for (int j = 0; j < 16; ++j) acc[j] = 0.0;
             for (int c = 0; c < nch; ++c) {
                 const int buf = (lt * nch + c) & 1;
                 bool got = false;
@@ -475,17 +478,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
                 }
                 ++use[buf];
                 tc_fence_after();
-                const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS);
+                const uint32_t dbuf = tmem + lane_base + (uint32_t)buf * (OZ_D * OZ_COLS) + 16u * hc;
                 // The diagonal sums are integers below 2^24: four consecutive ones combine exactly
                 // in an int64 (below 2^46), the two groups in an int128.
 #pragma unroll
-                for (int h2 = 0; h2 < OZ_COLS / 16; ++h2) {
-                    float v[OZ_D][16];
+                for (int h8 = 0; h8 < 2; ++h8) {  // two groups of 8 columns (register budget)
+                    float v[OZ_D][8];
 #pragma unroll
-                    for (int q = 0; q < OZ_D; ++q) tc_ld16(dbuf + (uint32_t)q * OZ_COLS + 16 * h2, v[q]);
+                    for (int q = 0; q < OZ_D; ++q) tc_ld8(dbuf + (uint32_t)q * OZ_COLS + 8u * h8, v[q]);
                     tc_wait_ld();
+                    if (h8 == 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh.bar[6 + buf]);  // the values are in registers
+                    }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    for (int j = 0; j < 8; ++j) {
                         long long g[2];
 #pragma unroll
                         for (int hq = 0; hq < 2; ++hq) {
@@ -494,14 +502,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
                                     ((long long)__float2int_rn(v[q0 + 2][j]) << 7) + (long long)__float2int_rn(v[q0 + 3][j]);
                         }
                         // weights: diagonal q carries 2^(7 (14 - q)); g[0] is in units of q = 3, g[1] of
-                        // q = 7, so the chunk's exact sum is 2^49 (g[0] 2^28 + g[1]); acc is in units of 2^49
+                        // q = 7, so the chunk's exact sum is 2^49 (g[0] 2^28 + g[1]); acc in units of 2^49
                         const __int128 t = ((__int128)g[0] << 28) + (__int128)g[1];
-                        acc[16 * h2 + j] += oz_i128_to_double(t);
+                        acc[8 * h8 + j] += oz_i128_to_double(t);
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh.bar[6 + buf]);
             }
             // every epilogue warp takes the same decision (the flag is read between two barriers)
             oz_epi_sync();
@@ -516,47 +521,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(OzArgs a) {
             const int Fl = jl < a.N ? oz_exp(a.cmax[(int64_t)tt.b * a.N + jl]) : 0;
             c128* Cb = a.C + tt.b * a.sC;
 #pragma unroll
-            for (int xg = 0; xg < OZ_COLS / OZ_XCOLS; ++xg) {
-#pragma unroll
-                for (int jx = 0; jx < OZ_XCOLS; ++jx) {
-                    const int j = xg * OZ_XCOLS + jx;
-                    const int F = __shfl_sync(0xffffffffu, Fl, j);
-                    const double y = oz_scale2(acc[j], E + F - 61);
-                    xs[r * (OZ_XCOLS + 1) + jx] = __longlong_as_double(__double_as_longlong(y) ^ (long long)sgn);
-                }
-                // this thread's C entries of the group, all loads in flight before any use
-                constexpr int kPer = OZ_CROWS * OZ_XCOLS / (OZ_EPI_WARPS * 32);
-                c128 cold[kPer];
-                const bool need_c = a.ksplit == 1 && !beta0;
-#pragma unroll
-                for (int it = 0; it < kPer; ++it) {
-                    const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
-                    const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + xg * OZ_XCOLS + jx;
-                    cold[it] = (need_c && i2 < a.M && j2 < a.N) ? Cb[(int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j]
-                                                               : czero<double>();
-                }
-                oz_epi_sync();
-#pragma unroll
-                for (int it = 0; it < kPer; ++it) {
-                    const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
-                    const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + xg * OZ_XCOLS + jx;
-                    if (i2 >= a.M || j2 >= a.N) continue;
-                    const c128 p = mk<double>(xs[il2 * (OZ_XCOLS + 1) + jx], xs[(il2 + OZ_CROWS) * (OZ_XCOLS + 1) + jx]);
-                    const c128 v = alpha_pm1 ? p : a.alpha * p;
-                    c128* cp = Cb + (int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j;
-                    if (a.ksplit > 1) {
-                        atomicAdd(&cp->re, v.re);
-                        atomicAdd(&cp->im, v.im);
-                    } else if (beta0) {
-                        *cp = v;
-                    } else if (beta1) {
-                        *cp = v + cold[it];
-                    } else {
-                        *cp = v + a.beta * cold[it];
-                    }
-                }
-                oz_epi_sync();  // the exchange buffer is reused by the next column group
+            for (int jx = 0; jx < 16; ++jx) {
+                const int j = 16 * hc + jx;
+                const int F = __shfl_sync(0xffffffffu, Fl, j);
+                const double y = oz_scale2(acc[jx], E + F - 61);
+                xs[r * (OZ_XCOLS + 1) + j] = __longlong_as_double(__double_as_longlong(y) ^ (long long)sgn);
             }
+            // this thread's C entries, all loads in flight before any use
+            constexpr int kPer = OZ_CROWS * OZ_XCOLS / (OZ_EPI_WARPS * 32);
+            c128 cold[kPer];
+            const bool need_c = a.ksplit == 1 && !beta0;
+#pragma unroll
+            for (int it = 0; it < kPer; ++it) {
+                const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
+                const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + jx;
+                cold[it] = (need_c && i2 < a.M && j2 < a.N) ? Cb[(int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j]
+                                                           : czero<double>();
+            }
+            oz_epi_sync();
+#pragma unroll
+            for (int it = 0; it < kPer; ++it) {
+                const int e = threadIdx.x + it * OZ_EPI_WARPS * 32, il2 = e % OZ_CROWS, jx = e / OZ_CROWS;
+                const int i2 = tt.rt * OZ_CROWS + il2, j2 = tt.ct * OZ_COLS + jx;
+                if (i2 >= a.M || j2 >= a.N) continue;
+                const c128 p = mk<double>(xs[il2 * (OZ_XCOLS + 1) + jx], xs[(il2 + OZ_CROWS) * (OZ_XCOLS + 1) + jx]);
+                const c128 v = alpha_pm1 ? p : a.alpha * p;
+                c128* cp = Cb + (int64_t)i2 * a.cs_i + (int64_t)j2 * a.cs_j;
+                if (a.ksplit > 1) {
+                    atomicAdd(&cp->re, v.re);
+                    atomicAdd(&cp->im, v.im);
+                } else if (beta0) {
+                    *cp = v;
+                } else if (beta1) {
+                    *cp = v + cold[it];
+                } else {
+                    *cp = v + a.beta * cold[it];
+                }
+            }
+            oz_epi_sync();  // the exchange buffer is reused by the next tile
         }
     }
     tc_fence_before();
