@@ -203,7 +203,12 @@ __global__ void oz_slice_a(const c128* A, int64_t lda, int64_t sA, int op, int M
     const int b = blockIdx.z, kgroups = K2 / 8;
     const int64_t rows = (int64_t)MT * OZ_CROWS;
     if (t >= rows * kgroups) return;
-    const int i = (int)(t % rows), k0 = (int)(t / rows) * 8;  // consecutive threads: consecutive rows
+    // consecutive threads take consecutive rows when op(A)'s rows are contiguous in memory (op 0,
+    // 3), else consecutive k groups of one row: the reads are coalesced either way, and in the second
+    // case the image stores too (eight threads fill a 128-byte row of a digit plane)
+    const bool kfast = op == 1 || op == 2;
+    const int i = kfast ? (int)(t / kgroups) : (int)(t % rows);
+    const int k0 = kfast ? (int)(t % kgroups) * 8 : (int)(t / rows) * 8;
     const c128* Ab = A + b * sA;
     const int E = i < M ? oz_exp(rmax[(int64_t)b * M + i]) : 0;
     c128 x[8];
@@ -249,7 +254,10 @@ __global__ void oz_slice_b(const c128* B, int64_t ldb, int64_t sB, int op, int N
     const int b = blockIdx.z, kgroups = K2 / 8;
     const int64_t cols = (int64_t)NTt * OZ_COLS;
     if (t >= cols * kgroups) return;
-    const int j = (int)(t % cols), k0 = (int)(t / cols) * 8;
+    // as for A': k groups fastest when a column of op(B) is contiguous (op 0, 3)
+    const bool kfast = op == 0 || op == 3;
+    const int j = kfast ? (int)(t / kgroups) : (int)(t % cols);
+    const int k0 = kfast ? (int)(t % kgroups) * 8 : (int)(t / cols) * 8;
     const c128* Bb = B + b * sB;
     const int F = j < N ? oz_exp(cmax[(int64_t)b * N + j]) : 0;
     c128 x[8];
@@ -593,10 +601,12 @@ static int oz_max(const c128* X, int64_t ld, int64_t sb, int op, int U, int V, i
 
 // Worth it when the FP64 GEMM would take a while.  A thin output side (the moments' 2K columns,
 // the traces' J columns) wastes most of a 32-column tile, but the FP64 kernel wastes more of
-// its 64 x 64 tile on such shapes (measured 0.05-0.07 TFLOP/s on the moments and traces).
+// its 64 x 64 tile on such shapes (measured 0.05-0.07 TFLOP/s on the moments and traces).  The
+// QR updates of an 800-column Hankel matrix (0.17 GFLOP each) ran at 0.2 TFLOP/s on the FP64
+// kernel: from 0.1 GFLOP on, the emulation's fixed costs (five launches, one host wait) are paid.
 bool zgemm_tc_fits(const Zgemm& g) {
     const double work = 8.0 * g.M * (double)g.N * g.K * g.batch;
-    return work >= 4e8 && g.K >= 16;
+    return work >= 1e8 && g.K >= 16;
 }
 
 int zgemm_tc(const Zgemm& g0, cudaStream_t s) {
