@@ -88,6 +88,8 @@ def parse():
                     help="config 3: the dense LU for every member (no autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 arm of the same workload")
+    ap.add_argument("--no-eigs", action="store_true",
+                    help="skip the pass over the same matrices with a contour that encloses eigenvalues")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="points in the CPU baseline sample (0 = cores)")
     return ap.parse_args()
@@ -418,6 +420,43 @@ def run_ours(args):
                    "note": "the same full pass with complex128 band LU and solves (RSRR_FP64), events on "
                            "the same stream; factor = mixed-precision value / this value at the same tol"}
 
+    # ---- the same matrices with a contour that encloses eigenvalues (the benchmark contour
+    # encloses none): one full pass returning eigenpairs at full size, timed the same way, with
+    # its eigenvalues against the closed form of the damped problem ----------------------------
+    eig_arm = None
+    if args.config == "1" and args.grid == 0 and not args.no_eigs:
+        import workloads
+        pb = workloads.config1b()
+        g = rs.Nep(pb.n, pb.rowptr, pb.colind, pb.vals, fns_of(pb), 0, sp)
+
+        def step_b():
+            g.sample(pb.gamma, pb.a, pb.b, pb.N, pb.L, pb.U, prec, args.tol, 20)
+            g.project(W["delta"])
+            return g.solve(W["N_S"], W["K"], 1e3, 4096, True)
+        step_b()
+        kb = 2
+        barrier()
+        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kb)]
+        for e0, e1 in evb:
+            e0.record(stream)
+            lam_b, _, res_b = step_b()
+            e1.record(stream)
+        barrier()
+        infb = g.info()
+        g.close()
+        msb = sum(e0.elapsed_time(e1) for e0, e1 in evb)
+        vb, _ = job_value(pb.N, kb, msb, device="cuda")
+        nrm = [float(np.linalg.norm(pb.vals[i])) for i in range(pb.vals.shape[0])]
+        al = np.abs(lam_b)
+        scaled_res = res_b / (nrm[0] + al * nrm[1] + al ** 2 * nrm[2]) if lam_b.size else np.zeros(0)
+        ex = np.asarray(pb.meta["expected"])
+        err = max((float(np.min(np.abs(ex - l)) / abs(l)) for l in lam_b), default=None)
+        eig_arm = {"workload": "the same n = 40000 damped QEP, ellipse around its 10 lowest upper-branch "
+                               "eigenvalues (N=64, L=32)", "value": vb, "unit": UNIT, "steps": kb,
+                   "ms_per_step": msb / kb, "n_eigs_inside": int(lam_b.size), "expected": int(ex.size),
+                   "max_scaled_residual": float(scaled_res.max()) if lam_b.size else None,
+                   "max_rel_err_vs_closed_form": err, "k_S": infb["k_S"], "max_eta": infb["max_eta"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
@@ -439,7 +478,8 @@ def run_ours(args):
                 "max_eta": max(i["max_eta"] for i in infos), "n_eigs_inside": int(lam.size),
                 "roofline": roof, "rooflines": {"band_lu": roof_lu, "zgemm_tc": roof_tc, "jacobi": roof_jac,
                                                 "svd_stage": roof_svd},
-                "vs_fp64": vs_fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "vs_fp64": vs_fp64, "with_eigenpairs": eig_arm, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -630,6 +670,43 @@ def run_batch(args):
         barrier()
         e2e_value, _ = job_value(points, args.steps, 1e3 * (time.perf_counter() - t0), device="cuda")
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    # ---- the same matrices with a contour that encloses eigenvalues (the benchmark contour
+    # encloses none): one full pass returning eigenpairs at full size, timed the same way, with
+    # its eigenvalues against the closed form of the damped problem ----------------------------
+    eig_arm = None
+    if args.config == "1" and args.grid == 0 and not args.no_eigs:
+        import workloads
+        pb = workloads.config1b()
+        g = rs.Nep(pb.n, pb.rowptr, pb.colind, pb.vals, fns_of(pb), 0, sp)
+
+        def step_b():
+            g.sample(pb.gamma, pb.a, pb.b, pb.N, pb.L, pb.U, prec, args.tol, 20)
+            g.project(W["delta"])
+            return g.solve(W["N_S"], W["K"], 1e3, 4096, True)
+        step_b()
+        kb = 2
+        barrier()
+        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kb)]
+        for e0, e1 in evb:
+            e0.record(stream)
+            lam_b, _, res_b = step_b()
+            e1.record(stream)
+        barrier()
+        infb = g.info()
+        g.close()
+        msb = sum(e0.elapsed_time(e1) for e0, e1 in evb)
+        vb, _ = job_value(pb.N, kb, msb, device="cuda")
+        nrm = [float(np.linalg.norm(pb.vals[i])) for i in range(pb.vals.shape[0])]
+        al = np.abs(lam_b)
+        scaled_res = res_b / (nrm[0] + al * nrm[1] + al ** 2 * nrm[2]) if lam_b.size else np.zeros(0)
+        ex = np.asarray(pb.meta["expected"])
+        err = max((float(np.min(np.abs(ex - l)) / abs(l)) for l in lam_b), default=None)
+        eig_arm = {"workload": "the same n = 40000 damped QEP, ellipse around its 10 lowest upper-branch "
+                               "eigenvalues (N=64, L=32)", "value": vb, "unit": UNIT, "steps": kb,
+                   "ms_per_step": msb / kb, "n_eigs_inside": int(lam_b.size), "expected": int(ex.size),
+                   "max_scaled_residual": float(scaled_res.max()) if lam_b.size else None,
+                   "max_rel_err_vs_closed_form": err, "k_S": infb["k_S"], "max_eta": infb["max_eta"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, sample = cpu_dense_rate(probs)
