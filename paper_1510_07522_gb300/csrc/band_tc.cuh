@@ -32,9 +32,10 @@ int64_t tc_ab_stride(const BandDims& d);
 int launch_factor_tc(const FactorArgs<float>& a, int npts, cudaStream_t s);
 // Solves take at most 64 right-hand sides per launch (EINVAL beyond).
 int launch_fwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
-// Backward solve with U in the band and the stored inv(U11) blocks; its shared-memory window of
-// kv + 64 solved rows fits for kv up to about 770 (band_bwd_tc_fits), beyond that the CUDA-core
-// backward solve (band.cuh) takes the same storage.
+// Backward solve with U in the band and the stored inv(U11) blocks.  Its shared memory holds a
+// window of kv + 64 solved rows (16 right-hand sides) and a ring of TMA-loaded U12 chunks (8
+// buffers up to kv ~ 480, 4 up to ~990, 2 up to ~1250: band_bwd_tc_fits); beyond that the
+// CUDA-core backward solve (band.cuh) takes the same storage.
 bool band_bwd_tc_fits(const BandDims& d);
 int launch_bwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
 
