@@ -32,15 +32,16 @@ def run(rs, prob, precision, tol, max_refine=20, flags=0):
     return out
 
 
-def banded_problem(n, kl, ku, seed, N=6, L=5):
+def banded_problem(n, kl, ku, seed, N=6, L=5, shift=0.0):
     """T(z) = A0 - z I with A0 a random complex band matrix (kl, ku): partial pivoting moves
     nearly every row, and for kl >> ku the matrix is ill-conditioned (up to ~1e9), where only
-    backward errors are comparable between solvers."""
+    backward errors are comparable between solvers.  A diagonal shift makes A0 well conditioned."""
     rng = np.random.default_rng(seed)
     diags, offs = [], []
     for o in range(-kl, ku + 1):
         m = n - abs(o)
-        diags.append(rng.standard_normal(m) + 1j * rng.standard_normal(m))
+        d = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+        diags.append(d + shift if o == 0 else d)
         offs.append(o)
     A0 = sp.diags(diags, offs, shape=(n, n), format="csr")
     rowptr, colind, vals = w.problems._union([A0, -sp.identity(n, format="csr")])
@@ -82,6 +83,20 @@ def test_tc_band_lu_unsymmetric_bands(rs, n, kl, ku, seed):
     X, eta, info = run(rs, prob, rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL, 1e-10, flags=rs.RSRR_NATURAL_ORDER)
     assert info["band_lu_tc"] == 1
     assert (info["kl"], info["ku"]) == (kl, ku)
+    ref, _, _ = oracle.sample(prob)
+    assert eta.max() <= 2e-15
+    assert rel_err_cols(X, ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("n,kl,ku,seed", [(900, 40, 600, 5), (1400, 33, 1100, 6), (1500, 36, 1300, 7)])
+def test_tc_backward_solve_wide_upper_band(rs, n, kl, ku, seed):
+    """Upper bandwidths that change the backward solve's shared-memory plan: kv = 640 (a TMA ring of
+    four U12 chunk buffers), 1134 (two) and 1336 (past the solved-row window: the CUDA-core backward
+    solve on the same storage).  The diagonal shift keeps cond(T(z)) near 30-60, so the refined
+    samples compare with the oracle's column by column."""
+    prob = banded_problem(n, kl, ku, seed, shift=float(np.sqrt(kl + ku)))
+    X, eta, info = run(rs, prob, rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL, 1e-10, flags=rs.RSRR_NATURAL_ORDER)
+    assert info["band_lu_tc"] == 1
     ref, _, _ = oracle.sample(prob)
     assert eta.max() <= 2e-15
     assert rel_err_cols(X, ref).max() < 1e-9
