@@ -35,7 +35,8 @@ int launch_fwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
 // Backward solve with U in the band and the stored inv(U11) blocks.  Its shared memory holds a
 // window of kv + 64 solved rows (16 right-hand sides) and a ring of TMA-loaded U12 chunks (8
 // buffers up to kv ~ 480, 4 up to ~990, 2 up to ~1250: band_bwd_tc_fits); beyond that the
-// CUDA-core backward solve (band.cuh) takes the same storage.
+// CUDA-core backward solve (band.cuh) takes the same storage.  (The sampler sends bands with
+// ku > 768 to the dense LU, so it uses the eight- and four-buffer plans.)
 bool band_bwd_tc_fits(const BandDims& d);
 int launch_bwd_tc(const SolveArgs<float>& a, int npts, cudaStream_t s);
 

@@ -65,23 +65,28 @@ def band_of(n: int, rowptr: np.ndarray, colind: np.ndarray):
 
 def footprint_bytes(n: int, kl: int, ku: int, N: int, L: int, nnz: int, J: int, c64: bool = True,
                     N_S: int = 500, K: int = 2) -> int:
-    """An upper bound of the device memory a request holds at its peak: the sum of the sampling
-    factors, the projection work and the reduced solve's inverses (each phase frees its work
-    before the next, so the sum over-states the peak).  The reduced solve factors at most N_S
-    points of T_S(z) at once, and no more than 24 GiB of them (k_S <= min(n, N L) rows, dense
-    kept in band storage with kl = ku = k_S - 1: about 5 k_S^2 complex128 values per point)."""
+    """An upper bound of the device memory a request holds at its peak.  The handle keeps the CSR
+    values and S_hat throughout; each phase frees its own work before the next starts, so the
+    peak is that plus the largest phase:
+      sampling   the band factors, right-hand sides and FP64 residuals of all N points (fewer
+                 when they are chunked);
+      projection the QR's copy of S_hat, the digit images of its trailing block (4 bytes of image
+                 per byte of matrix) and the products A_i S (k_S <= min(n, N L) columns);
+      reduced    at most N_S points of T_S(z) at once and no more than 24 GiB of them (dense in band
+                 storage, about 5 k_S^2 complex128 values per point), moments, Hankel matrices."""
     es = 8 if c64 else 16
     ldab = 2 * kl + ku + 1
     ldp = (32 + kl + 31) // 32 * 32
-    per_point = ldab * n * es + n * ldp * es + n * L * es + nnz * 16 + n * 16
+    per_point = ldab * n * es + n * ldp * es + n * L * es + n * L * 16 + nnz * 16 + n * 16
     sample = N * per_point
     s_hat = n * N * L * 16
     k = min(n, N * L)
-    project = 4 * s_hat + J * n * k * 16
+    project = 6 * s_hat + J * n * k * 16
     per_sample = 16 * (5 * k * k + 64 * k) + k * (k + 64) + 4 * k + 64
     reduced = min(N_S * per_sample, max(per_sample, 24 << 30)) + 16 * k * k * (J + 2 * K + 4 * K * K + 8) \
         + N_S * J * 16
-    return int(sample + s_hat + project + reduced + J * nnz * 16 + (64 << 20))
+    persistent = s_hat + J * nnz * 16 + (64 << 20)
+    return int(persistent + max(sample, project, reduced))
 
 
 @dataclass

@@ -88,12 +88,13 @@ def test_tc_band_lu_unsymmetric_bands(rs, n, kl, ku, seed):
     assert rel_err_cols(X, ref).max() < 1e-9
 
 
-@pytest.mark.parametrize("n,kl,ku,seed", [(900, 40, 600, 5), (1400, 33, 1100, 6), (1500, 36, 1300, 7)])
+@pytest.mark.parametrize("n,kl,ku,seed", [(1500, 36, 300, 7), (2000, 40, 600, 5), (2600, 200, 760, 6)])
 def test_tc_backward_solve_wide_upper_band(rs, n, kl, ku, seed):
-    """Upper bandwidths that change the backward solve's shared-memory plan: kv = 640 (a TMA ring of
-    four U12 chunk buffers), 1134 (two) and 1336 (past the solved-row window: the CUDA-core backward
-    solve on the same storage).  The diagonal shift keeps cond(T(z)) near 30-60, so the refined
-    samples compare with the oracle's column by column."""
+    """Upper bandwidths that change the backward solve's shared-memory plan: kv = 336 (a TMA ring of
+    eight U12 chunk buffers), 640 and 960 (four; the band path takes ku <= 768, wider bands and
+    5 (kl + ku) > 2 n go to the dense LU, so the two-buffer ring is not reached through the API).
+    The diagonal shift keeps cond(T(z)) small, so the refined samples compare with the oracle's
+    column by column."""
     prob = banded_problem(n, kl, ku, seed, shift=float(np.sqrt(kl + ku)))
     X, eta, info = run(rs, prob, rs.RSRR_C64_IR | rs.RSRR_REFINE_FULL, 1e-10, flags=rs.RSRR_NATURAL_ORDER)
     assert info["band_lu_tc"] == 1

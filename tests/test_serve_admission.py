@@ -31,17 +31,23 @@ def test_nothing_fits():
     assert select_admissible([], 50, 4) is None
 
 
-def test_footprint_grows_with_band_and_points():
-    a = footprint_bytes(40000, 200, 200, 64, 32, 200000, 3)
-    b = footprint_bytes(40000, 200, 200, 32, 32, 200000, 3)
-    c = footprint_bytes(40000, 100, 100, 64, 32, 200000, 3)
+def test_footprint_is_persistent_plus_largest_phase():
+    """S_hat and the CSR values stay; the sampling factors, the projection work and the reduced
+    solve's inverses come one after another, so the bound is their maximum on top."""
+    n, kl, ku, N, L, nnz, J = 40000, 200, 200, 64, 32, 200000, 3
+    s_hat = n * N * L * 16
+    persistent = s_hat + J * nnz * 16 + (64 << 20)
+    # ten reduced points: the 64 band factors (~17 GB of complex64) are the largest phase
+    a = footprint_bytes(n, kl, ku, N, L, nnz, J, N_S=10)
+    b = footprint_bytes(n, kl, ku, 32, L, nnz, J, N_S=10)
+    c = footprint_bytes(n, 100, 100, N, L, nnz, J, N_S=10)
     assert a > b and a > c
-    # 64 points of a band-200 problem: ~17.5 GB of factors, S_hat and the projection work, and
-    # the reduced solve's inverses (k_S <= N L = 2048: capped at 24 GiB)
-    assert 15e9 < a < 80e9
-    d = footprint_bytes(40000, 200, 200, 64, 32, 200000, 3, N_S=50)
-    # 500 points of k_S = 2048 hit the cap (25.8 GB), 50 points take 50 x 0.34 GB
-    assert 7e9 < a - d < 10e9
+    assert 15e9 < a - persistent < 25e9
+    # FP64 factors take twice the bytes
+    assert footprint_bytes(n, kl, ku, N, L, nnz, J, False, N_S=10) - persistent > 1.9 * (a - persistent)
+    # 500 reduced points of k_S <= N L = 2048 hit the 24 GiB cap and become the largest phase
+    d = footprint_bytes(n, kl, ku, N, L, nnz, J)
+    assert 24 * 2 ** 30 < d - persistent < 28e9
 
 
 def test_enomem_alone_finishes_with_error():
