@@ -15,12 +15,14 @@ namespace rsrr {
 namespace {
 constexpr int BK = 8;
 
-// Tile BM x BN, 256 threads as TY x TX = (BM/4) x (BN/4), each owning a 4 x 4 grid of outputs
-// spaced TY rows and TX columns apart.  64 x 64 for general shapes, 32 x 128 when M <= 32.
+// Tile BM x BN, NT = BM BN / 16 threads as TY x TX = (BM/4) x (BN/4), each owning a 4 x 4 grid
+// of outputs spaced TY rows and TX columns apart.  64 x 64 for general shapes, 32 x 128 when
+// M <= 32, 32 x 32 (64 threads) when those give too few CTAs to fill the GPU.  Every output
+// accumulates over k in the same order whatever the tile.
 template <int OPA, int OPB, int BM, int BN>
-__global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
-    constexpr int TY = BM / 4, TX = BN / 4;
-    static_assert(TX * TY == 256, "256 threads");
+__global__ void __launch_bounds__(BM * BN / 16) zgemm_kernel(Zgemm g, int kchunk) {
+    constexpr int TY = BM / 4, TX = BN / 4, NT = TY * TX;
+    static_assert(BM * BK % NT == 0 && BN * BK % NT == 0, "tile loads");
     __shared__ c128 As[BK][BM + 1];
     __shared__ c128 Bs[BK][BN + 1];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -37,8 +39,8 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
         for (int j = 0; j < 4; ++j) acc[i][j] = czero<double>();
     for (int k0 = k_begin; k0 < k_end; k0 += BK) {
 #pragma unroll
-        for (int r = 0; r < BM * BK / 256; ++r) {
-            const int idx = tid + 256 * r;
+        for (int r = 0; r < BM * BK / NT; ++r) {
+            const int idx = tid + NT * r;
             int i, k;
             if (OPA == OP_N) { i = idx % BM; k = idx / BM; } else { k = idx % BK; i = idx / BK; }
             const int gi = bm + i, gk = k0 + k;
@@ -50,8 +52,8 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Zgemm g, int kchunk) {
             As[k][i] = v;
         }
 #pragma unroll
-        for (int r = 0; r < BN * BK / 256; ++r) {
-            const int idx = tid + 256 * r;
+        for (int r = 0; r < BN * BK / NT; ++r) {
+            const int idx = tid + NT * r;
             int j, k;
             if (OPB == OP_N) { k = idx % BK; j = idx / BK; } else { j = idx % BN; k = idx / BN; }
             const int gj = bn + j, gk = k0 + k;
@@ -124,8 +126,12 @@ int zgemm_shape(Zgemm g, cudaStream_t s) {
         dim3 grid((unsigned)ceil_div((int64_t)g.M * g.N, 256), g.batch);
         { scale_kernel<<<grid, 256, 0, s>>>(g.C, g.M, g.N, g.ldc, g.sC, g.beta); note_launch(); }
     }
+    if constexpr (BM * BN > 32 * 32) {
+        // too few tiles and no K split: 32 x 32 tiles give up to four times the CTAs
+        if (g.ksplit == 1 && (int64_t)tm * tn * g.batch < 2 * 152) return zgemm_shape<32, 32>(g, s);
+    }
     dim3 grid(tm, tn, g.batch * g.ksplit);
-#define ZG(a, b) { zgemm_kernel<a, b, BM, BN><<<grid, 256, 0, s>>>(g, kchunk); note_launch(); }
+#define ZG(a, b) { zgemm_kernel<a, b, BM, BN><<<grid, BM * BN / 16, 0, s>>>(g, kchunk); note_launch(); }
     if (g.opA == OP_N && g.opB == OP_N) ZG(OP_N, OP_N)
     else if (g.opA == OP_N && g.opB == OP_T) ZG(OP_N, OP_T)
     else if (g.opA == OP_N && g.opB == OP_C) ZG(OP_N, OP_C)
