@@ -380,6 +380,8 @@ __global__ void gemv_n_kernel(const c128* A, int64_t lda, int r0, int r1, int c0
     const int64_t i = r0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= r1) return;
     c128 acc = czero<double>();
+    // unrolled so that the loads of several columns are in flight; the sum keeps its order
+#pragma unroll 8
     for (int c = c0; c < c1; ++c) cfma(acc, A[i + (int64_t)c * lda], x[c - c0]);
     y[i - r0] = acc;
 }
@@ -390,6 +392,7 @@ __global__ void gemv_c_kernel(const c128* A, int64_t lda, int r0, int r1, int c0
     const int lane = threadIdx.x & 31;
     if (c >= c1) return;
     c128 acc = czero<double>();
+#pragma unroll 8
     for (int i = r0 + lane; i < r1; i += 32) cfma_conj(acc, A[i + (int64_t)c * lda], y[i - r0]);
     for (int off = 16; off; off >>= 1) {
         acc.re += __shfl_down_sync(0xffffffffu, acc.re, off);
