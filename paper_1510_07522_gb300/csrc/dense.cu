@@ -329,6 +329,7 @@ struct JacobiArgs {
     double tol, floor2, abs_g;
     double* nrm2;  // squared column norms of B (kk entries)
     int* ver;      // rounds each column has finished in this sweep (kk entries, zero at launch)
+    int* jver;     // rounds whose rotation of J's column is done (kk entries, zero at launch)
     unsigned long long* max_off;
     int* rotations;  // [0] pairs rotated, [1] pairs whose inner product was formed
     GridBar gb;      // the barrier after the norms; its error word also records a wait that gave up
@@ -382,10 +383,16 @@ __device__ __forceinline__ void jac_rotate(c128& x, c128& y, double c, double s,
 }
 
 // One column pair (p, q) of a round, p < q < kk; every thread of the CTA takes the same branches.
-__device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
+// Rotates the pair's columns of B and stores their norms; returns whether it rotated, with the
+// rotation in (c, s, sp, cp) for J's columns, which the caller rotates after releasing B's.
+// The rotation of the CTA's current pair (c, s, s e^{-i phi}, c e^{-i phi}): written by thread 0,
+// read by every thread for B's columns and, after B's release, for J's.
+__shared__ double jac_spar[6];
+
+__device__ __forceinline__ bool jac_pair(const JacobiArgs& a, int p, int q) {
     const int tid = threadIdx.x;
     const double al = __ldcg(a.nrm2 + p), be = __ldcg(a.nrm2 + q);
-    if (fmin(al, be) <= a.floor2) return;
+    if (fmin(al, be) <= a.floor2) return false;
     c128* bp = a.B + (int64_t)p * a.mb;
     c128* bq = a.B + (int64_t)q * a.mb;
     c128 xc[kJacCache], yc[kJacCache];
@@ -404,7 +411,6 @@ __device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
         jac_dot_acc(gr, gi, ldcg_c(bp + r), ldcg_c(bq + r));
     block_sum2(gr, gi);
     // the decision and the rotation are computed once, by thread 0, and shared
-    __shared__ double s_par[6];
     __shared__ int s_act;
     if (tid == 0) {
         atomicAdd(a.rotations + 1, 1);
@@ -419,22 +425,22 @@ __device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
                 const double zeta = (be - al) * (0.5 * ig);
                 const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                 const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                s_par[0] = c;
-                s_par[1] = sn;
-                s_par[2] = ph.re * sn;
-                s_par[3] = ph.im * sn;
-                s_par[4] = ph.re * c;
-                s_par[5] = ph.im * c;
+                jac_spar[0] = c;
+                jac_spar[1] = sn;
+                jac_spar[2] = ph.re * sn;
+                jac_spar[3] = ph.im * sn;
+                jac_spar[4] = ph.re * c;
+                jac_spar[5] = ph.im * c;
                 act = 1;
             }
         }
         s_act = act;
     }
     __syncthreads();
-    if (!s_act) return;
+    if (!s_act) return false;
     // (b_p, b_q) <- (c b_p - s e^{-i phi} b_q, s b_p + c e^{-i phi} b_q)
-    const double c = s_par[0], s = s_par[1];
-    const c128 sp = mk<double>(s_par[2], s_par[3]), cp = mk<double>(s_par[4], s_par[5]);
+    const double c = jac_spar[0], s = jac_spar[1];
+    const c128 sp = mk<double>(jac_spar[2], jac_spar[3]), cp = mk<double>(jac_spar[4], jac_spar[5]);
     double an = 0.0, bn = 0.0;
 #pragma unroll
     for (int u = 0; u < kJacCache; ++u) {
@@ -455,22 +461,13 @@ __device__ __forceinline__ void jac_pair(const JacobiArgs& a, int p, int q) {
         jac_norm_acc(an, x);
         jac_norm_acc(bn, y);
     }
-    if (a.J) {
-        c128* jp = a.J + (int64_t)p * a.kk;
-        c128* jq = a.J + (int64_t)q * a.kk;
-        for (int r = tid; r < a.kk; r += kJacThreads) {
-            c128 x = ldcg_c(jp + r), y = ldcg_c(jq + r);
-            jac_rotate(x, y, c, s, sp, cp);
-            jp[r] = x;
-            jq[r] = y;
-        }
-    }
     block_sum2(an, bn);
     if (tid == 0) {
         a.nrm2[p] = an;
         a.nrm2[q] = bn;
         atomicAdd(a.rotations, 1);
     }
+    return true;
 }
 
 // Thread 0 waits until column c has finished `target` rounds.  Bounded: after the spin limit, or
@@ -491,7 +488,7 @@ __device__ __forceinline__ bool jac_wait(const int* ver, int c, int target, int*
 }
 
 __global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs a) {
-    // One CTA per column pair (CTAs loop over the pairs of a round), so every round spreads its
+    // One CTA per column pair (CTAs take the pairs in order, see below), so every round spreads its
     // FP64 work over all SMs.  The rounds are not separated by grid barriers: a pair of round r
     // starts as soon as both of its columns have come out of round r - 1 (a per-column count of
     // finished rounds), so a slow pair holds up only the pairs that need its columns.  The pairs,
@@ -506,24 +503,61 @@ __global__ void __launch_bounds__(kJacThreads, 3) jacobi_sweep_kernel(JacobiArgs
         if (tid == 0) a.nrm2[c] = s;
     }
     if (!grid_sync(a.gb)) return;
-    for (int round = 0; round < a.npad - 1; ++round) {
-        for (int i = blockIdx.x; i < a.npad / 2; i += gridDim.x) {
-            int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
-            if (p > q) { const int t = p; p = q; q = t; }
-            const bool real_pair = q < a.kk;  // q == kk is the padding column of an odd count
+    // The pairs of all rounds are numbered g = round * (npad / 2) + i and dealt out in that order.
+    // A pair releases its columns of B (and their norms) to the next round as soon as they are
+    // rotated; it then rotates its columns of J, once the previous round's rotation of them is done
+    // (jver), and releases those.  With more CTAs than pairs in a round, CTAs start pairs of the next
+    // round while J's rotations of this one run.  Every wait is on a smaller g (or the same g's B
+    // part), every CTA takes its pairs in increasing g and all are resident (cooperative launch), so
+    // the smallest unfinished step can always proceed.  The arithmetic is that of the sweep with a
+    // grid barrier between rounds.
+    const int ppr = a.npad / 2;
+    const int64_t npairs = (int64_t)(a.npad - 1) * ppr;
+    for (int64_t gi = blockIdx.x; gi < npairs; gi += gridDim.x) {
+        const int round = (int)(gi / ppr), i = (int)(gi % ppr);
+        int p = rr_pos(i, round, a.npad), q = rr_pos(a.npad - 1 - i, round, a.npad);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const bool real_pair = q < a.kk;  // q == kk is the padding column of an odd count
+        if (tid == 0) {
+            const bool ok = jac_wait(a.ver, p, round, a.gb.err) && (!real_pair || jac_wait(a.ver, q, round, a.gb.err));
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const bool rot = real_pair && jac_pair(a, p, q);
+        __syncthreads();  // every store of B and of the norms issued
+        if (tid == 0) {
+            __threadfence();
+            atomicExch(a.ver + p, round + 1);
+            if (real_pair) atomicExch(a.ver + q, round + 1);
+        }
+        if (a.J) {
             if (tid == 0) {
-                const bool ok = jac_wait(a.ver, p, round, a.gb.err) && (!real_pair || jac_wait(a.ver, q, round, a.gb.err));
+                const bool ok = jac_wait(a.jver, p, round, a.gb.err) &&
+                                (!real_pair || jac_wait(a.jver, q, round, a.gb.err));
                 __threadfence();
                 s_ok = ok;
             }
             __syncthreads();
             if (!s_ok) return;
-            if (real_pair) jac_pair(a, p, q);
-            __syncthreads();  // every store of the pair issued
+            if (rot) {
+                const double c = jac_spar[0], sn = jac_spar[1];
+                const c128 sp = mk<double>(jac_spar[2], jac_spar[3]), cp = mk<double>(jac_spar[4], jac_spar[5]);
+                c128* jp = a.J + (int64_t)p * a.kk;
+                c128* jq = a.J + (int64_t)q * a.kk;
+                for (int r = tid; r < a.kk; r += kJacThreads) {
+                    c128 x = ldcg_c(jp + r), y = ldcg_c(jq + r);
+                    jac_rotate(x, y, c, sn, sp, cp);
+                    jp[r] = x;
+                    jq[r] = y;
+                }
+            }
+            __syncthreads();  // every store of J issued
             if (tid == 0) {
                 __threadfence();
-                atomicExch(a.ver + p, round + 1);
-                if (real_pair) atomicExch(a.ver + q, round + 1);
+                atomicExch(a.jver + p, round + 1);
+                if (real_pair) atomicExch(a.jver + q, round + 1);
             }
         }
     }
@@ -551,18 +585,22 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
     RSRR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     RSRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_sweep_kernel, kJacThreads, 0));
     if (occ < 1) return set_error(RSRR_ECUDA, "jacobi kernel cannot be resident");
-    const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 4), npad / 2);
+    // as many CTAs as are resident (up to 4 per SM), also when that is more than a round's npad / 2
+    // pairs: the surplus starts the next round's pairs while this round's J rotations finish
+    const int G = (int)std::min<int64_t>((int64_t)nsm * std::min(occ, 4), (int64_t)(npad - 1) * (npad / 2));
     unsigned long long* dmax = nullptr;
     int* drot = nullptr;
     unsigned* bar = nullptr;
     double* dn2 = nullptr;
     int* dver = nullptr;
+    int* djver = nullptr;
     double* dnrm = nullptr;
     int* dperm = nullptr;
     c128* tmp = nullptr;
     auto cleanup = [&]() {
         dfree(dn2, s);
         dfree(dver, s);
+        dfree(djver, s);
         dfree(dmax, s);
         dfree(drot, s);
         dfree(bar, s);
@@ -574,6 +612,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
 #define JTRY(expr) do { rc = (expr); if (rc != RSRR_OK) { cleanup(); return rc; } } while (0)
     JTRY(dalloc_n(&dn2, (size_t)k, s));
     JTRY(dalloc_n(&dver, (size_t)k, s));
+    JTRY(dalloc_n(&djver, (size_t)k, s));
     JTRY(dalloc_n(&dmax, 1, s));
     JTRY(dalloc_n(&drot, 2, s));
     JTRY(dalloc_n(&bar, kGridBarWords, s));
@@ -587,7 +626,7 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
         JTRY(set_error(RSRR_ECUDA, "jacobi: clearing the grid barrier"));
 #undef JTRY
     JacobiArgs ja{B, mb, k, npad, J, sqrt((double)mb) * 1.1102230246251565e-16, abs_floor * abs_floor, abs_inner,
-                  dn2, dver, dmax, drot, grid_bar_at(bar)};
+                  dn2, dver, djver, dmax, drot, grid_bar_at(bar)};
     std::vector<double> hn(k);
     std::vector<int> order(k);
     int sweep = 0;
@@ -614,7 +653,8 @@ int jacobi_orthogonalize(c128* B, int mb, int k, c128* J, cudaStream_t s, int ma
             if (ce != cudaSuccess) { rc = set_error(RSRR_ECUDA, "jacobi: column reorder"); break; }
         }
         if (cudaMemsetAsync(dmax, 0, 8, s) != cudaSuccess || cudaMemsetAsync(drot, 0, 8, s) != cudaSuccess ||
-            cudaMemsetAsync(dver, 0, (size_t)k * sizeof(int), s) != cudaSuccess) {
+            cudaMemsetAsync(dver, 0, (size_t)k * sizeof(int), s) != cudaSuccess ||
+            cudaMemsetAsync(djver, 0, (size_t)k * sizeof(int), s) != cudaSuccess) {
             rc = set_error(RSRR_ECUDA, "jacobi: clearing the sweep counters");
             break;
         }
